@@ -1,0 +1,520 @@
+// TEST INFRASTRUCTURE -- CPU oracle for the per-scan TSDF integration path.
+//
+// A plain, slow, single-threaded restatement of FeatSense's TSDF map
+// generation (Section "TSDF Map Generation": the ray traversal from the scan
+// pose to each scan point, the per-scan volume V, Eq. 1 and Eq. 2, the
+// vertical interpolation vector and Eq. 3 / Eq. 4) plus the local-map shift
+// of the Introduction (a window that is shifted after a movement threshold,
+// with map parts written out to and loaded back from a global store).
+//
+// Only tests/, __graft_entry__.smoke() and bench.py's CPU baseline may load
+// this library. It shares no code, header or constant with the CUDA library.
+//
+// Conventions (each one a reading of the paper, stated once):
+//  * Floating point: IEEE binary32, round to nearest even, evaluated in the
+//    exact operation order written below; compiled with -ffp-contract=off so
+//    no multiply-add is fused. Constants that need a division are derived in
+//    binary64 and rounded once to binary32.
+//  * The map window is a dense array indexed by (g - origin): no ring
+//    addressing here; a shift physically rebuilds the window.
+//  * Per-scan volume V: WSUM keeps sum(q) and the hit count per voxel (each
+//    hit has weight 1); MIN_ABS keeps the quantised distance of smallest
+//    magnitude (tie -> the positive one), the paper's "smallest distance of
+//    all rays" with weight 1.
+//  * Eq. 1 is evaluated exactly in integers with one rounding, half away
+//    from zero. Eq. 2 clamps the summed weight at weight_max.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <array>
+#include <unordered_map>
+#include <vector>
+
+extern "C" {
+
+// Map parameters, same field order as the library's public struct but an
+// independent definition.
+struct orc_params {
+    int32_t dims[3];
+    float voxel_size;
+    float tau;
+    int32_t w_max;
+    float delta_z;
+    float r_min;
+    float r_max;
+    int32_t reduce;   // 0 = WSUM, 1 = MIN_ABS
+    int32_t pad_;
+    int64_t origin[3];
+};
+
+}  // extern "C"
+
+namespace {
+
+const int32_t QMAX = 32767;
+
+struct Derived {
+    float inv_vs;   // 1 / voxel_size
+    float qs;       // QMAX / tau
+    int K;          // number of march steps on each side of the hit
+};
+
+Derived derive(const orc_params& p) {
+    Derived d;
+    d.inv_vs = (float)(1.0 / (double)p.voxel_size);
+    d.qs = (float)((double)QMAX / (double)p.tau);
+    d.K = (int)std::floor((double)p.tau / (double)p.voxel_size + 1e-9);
+    return d;
+}
+
+struct Cell {
+    int16_t v;
+    int16_t w;
+};
+
+struct Ray {
+    bool valid;
+    bool fill;      // vertical interpolation active for this ray
+    float r;        // range from the sensor to the scan point
+    float t[3];     // sensor position (pose translation)
+    float dir[3];   // unit ray direction
+    float ih[3];    // unit interpolation direction
+};
+
+// Transform a sensor-frame point by the pose and set up its ray.
+// Section "TSDF Map Generation": ray from the scan position to the scan
+// point; interpolation vector int = d x (d x up), up = the sensor's z axis,
+// the direction orthogonal to the scan lines.
+Ray ray_setup(const float pose[12], const float pt[4], float r_min, float r_max, float delta_z) {
+    Ray ry;
+    const float R00 = pose[0], R01 = pose[1], R02 = pose[2], tx = pose[3];
+    const float R10 = pose[4], R11 = pose[5], R12 = pose[6], ty = pose[7];
+    const float R20 = pose[8], R21 = pose[9], R22 = pose[10], tz = pose[11];
+    const float x = pt[0], y = pt[1], z = pt[2];
+    float pwx = ((R00 * x + R01 * y) + R02 * z) + tx;
+    float pwy = ((R10 * x + R11 * y) + R12 * z) + ty;
+    float pwz = ((R20 * x + R21 * y) + R22 * z) + tz;
+    float vx = pwx - tx, vy = pwy - ty, vz = pwz - tz;
+    float r2 = (vx * vx + vy * vy) + vz * vz;
+    float r = std::sqrt(r2);
+    ry.r = r;
+    ry.t[0] = tx; ry.t[1] = ty; ry.t[2] = tz;
+    ry.valid = (r >= r_min) && (r <= r_max);   // false for NaN and inf
+    ry.fill = false;
+    ry.dir[0] = ry.dir[1] = ry.dir[2] = 0.f;
+    ry.ih[0] = ry.ih[1] = ry.ih[2] = 0.f;
+    if (!ry.valid) return ry;
+    float dx = vx / r, dy = vy / r, dz = vz / r;
+    ry.dir[0] = dx; ry.dir[1] = dy; ry.dir[2] = dz;
+    const float ux = R02, uy = R12, uz = R22;
+    // a = d x up
+    float ax = dy * uz - dz * uy;
+    float ay = dz * ux - dx * uz;
+    float az = dx * uy - dy * ux;
+    // iv = d x a = d x (d x up)
+    float ivx = dy * az - dz * ay;
+    float ivy = dz * ax - dx * az;
+    float ivz = dx * ay - dy * ax;
+    float n2 = (ivx * ivx + ivy * ivy) + ivz * ivz;
+    if (delta_z > 0.f && n2 >= 1e-12f) {
+        float n = std::sqrt(n2);
+        ry.fill = true;
+        ry.ih[0] = ivx / n; ry.ih[1] = ivy / n; ry.ih[2] = ivz / n;
+    }
+    return ry;
+}
+
+// Quantise a truncated signed distance to the int16 fixed-point code:
+// clamp to [-tau, tau], scale by QMAX / tau, round to nearest even, clamp.
+int32_t quantize(float d, float tau, float qs) {
+    if (d < -tau) d = -tau;
+    if (d > tau) d = tau;
+    float s = d * qs;
+    long q = std::lrint(s);
+    if (q > QMAX) q = QMAX;
+    if (q < -QMAX) q = -QMAX;
+    return (int32_t)q;
+}
+
+// Eq. 1 and Eq. 2 with v.value * v.weight = S and v.weight = W.
+void eq12(int32_t gv, int32_t gw, int64_t S, int64_t W, int32_t w_max, int32_t* nv, int32_t* nw) {
+    int64_t num = (int64_t)gv * (int64_t)gw + S;
+    int64_t den = (int64_t)gw + W;
+    int64_t a = num < 0 ? -num : num;
+    int64_t q = (2 * a + den) / (2 * den);   // floor(|num|/den + 1/2)
+    *nv = (int32_t)(num < 0 ? -q : q);
+    int64_t w = (int64_t)gw + W;
+    *nw = (int32_t)(w > w_max ? w_max : w);
+}
+
+// Visit every (voxel, quantised distance) contribution of one ray, in march
+// order (k outer, j inner). Eq. 3 gives delta_z; Eq. 4 the fill height
+// h = delta_z * l at step distance l; voxels are taken at spacing voxel_size
+// along +-int up to h. The distance of a voxel is the projective distance of
+// its centre along the ray: r - (c - s) . dir.
+template <class F>
+void for_each_hit(const Ray& ry, const orc_params& p, const Derived& dv, F&& f) {
+    if (!ry.valid) return;
+    const float vs = p.voxel_size;
+    const float tx = ry.t[0], ty = ry.t[1], tz = ry.t[2];
+    const float dx = ry.dir[0], dy = ry.dir[1], dz = ry.dir[2];
+    for (int k = -dv.K; k <= dv.K; ++k) {
+        float l = ry.r + (float)k * vs;
+        if (!(l > 0.f)) continue;
+        int J = 0;
+        if (ry.fill) J = (int)std::floor((p.delta_z * l) * dv.inv_vs);
+        float bx = tx + dx * l;
+        float by = ty + dy * l;
+        float bz = tz + dz * l;
+        for (int j = -J; j <= J; ++j) {
+            float jd = (float)j * vs;
+            float qx = bx + ry.ih[0] * jd;
+            float qy = by + ry.ih[1] * jd;
+            float qz = bz + ry.ih[2] * jd;
+            float fx = std::floor(qx * dv.inv_vs);
+            float fy = std::floor(qy * dv.inv_vs);
+            float fz = std::floor(qz * dv.inv_vs);
+            const float LIM = 4.0e18f;   // far outside any window: skip
+            if (!(std::fabs(fx) < LIM && std::fabs(fy) < LIM && std::fabs(fz) < LIM)) continue;
+            int64_t g[3] = {(int64_t)fx, (int64_t)fy, (int64_t)fz};
+            float cx = ((float)g[0] + 0.5f) * vs;
+            float cy = ((float)g[1] + 0.5f) * vs;
+            float cz = ((float)g[2] + 0.5f) * vs;
+            float proj = (((cx - tx) * dx) + ((cy - ty) * dy)) + ((cz - tz) * dz);
+            float d = ry.r - proj;
+            f(g, quantize(d, p.tau, dv.qs));
+        }
+    }
+}
+
+struct Acc {
+    int64_t S = 0;
+    int64_t W = 0;
+};
+
+struct OracleMap {
+    orc_params p;
+    Derived dv;
+    int64_t origin[3];
+    std::vector<Cell> win;
+    std::map<std::array<int64_t, 3>, std::vector<Cell>> store;   // global chunk -> 8^3 cells
+    int64_t st_valid = 0, st_hits = 0, st_touched = 0;
+
+    int64_t X() const { return p.dims[0]; }
+    int64_t Y() const { return p.dims[1]; }
+    int64_t Z() const { return p.dims[2]; }
+    bool inside(const int64_t g[3]) const {
+        for (int a = 0; a < 3; ++a)
+            if (g[a] < origin[a] || g[a] >= origin[a] + p.dims[a]) return false;
+        return true;
+    }
+    int64_t lin(const int64_t g[3]) const {
+        return ((g[2] - origin[2]) * Y() + (g[1] - origin[1])) * X() + (g[0] - origin[0]);
+    }
+};
+
+bool params_ok(const orc_params& p) {
+    for (int a = 0; a < 3; ++a) {
+        if (p.dims[a] < 8 || p.dims[a] % 8 != 0) return false;
+        if (p.origin[a] % 8 != 0) return false;
+    }
+    if (!(p.voxel_size > 0.f) || !(p.tau >= p.voxel_size)) return false;
+    if (p.w_max < 1 || p.w_max > 32767) return false;
+    if (!(p.delta_z >= 0.f)) return false;
+    if (!(p.r_min >= 0.f) || !(p.r_max >= p.r_min)) return false;
+    if (p.reduce != 0 && p.reduce != 1) return false;
+    return true;
+}
+
+// Apply a per-scan volume to the window: Eq. 1 / Eq. 2 for every touched voxel.
+void apply_volume(OracleMap* m, const std::unordered_map<int64_t, Acc>& vol,
+                  const std::unordered_map<int64_t, int32_t>& best) {
+    if (m->p.reduce == 0) {
+        for (const auto& kv : vol) {
+            Cell& c = m->win[kv.first];
+            int32_t nv, nw;
+            eq12(c.v, c.w, kv.second.S, kv.second.W, m->p.w_max, &nv, &nw);
+            c.v = (int16_t)nv;
+            c.w = (int16_t)nw;
+        }
+        m->st_touched = (int64_t)vol.size();
+    } else {
+        for (const auto& kv : best) {
+            Cell& c = m->win[kv.first];
+            int32_t nv, nw;
+            eq12(c.v, c.w, kv.second, 1, m->p.w_max, &nv, &nw);
+            c.v = (int16_t)nv;
+            c.w = (int16_t)nw;
+        }
+        m->st_touched = (int64_t)best.size();
+    }
+}
+
+// MIN_ABS order: smaller magnitude wins; equal magnitude -> the positive value.
+bool min_abs_better(int32_t a, int32_t b) {
+    int32_t aa = a < 0 ? -a : a, bb = b < 0 ? -b : b;
+    if (aa != bb) return aa < bb;
+    return a > b;
+}
+
+}  // namespace
+
+extern "C" {
+
+void* orc_create(const orc_params* p) {
+    if (!p || !params_ok(*p)) return nullptr;
+    OracleMap* m = new OracleMap();
+    m->p = *p;
+    m->dv = derive(*p);
+    for (int a = 0; a < 3; ++a) m->origin[a] = p->origin[a];
+    m->win.assign((size_t)p->dims[0] * p->dims[1] * p->dims[2], Cell{0, 0});
+    return m;
+}
+
+void orc_destroy(void* h) { delete (OracleMap*)h; }
+
+void orc_derived(const orc_params* p, float* inv_vs, float* qs, int32_t* K) {
+    Derived d = derive(*p);
+    *inv_vs = d.inv_vs;
+    *qs = d.qs;
+    *K = d.K;
+}
+
+// Ray-major integration of one scan (points: float[n][4], sensor frame).
+int orc_integrate(void* h, const float* pts, int64_t n, const float pose[12]) {
+    OracleMap* m = (OracleMap*)h;
+    if (!m || n < 0 || (n > 0 && !pts) || !pose) return -1;
+    std::unordered_map<int64_t, Acc> vol;
+    std::unordered_map<int64_t, int32_t> best;
+    int64_t valid = 0, hits = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        Ray ry = ray_setup(pose, pts + 4 * i, m->p.r_min, m->p.r_max, m->p.delta_z);
+        if (!ry.valid) continue;
+        ++valid;
+        for_each_hit(ry, m->p, m->dv, [&](const int64_t g[3], int32_t q) {
+            if (!m->inside(g)) return;
+            ++hits;
+            int64_t key = m->lin(g);
+            if (m->p.reduce == 0) {
+                Acc& a = vol[key];
+                a.S += q;
+                a.W += 1;
+            } else {
+                auto it = best.find(key);
+                if (it == best.end()) best.emplace(key, q);
+                else if (min_abs_better(q, it->second)) it->second = q;
+            }
+        });
+    }
+    apply_volume(m, vol, best);
+    m->st_valid = valid;
+    m->st_hits = hits;
+    return 0;
+}
+
+// Voxel-major brute force of the same scan: for every window voxel, scan all
+// rays and all (k, j) steps and collect the contributions that land on it.
+// Loop order differs from orc_integrate on purpose. Tiny inputs only.
+int orc_integrate_bruteforce(void* h, const float* pts, int64_t n, const float pose[12]) {
+    OracleMap* m = (OracleMap*)h;
+    if (!m || n < 0 || (n > 0 && !pts) || !pose) return -1;
+    std::vector<Ray> rays;
+    int64_t valid = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        Ray ry = ray_setup(pose, pts + 4 * i, m->p.r_min, m->p.r_max, m->p.delta_z);
+        if (ry.valid) ++valid;
+        rays.push_back(ry);
+    }
+    const float vs = m->p.voxel_size;
+    std::vector<Cell> next = m->win;
+    int64_t hits = 0, touched = 0;
+    for (int64_t gz = m->origin[2]; gz < m->origin[2] + m->Z(); ++gz)
+    for (int64_t gy = m->origin[1]; gy < m->origin[1] + m->Y(); ++gy)
+    for (int64_t gx = m->origin[0]; gx < m->origin[0] + m->X(); ++gx) {
+        int64_t S = 0, W = 0;
+        bool any = false;
+        int32_t bq = 0;
+        for (const Ray& ry : rays) {
+            if (!ry.valid) continue;
+            for (int k = -m->dv.K; k <= m->dv.K; ++k) {
+                float l = ry.r + (float)k * vs;
+                if (!(l > 0.f)) continue;
+                int J = ry.fill ? (int)std::floor((m->p.delta_z * l) * m->dv.inv_vs) : 0;
+                for (int j = -J; j <= J; ++j) {
+                    float jd = (float)j * vs;
+                    float qx = (ry.t[0] + ry.dir[0] * l) + ry.ih[0] * jd;
+                    float qy = (ry.t[1] + ry.dir[1] * l) + ry.ih[1] * jd;
+                    float qz = (ry.t[2] + ry.dir[2] * l) + ry.ih[2] * jd;
+                    if ((int64_t)std::floor(qx * m->dv.inv_vs) != gx) continue;
+                    if ((int64_t)std::floor(qy * m->dv.inv_vs) != gy) continue;
+                    if ((int64_t)std::floor(qz * m->dv.inv_vs) != gz) continue;
+                    float cx = ((float)gx + 0.5f) * vs;
+                    float cy = ((float)gy + 0.5f) * vs;
+                    float cz = ((float)gz + 0.5f) * vs;
+                    float d = ry.r - ((((cx - ry.t[0]) * ry.dir[0]) + ((cy - ry.t[1]) * ry.dir[1])) +
+                                      ((cz - ry.t[2]) * ry.dir[2]));
+                    int32_t q = quantize(d, m->p.tau, m->dv.qs);
+                    S += q;
+                    W += 1;
+                    if (!any || min_abs_better(q, bq)) bq = q;
+                    any = true;
+                }
+            }
+        }
+        if (!any) continue;
+        ++touched;
+        hits += W;
+        int64_t g[3] = {gx, gy, gz};
+        Cell& c = next[m->lin(g)];
+        int32_t nv, nw;
+        if (m->p.reduce == 0) eq12(c.v, c.w, S, W, m->p.w_max, &nv, &nw);
+        else eq12(c.v, c.w, bq, 1, m->p.w_max, &nv, &nw);
+        c.v = (int16_t)nv;
+        c.w = (int16_t)nw;
+    }
+    m->win.swap(next);
+    m->st_valid = valid;
+    m->st_hits = hits;
+    m->st_touched = touched;
+    return 0;
+}
+
+// Every contribution of a scan, in enumeration order, whether or not it lands
+// in the window: out_g int64[cap][3], out_q int32[cap]. Returns the count
+// (which may exceed cap; only the first cap are written).
+int64_t orc_hits(const orc_params* p, const float* pts, int64_t n, const float pose[12],
+                 int64_t* out_g, int32_t* out_q, int64_t* out_ray, int64_t cap) {
+    Derived dv = derive(*p);
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        Ray ry = ray_setup(pose, pts + 4 * i, p->r_min, p->r_max, p->delta_z);
+        for_each_hit(ry, *p, dv, [&](const int64_t g[3], int32_t q) {
+            if (cnt < cap) {
+                out_g[3 * cnt + 0] = g[0];
+                out_g[3 * cnt + 1] = g[1];
+                out_g[3 * cnt + 2] = g[2];
+                out_q[cnt] = q;
+                if (out_ray) out_ray[cnt] = i;
+            }
+            ++cnt;
+        });
+    }
+    return cnt;
+}
+
+// Ray set-up of one point, for pin tests: out[0]=valid, [1]=fill, [2]=r,
+// [3..5]=dir, [6..8]=ih.
+void orc_ray(const float pose[12], const float pt[4], float r_min, float r_max, float delta_z, float out[9]) {
+    Ray ry = ray_setup(pose, pt, r_min, r_max, delta_z);
+    out[0] = ry.valid ? 1.f : 0.f;
+    out[1] = ry.fill ? 1.f : 0.f;
+    out[2] = ry.r;
+    for (int a = 0; a < 3; ++a) {
+        out[3 + a] = ry.dir[a];
+        out[6 + a] = ry.ih[a];
+    }
+}
+
+int32_t orc_quantize(float d, float tau, float qs) { return quantize(d, tau, qs); }
+
+void orc_eq12(int32_t gv, int32_t gw, int64_t S, int64_t W, int32_t w_max, int32_t* nv, int32_t* nw) {
+    eq12(gv, gw, S, W, w_max, nv, nw);
+}
+
+// Move the window to new_origin (multiples of 8). Chunks (8^3 voxels) that
+// leave are kept in the global store when any of their cells is non-zero;
+// cells that enter are loaded from the store, else (0, 0).
+int orc_shift(void* h, const int64_t no[3]) {
+    OracleMap* m = (OracleMap*)h;
+    if (!m || !no) return -1;
+    for (int a = 0; a < 3; ++a)
+        if (no[a] % 8 != 0) return -1;
+    const int64_t X = m->X(), Y = m->Y(), Z = m->Z();
+    // 1. evict chunks of the old window that are not inside the new one
+    for (int64_t cz = m->origin[2]; cz < m->origin[2] + Z; cz += 8)
+    for (int64_t cy = m->origin[1]; cy < m->origin[1] + Y; cy += 8)
+    for (int64_t cx = m->origin[0]; cx < m->origin[0] + X; cx += 8) {
+        bool stays = cx >= no[0] && cx < no[0] + X && cy >= no[1] && cy < no[1] + Y &&
+                     cz >= no[2] && cz < no[2] + Z;
+        if (stays) continue;
+        std::vector<Cell> cells(512);
+        bool nonzero = false;
+        for (int z = 0; z < 8; ++z)
+        for (int y = 0; y < 8; ++y)
+        for (int x = 0; x < 8; ++x) {
+            int64_t g[3] = {cx + x, cy + y, cz + z};
+            Cell c = m->win[m->lin(g)];
+            cells[(z * 8 + y) * 8 + x] = c;
+            if (c.v != 0 || c.w != 0) nonzero = true;
+        }
+        std::array<int64_t, 3> key = {cx / 8, cy / 8, cz / 8};
+        if (nonzero) m->store[key] = cells;
+        else m->store.erase(key);
+    }
+    // 2. build the new window: copy the overlap, load or zero the rest
+    std::vector<Cell> next((size_t)(X * Y * Z), Cell{0, 0});
+    for (int64_t gz = no[2]; gz < no[2] + Z; ++gz)
+    for (int64_t gy = no[1]; gy < no[1] + Y; ++gy)
+    for (int64_t gx = no[0]; gx < no[0] + X; ++gx) {
+        int64_t g[3] = {gx, gy, gz};
+        Cell c{0, 0};
+        if (m->inside(g)) {
+            c = m->win[m->lin(g)];
+        } else {
+            auto fl = [](int64_t v) { return v >= 0 ? v / 8 : -((-v + 7) / 8); };
+            std::array<int64_t, 3> key = {fl(gx), fl(gy), fl(gz)};
+            auto it = m->store.find(key);
+            if (it != m->store.end()) {
+                int64_t x = gx - key[0] * 8, y = gy - key[1] * 8, z = gz - key[2] * 8;
+                c = it->second[(z * 8 + y) * 8 + x];
+            }
+        }
+        next[(size_t)(((gz - no[2]) * Y + (gy - no[1])) * X + (gx - no[0]))] = c;
+    }
+    m->win.swap(next);
+    for (int a = 0; a < 3; ++a) m->origin[a] = no[a];
+    return 0;
+}
+
+// Copy the global box [lo, hi) (inside the window) to v/w in [z][y][x] order.
+int orc_read(void* h, const int64_t lo[3], const int64_t hi[3], int16_t* v, int16_t* w) {
+    OracleMap* m = (OracleMap*)h;
+    if (!m) return -1;
+    for (int a = 0; a < 3; ++a)
+        if (lo[a] < m->origin[a] || hi[a] > m->origin[a] + m->p.dims[a] || hi[a] < lo[a]) return -1;
+    int64_t i = 0;
+    for (int64_t gz = lo[2]; gz < hi[2]; ++gz)
+    for (int64_t gy = lo[1]; gy < hi[1]; ++gy)
+    for (int64_t gx = lo[0]; gx < hi[0]; ++gx, ++i) {
+        int64_t g[3] = {gx, gy, gz};
+        Cell c = m->win[m->lin(g)];
+        if (v) v[i] = c.v;
+        if (w) w[i] = c.w;
+    }
+    return 0;
+}
+
+// Overwrite the window's cells from v/w in [z][y][x] window order (test set-up).
+int orc_load_window(void* h, const int16_t* v, const int16_t* w) {
+    OracleMap* m = (OracleMap*)h;
+    if (!m) return -1;
+    for (size_t i = 0; i < m->win.size(); ++i) m->win[i] = Cell{v[i], w[i]};
+    return 0;
+}
+
+void orc_origin(void* h, int64_t out[3]) {
+    OracleMap* m = (OracleMap*)h;
+    for (int a = 0; a < 3; ++a) out[a] = m->origin[a];
+}
+
+void orc_stats(void* h, int64_t out[3]) {
+    OracleMap* m = (OracleMap*)h;
+    out[0] = m->st_valid;
+    out[1] = m->st_hits;
+    out[2] = m->st_touched;
+}
+
+int64_t orc_store_chunks(void* h) { return (int64_t)((OracleMap*)h)->store.size(); }
+
+}  // extern "C"

@@ -1,0 +1,537 @@
+"""Pins of the CPU oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: hand-derived
+golden values (tests/golden/), closed forms for axis-aligned rays, an FP64
+analytic signed distance field, a brute-force voxel-major enumeration in a
+different loop order, textbook reductions (numpy min / sums) over the raw
+contribution list, and invariants of Eq. 1 / Eq. 2 and of the map shift.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_05766_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _table(name):
+    rows = []
+    for line in open(os.path.join(GOLD, name)):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            rows.append(line.split())
+    return rows
+
+
+# ---------------------------------------------------------------- constants
+
+@pytest.mark.parametrize("vs,tau,K", [(0.05, 0.2, 4), (0.064, 0.6, 9), (0.02, 0.1, 5), (0.125, 0.5, 4),
+                                      (0.1, 0.2, 2), (0.08, 0.6, 7)])
+def test_march_step_count(vs, tau, K):
+    """K = floor(tau / voxel): the march covers +-tau around the hit in voxel steps."""
+    p = synth.params_dict((8, 8, 8), vs, tau, 64, 0.0, 0.1, 10.0)
+    assert oracle.derived(p)[2] == K
+
+
+# ---------------------------------------------------------------- Eq. 1 / Eq. 2
+
+def test_eq12_golden_table():
+    """Eq. 1 / Eq. 2 against the hand-computed table (tests/golden/eq12_table.txt)."""
+    rows = _table("eq12_table.txt")
+    assert len(rows) >= 15
+    for r in rows:
+        gv, gw, S, W, wmax, ev, ew = (int(x) for x in r)
+        assert oracle.eq12(gv, gw, S, W, wmax) == (ev, ew), r
+
+
+def test_eq12_exact_rational_rounding():
+    """Random Eq. 1 cases against exact rational arithmetic, rounding half away from zero."""
+    rng = np.random.default_rng(5)
+    for _ in range(3000):
+        gv = int(rng.integers(-32767, 32768))
+        gw = int(rng.integers(0, 65))
+        W = int(rng.integers(1, 200))
+        S = int(rng.integers(-32767, 32768)) * W // max(1, int(rng.integers(1, 4)))
+        S = max(-32767 * W, min(32767 * W, S))
+        wmax = int(rng.integers(1, 65))
+        x = Fraction(gv * gw + S, gw + W)
+        mag = abs(x)
+        expect = int(mag + Fraction(1, 2)) if mag.denominator != 1 else int(mag)
+        expect = expect if x >= 0 else -expect
+        nv, nw = oracle.eq12(gv, gw, S, W, wmax)
+        assert nv == expect
+        assert nw == min(wmax, gw + W)
+        assert -32767 <= nv <= 32767
+
+
+# ---------------------------------------------------------------- quantiser
+
+def test_quantize_ties_golden():
+    tau = float(np.float32(32767 / 65536))
+    qs = float(np.float32(32767.0 / tau))
+    assert qs == 65536.0
+    for m, expect in _table("quantize_ties.txt"):
+        d = float(np.float32(float(m) / 65536.0))
+        assert d == float(m) / 65536.0  # exactly representable
+        assert oracle.quantize(d, tau, qs) == int(expect), m
+
+
+# ---------------------------------------------------------------- ray set-up
+
+def test_ray_setup_geometry():
+    """dir is the unit vector sensor->point; int is unit, orthogonal to dir and in
+    the plane spanned by dir and up = R e_z (the scan-line normal)."""
+    rng = np.random.default_rng(11)
+    for _ in range(300):
+        R = synth.rot_zyx(*rng.uniform(-math.pi, math.pi, 3))
+        t = rng.uniform(-50, 50, 3)
+        pose = synth.pose12(R, t)
+        p = np.zeros(4, np.float32)
+        p[:3] = rng.uniform(-30, 30, 3)
+        ry = oracle.ray(pose, p, 0.1, 100.0, 0.01)
+        Rf = pose.reshape(3, 4)[:, :3].astype(np.float64)
+        v = Rf @ p[:3].astype(np.float64)
+        r = np.linalg.norm(v)
+        if r < 0.1:
+            continue
+        assert ry["valid"]
+        assert abs(ry["r"] - r) <= 1e-5 * r + 1e-4
+        assert np.allclose(ry["dir"], v / r, atol=1e-5)
+        up = Rf[:, 2]
+        ih = ry["ih"].astype(np.float64)
+        assert ry["fill"]
+        assert abs(np.linalg.norm(ih) - 1) < 1e-5
+        assert abs(ih @ (v / r)) < 1e-5
+        assert abs(ih @ np.cross(v / r, up)) < 1e-5
+
+
+def test_ray_validity():
+    pose = synth.pose12(np.eye(3), np.zeros(3))
+    assert not oracle.ray(pose, [np.nan, 0, 0, 0], 0.5, 10, 0.01)["valid"]
+    assert not oracle.ray(pose, [np.inf, 0, 0, 0], 0.5, 10, 0.01)["valid"]
+    assert not oracle.ray(pose, [0, 0, 0, 0], 0.5, 10, 0.01)["valid"]
+    assert not oracle.ray(pose, [0.25, 0, 0, 0], 0.5, 10, 0.01)["valid"]
+    assert oracle.ray(pose, [0.5, 0, 0, 0], 0.5, 10, 0.01)["valid"]
+    assert oracle.ray(pose, [10, 0, 0, 0], 0.5, 10, 0.01)["valid"]
+    assert not oracle.ray(pose, [10.5, 0, 0, 0], 0.5, 10, 0.01)["valid"]
+    # a ray along up has no interpolation direction
+    ry = oracle.ray(pose, [0, 0, 3, 0], 0.5, 10, 0.01)
+    assert ry["valid"] and not ry["fill"]
+    # delta_z = 0 disables the fill
+    assert not oracle.ray(pose, [3, 0, 0, 0], 0.5, 10, 0.0)["fill"]
+
+
+# ---------------------------------------------------------------- closed-form enumeration
+
+def test_axis_ray_fill_closed_form():
+    """The hit list of an axis-aligned ray with fill equals the hand derivation
+    in tests/golden/axis_ray_fill.json (Eq. 3 / Eq. 4, int = d x (d x up))."""
+    gold = json.load(open(os.path.join(GOLD, "axis_ray_fill.json")))
+    p = synth.params_dict(gold["params"]["dims"], gold["params"]["voxel_size"], gold["params"]["tau"],
+                          gold["params"]["w_max"], gold["params"]["delta_z"], gold["params"]["r_min"],
+                          gold["params"]["r_max"], 0, gold["params"]["origin"])
+    assert oracle.derived(p)[2] == gold["K"]
+    pts = np.array([gold["point"]], np.float32)
+    pose = np.array(gold["pose"], np.float32)
+    g, q, _ = oracle.hits(p, pts, pose)
+    expect = []
+    for s in gold["steps"]:
+        for j in range(-s["J"], s["J"] + 1):
+            expect.append((s["x"], 0, -j, s["q"]))
+    got = [(int(a), int(b), int(c), int(d)) for (a, b, c), d in zip(g, q)]
+    assert len(got) == gold["total_hits"]
+    assert sorted(got) == sorted(expect)
+    # the map after one scan: each voxel hit once, value = its code, weight 1
+    m = oracle.OracleMap(p)
+    m.integrate(pts, pose)
+    v, w = m.read()
+    o = p["origin"]
+    for x, y, z, code in expect:
+        assert v[z - o[2], y - o[1], x - o[0]] == code
+        assert w[z - o[2], y - o[1], x - o[0]] == 1
+    assert int((w > 0).sum()) == gold["total_hits"]
+    assert m.stats() == dict(valid_rays=1, hits=75, touched=75)
+
+
+def test_no_fill_gives_2k_plus_1_hits():
+    """delta_z = 0: every valid ray contributes exactly 2K+1 steps (all in the window)."""
+    rng = np.random.default_rng(3)
+    p = synth.params_dict((64, 64, 64), 0.1, 0.35, 64, 0.0, 0.5, 2.5, 0, (-32, -32, -32))
+    K = oracle.derived(p)[2]
+    assert K == 3
+    pts = np.zeros((50, 4), np.float32)
+    d = rng.normal(size=(50, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    pts[:, :3] = d * rng.uniform(0.8, 2.0, (50, 1))
+    pose = synth.pose12(synth.rot_zyx(0.3, 0.1, -0.2), np.array([0.05, -0.1, 0.2]))
+    g, q, ray = oracle.hits(p, pts, pose)
+    assert len(g) == 50 * (2 * K + 1)
+    assert np.all(np.bincount(ray, minlength=50) == 2 * K + 1)
+
+
+def test_step_distances_follow_ray():
+    """Without fill, step k of a ray lands in the voxel containing s + (r + k vs) d
+    (FP64 check with a one-voxel tolerance) and its code is within rounding of the
+    projective distance of that voxel's centre."""
+    rng = np.random.default_rng(4)
+    p = synth.params_dict((128, 128, 128), 0.05, 0.2, 64, 0.0, 0.3, 3.0, 0, (-64, -64, -64))
+    inv, qs, K = oracle.derived(p)
+    pts = np.zeros((40, 4), np.float32)
+    d = rng.normal(size=(40, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    pts[:, :3] = d * rng.uniform(0.5, 2.5, (40, 1))
+    R = synth.rot_zyx(1.0, 0.2, 0.1)
+    t = np.array([0.1, 0.2, -0.3])
+    pose = synth.pose12(R, t)
+    g, q, ray = oracle.hits(p, pts, pose)
+    Rf = pose.reshape(3, 4)[:, :3].astype(np.float64)
+    tf = pose.reshape(3, 4)[:, 3].astype(np.float64)
+    vs = p["voxel_size"]
+    idx = 0
+    for i in range(40):
+        v = Rf @ pts[i, :3].astype(np.float64)
+        r = np.linalg.norm(v)
+        dirn = v / r
+        for k in range(-K, K + 1):
+            l = r + k * vs
+            expect_pt = tf + dirn * l
+            assert np.all(np.abs((g[idx] + 0.5) * vs - expect_pt) <= 0.5 * vs + 1e-4)
+            c = (g[idx] + 0.5) * vs
+            dist = r - (c - tf) @ dirn
+            dist = min(max(dist, -p["tau"]), p["tau"])
+            assert abs(q[idx] - dist * 32767 / p["tau"]) <= 2.0
+            idx += 1
+    assert idx == len(g)
+
+
+# ---------------------------------------------------------------- brute force, tiny grids
+
+def _random_scan(rng, n, spread, sensor_box, origin_vox, vs):
+    pts = np.zeros((n, 4), np.float32)
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    pts[:, :3] = d * rng.uniform(spread[0], spread[1], (n, 1))
+    # a few invalid points
+    pts[rng.integers(0, n, max(1, n // 16)), 0] = np.nan
+    R = synth.rot_zyx(*rng.uniform(-math.pi, math.pi, 3))
+    t = rng.uniform(sensor_box[0], sensor_box[1], 3)
+    return pts, synth.pose12(R, t)
+
+
+@pytest.mark.parametrize("reduce", [0, 1])
+@pytest.mark.parametrize("seed", range(6))
+def test_bruteforce_matches_ray_major(reduce, seed):
+    """Ray-major oracle == voxel-major brute force (different loop order), bit for
+    bit, on 16^3 windows (some straddling negative coordinates) with a random
+    pre-existing map, for both per-scan reductions."""
+    rng = np.random.default_rng(100 + seed)
+    vs = [0.1, 0.125, 0.08][seed % 3]
+    origin = [(-8, -8, -8), (0, -16, 8), (-16, 0, -8)][seed % 3]
+    tau = [0.2, 0.3, 0.25][seed % 3]
+    dz = [0.0, 0.05, 0.2][seed % 3]
+    p = synth.params_dict((16, 16, 16), vs, tau, int(rng.integers(1, 20)), dz, 0.05, 3.0, reduce, origin)
+    centre = np.array([(o + 8) * vs for o in origin])
+    pts, pose = _random_scan(rng, 48, (0.3, 1.0), (centre - 0.2, centre + 0.2), origin, vs)
+    v0 = rng.integers(-32767, 32768, size=(16, 16, 16)).astype(np.int16)
+    w0 = rng.integers(0, p["w_max"] + 1, size=(16, 16, 16)).astype(np.int16)
+    a = oracle.OracleMap(p)
+    b = oracle.OracleMap(p)
+    a.load_window(v0, w0)
+    b.load_window(v0, w0)
+    a.integrate(pts, pose)
+    b.integrate(pts, pose, bruteforce=True)
+    va, wa = a.read()
+    vb, wb = b.read()
+    assert a.stats()["hits"] > 100
+    assert np.array_equal(va, vb) and np.array_equal(wa, wb)
+    assert a.stats() == b.stats()
+
+
+def test_reductions_match_textbook():
+    """Per-scan V from the raw contribution list with numpy: WSUM = mean code
+    rounded half away from zero, MIN_ABS = code of smallest magnitude (ties to
+    the positive value); each applied to an empty map with weight 1 or W."""
+    rng = np.random.default_rng(8)
+    p0 = synth.params_dict((32, 32, 32), 0.1, 0.3, 1000, 0.05, 0.05, 3.0, 0, (-16, -16, -16))
+    p1 = dict(p0, reduce=1)
+    pts, pose = _random_scan(rng, 200, (0.4, 1.5), (np.full(3, -0.1), np.full(3, 0.1)), None, 0.1)
+    g, q, _ = oracle.hits(p0, pts, pose)
+    o = np.array(p0["origin"])
+    inside = np.all((g >= o) & (g < o + 32), axis=1)
+    g, q = g[inside], q[inside]
+    lin = ((g[:, 2] - o[2]) * 32 + (g[:, 1] - o[1])) * 32 + (g[:, 0] - o[0])
+    S = np.bincount(lin, weights=q, minlength=32 ** 3).astype(np.int64)
+    W = np.bincount(lin, minlength=32 ** 3)
+    m0 = oracle.OracleMap(p0)
+    m0.integrate(pts, pose)
+    v0, w0 = m0.read()
+    v0, w0 = v0.reshape(-1), w0.reshape(-1)
+    touched = W > 0
+    assert np.array_equal(w0, np.minimum(W, 1000).astype(np.int16))
+    for i in np.nonzero(touched)[0]:
+        x = Fraction(int(S[i]), int(W[i]))
+        mag = abs(x)
+        e = int(mag + Fraction(1, 2))
+        assert v0[i] == (e if x >= 0 else -e)
+    # MIN_ABS
+    key = np.abs(q).astype(np.int64) * 2 + (q < 0)
+    order = np.lexsort((key, lin))
+    first = np.ones(len(order), bool)
+    first[1:] = lin[order][1:] != lin[order][:-1]
+    best = np.zeros(32 ** 3, np.int64)
+    best[lin[order][first]] = q[order][first]
+    m1 = oracle.OracleMap(p1)
+    m1.integrate(pts, pose)
+    v1, w1 = m1.read()
+    assert np.array_equal(v1.reshape(-1)[touched], best[touched])
+    assert np.all(w1.reshape(-1)[touched] == 1) and np.all(w1.reshape(-1)[~touched] == 0)
+
+
+def test_single_hit_voxels_wsum_equals_min_abs():
+    """When every voxel gets at most one contribution, both reductions agree."""
+    p = synth.params_dict((64, 64, 64), 0.0625, 0.25, 64, 0.0, 0.1, 5.0, 0, (-32, -32, -32))
+    # axis rays with a power-of-two voxel: consecutive steps land in distinct voxels
+    pts = np.array([[1.03, 0, 0, 0], [0, -1.52, 0, 0], [0, 0, 1.23, 0]], np.float32)
+    pose = synth.pose12(np.eye(3), np.array([0.01, 0.02, 0.03]))
+    g, q, _ = oracle.hits(p, pts, pose)
+    assert len({tuple(x) for x in g}) == len(g)
+    a = oracle.OracleMap(p)
+    b = oracle.OracleMap(dict(p, reduce=1))
+    a.integrate(pts, pose)
+    b.integrate(pts, pose)
+    assert all(np.array_equal(x, y) for x, y in zip(a.read(), b.read()))
+
+
+# ---------------------------------------------------------------- analytic SDF
+
+def _wall_setup(fill):
+    vs, tau, sigma = 0.05, 0.2, 0.01
+    R = synth.rot_zyx(math.radians(20.0), 0.0, 0.0)
+    t = np.array([0.3, -0.2, 0.1])
+    d_wall = 3.0 - t[0]
+    r_max = d_wall / math.cos(math.radians(20.0))
+    scene = synth.Scene(boxes=np.array([[3.0, -50.0, -50.0, 10.0, 50.0, 50.0]]))
+    dirs = synth.beam_directions(16, 360, -15.0, 15.0)
+    pts = synth.make_scan(scene, R, t, dirs, sigma, synth.SplitMix64(77), r_max=r_max)
+    dz = synth.delta_z_for(30.0, 16) if fill else 0.0
+    p = synth.params_dict((128, 128, 64), vs, tau, 64, dz, 0.3, r_max, 0, (-64, -64, -32))
+    return p, pts, synth.pose12(R, t), sigma, r_max
+
+
+@pytest.mark.parametrize("fill", [False, True])
+def test_planar_wall_sdf(fill):
+    """Wall x = 3 m seen at incidence <= 20 deg from a rotated, translated sensor:
+    every observed voxel satisfies |tau v / QMAX - clamp(3 - c_x)| <= vs + 3 sigma
+    (+ h_max sin 15 deg with fill), against the FP64 signed distance."""
+    p, pts, pose, sigma, r_max = _wall_setup(fill)
+    m = oracle.OracleMap(p)
+    m.integrate(pts, pose)
+    v, w = m.read()
+    st = m.stats()
+    assert st["valid_rays"] > 300 and st["touched"] > 1000
+    zz, yy, xx = np.nonzero(w > 0)
+    o = p["origin"]
+    vs = p["voxel_size"]
+    cx = (xx + o[0] + 0.5) * vs
+    sdf = np.clip(3.0 - cx, -p["tau"], p["tau"])
+    val = v[zz, yy, xx].astype(np.float64) * p["tau"] / 32767.0
+    bound = vs + 3 * sigma
+    if fill:
+        h_max = p["delta_z"] * (r_max + p["tau"])
+        bound += h_max * math.sin(math.radians(15.0))
+    err = np.abs(val - sdf)
+    assert err.max() <= bound, (err.max(), bound)
+    # the sign convention: positive in front of the surface (sensor side)
+    assert np.all(val[cx < 3.0 - vs - 3 * sigma - 0.03] > 0)
+    assert np.all(val[cx > 3.0 + vs + 3 * sigma + 0.03] < 0)
+
+
+def test_planar_wall_catches_transposed_rotation():
+    """Mutation check: the same scan with R transposed (a plausible mistake)
+    violates the wall bound, so the bound above does pin the transform."""
+    p, pts, pose, sigma, r_max = _wall_setup(False)
+    M = pose.reshape(3, 4).copy()
+    M[:, :3] = M[:, :3].T
+    m = oracle.OracleMap(p)
+    m.integrate(pts, M.reshape(12))
+    v, w = m.read()
+    zz, yy, xx = np.nonzero(w > 0)
+    cx = (xx + p["origin"][0] + 0.5) * p["voxel_size"]
+    val = v[zz, yy, xx] * p["tau"] / 32767.0
+    err = np.abs(val - np.clip(3.0 - cx, -p["tau"], p["tau"]))
+    assert err.max() > p["voxel_size"] + 3 * sigma
+
+
+def test_box_room_accuracy():
+    """Box room (16 x 360 beams, 0.05 m voxels, tau 0.2): most observed voxels are
+    within vs + 3 sigma (+ fill height) of the FP64 signed distance of room + box."""
+    w = synth.workload_room()
+    p = w.params
+    m = oracle.OracleMap(p)
+    m.integrate(w.scans[0], w.poses[0])
+    v, wt = m.read()
+    zz, yy, xx = np.nonzero(wt > 0)
+    o = p["origin"]
+    vs = p["voxel_size"]
+    c = np.stack([(xx + o[0] + 0.5) * vs, (yy + o[1] + 0.5) * vs, (zz + o[2] + 0.5) * vs], axis=1)
+    ud = w.scene.sdf(c)
+    room = w.scene.room
+    inside_room = np.all((c > room[:3]) & (c < room[3:]), axis=1)
+    bx = w.scene.boxes[0]
+    in_box = np.all((c > bx[:3]) & (c < bx[3:]), axis=1)
+    sdf = np.where(inside_room & ~in_box, ud, -ud)
+    sdf = np.clip(sdf, -p["tau"], p["tau"])
+    val = v[zz, yy, xx] * p["tau"] / 32767.0
+    h_max = p["delta_z"] * 8.0
+    ok = np.abs(val - sdf) <= vs + 0.03 + h_max * math.sin(math.radians(15))
+    assert ok.mean() > 0.9, ok.mean()
+    assert m.stats()["valid_rays"] == 5760
+
+
+# ---------------------------------------------------------------- invariants
+
+def test_invariants_room_scan():
+    w = synth.workload_room()
+    p = w.params
+    rng = np.random.default_rng(9)
+    dims = p["dims"]
+    v0 = rng.integers(-32767, 32768, size=(dims[2], dims[1], dims[0])).astype(np.int16)
+    w0 = rng.integers(0, 65, size=v0.shape).astype(np.int16)
+    m = oracle.OracleMap(p)
+    m.load_window(v0, w0)
+    m.integrate(w.scans[0], w.poses[0])
+    v1, w1 = m.read()
+    # weight never exceeds Wmax; untouched voxels are byte-identical
+    assert w1.max() <= p["w_max"]
+    g, q, _ = oracle.hits(p, w.scans[0], w.poses[0])
+    o = np.array(p["origin"])
+    inside = np.all((g >= o) & (g < o + np.array(dims)), axis=1)
+    g = g[inside] - o
+    touched = np.zeros(v0.shape, bool)
+    touched[g[:, 2], g[:, 1], g[:, 0]] = True
+    assert np.array_equal(v1[~touched], v0[~touched]) and np.array_equal(w1[~touched], w0[~touched])
+    assert np.all(w1[touched] >= np.minimum(w0[touched] + 1, p["w_max"]))
+    assert m.stats()["touched"] == int(touched.sum())
+    assert m.stats()["hits"] == int(inside.sum())
+
+
+def test_same_scan_twice():
+    """Integrating one scan twice into an empty map: value moves by at most one
+    code, weight doubles (clamped)."""
+    w = synth.workload_room()
+    m = oracle.OracleMap(w.params)
+    m.integrate(w.scans[0], w.poses[0])
+    v1, w1 = m.read()
+    m.integrate(w.scans[0], w.poses[0])
+    v2, w2 = m.read()
+    t = w1 > 0
+    assert np.abs(v2[t].astype(np.int32) - v1[t]).max() <= 1
+    assert np.array_equal(w2[t], np.minimum(2 * w1[t].astype(np.int32), w.params["w_max"]).astype(np.int16))
+    assert np.array_equal(w2[~t], w1[~t])
+
+
+def test_empty_and_invalid_scans():
+    w = synth.workload_room()
+    m = oracle.OracleMap(w.params)
+    m.integrate(np.zeros((0, 4), np.float32), w.poses[0])
+    assert m.stats() == dict(valid_rays=0, hits=0, touched=0)
+    bad = np.full((100, 4), np.nan, np.float32)
+    bad[:50] = 0.0
+    m.integrate(bad, w.poses[0])
+    v, wt = m.read()
+    assert m.stats() == dict(valid_rays=0, hits=0, touched=0)
+    assert not v.any() and not wt.any()
+
+
+# ---------------------------------------------------------------- shift
+
+def _map_after_room_scan(shift_dims=(128, 128, 64)):
+    w = synth.workload_room()
+    p = dict(w.params, dims=shift_dims, origin=synth.window_origin((0, 0, 0), shift_dims, 0.05))
+    m = oracle.OracleMap(p)
+    m.integrate(w.scans[0], w.poses[0])
+    return m, p, w
+
+
+def test_shift_zero_is_noop():
+    m, p, _ = _map_after_room_scan()
+    v0, w0 = m.read()
+    m.shift(p["origin"])
+    v1, w1 = m.read()
+    assert np.array_equal(v0, v1) and np.array_equal(w0, w1)
+
+
+@pytest.mark.parametrize("delta", [(8, 0, 0), (-16, 8, 0), (0, 0, 8), (24, -40, 16), (200, 0, 0)])
+def test_shift_then_unshift_identity(delta):
+    m, p, _ = _map_after_room_scan()
+    o = p["origin"]
+    v0, w0 = m.read()
+    assert w0.any()
+    no = tuple(o[a] + delta[a] for a in range(3))
+    m.shift(no)
+    assert m.origin == no
+    m.shift(o)
+    v1, w1 = m.read()
+    assert np.array_equal(v0, v1) and np.array_equal(w0, w1)
+
+
+def test_shift_preserves_global_coordinates():
+    """A voxel keeps its value (read by global coordinates) while it stays in the
+    window; voxels that enter for the first time are (0, 0)."""
+    m, p, _ = _map_after_room_scan()
+    o = np.array(p["origin"])
+    d = np.array(p["dims"])
+    delta = np.array([16, -8, 8])
+    no = o + delta
+    lo = np.maximum(o, no)
+    hi = np.minimum(o + d, no + d)
+    before = m.read(tuple(lo), tuple(hi))
+    m.shift(tuple(no))
+    after = m.read(tuple(lo), tuple(hi))
+    assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+    v, w = m.read()
+    # region x >= o.x + d.x (relative to the new origin) is new
+    new_x0 = int(o[0] + d[0] - no[0])
+    assert not v[:, :, new_x0:].any() and not w[:, :, new_x0:].any()
+
+
+def test_shift_store_drops_empty_chunks():
+    m, p, _ = _map_after_room_scan()
+    o = p["origin"]
+    m.shift((o[0] + 512, o[1], o[2]))   # everything leaves
+    v, w = m.read()
+    assert not v.any() and not w.any()
+    n_store = m.store_chunks()
+    assert 0 < n_store < (128 * 128 * 64) // 512   # only non-empty chunks were kept
+    m.shift(o)
+    v1, w1 = m.read()
+    assert w1.any()
+
+
+def test_shift_rejects_unaligned_origin():
+    m, p, _ = _map_after_room_scan()
+    with pytest.raises(ValueError):
+        m.shift((p["origin"][0] + 3, p["origin"][1], p["origin"][2]))
+
+
+def test_integrate_after_shift_matches_bigger_window():
+    """Integrating into a shifted window gives the same values as integrating
+    into a window that never moved and covers the same voxels."""
+    w = synth.workload_room()
+    dims_small = (64, 64, 32)
+    o_small = (-32, -32, -16)
+    ps = dict(w.params, dims=dims_small, origin=o_small)
+    m = oracle.OracleMap(ps)
+    m.shift((-24, -40, -16))
+    m.integrate(w.scans[0], w.poses[0])
+    big = oracle.OracleMap(dict(w.params, dims=(128, 128, 64), origin=(-64, -64, -32)))
+    big.integrate(w.scans[0], w.poses[0])
+    a = m.read()
+    b = big.read((-24, -40, -16), (40, 24, 16))
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
