@@ -1,0 +1,182 @@
+/*
+ * tsdf.h -- C ABI of the GB300 TSDF map-generation library (libtsdf_gb300.so).
+ *
+ * The library integrates registered LiDAR scans into a truncated signed
+ * distance field held on one GPU as a fixed-point, ring-addressed local map,
+ * as described in FeatSense (Gaal et al.), Section "TSDF Map Generation":
+ * each voxel is a (value, weight) pair of 16 bits each; a scan is traversed
+ * ray by ray from the scan pose to each point; every voxel within +-tau of a
+ * hit receives the truncated signed distance of its centre; neighbouring
+ * scan lines are bridged by the vertical interpolation of Eq. 3 / Eq. 4; the
+ * per-scan volume is merged into the map with the weighted average of Eq. 1
+ * and the clamped weight of Eq. 2. The local map is shifted as the sensor
+ * moves (Introduction: a local map that is shifted after a movement
+ * threshold, its parts written to and read back from a global map).
+ *
+ * Conventions for every function:
+ *  - Return value: TSDF_OK (0) or a negative TSDF_ERR_* code. On error no
+ *    state visible through this API has changed unless stated otherwise.
+ *  - Device pointers must come from the same CUDA device the map was created
+ *    on (the device current at tsdf_map_create). The library makes that
+ *    device current for the duration of each call.
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream. Calls marked "asynchronous" only enqueue work on `stream`; calls
+ *    on one map must be serialised by the caller (one stream, or events).
+ *  - All sizes are counts of elements unless named *_bytes.
+ *  - Thread safety: different maps may be used from different host threads;
+ *    one map must not be used by two host threads at once.
+ *
+ * Fixed-point encoding: value code q in [-32767, 32767] stands for the
+ * truncated signed distance q * tau / 32767 metres, positive in front of the
+ * surface (on the sensor side). Weight 0 means "never observed".
+ */
+#ifndef TSDF_GB300_H
+#define TSDF_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---------------------------------------------------------- */
+#define TSDF_OK              0
+#define TSDF_ERR_INVALID    -1  /* bad argument: null pointer, bad dims/params, misaligned points, n out of range, box outside the window */
+#define TSDF_ERR_OOM        -2  /* a device or pinned-host allocation failed */
+#define TSDF_ERR_CUDA       -3  /* a CUDA runtime call or kernel launch failed; see tsdf_last_cuda_error() */
+#define TSDF_ERR_TIMEOUT    -4  /* a bounded device-side wait expired */
+#define TSDF_ERR_ADMISSION  -5  /* a session would exceed the device-memory budget */
+#define TSDF_ERR_BUSY       -6  /* the resource is in use (e.g. an outstanding request) */
+
+/* ---- per-scan reduction of the contributions to one voxel ----------------- */
+#define TSDF_REDUCE_WSUM     0  /* sum of weight * distance and sum of weights (weight 1 per contribution) */
+#define TSDF_REDUCE_MIN_ABS  1  /* the paper's "smallest distance of all rays": smallest |q|, ties -> positive; weight 1 */
+
+/* Largest number of points accepted by one integrate call. With weight 1 per
+ * contribution, a voxel receives at most 4 contributions per ray, so the
+ * per-scan weight sum of a voxel stays below 2^24 and its distance sum below
+ * 2^39: both fit the packed 64-bit accumulator exactly. */
+#define TSDF_MAX_POINTS      (1LL << 22)
+
+/* Map parameters. */
+typedef struct tsdf_params {
+    int32_t dims[3];      /* window size in voxels (x, y, z): each a power of two, 8..32768; product <= 2^31 */
+    float   voxel_size;   /* voxel edge length in metres, > 0 */
+    float   tau;          /* truncation distance in metres, voxel_size <= tau <= 1024 voxels */
+    int32_t w_max;        /* weight cap of Eq. 2, 1..32767 */
+    float   delta_z;      /* Eq. 3, tan(vfov / hlines) computed by the caller; 0 disables vertical interpolation; 0..1 */
+    float   r_min;        /* points with range < r_min are skipped, >= 0 */
+    float   r_max;        /* points with range > r_max are skipped, r_min <= r_max <= 1e5 */
+    int32_t reduce;       /* TSDF_REDUCE_WSUM or TSDF_REDUCE_MIN_ABS */
+    int32_t reserved;     /* must be 0 */
+    int64_t origin[3];    /* initial window origin in global voxel coordinates; multiples of 8, |origin| <= 2^40 */
+} tsdf_params;
+
+/* Counters of the most recent integrate call on a map. */
+typedef struct tsdf_scan_stats {
+    int64_t valid_rays;   /* points with a finite range inside [r_min, r_max] */
+    int64_t hits;         /* (ray, voxel) contributions that fell inside the window */
+    int64_t touched;      /* distinct voxels updated by Eq. 1 / Eq. 2 */
+} tsdf_scan_stats;
+
+typedef struct tsdf_map tsdf_map;   /* opaque; owns all of its device memory */
+
+/* Create a map on the current CUDA device. The window starts at
+ * params->origin with every voxel (0, 0). Allocates the voxel grid (4 bytes
+ * per voxel: int16 value, int16 weight), the per-scan accumulator (8 bytes
+ * per voxel, kept all-zero between calls) and the touched list (4 bytes per
+ * voxel). Synchronous. On success *out receives the handle, which the caller
+ * releases with tsdf_map_destroy. Errors: INVALID, OOM, CUDA. */
+int tsdf_map_create(const tsdf_params* params, tsdf_map** out);
+
+/* Release a map and all of its device memory. Waits for the map's work to
+ * finish (device synchronisation). NULL is accepted and ignored. */
+int tsdf_map_destroy(tsdf_map* map);
+
+/* Integrate one registered scan (Section "TSDF Map Generation": ray march
+ * within +-tau of each point, vertical interpolation of Eq. 3 / Eq. 4,
+ * per-scan volume, Eq. 1 / Eq. 2). Asynchronous on `stream`.
+ *   points_dev : device pointer to n float4 values (x, y, z, unused) in the
+ *                sensor frame, 16-byte aligned, any point order (beam-major
+ *                for locality). Non-finite points and points out of
+ *                [r_min, r_max] are skipped. Owned by the caller, who keeps
+ *                it alive until the stream has passed this call.
+ *   n          : 0 <= n <= TSDF_MAX_POINTS; n = 0 only records zero counters.
+ *   pose       : host pointer to 12 floats, the row-major 3x4 sensor-to-world
+ *                transform [R | t]; R's third column is the direction
+ *                orthogonal to the scan lines. Copied at call time.
+ * The result is bit-identical to a serial evaluation in any launch order.
+ * Errors: INVALID, CUDA. */
+int tsdf_integrate(tsdf_map* map, const float* points_dev, int64_t n, const float pose[12], void* stream);
+
+/* As tsdf_integrate, but points_host is a HOST pointer (pinned or pageable)
+ * to n float4 values. The points are copied into a map-owned device buffer on
+ * `stream` and integrated. Returns once the copy has been enqueued (for
+ * pageable memory the CUDA runtime may wait for the copy). Errors: INVALID,
+ * OOM, CUDA. */
+int tsdf_integrate_host(tsdf_map* map, const float* points_host, int64_t n, const float pose[12], void* stream);
+
+/* Move the window to new_origin (global voxel coordinates, multiples of 8,
+ * |new_origin| <= 2^40). Voxels inside both windows keep their values (ring
+ * addressing: no data moves). Chunks of 8^3 voxels that leave the window are
+ * written to the map's device-resident global store; chunks that enter are
+ * read back from the store, or set to (0, 0) if never stored. Asynchronous
+ * on `stream`; may allocate store memory synchronously. Errors: INVALID, OOM,
+ * CUDA. */
+int tsdf_shift(tsdf_map* map, const int64_t new_origin[3], void* stream);
+
+/* Copy the global voxel box [lo, hi) (must lie inside the current window) to
+ * the host in [z][y][x] order: value_host and weight_host each receive
+ * (hi-lo).x*(hi-lo).y*(hi-lo).z int16 values; either may be NULL. Enqueued on
+ * `stream`, then synchronises `stream`. Errors: INVALID, OOM, CUDA. */
+int tsdf_read(tsdf_map* map, const int64_t lo[3], const int64_t hi[3], int16_t* value_host,
+              int16_t* weight_host, void* stream);
+
+/* Overwrite the global box [lo, hi) (inside the window) from host arrays in
+ * [z][y][x] order (restore / test set-up). Weights must be in [0, w_max].
+ * Synchronises `stream`. Errors: INVALID, OOM, CUDA. */
+int tsdf_write(tsdf_map* map, const int64_t lo[3], const int64_t hi[3], const int16_t* value_host,
+               const int16_t* weight_host, void* stream);
+
+/* Counters of the most recent integrate call (zero before the first).
+ * Synchronises `stream`. Errors: INVALID, CUDA. */
+int tsdf_stats(tsdf_map* map, tsdf_scan_stats* out, void* stream);
+
+/* Current window origin (host-side state; no synchronisation). */
+int tsdf_get_origin(const tsdf_map* map, int64_t out[3]);
+
+/* Device pointer of the voxel grid: uint32 words, value in the low 16 bits,
+ * weight in the high 16 bits, ring-addressed: global voxel g lives at
+ * ((g.z & (Z-1)) * Y + (g.y & (Y-1))) * X + (g.x & (X-1)). Valid until destroy. */
+int tsdf_grid_device_ptr(const tsdf_map* map, void** out);
+
+/* Per-kernel device time of this map's launches, measured with CUDA events
+ * recorded on the launching stream around each kernel while profiling is on. */
+typedef struct tsdf_kernel_time {
+    char    name[24];     /* "contrib", "apply" or "shift" */
+    int64_t launches;     /* kernel launches since profiling was enabled */
+    double  total_ms;     /* summed event-to-event device time */
+} tsdf_kernel_time;
+
+/* Turn per-kernel event timing on (enable != 0) or off, and reset the
+ * accumulated times. Host-side state only. Errors: INVALID. */
+int tsdf_profile_enable(tsdf_map* map, int32_t enable);
+
+/* Accumulated per-kernel times: writes up to `capacity` entries to out and
+ * the number of kernels with launches to *count. Waits for the recorded
+ * events (host blocks until the profiled launches have finished).
+ * Errors: INVALID, CUDA. */
+int tsdf_profile_read(tsdf_map* map, tsdf_kernel_time* out, int32_t capacity, int32_t* count);
+
+/* Static description of an error code. Never NULL. */
+const char* tsdf_error_string(int code);
+
+/* The last CUDA error seen by the library on this host thread (cudaError_t
+ * as int, 0 if none). */
+int tsdf_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSDF_GB300_H */

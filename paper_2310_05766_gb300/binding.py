@@ -1,0 +1,274 @@
+"""Thin Python binding of libtsdf_gb300.so (the C ABI in include/tsdf.h).
+
+Argument marshalling only: every step of the TSDF path runs in the library's
+CUDA kernels. PyTorch is used for device memory (tensors' data pointers) and
+streams (`torch.cuda.current_stream().cuda_stream`). There is no CPU
+fallback: if the library has not been built, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+TSDF_OK = 0
+TSDF_ERR_INVALID = -1
+TSDF_ERR_OOM = -2
+TSDF_ERR_CUDA = -3
+TSDF_ERR_TIMEOUT = -4
+TSDF_ERR_ADMISSION = -5
+TSDF_ERR_BUSY = -6
+TSDF_REDUCE_WSUM = 0
+TSDF_REDUCE_MIN_ABS = 1
+TSDF_MAX_POINTS = 1 << 22
+
+
+class TsdfError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {tsdf_error_string(code)} ({code})"
+                         + (f", cudaError {tsdf_last_cuda_error()}" if code == TSDF_ERR_CUDA else ""))
+
+
+class tsdf_params(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int32 * 3), ("voxel_size", ctypes.c_float), ("tau", ctypes.c_float),
+                ("w_max", ctypes.c_int32), ("delta_z", ctypes.c_float), ("r_min", ctypes.c_float),
+                ("r_max", ctypes.c_float), ("reduce", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("origin", ctypes.c_int64 * 3)]
+
+
+class tsdf_scan_stats(ctypes.Structure):
+    _fields_ = [("valid_rays", ctypes.c_int64), ("hits", ctypes.c_int64), ("touched", ctypes.c_int64)]
+
+
+class tsdf_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load the CUDA library. Raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: run __graft_entry__.build() "
+                           "(the TSDF path has no CPU fallback)")
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    f32p = P(ctypes.c_float)
+    L.tsdf_map_create.argtypes = [P(tsdf_params), P(vp)]
+    L.tsdf_map_destroy.argtypes = [vp]
+    L.tsdf_integrate.argtypes = [vp, vp, i64, f32p, vp]
+    L.tsdf_integrate_host.argtypes = [vp, vp, i64, f32p, vp]
+    L.tsdf_shift.argtypes = [vp, P(i64), vp]
+    L.tsdf_read.argtypes = [vp, P(i64), P(i64), vp, vp, vp]
+    L.tsdf_write.argtypes = [vp, P(i64), P(i64), vp, vp, vp]
+    L.tsdf_stats.argtypes = [vp, P(tsdf_scan_stats), vp]
+    L.tsdf_get_origin.argtypes = [vp, P(i64)]
+    L.tsdf_grid_device_ptr.argtypes = [vp, P(vp)]
+    L.tsdf_profile_enable.argtypes = [vp, ctypes.c_int32]
+    L.tsdf_profile_read.argtypes = [vp, P(tsdf_kernel_time), ctypes.c_int32, P(ctypes.c_int32)]
+    L.tsdf_error_string.argtypes = [i32]
+    L.tsdf_error_string.restype = ctypes.c_char_p
+    L.tsdf_last_cuda_error.argtypes = []
+    for name in ("tsdf_map_create", "tsdf_map_destroy", "tsdf_integrate", "tsdf_integrate_host", "tsdf_shift",
+                 "tsdf_read", "tsdf_write", "tsdf_stats", "tsdf_get_origin", "tsdf_grid_device_ptr",
+                 "tsdf_last_cuda_error", "tsdf_profile_enable", "tsdf_profile_read"):
+        getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str):
+    if rc != TSDF_OK:
+        raise TsdfError(rc, what)
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_params(p: dict) -> tsdf_params:
+    s = tsdf_params()
+    for a in range(3):
+        s.dims[a] = int(p["dims"][a])
+        s.origin[a] = int(p["origin"][a])
+    s.voxel_size = float(p["voxel_size"])
+    s.tau = float(p["tau"])
+    s.w_max = int(p["w_max"])
+    s.delta_z = float(p["delta_z"])
+    s.r_min = float(p["r_min"])
+    s.r_max = float(p["r_max"])
+    s.reduce = int(p.get("reduce", 0))
+    s.reserved = 0
+    return s
+
+
+def _pose_arg(pose):
+    a = np.ascontiguousarray(np.asarray(pose, dtype=np.float32).reshape(12))
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _i64_3(v):
+    a = (ctypes.c_int64 * 3)(*[int(x) for x in v])
+    return a
+
+
+# ---- functions with the C ABI's names -------------------------------------
+
+def tsdf_error_string(code: int) -> str:
+    return lib().tsdf_error_string(int(code)).decode()
+
+
+def tsdf_last_cuda_error() -> int:
+    return int(lib().tsdf_last_cuda_error())
+
+
+def tsdf_map_create(params: dict | tsdf_params) -> int:
+    prm = params if isinstance(params, tsdf_params) else make_params(params)
+    h = ctypes.c_void_p()
+    _check(lib().tsdf_map_create(ctypes.byref(prm), ctypes.byref(h)), "tsdf_map_create")
+    return h.value
+
+
+def tsdf_map_destroy(handle: int) -> None:
+    _check(lib().tsdf_map_destroy(handle), "tsdf_map_destroy")
+
+
+def tsdf_integrate(handle: int, points_dev, n: int, pose, stream=None) -> None:
+    """points_dev: a CUDA float32 tensor of shape (n, 4) (or a raw device pointer)."""
+    ptr = points_dev if isinstance(points_dev, int) else points_dev.data_ptr()
+    pa, pp = _pose_arg(pose)
+    _check(lib().tsdf_integrate(handle, ptr, int(n), pp, _stream_ptr(stream)), "tsdf_integrate")
+
+
+def tsdf_integrate_host(handle: int, points_host, n: int, pose, stream=None) -> None:
+    """points_host: a host float32 array/tensor of shape (n, 4), pinned or pageable."""
+    if isinstance(points_host, int):
+        ptr = points_host
+    elif isinstance(points_host, np.ndarray):
+        assert points_host.dtype == np.float32 and points_host.flags.c_contiguous
+        ptr = points_host.ctypes.data
+    else:
+        ptr = points_host.data_ptr()
+    pa, pp = _pose_arg(pose)
+    _check(lib().tsdf_integrate_host(handle, ptr, int(n), pp, _stream_ptr(stream)), "tsdf_integrate_host")
+
+
+def tsdf_shift(handle: int, new_origin, stream=None) -> None:
+    _check(lib().tsdf_shift(handle, _i64_3(new_origin), _stream_ptr(stream)), "tsdf_shift")
+
+
+def tsdf_read(handle: int, lo, hi, stream=None):
+    """Returns (value, weight) int16 numpy arrays of shape (z, y, x) for the global box [lo, hi)."""
+    shape = (int(hi[2] - lo[2]), int(hi[1] - lo[1]), int(hi[0] - lo[0]))
+    v = np.zeros(shape, dtype=np.int16)
+    w = np.zeros(shape, dtype=np.int16)
+    _check(lib().tsdf_read(handle, _i64_3(lo), _i64_3(hi), v.ctypes.data, w.ctypes.data, _stream_ptr(stream)),
+           "tsdf_read")
+    return v, w
+
+
+def tsdf_write(handle: int, lo, hi, value, weight, stream=None) -> None:
+    v = np.ascontiguousarray(value, dtype=np.int16)
+    w = np.ascontiguousarray(weight, dtype=np.int16)
+    _check(lib().tsdf_write(handle, _i64_3(lo), _i64_3(hi), v.ctypes.data, w.ctypes.data, _stream_ptr(stream)),
+           "tsdf_write")
+
+
+def tsdf_stats(handle: int, stream=None) -> dict:
+    st = tsdf_scan_stats()
+    _check(lib().tsdf_stats(handle, ctypes.byref(st), _stream_ptr(stream)), "tsdf_stats")
+    return dict(valid_rays=st.valid_rays, hits=st.hits, touched=st.touched)
+
+
+def tsdf_get_origin(handle: int):
+    o = (ctypes.c_int64 * 3)()
+    _check(lib().tsdf_get_origin(handle, o), "tsdf_get_origin")
+    return tuple(int(x) for x in o)
+
+
+def tsdf_grid_device_ptr(handle: int) -> int:
+    p = ctypes.c_void_p()
+    _check(lib().tsdf_grid_device_ptr(handle, ctypes.byref(p)), "tsdf_grid_device_ptr")
+    return p.value
+
+
+def tsdf_profile_enable(handle: int, enable: bool = True) -> None:
+    _check(lib().tsdf_profile_enable(handle, 1 if enable else 0), "tsdf_profile_enable")
+
+
+def tsdf_profile_read(handle: int) -> dict:
+    """{kernel name: (launches, total_ms)} accumulated since profiling was enabled."""
+    buf = (tsdf_kernel_time * 8)()
+    cnt = ctypes.c_int32()
+    _check(lib().tsdf_profile_read(handle, buf, 8, ctypes.byref(cnt)), "tsdf_profile_read")
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(cnt.value)}
+
+
+# ---- convenience wrapper ---------------------------------------------------
+
+class TsdfMap:
+    """Owning wrapper of a tsdf_map handle."""
+
+    def __init__(self, params: dict):
+        self.params = dict(params)
+        self.handle = tsdf_map_create(params)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            tsdf_map_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def integrate(self, points_dev, pose, stream=None):
+        tsdf_integrate(self.handle, points_dev, points_dev.shape[0], pose, stream)
+
+    def integrate_host(self, points_host, pose, stream=None):
+        tsdf_integrate_host(self.handle, points_host, points_host.shape[0], pose, stream)
+
+    def shift(self, new_origin, stream=None):
+        tsdf_shift(self.handle, new_origin, stream)
+
+    @property
+    def origin(self):
+        return tsdf_get_origin(self.handle)
+
+    def read(self, lo=None, hi=None, stream=None):
+        o = self.origin
+        d = self.params["dims"]
+        lo = o if lo is None else lo
+        hi = tuple(o[a] + d[a] for a in range(3)) if hi is None else hi
+        return tsdf_read(self.handle, lo, hi, stream)
+
+    def write(self, value, weight, lo=None, hi=None, stream=None):
+        o = self.origin
+        d = self.params["dims"]
+        lo = o if lo is None else lo
+        hi = tuple(o[a] + d[a] for a in range(3)) if hi is None else hi
+        tsdf_write(self.handle, lo, hi, value, weight, stream)
+
+    def stats(self, stream=None):
+        return tsdf_stats(self.handle, stream)

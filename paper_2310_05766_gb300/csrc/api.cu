@@ -1,0 +1,553 @@
+// Host side of the C ABI declared in include/tsdf.h: argument validation,
+// device memory ownership, the device-resident global chunk store and the
+// launch sequence of each call. No float arithmetic of the method runs here
+// beyond the per-map constants 1/voxel, QMAX/tau and K, derived once in
+// binary64 and rounded to binary32.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "tsdf_internal.cuh"
+#include "../../include/tsdf.h"
+
+using namespace tsdf;
+
+namespace {
+
+thread_local int g_last_cuda_error = 0;
+
+int cuda_fail(cudaError_t e) {
+    g_last_cuda_error = (int)e;
+    return e == cudaErrorMemoryAllocation ? TSDF_ERR_OOM : TSDF_ERR_CUDA;
+}
+
+#define TSDF_CU(call)                          \
+    do {                                       \
+        cudaError_t e_ = (call);               \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+// Makes the map's device current for the scope of one call.
+struct DeviceScope {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceScope(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = cudaSetDevice(dev) == cudaSuccess;
+        }
+    }
+    ~DeviceScope() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+struct ChunkKey {
+    long long x, y, z;
+    bool operator==(const ChunkKey& o) const { return x == o.x && y == o.y && z == o.z; }
+};
+struct ChunkKeyHash {
+    size_t operator()(const ChunkKey& k) const {
+        unsigned long long h = (unsigned long long)k.x * 0x9E3779B97F4A7C15ull;
+        h ^= (unsigned long long)k.y * 0xC2B2AE3D27D4EB4Full + (h << 6) + (h >> 2);
+        h ^= (unsigned long long)k.z * 0x165667B19E3779F9ull + (h << 6) + (h >> 2);
+        return (size_t)h;
+    }
+};
+
+constexpr uint32_t kChunkBytes = 8 * 8 * 8 * 4;
+constexpr uint32_t kSegChunks = 4096;   // 8 MiB store segments
+
+bool is_pow2(int32_t v) { return v > 0 && (v & (v - 1)) == 0; }
+int log2u(uint32_t v) {
+    int s = 0;
+    while ((1u << s) < v) ++s;
+    return s;
+}
+long long floordiv8(long long v) { return v >= 0 ? v / 8 : -((-v + 7) / 8); }
+
+const long long kOriginLimit = 1LL << 40;
+
+enum KernelId { kContrib = 0, kApply = 1, kShift = 2, kNumKernels = 3 };
+const char* const kKernelNames[kNumKernels] = {"contrib", "apply", "shift"};
+
+struct Pending {
+    int kernel;
+    cudaEvent_t start, stop;
+};
+
+}  // namespace
+
+struct tsdf_map {
+    tsdf_params p;
+    int device = 0;
+    int num_sms = 1;
+    float inv_vs = 0.f, qs = 0.f;
+    int K = 0;
+    uint32_t shx = 0, shxy = 0;
+    long long origin[3] = {0, 0, 0};
+    size_t voxels = 0;
+    MapDev dev{};
+    // device-resident global store of 8^3 chunks
+    std::unordered_map<ChunkKey, uint32_t, ChunkKeyHash> store_index;
+    std::vector<char*> store_segments;
+    uint32_t store_count = 0;
+    ShiftItem* items_dev = nullptr;
+    size_t items_dev_cap = 0;
+    ShiftItem* items_host = nullptr;
+    size_t items_host_cap = 0;
+    cudaEvent_t items_event = nullptr;
+    bool items_event_pending = false;
+    // staging for host-resident points
+    float4* stage_dev = nullptr;
+    size_t stage_cap = 0;
+    // optional per-kernel event timing
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<Pending> pending;
+    int64_t prof_launches[kNumKernels] = {0, 0, 0};
+    double prof_ms[kNumKernels] = {0.0, 0.0, 0.0};
+};
+
+namespace {
+
+int validate_params(const tsdf_params* p) {
+    if (!p) return TSDF_ERR_INVALID;
+    unsigned long long prod = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (!is_pow2(p->dims[a]) || p->dims[a] < 8 || p->dims[a] > 32768) return TSDF_ERR_INVALID;
+        prod *= (unsigned long long)p->dims[a];
+        if (p->origin[a] % 8 != 0 || p->origin[a] > kOriginLimit || p->origin[a] < -kOriginLimit)
+            return TSDF_ERR_INVALID;
+    }
+    if (prod > (1ull << 31)) return TSDF_ERR_INVALID;
+    if (!std::isfinite(p->voxel_size) || !(p->voxel_size > 0.f)) return TSDF_ERR_INVALID;
+    if (!std::isfinite(p->tau) || !(p->tau >= p->voxel_size) || (double)p->tau / p->voxel_size > 1024.0)
+        return TSDF_ERR_INVALID;
+    if (p->w_max < 1 || p->w_max > 32767) return TSDF_ERR_INVALID;
+    if (!std::isfinite(p->delta_z) || p->delta_z < 0.f || p->delta_z > 1.f) return TSDF_ERR_INVALID;
+    if (!std::isfinite(p->r_min) || !std::isfinite(p->r_max) || p->r_min < 0.f || p->r_max < p->r_min ||
+        p->r_max > 1e5f)
+        return TSDF_ERR_INVALID;
+    if ((double)p->delta_z * ((double)p->r_max + p->tau) / p->voxel_size > 1e6) return TSDF_ERR_INVALID;
+    if (p->reduce != TSDF_REDUCE_WSUM && p->reduce != TSDF_REDUCE_MIN_ABS) return TSDF_ERR_INVALID;
+    if (p->reserved != 0) return TSDF_ERR_INVALID;
+    return TSDF_OK;
+}
+
+cudaEvent_t take_event(tsdf_map* m) {
+    if (!m->ev_pool.empty()) {
+        cudaEvent_t e = m->ev_pool.back();
+        m->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Records an event on `s` when profiling; returns nullptr otherwise.
+cudaEvent_t prof_mark(tsdf_map* m, cudaStream_t s) {
+    if (!m->prof) return nullptr;
+    cudaEvent_t e = take_event(m);
+    if (e && cudaEventRecord(e, s) != cudaSuccess) {
+        m->ev_pool.push_back(e);
+        return nullptr;
+    }
+    return e;
+}
+
+void prof_push(tsdf_map* m, int kernel, cudaEvent_t a, cudaEvent_t b) {
+    if (a && b) {
+        m->pending.push_back(Pending{kernel, a, b});
+        return;
+    }
+    if (a) m->ev_pool.push_back(a);
+    if (b) m->ev_pool.push_back(b);
+}
+
+int prof_drain(tsdf_map* m) {
+    for (const Pending& p : m->pending) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(p.stop);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.start, p.stop);
+        if (e != cudaSuccess) return cuda_fail(e);
+        m->prof_launches[p.kernel] += 1;
+        m->prof_ms[p.kernel] += ms;
+        m->ev_pool.push_back(p.start);
+        m->ev_pool.push_back(p.stop);
+    }
+    m->pending.clear();
+    return TSDF_OK;
+}
+
+void free_map(tsdf_map* m) {
+    if (!m) return;
+    for (const Pending& p : m->pending) {
+        cudaEventDestroy(p.start);
+        cudaEventDestroy(p.stop);
+    }
+    for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
+    cudaFree(m->dev.grid);
+    cudaFree(m->dev.acc);
+    cudaFree(m->dev.touched);
+    cudaFree(m->dev.ctr);
+    for (char* s : m->store_segments) cudaFree(s);
+    cudaFree(m->items_dev);
+    if (m->items_host) cudaFreeHost(m->items_host);
+    if (m->items_event) cudaEventDestroy(m->items_event);
+    cudaFree(m->stage_dev);
+    delete m;
+}
+
+bool box_inside(const tsdf_map* m, const int64_t lo[3], const int64_t hi[3], uint32_t box[3]) {
+    for (int a = 0; a < 3; ++a) {
+        if (lo[a] < m->origin[a] || hi[a] > m->origin[a] + m->p.dims[a] || hi[a] < lo[a]) return false;
+        box[a] = (uint32_t)(hi[a] - lo[a]);
+    }
+    return true;
+}
+
+// Store address of a chunk, allocating a new store slot when `create`.
+int store_lookup(tsdf_map* m, const ChunkKey& k, bool create, unsigned long long* out) {
+    auto it = m->store_index.find(k);
+    if (it != m->store_index.end()) {
+        uint32_t idx = it->second;
+        *out = (unsigned long long)(m->store_segments[idx / kSegChunks] + (size_t)(idx % kSegChunks) * kChunkBytes);
+        return TSDF_OK;
+    }
+    if (!create) {
+        *out = 0ull;
+        return TSDF_OK;
+    }
+    uint32_t idx = m->store_count;
+    if (idx / kSegChunks >= m->store_segments.size()) {
+        char* seg = nullptr;
+        cudaError_t e = cudaMalloc(&seg, (size_t)kSegChunks * kChunkBytes);
+        if (e != cudaSuccess) return cuda_fail(e);
+        m->store_segments.push_back(seg);
+    }
+    m->store_count++;
+    m->store_index.emplace(k, idx);
+    *out = (unsigned long long)(m->store_segments[idx / kSegChunks] + (size_t)(idx % kSegChunks) * kChunkBytes);
+    return TSDF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tsdf_map_create(const tsdf_params* params, tsdf_map** out) {
+    if (!out) return TSDF_ERR_INVALID;
+    *out = nullptr;
+    int rc = validate_params(params);
+    if (rc != TSDF_OK) return rc;
+    tsdf_map* m = new tsdf_map();
+    m->p = *params;
+    TSDF_CU(cudaGetDevice(&m->device));
+    cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device);
+    if (m->num_sms < 1) m->num_sms = 1;
+    m->inv_vs = (float)(1.0 / (double)params->voxel_size);
+    m->qs = (float)((double)kQMax / (double)params->tau);
+    m->K = (int)std::floor((double)params->tau / (double)params->voxel_size + 1e-9);
+    m->shx = (uint32_t)log2u((uint32_t)params->dims[0]);
+    m->shxy = m->shx + (uint32_t)log2u((uint32_t)params->dims[1]);
+    for (int a = 0; a < 3; ++a) m->origin[a] = params->origin[a];
+    m->voxels = (size_t)params->dims[0] * params->dims[1] * params->dims[2];
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&m->dev.grid, m->voxels * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&m->dev.acc, m->voxels * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&m->dev.touched, m->voxels * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&m->dev.ctr, sizeof(MapCounters));
+    if (e == cudaSuccess) e = cudaMemset(m->dev.grid, 0, m->voxels * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(m->dev.acc, 0, m->voxels * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(m->dev.ctr, 0, sizeof(MapCounters));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->items_event, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_map(m);
+        return cuda_fail(e);
+    }
+    *out = m;
+    return TSDF_OK;
+}
+
+int tsdf_map_destroy(tsdf_map* map) {
+    if (!map) return TSDF_OK;
+    DeviceScope ds(map->device);
+    cudaDeviceSynchronize();
+    free_map(map);
+    return TSDF_OK;
+}
+
+static int integrate_dev(tsdf_map* map, const float* points_dev, int64_t n, const float pose[12],
+                         cudaStream_t s) {
+    ScanArgs a{};
+    a.pts = reinterpret_cast<const float4*>(points_dev);
+    a.n = (int32_t)n;
+    a.K = map->K;
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) a.R[r * 3 + c] = pose[r * 4 + c];
+        a.t[r] = pose[r * 4 + 3];
+    }
+    a.vs = map->p.voxel_size;
+    a.inv_vs = map->inv_vs;
+    a.tau = map->p.tau;
+    a.qs = map->qs;
+    a.dz = map->p.delta_z;
+    a.rmin = map->p.r_min;
+    a.rmax = map->p.r_max;
+    a.fill = map->p.delta_z > 0.f ? 1 : 0;
+    a.reduce = map->p.reduce;
+    a.ox = map->origin[0];
+    a.oy = map->origin[1];
+    a.oz = map->origin[2];
+    a.dimx = (uint32_t)map->p.dims[0];
+    a.dimy = (uint32_t)map->p.dims[1];
+    a.dimz = (uint32_t)map->p.dims[2];
+    a.shx = map->shx;
+    a.shxy = map->shxy;
+    a.w_max = map->p.w_max;
+    cudaEvent_t e0 = n > 0 ? prof_mark(map, s) : nullptr;
+    TSDF_CU(launch_contrib(a, map->dev, s));
+    cudaEvent_t e1 = n > 0 ? prof_mark(map, s) : nullptr;
+    cudaEvent_t e2 = prof_mark(map, s);
+    TSDF_CU(launch_apply(map->dev, map->p.reduce, map->p.w_max, map->num_sms * 4, s));
+    cudaEvent_t e3 = prof_mark(map, s);
+    prof_push(map, kContrib, e0, e1);
+    prof_push(map, kApply, e2, e3);
+    return TSDF_OK;
+}
+
+static int check_scan_args(tsdf_map* map, const float* pts, int64_t n, const float pose[12]) {
+    if (!map || !pose || n < 0 || n > TSDF_MAX_POINTS) return TSDF_ERR_INVALID;
+    if (n > 0 && !pts) return TSDF_ERR_INVALID;
+    for (int i = 0; i < 12; ++i)
+        if (!std::isfinite(pose[i])) return TSDF_ERR_INVALID;
+    return TSDF_OK;
+}
+
+int tsdf_integrate(tsdf_map* map, const float* points_dev, int64_t n, const float pose[12], void* stream) {
+    int rc = check_scan_args(map, points_dev, n, pose);
+    if (rc != TSDF_OK) return rc;
+    if (((uintptr_t)points_dev & 15u) != 0) return TSDF_ERR_INVALID;
+    DeviceScope ds(map->device);
+    return integrate_dev(map, points_dev, n, pose, (cudaStream_t)stream);
+}
+
+int tsdf_integrate_host(tsdf_map* map, const float* points_host, int64_t n, const float pose[12], void* stream) {
+    int rc = check_scan_args(map, points_host, n, pose);
+    if (rc != TSDF_OK) return rc;
+    DeviceScope ds(map->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((size_t)n > map->stage_cap) {
+        // a previous call may still read the old buffer: cudaFree waits for the device
+        cudaFree(map->stage_dev);
+        map->stage_dev = nullptr;
+        map->stage_cap = 0;
+        size_t cap = (size_t)n < 4096 ? 4096 : (size_t)n;
+        TSDF_CU(cudaMalloc(&map->stage_dev, cap * sizeof(float4)));
+        map->stage_cap = cap;
+    }
+    if (n > 0) TSDF_CU(cudaMemcpyAsync(map->stage_dev, points_host, (size_t)n * sizeof(float4), cudaMemcpyHostToDevice, s));
+    return integrate_dev(map, reinterpret_cast<const float*>(map->stage_dev), n, pose, s);
+}
+
+int tsdf_shift(tsdf_map* map, const int64_t new_origin[3], void* stream) {
+    if (!map || !new_origin) return TSDF_ERR_INVALID;
+    for (int a = 0; a < 3; ++a)
+        if (new_origin[a] % 8 != 0 || new_origin[a] > kOriginLimit || new_origin[a] < -kOriginLimit)
+            return TSDF_ERR_INVALID;
+    if (new_origin[0] == map->origin[0] && new_origin[1] == map->origin[1] && new_origin[2] == map->origin[2])
+        return TSDF_OK;
+    DeviceScope ds(map->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long C[3] = {map->p.dims[0] / 8, map->p.dims[1] / 8, map->p.dims[2] / 8};
+    std::vector<long long> oldc[3], newc[3];
+    std::vector<char> chg[3];
+    for (int a = 0; a < 3; ++a) {
+        const long long co = floordiv8(map->origin[a]), cn = floordiv8(new_origin[a]);
+        oldc[a].resize(C[a]);
+        newc[a].resize(C[a]);
+        chg[a].resize(C[a]);
+        for (long long sl = 0; sl < C[a]; ++sl) {
+            // the chunk of each window that occupies ring slot sl
+            oldc[a][sl] = co + (((sl - co) % C[a]) + C[a]) % C[a];
+            newc[a][sl] = cn + (((sl - cn) % C[a]) + C[a]) % C[a];
+            chg[a][sl] = oldc[a][sl] != newc[a][sl];
+        }
+    }
+    std::vector<ShiftItem> items;
+    for (long long sz = 0; sz < C[2]; ++sz) {
+        for (long long sy = 0; sy < C[1]; ++sy) {
+            const bool row_changes = chg[2][sz] || chg[1][sy];
+            for (long long sx = 0; sx < C[0]; ++sx) {
+                if (!row_changes && !chg[0][sx]) continue;
+                ShiftItem it{};
+                it.chunk_slot = (uint32_t)((sz * C[1] + sy) * C[0] + sx);
+                int rc = store_lookup(map, ChunkKey{oldc[0][sx], oldc[1][sy], oldc[2][sz]}, true, &it.out_ptr);
+                if (rc != TSDF_OK) return rc;
+                rc = store_lookup(map, ChunkKey{newc[0][sx], newc[1][sy], newc[2][sz]}, false, &it.in_ptr);
+                if (rc != TSDF_OK) return rc;
+                items.push_back(it);
+            }
+        }
+    }
+    const size_t cnt = items.size();
+    if (cnt > 0) {
+        if (map->items_event_pending) {
+            TSDF_CU(cudaEventSynchronize(map->items_event));
+            map->items_event_pending = false;
+        }
+        if (cnt > map->items_host_cap) {
+            if (map->items_host) cudaFreeHost(map->items_host);
+            map->items_host = nullptr;
+            map->items_host_cap = 0;
+            TSDF_CU(cudaMallocHost(&map->items_host, cnt * sizeof(ShiftItem)));
+            map->items_host_cap = cnt;
+        }
+        if (cnt > map->items_dev_cap) {
+            cudaFree(map->items_dev);   // waits for the device
+            map->items_dev = nullptr;
+            map->items_dev_cap = 0;
+            TSDF_CU(cudaMalloc(&map->items_dev, cnt * sizeof(ShiftItem)));
+            map->items_dev_cap = cnt;
+        }
+        std::memcpy(map->items_host, items.data(), cnt * sizeof(ShiftItem));
+        TSDF_CU(cudaMemcpyAsync(map->items_dev, map->items_host, cnt * sizeof(ShiftItem), cudaMemcpyHostToDevice, s));
+        TSDF_CU(cudaEventRecord(map->items_event, s));
+        map->items_event_pending = true;
+        cudaEvent_t e0 = prof_mark(map, s);
+        TSDF_CU(launch_shift(map->dev.grid, map->items_dev, (int)cnt, (uint32_t)map->p.dims[0],
+                             (uint32_t)map->p.dims[1], s));
+        prof_push(map, kShift, e0, prof_mark(map, s));
+    }
+    for (int a = 0; a < 3; ++a) map->origin[a] = new_origin[a];
+    return TSDF_OK;
+}
+
+int tsdf_read(tsdf_map* map, const int64_t lo[3], const int64_t hi[3], int16_t* value_host, int16_t* weight_host,
+              void* stream) {
+    if (!map || !lo || !hi) return TSDF_ERR_INVALID;
+    uint32_t box[3];
+    if (!box_inside(map, lo, hi, box)) return TSDF_ERR_INVALID;
+    const size_t total = (size_t)box[0] * box[1] * box[2];
+    if (total == 0 || (!value_host && !weight_host)) return TSDF_OK;
+    DeviceScope ds(map->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int16_t* tmp = nullptr;
+    TSDF_CU(cudaMallocAsync(&tmp, 2 * total * sizeof(int16_t), s));
+    const long long l[3] = {lo[0], lo[1], lo[2]};
+    cudaError_t e = launch_read_box(map->dev.grid, l, box, (uint32_t)map->p.dims[0], (uint32_t)map->p.dims[1],
+                                    (uint32_t)map->p.dims[2], tmp, tmp + total, s);
+    if (e == cudaSuccess && value_host)
+        e = cudaMemcpyAsync(value_host, tmp, total * sizeof(int16_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && weight_host)
+        e = cudaMemcpyAsync(weight_host, tmp + total, total * sizeof(int16_t), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(tmp, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return TSDF_OK;
+}
+
+int tsdf_write(tsdf_map* map, const int64_t lo[3], const int64_t hi[3], const int16_t* value_host,
+               const int16_t* weight_host, void* stream) {
+    if (!map || !lo || !hi || !value_host || !weight_host) return TSDF_ERR_INVALID;
+    uint32_t box[3];
+    if (!box_inside(map, lo, hi, box)) return TSDF_ERR_INVALID;
+    const size_t total = (size_t)box[0] * box[1] * box[2];
+    for (size_t i = 0; i < total; ++i)
+        if (weight_host[i] < 0 || weight_host[i] > map->p.w_max) return TSDF_ERR_INVALID;
+    if (total == 0) return TSDF_OK;
+    DeviceScope ds(map->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int16_t* tmp = nullptr;
+    TSDF_CU(cudaMallocAsync(&tmp, 2 * total * sizeof(int16_t), s));
+    cudaError_t e = cudaMemcpyAsync(tmp, value_host, total * sizeof(int16_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tmp + total, weight_host, total * sizeof(int16_t), cudaMemcpyHostToDevice, s);
+    const long long l[3] = {lo[0], lo[1], lo[2]};
+    if (e == cudaSuccess)
+        e = launch_write_box(map->dev.grid, l, box, (uint32_t)map->p.dims[0], (uint32_t)map->p.dims[1],
+                             (uint32_t)map->p.dims[2], tmp, tmp + total, s);
+    cudaFreeAsync(tmp, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return TSDF_OK;
+}
+
+int tsdf_stats(tsdf_map* map, tsdf_scan_stats* out, void* stream) {
+    if (!map || !out) return TSDF_ERR_INVALID;
+    DeviceScope ds(map->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    long long last[3] = {0, 0, 0};   // last_valid, last_hits, last_touched are contiguous
+    TSDF_CU(cudaMemcpyAsync(last, &map->dev.ctr->last_valid, sizeof(last), cudaMemcpyDeviceToHost, s));
+    TSDF_CU(cudaStreamSynchronize(s));
+    out->valid_rays = last[0];
+    out->hits = last[1];
+    out->touched = last[2];
+    return TSDF_OK;
+}
+
+int tsdf_profile_enable(tsdf_map* map, int32_t enable) {
+    if (!map) return TSDF_ERR_INVALID;
+    DeviceScope ds(map->device);
+    prof_drain(map);
+    map->prof = enable != 0;
+    for (int k = 0; k < kNumKernels; ++k) {
+        map->prof_launches[k] = 0;
+        map->prof_ms[k] = 0.0;
+    }
+    return TSDF_OK;
+}
+
+int tsdf_profile_read(tsdf_map* map, tsdf_kernel_time* out, int32_t capacity, int32_t* count) {
+    if (!map || !count || capacity < 0 || (capacity > 0 && !out)) return TSDF_ERR_INVALID;
+    DeviceScope ds(map->device);
+    int rc = prof_drain(map);
+    if (rc != TSDF_OK) return rc;
+    int32_t c = 0;
+    for (int k = 0; k < kNumKernels; ++k) {
+        if (map->prof_launches[k] == 0) continue;
+        if (c < capacity) {
+            std::memset(out[c].name, 0, sizeof(out[c].name));
+            std::strncpy(out[c].name, kKernelNames[k], sizeof(out[c].name) - 1);
+            out[c].launches = map->prof_launches[k];
+            out[c].total_ms = map->prof_ms[k];
+        }
+        ++c;
+    }
+    *count = c;
+    return TSDF_OK;
+}
+
+int tsdf_get_origin(const tsdf_map* map, int64_t out[3]) {
+    if (!map || !out) return TSDF_ERR_INVALID;
+    for (int a = 0; a < 3; ++a) out[a] = map->origin[a];
+    return TSDF_OK;
+}
+
+int tsdf_grid_device_ptr(const tsdf_map* map, void** out) {
+    if (!map || !out) return TSDF_ERR_INVALID;
+    *out = map->dev.grid;
+    return TSDF_OK;
+}
+
+const char* tsdf_error_string(int code) {
+    switch (code) {
+        case TSDF_OK: return "ok";
+        case TSDF_ERR_INVALID: return "invalid argument";
+        case TSDF_ERR_OOM: return "out of memory";
+        case TSDF_ERR_CUDA: return "CUDA error";
+        case TSDF_ERR_TIMEOUT: return "device wait timed out";
+        case TSDF_ERR_ADMISSION: return "device-memory budget exceeded";
+        case TSDF_ERR_BUSY: return "resource busy";
+        default: return "unknown error";
+    }
+}
+
+int tsdf_last_cuda_error(void) { return g_last_cuda_error; }
+
+}  // extern "C"

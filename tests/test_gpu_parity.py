@@ -1,0 +1,286 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle.
+
+Every comparison is bit-exact on the whole value + weight window (integer
+results; the float geometry is evaluated in the same IEEE order on both
+sides), plus equality of the per-scan counters (valid rays, in-window
+contributions, touched voxels).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_05766_gb300 import synth
+from helpers import assert_same, run_gpu, run_oracle, workload_steps
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2310_05766_gb300 import binding
+    binding.lib()
+    yield
+
+
+def both(params, steps, prefill=None, host=False, label=""):
+    g = run_gpu(params, steps, torch, prefill=prefill, host=host)
+    o = run_oracle(params, steps, prefill=prefill)
+    assert_same(g, o, label)
+    return g, o
+
+
+# ---------------------------------------------------------------- box room, one scan
+
+@pytest.mark.parametrize("reduce", [0, 1])
+def test_room_scan_exact(reduce):
+    w = synth.workload_room(reduce=reduce)
+    g, o = both(w.params, workload_steps(w), label=f"room reduce={reduce}")
+    assert g[2][0]["hits"] > 300000 and g[2][0]["valid_rays"] == 5760
+
+
+def test_room_scan_into_prefilled_map():
+    w = synth.workload_room()
+    rng = np.random.default_rng(1)
+    d = w.params["dims"]
+    v0 = rng.integers(-32767, 32768, size=(d[2], d[1], d[0])).astype(np.int16)
+    w0 = rng.integers(0, w.params["w_max"] + 1, size=v0.shape).astype(np.int16)
+    steps = workload_steps(w) + [("scan", w.scans[0], w.poses[0])]
+    both(w.params, steps, prefill=(v0, w0), label="prefilled")
+
+
+def test_room_host_points_path():
+    w = synth.workload_room()
+    both(w.params, workload_steps(w), host=True, label="host points")
+
+
+def test_point_order_does_not_matter():
+    w = synth.workload_room()
+    perm = np.random.default_rng(2).permutation(w.scans[0].shape[0])
+    a = run_gpu(w.params, [("scan", w.scans[0], w.poses[0])], torch)
+    b = run_gpu(w.params, [("scan", w.scans[0][perm], w.poses[0])], torch)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2]
+
+
+# ---------------------------------------------------------------- random small cases
+
+def _rand_case(seed):
+    rng = np.random.default_rng(1000 + seed)
+    dims = tuple(int(x) for x in rng.choice([8, 16, 32, 64], size=3))
+    vs = float(rng.choice([0.05, 0.0625, 0.08, 0.1]))
+    tau = float(vs * rng.uniform(1.0, 5.0))
+    origin = tuple(int(8 * rng.integers(-8, 4)) for _ in range(3))
+    dz = float(rng.choice([0.0, 0.01, 0.05, 0.2]))
+    reduce = int(rng.integers(0, 2))
+    w_max = int(rng.integers(1, 40))
+    p = synth.params_dict(dims, vs, tau, w_max, dz, 0.05, 6.0, reduce, origin)
+    centre = np.array([(origin[a] + dims[a] / 2) * vs for a in range(3)])
+    steps = []
+    cur = origin
+    for s in range(int(rng.integers(1, 5))):
+        n = int(rng.choice([1, 31, 33, 255, 257, 1000, 3001]))
+        pts = np.zeros((n, 4), np.float32)
+        d = rng.normal(size=(n, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        pts[:, :3] = d * rng.uniform(0.02, 2.5, (n, 1))
+        if n > 4:
+            pts[rng.integers(0, n, n // 8), rng.integers(0, 3)] = np.nan
+        R = synth.rot_zyx(*rng.uniform(-math.pi, math.pi, 3))
+        t = centre + rng.uniform(-0.5, 0.5, 3)
+        steps.append(("scan", pts, synth.pose12(R, t)))
+        if rng.uniform() < 0.5:
+            cur = tuple(int(cur[a] + 8 * rng.integers(-2, 3)) for a in range(3))
+            steps.append(("shift", cur))
+    return p, steps
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_small_exact(seed):
+    p, steps = _rand_case(seed)
+    both(p, steps, label=f"random seed {seed}")
+
+
+# ---------------------------------------------------------------- edge cases
+
+def _edge_params(**kw):
+    base = synth.params_dict((32, 32, 32), 0.1, 0.3, 64, 0.05, 0.5, 2.0, 0, (-16, -16, -16))
+    base.update(kw)
+    return base
+
+
+def test_empty_scan_and_all_invalid():
+    p = _edge_params()
+    pose = synth.pose12(np.eye(3), np.zeros(3))
+    nan = np.full((100, 4), np.nan, np.float32)
+    zeros = np.zeros((64, 4), np.float32)
+    far = np.tile(np.array([[5.0, 0, 0, 0]], np.float32), (40, 1))   # beyond r_max
+    g, o = both(p, [("scan", np.zeros((0, 4), np.float32), pose), ("scan", nan, pose), ("scan", zeros, pose),
+                    ("scan", far, pose)], label="empty/invalid")
+    assert all(s == dict(valid_rays=0, hits=0, touched=0) for s in g[2])
+    assert not g[0].any() and not g[1].any()
+
+
+def test_range_limits_and_degenerate_fill():
+    p = _edge_params()
+    pose = synth.pose12(np.eye(3), np.zeros(3))
+    pts = np.array([[0.5, 0, 0, 0], [2.0, 0, 0, 0], [0, 0, 1.5, 0], [0, 0, -1.2, 0], [0.49999, 0, 0, 0],
+                    [2.0001, 0, 0, 0], [1.0, 1.0, 0.5, 0]], np.float32)
+    g, o = both(p, [("scan", pts, pose)], label="limits")
+    assert g[2][0]["valid_rays"] == 5
+
+
+def test_fill_disabled_and_tiny_window():
+    p = _edge_params(dims=(8, 8, 8), origin=(-8, 0, -8), delta_z=0.0)
+    rng = np.random.default_rng(3)
+    pts = np.zeros((500, 4), np.float32)
+    pts[:, :3] = rng.uniform(-1.2, 1.2, (500, 3))
+    both(p, [("scan", pts, synth.pose12(synth.rot_zyx(0.3, 0.2, 0.1), np.array([0.0, 0.4, 0.0])))], label="tiny")
+
+
+def test_weight_cap_reached():
+    p = _edge_params(w_max=3)
+    pose = synth.pose12(np.eye(3), np.zeros(3))
+    pts = np.tile(np.array([[1.03, 0.21, 0.05, 0]], np.float32), (20, 1))
+    g, o = both(p, [("scan", pts, pose)] * 3, label="cap")
+    assert g[1].max() == 3
+
+
+def test_many_hits_on_one_voxel():
+    """Hundreds of rays through the same voxels: heavy intra-warp and inter-warp merging."""
+    p = _edge_params(delta_z=0.3)
+    pose = synth.pose12(np.eye(3), np.array([0.01, 0.02, 0.03]))
+    rng = np.random.default_rng(5)
+    pts = np.tile(np.array([[1.2, 0.3, 0.1, 0]], np.float32), (4096, 1))
+    pts[:, :3] += rng.normal(scale=0.002, size=(4096, 3)).astype(np.float32)
+    for reduce in (0, 1):
+        both(dict(p, reduce=reduce), [("scan", pts, pose)], label=f"dense reduce={reduce}")
+
+
+# ---------------------------------------------------------------- shift
+
+def test_shift_sequence_exact():
+    w = synth.workload_room()
+    p = dict(w.params, dims=(128, 128, 64), origin=(-64, -64, -32))
+    o = p["origin"]
+    steps = [("scan", w.scans[0], w.poses[0])]
+    for d in [(8, 0, 0), (8, -16, 0), (0, 0, 8), (-64, 40, -8), (512, 0, 0), (0, 0, 0), (24, 24, 8)]:
+        steps.append(("shift", (o[0] + d[0], o[1] + d[1], o[2] + d[2])))
+        steps.append(("scan", w.scans[0], w.poses[0]))
+    both(p, steps, label="shift sequence")
+
+
+def test_shift_unshift_identity_gpu():
+    from paper_2310_05766_gb300 import binding as b
+    w = synth.workload_room()
+    m = b.TsdfMap(w.params)
+    try:
+        m.integrate(torch.from_numpy(w.scans[0]).cuda(), w.poses[0])
+        v0, w0 = m.read()
+        o = w.params["origin"]
+        m.shift((o[0] + 40, o[1] - 16, o[2] + 8))
+        m.shift((o[0] + 4096, o[1], o[2]))
+        m.shift(o)
+        v1, w1 = m.read()
+        assert np.array_equal(v0, v1) and np.array_equal(w0, w1)
+    finally:
+        m.close()
+
+
+# ---------------------------------------------------------------- full-size workloads
+
+def test_outdoor_sequence_prefix_exact():
+    """OS1-128-shaped outdoor sequence at full size (512 x 512 x 128 at 0.064 m):
+    the first 12 scans, including the first 1 m re-centring shift."""
+    w = synth.workload_outdoor(n_scans=12)
+    steps = workload_steps(w)
+    assert any(s[0] == "shift" for s in steps)
+    g, o = both(w.params, steps, label="outdoor prefix")
+    assert min(s["hits"] for s in g[2]) > 1_000_000
+
+
+def test_corridor_prefix_exact():
+    """High-resolution corridor at full size (1024 x 1024 x 256 at 0.02 m): two
+    scans, a 24-voxel shift along x, one more scan."""
+    w = synth.workload_corridor(n_scans=3)
+    o = w.params["origin"]
+    steps = [("scan", w.scans[0], w.poses[0]), ("scan", w.scans[1], w.poses[1]),
+             ("shift", (o[0] + 24, o[1], o[2])), ("scan", w.scans[2], w.poses[2])]
+    g, o2 = both(w.params, steps, label="corridor prefix")
+    assert min(s["hits"] for s in g[2]) > 3_000_000
+
+
+def test_maximum_window_size():
+    """A 2048 x 2048 x 512 window (2^31 voxels, the largest accepted): the box-room
+    scan gives, inside the room's 256 x 256 x 64 sub-box, exactly the oracle's
+    result for a window of that sub-box."""
+    from paper_2310_05766_gb300 import binding as b
+    w = synth.workload_room()
+    pbig = dict(w.params, dims=(2048, 2048, 512), origin=(-1024, -1024, -256))
+    m = b.TsdfMap(pbig)
+    try:
+        m.integrate(torch.from_numpy(w.scans[0]).cuda(), w.poses[0])
+        lo = w.params["origin"]
+        hi = tuple(lo[a] + w.params["dims"][a] for a in range(3))
+        vg, wg = m.read(lo, hi)
+    finally:
+        m.close()
+    om = oracle.OracleMap(w.params)
+    om.integrate(w.scans[0], w.poses[0])
+    vo, wo = om.read()
+    assert np.array_equal(vg, vo) and np.array_equal(wg, wo)
+
+
+# ---------------------------------------------------------------- argument errors on the GPU path
+
+def test_invalid_arguments_leave_map_unchanged():
+    from paper_2310_05766_gb300 import binding as b
+    w = synth.workload_room()
+    m = b.TsdfMap(w.params)
+    try:
+        pts = torch.from_numpy(w.scans[0]).cuda()
+        m.integrate(pts, w.poses[0])
+        v0, w0 = m.read()
+        raw = pts.data_ptr()
+        with pytest.raises(b.TsdfError) as e:
+            b.tsdf_integrate(m.handle, raw + 4, 10, w.poses[0])   # misaligned
+        assert e.value.code == b.TSDF_ERR_INVALID
+        with pytest.raises(b.TsdfError):
+            b.tsdf_integrate(m.handle, raw, b.TSDF_MAX_POINTS + 1, w.poses[0])
+        bad_pose = w.poses[0].copy()
+        bad_pose[3] = np.nan
+        with pytest.raises(b.TsdfError):
+            b.tsdf_integrate(m.handle, raw, 10, bad_pose)
+        with pytest.raises(b.TsdfError):
+            m.shift((3, 0, 0))
+        with pytest.raises(b.TsdfError):
+            m.read((0, 0, 0), (10**6, 1, 1))
+        v1, w1 = m.read()
+        assert np.array_equal(v0, v1) and np.array_equal(w0, w1)
+    finally:
+        m.close()
+
+
+def test_write_read_roundtrip():
+    from paper_2310_05766_gb300 import binding as b
+    p = _edge_params()
+    rng = np.random.default_rng(7)
+    v = rng.integers(-32767, 32768, size=(32, 32, 32)).astype(np.int16)
+    wt = rng.integers(0, 65, size=(32, 32, 32)).astype(np.int16)
+    m = b.TsdfMap(p)
+    try:
+        m.write(v, wt)
+        v1, w1 = m.read()
+        assert np.array_equal(v, v1) and np.array_equal(wt, w1)
+        lo = (-10, -3, 0)
+        hi = (5, 7, 9)
+        vs, ws = m.read(lo, hi)
+        o = p["origin"]
+        assert np.array_equal(vs, v[lo[2] - o[2]:hi[2] - o[2], lo[1] - o[1]:hi[1] - o[1], lo[0] - o[0]:hi[0] - o[0]])
+        bad = wt.copy()
+        bad[0, 0, 0] = 65
+        with pytest.raises(b.TsdfError):
+            m.write(v, bad)
+    finally:
+        m.close()
