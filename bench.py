@@ -165,6 +165,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
 
     m = b.TsdfMap(p)
     h = m.handle
+    for opt, val in ((b.TSDF_OPT_WARP_MERGE, args.merge), (b.TSDF_OPT_STEPS_PER_THREAD, args.kpt),
+                     (b.TSDF_OPT_PDL, args.pdl)):
+        if val is not None:
+            b.tsdf_set_option(h, opt, val)
     cur = tuple(p["origin"])
 
     def step(i, host=False):
@@ -369,6 +373,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--merge", type=int, default=None, help="tuning: warp match-merge (0/1)")
+    ap.add_argument("--kpt", type=int, default=None, help="tuning: march steps per contribution thread (1/2/4)")
+    ap.add_argument("--pdl", type=int, default=None, help="tuning: programmatic dependent launch (0/1)")
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=120.0, help="seconds of oracle time for --impl reference")
     args = ap.parse_args()

@@ -69,7 +69,7 @@ typedef struct tsdf_params {
     float   r_max;        /* points with range > r_max are skipped, r_min <= r_max <= 1e5 */
     int32_t reduce;       /* TSDF_REDUCE_WSUM or TSDF_REDUCE_MIN_ABS */
     int32_t reserved;     /* must be 0 */
-    int64_t origin[3];    /* initial window origin in global voxel coordinates; multiples of 8, |origin| <= 2^40 */
+    int64_t origin[3];    /* initial window origin in global voxel coordinates; multiples of 8, |origin| <= 2^23 */
 } tsdf_params;
 
 /* Counters of the most recent integrate call on a map. */
@@ -84,8 +84,9 @@ typedef struct tsdf_map tsdf_map;   /* opaque; owns all of its device memory */
 /* Create a map on the current CUDA device. The window starts at
  * params->origin with every voxel (0, 0). Allocates the voxel grid (4 bytes
  * per voxel: int16 value, int16 weight), the per-scan accumulator (8 bytes
- * per voxel, kept all-zero between calls) and the touched list (4 bytes per
- * voxel). Synchronous. On success *out receives the handle, which the caller
+ * per voxel, kept all-zero between calls) and a touched-brick flag array and list
+ * (bricks of 8^3 voxels). Per-ray buffers (32 bytes per point) are allocated
+ * by the first integrate call that needs them. Synchronous. On success *out receives the handle, which the caller
  * releases with tsdf_map_destroy. Errors: INVALID, OOM, CUDA. */
 int tsdf_map_create(const tsdf_params* params, tsdf_map** out);
 
@@ -106,7 +107,8 @@ int tsdf_map_destroy(tsdf_map* map);
  *                transform [R | t]; R's third column is the direction
  *                orthogonal to the scan lines. Copied at call time.
  * The result is bit-identical to a serial evaluation in any launch order.
- * Errors: INVALID, CUDA. */
+ * When n exceeds every earlier n of this map, the per-ray buffers grow first
+ * (a synchronous reallocation). Errors: INVALID, OOM, CUDA. */
 int tsdf_integrate(tsdf_map* map, const float* points_dev, int64_t n, const float pose[12], void* stream);
 
 /* As tsdf_integrate, but points_host is a HOST pointer (pinned or pageable)
@@ -117,7 +119,7 @@ int tsdf_integrate(tsdf_map* map, const float* points_dev, int64_t n, const floa
 int tsdf_integrate_host(tsdf_map* map, const float* points_host, int64_t n, const float pose[12], void* stream);
 
 /* Move the window to new_origin (global voxel coordinates, multiples of 8,
- * |new_origin| <= 2^40). Voxels inside both windows keep their values (ring
+ * |new_origin| <= 2^23). Voxels inside both windows keep their values (ring
  * addressing: no data moves). Chunks of 8^3 voxels that leave the window are
  * written to the map's device-resident global store; chunks that enter are
  * read back from the store, or set to (0, 0) if never stored. Asynchronous
@@ -142,18 +144,34 @@ int tsdf_write(tsdf_map* map, const int64_t lo[3], const int64_t hi[3], const in
  * Synchronises `stream`. Errors: INVALID, CUDA. */
 int tsdf_stats(tsdf_map* map, tsdf_scan_stats* out, void* stream);
 
+/* Tuning options (no effect on results, which are bit-identical for every
+ * setting; only on speed). */
+#define TSDF_OPT_WARP_MERGE  1  /* 1: lanes of a warp that hit the same voxel in the same step are merged
+                                   (match.any + redux) before one accumulator atomic; 0 (default): every
+                                   contribution issues its own atomic */
+#define TSDF_OPT_STEPS_PER_THREAD 2  /* march steps k handled by one contribution thread: 1, 2 (default) or 4 */
+#define TSDF_OPT_PDL         3  /* 1 (default): the kernels of one integrate call use programmatic dependent
+                                   launch, so each may be scheduled while the previous one drains; 0: plain
+                                   stream order */
+
+/* Set a tuning option of a map; takes effect for later calls. Host-side
+ * state only. Errors: INVALID (unknown option or value). */
+int tsdf_set_option(tsdf_map* map, int32_t option, int64_t value);
+
 /* Current window origin (host-side state; no synchronisation). */
 int tsdf_get_origin(const tsdf_map* map, int64_t out[3]);
 
 /* Device pointer of the voxel grid: uint32 words, value in the low 16 bits,
- * weight in the high 16 bits, ring-addressed: global voxel g lives at
- * ((g.z & (Z-1)) * Y + (g.y & (Y-1))) * X + (g.x & (X-1)). Valid until destroy. */
+ * weight in the high 16 bits, bricked and ring addressed: global voxel g
+ * lives in brick b = ((bz * CY) + by) * CX + bx with (bx, by, bz) =
+ * (g >> 3) mod (dims / 8) and (CX, CY) = dims.xy / 8, at word
+ * b * 512 + ((g.z & 7) * 8 + (g.y & 7)) * 8 + (g.x & 7). Valid until destroy. */
 int tsdf_grid_device_ptr(const tsdf_map* map, void** out);
 
 /* Per-kernel device time of this map's launches, measured with CUDA events
  * recorded on the launching stream around each kernel while profiling is on. */
 typedef struct tsdf_kernel_time {
-    char    name[24];     /* "contrib", "apply" or "shift" */
+    char    name[24];     /* "rays", "contrib", "apply" (brick compaction, update, counters) or "shift" */
     int64_t launches;     /* kernel launches since profiling was enabled */
     double  total_ms;     /* summed event-to-event device time */
 } tsdf_kernel_time;

@@ -24,6 +24,9 @@ TSDF_ERR_BUSY = -6
 TSDF_REDUCE_WSUM = 0
 TSDF_REDUCE_MIN_ABS = 1
 TSDF_MAX_POINTS = 1 << 22
+TSDF_OPT_WARP_MERGE = 1
+TSDF_OPT_STEPS_PER_THREAD = 2
+TSDF_OPT_PDL = 3
 
 
 class TsdfError(RuntimeError):
@@ -78,6 +81,7 @@ def lib():
     L.tsdf_stats.argtypes = [vp, P(tsdf_scan_stats), vp]
     L.tsdf_get_origin.argtypes = [vp, P(i64)]
     L.tsdf_grid_device_ptr.argtypes = [vp, P(vp)]
+    L.tsdf_set_option.argtypes = [vp, ctypes.c_int32, ctypes.c_int64]
     L.tsdf_profile_enable.argtypes = [vp, ctypes.c_int32]
     L.tsdf_profile_read.argtypes = [vp, P(tsdf_kernel_time), ctypes.c_int32, P(ctypes.c_int32)]
     L.tsdf_error_string.argtypes = [i32]
@@ -85,7 +89,7 @@ def lib():
     L.tsdf_last_cuda_error.argtypes = []
     for name in ("tsdf_map_create", "tsdf_map_destroy", "tsdf_integrate", "tsdf_integrate_host", "tsdf_shift",
                  "tsdf_read", "tsdf_write", "tsdf_stats", "tsdf_get_origin", "tsdf_grid_device_ptr",
-                 "tsdf_last_cuda_error", "tsdf_profile_enable", "tsdf_profile_read"):
+                 "tsdf_last_cuda_error", "tsdf_profile_enable", "tsdf_profile_read", "tsdf_set_option"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -209,6 +213,10 @@ def tsdf_grid_device_ptr(handle: int) -> int:
     p = ctypes.c_void_p()
     _check(lib().tsdf_grid_device_ptr(handle, ctypes.byref(p)), "tsdf_grid_device_ptr")
     return p.value
+
+
+def tsdf_set_option(handle: int, option: int, value: int) -> None:
+    _check(lib().tsdf_set_option(handle, int(option), int(value)), "tsdf_set_option")
 
 
 def tsdf_profile_enable(handle: int, enable: bool = True) -> None:

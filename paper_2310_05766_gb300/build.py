@@ -51,17 +51,23 @@ def stale() -> bool:
     return any(os.path.getmtime(d) > t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    """Compile and link the library if needed; returns its path."""
+def build(force: bool = False, verbose: bool = False, extra_flags=None, out: str | None = None) -> str:
+    """Compile and link the library if needed; returns its path.
+
+    `extra_flags` are appended to every nvcc compile; `out` names another
+    output file (used for build variants), which is always rebuilt.
+    """
     with _lock:
-        if not force and not stale():
+        target = out or LIB
+        if out is None and not force and not stale():
             return LIB
-        os.makedirs(BUILD, exist_ok=True)
+        bdir = BUILD if out is None else os.path.join(BUILD, os.path.basename(out) + ".objs")
+        os.makedirs(bdir, exist_ok=True)
         cc = nvcc()
         flags = NVCC_FLAGS + list(extra_flags or [])
 
         def compile_one(src):
-            obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+            obj = os.path.join(bdir, os.path.basename(src) + ".o")
             cmd = [cc, *ARCH, *flags, "-c", src, "-o", obj]
             r = subprocess.run(cmd, capture_output=True, text=True)
             if r.returncode != 0:
@@ -73,13 +79,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         srcs = sources()
         with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
             objs = list(ex.map(compile_one, srcs))
-        tmp = LIB + f".tmp{os.getpid()}"
+        tmp = target + f".tmp{os.getpid()}"
         cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fPIC", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-        return LIB
+        os.replace(tmp, target)
+        return target
 
 
 if __name__ == "__main__":

@@ -4,6 +4,7 @@
 // beyond the per-map constants 1/voxel, QMAX/tau and K, derived once in
 // binary64 and rounded to binary32.
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -68,10 +69,10 @@ int log2u(uint32_t v) {
 }
 long long floordiv8(long long v) { return v >= 0 ? v / 8 : -((-v + 7) / 8); }
 
-const long long kOriginLimit = 1LL << 40;
+const long long kOriginLimit = 1LL << 23;   // window voxels stay below 2^24: exact as float
 
-enum KernelId { kContrib = 0, kApply = 1, kShift = 2, kNumKernels = 3 };
-const char* const kKernelNames[kNumKernels] = {"contrib", "apply", "shift"};
+enum KernelId { kRays = 0, kContrib = 1, kApply = 2, kShift = 3, kNumKernels = 4 };
+const char* const kKernelNames[kNumKernels] = {"rays", "contrib", "apply", "shift"};
 
 struct Pending {
     int kernel;
@@ -86,9 +87,11 @@ struct tsdf_map {
     int num_sms = 1;
     float inv_vs = 0.f, qs = 0.f;
     int K = 0;
-    uint32_t shx = 0, shxy = 0;
+    WindowGeom geom{};
     long long origin[3] = {0, 0, 0};
     size_t voxels = 0;
+    size_t bricks = 0;
+    size_t ray_cap = 0;
     MapDev dev{};
     // device-resident global store of 8^3 chunks
     std::unordered_map<ChunkKey, uint32_t, ChunkKeyHash> store_index;
@@ -103,12 +106,16 @@ struct tsdf_map {
     // staging for host-resident points
     float4* stage_dev = nullptr;
     size_t stage_cap = 0;
+    // tuning options
+    bool merge = false;             // warp match-merge before the accumulator atomics
+    int kpt = 2;                    // march steps per contribution thread (1, 2 or 4)
+    bool pdl = true;                // programmatic dependent launch between the scan's kernels
     // optional per-kernel event timing
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<Pending> pending;
-    int64_t prof_launches[kNumKernels] = {0, 0, 0};
-    double prof_ms[kNumKernels] = {0.0, 0.0, 0.0};
+    int64_t prof_launches[kNumKernels] = {0, 0, 0, 0};
+    double prof_ms[kNumKernels] = {0.0, 0.0, 0.0, 0.0};
 };
 
 namespace {
@@ -192,7 +199,10 @@ void free_map(tsdf_map* m) {
     for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
     cudaFree(m->dev.grid);
     cudaFree(m->dev.acc);
-    cudaFree(m->dev.touched);
+    cudaFree(m->dev.brick_flag);
+    cudaFree(m->dev.brick_list);
+    cudaFree(m->dev.ray_a);
+    cudaFree(m->dev.ray_b);
     cudaFree(m->dev.ctr);
     for (char* s : m->store_segments) cudaFree(s);
     cudaFree(m->items_dev);
@@ -252,17 +262,25 @@ int tsdf_map_create(const tsdf_params* params, tsdf_map** out) {
     m->inv_vs = (float)(1.0 / (double)params->voxel_size);
     m->qs = (float)((double)kQMax / (double)params->tau);
     m->K = (int)std::floor((double)params->tau / (double)params->voxel_size + 1e-9);
-    m->shx = (uint32_t)log2u((uint32_t)params->dims[0]);
-    m->shxy = m->shx + (uint32_t)log2u((uint32_t)params->dims[1]);
-    for (int a = 0; a < 3; ++a) m->origin[a] = params->origin[a];
+    for (int a = 0; a < 3; ++a) {
+        m->geom.dims[a] = (uint32_t)params->dims[a];
+        m->geom.cmask[a] = (uint32_t)params->dims[a] / 8u - 1u;
+        m->origin[a] = params->origin[a];
+    }
+    m->geom.lcx = (uint32_t)log2u((uint32_t)params->dims[0] / 8u);
+    m->geom.lcxy = m->geom.lcx + (uint32_t)log2u((uint32_t)params->dims[1] / 8u);
     m->voxels = (size_t)params->dims[0] * params->dims[1] * params->dims[2];
+    m->bricks = m->voxels / kBrickVoxels;
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&m->dev.grid, m->voxels * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&m->dev.acc, m->voxels * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&m->dev.touched, m->voxels * sizeof(uint32_t));
+    const size_t flag_bytes = (m->bricks + 3) / 4 * 4;
+    if (e == cudaSuccess) e = cudaMalloc(&m->dev.brick_flag, flag_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&m->dev.brick_list, m->bricks * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&m->dev.ctr, sizeof(MapCounters));
     if (e == cudaSuccess) e = cudaMemset(m->dev.grid, 0, m->voxels * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(m->dev.acc, 0, m->voxels * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(m->dev.brick_flag, 0, flag_bytes);
     if (e == cudaSuccess) e = cudaMemset(m->dev.ctr, 0, sizeof(MapCounters));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->items_event, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -282,8 +300,25 @@ int tsdf_map_destroy(tsdf_map* map) {
     return TSDF_OK;
 }
 
+static int ensure_rays(tsdf_map* map, int64_t n) {
+    if ((size_t)n <= map->ray_cap) return TSDF_OK;
+    // a previous scan may still read the old buffers: cudaFree waits for the device
+    cudaFree(map->dev.ray_a);
+    cudaFree(map->dev.ray_b);
+    map->dev.ray_a = map->dev.ray_b = nullptr;
+    map->ray_cap = 0;
+    size_t cap = 1024;
+    while (cap < (size_t)n) cap *= 2;
+    TSDF_CU(cudaMalloc(&map->dev.ray_a, cap * sizeof(float4)));
+    TSDF_CU(cudaMalloc(&map->dev.ray_b, cap * sizeof(float4)));
+    map->ray_cap = cap;
+    return TSDF_OK;
+}
+
 static int integrate_dev(tsdf_map* map, const float* points_dev, int64_t n, const float pose[12],
                          cudaStream_t s) {
+    int rc = ensure_rays(map, n);
+    if (rc != TSDF_OK) return rc;
     ScanArgs a{};
     a.pts = reinterpret_cast<const float4*>(points_dev);
     a.n = (int32_t)n;
@@ -300,24 +335,32 @@ static int integrate_dev(tsdf_map* map, const float* points_dev, int64_t n, cons
     a.rmin = map->p.r_min;
     a.rmax = map->p.r_max;
     a.fill = map->p.delta_z > 0.f ? 1 : 0;
-    a.reduce = map->p.reduce;
-    a.ox = map->origin[0];
-    a.oy = map->origin[1];
-    a.oz = map->origin[2];
-    a.dimx = (uint32_t)map->p.dims[0];
-    a.dimy = (uint32_t)map->p.dims[1];
-    a.dimz = (uint32_t)map->p.dims[2];
-    a.shx = map->shx;
-    a.shxy = map->shxy;
-    a.w_max = map->p.w_max;
+    for (int ax = 0; ax < 3; ++ax) {
+        const double lo = (double)map->origin[ax] * (double)map->p.voxel_size;
+        const double hi = (double)(map->origin[ax] + map->p.dims[ax]) * (double)map->p.voxel_size;
+        a.win_lo[ax] = std::nextafter((float)lo, -INFINITY);
+        a.win_hi[ax] = std::nextafter((float)hi, INFINITY);
+        a.fo[ax] = (float)map->origin[ax];
+        a.fe[ax] = (float)(map->origin[ax] + map->p.dims[ax]);
+        a.cmask[ax] = map->geom.cmask[ax];
+    }
+    a.lcx = map->geom.lcx;
+    a.lcxy = map->geom.lcxy;
+    const bool pdl = map->pdl;
     cudaEvent_t e0 = n > 0 ? prof_mark(map, s) : nullptr;
-    TSDF_CU(launch_contrib(a, map->dev, s));
+    TSDF_CU(launch_rays(a, map->dev, pdl, s));
     cudaEvent_t e1 = n > 0 ? prof_mark(map, s) : nullptr;
-    cudaEvent_t e2 = prof_mark(map, s);
-    TSDF_CU(launch_apply(map->dev, map->p.reduce, map->p.w_max, map->num_sms * 4, s));
-    cudaEvent_t e3 = prof_mark(map, s);
-    prof_push(map, kContrib, e0, e1);
-    prof_push(map, kApply, e2, e3);
+    cudaEvent_t e2 = n > 0 ? prof_mark(map, s) : nullptr;
+    TSDF_CU(launch_contrib(a, map->dev, map->p.reduce, map->merge, map->kpt, pdl, s));
+    cudaEvent_t e3 = n > 0 ? prof_mark(map, s) : nullptr;
+    cudaEvent_t e4 = prof_mark(map, s);
+    TSDF_CU(launch_compact(map->dev, (uint32_t)map->bricks, pdl, s));
+    TSDF_CU(launch_apply(map->dev, map->p.reduce, map->p.w_max, map->num_sms * 8, pdl, s));
+    TSDF_CU(launch_finish(map->dev, pdl, s));
+    cudaEvent_t e5 = prof_mark(map, s);
+    prof_push(map, kRays, e0, e1);
+    prof_push(map, kContrib, e2, e3);
+    prof_push(map, kApply, e4, e5);
     return TSDF_OK;
 }
 
@@ -386,7 +429,7 @@ int tsdf_shift(tsdf_map* map, const int64_t new_origin[3], void* stream) {
             for (long long sx = 0; sx < C[0]; ++sx) {
                 if (!row_changes && !chg[0][sx]) continue;
                 ShiftItem it{};
-                it.chunk_slot = (uint32_t)((sz * C[1] + sy) * C[0] + sx);
+                it.brick = (uint32_t)((sz * C[1] + sy) * C[0] + sx);
                 int rc = store_lookup(map, ChunkKey{oldc[0][sx], oldc[1][sy], oldc[2][sz]}, true, &it.out_ptr);
                 if (rc != TSDF_OK) return rc;
                 rc = store_lookup(map, ChunkKey{newc[0][sx], newc[1][sy], newc[2][sz]}, false, &it.in_ptr);
@@ -420,8 +463,7 @@ int tsdf_shift(tsdf_map* map, const int64_t new_origin[3], void* stream) {
         TSDF_CU(cudaEventRecord(map->items_event, s));
         map->items_event_pending = true;
         cudaEvent_t e0 = prof_mark(map, s);
-        TSDF_CU(launch_shift(map->dev.grid, map->items_dev, (int)cnt, (uint32_t)map->p.dims[0],
-                             (uint32_t)map->p.dims[1], s));
+        TSDF_CU(launch_shift(map->dev.grid, map->items_dev, (int)cnt, s));
         prof_push(map, kShift, e0, prof_mark(map, s));
     }
     for (int a = 0; a < 3; ++a) map->origin[a] = new_origin[a];
@@ -440,8 +482,7 @@ int tsdf_read(tsdf_map* map, const int64_t lo[3], const int64_t hi[3], int16_t* 
     int16_t* tmp = nullptr;
     TSDF_CU(cudaMallocAsync(&tmp, 2 * total * sizeof(int16_t), s));
     const long long l[3] = {lo[0], lo[1], lo[2]};
-    cudaError_t e = launch_read_box(map->dev.grid, l, box, (uint32_t)map->p.dims[0], (uint32_t)map->p.dims[1],
-                                    (uint32_t)map->p.dims[2], tmp, tmp + total, s);
+    cudaError_t e = launch_read_box(map->dev.grid, l, box, map->geom, tmp, tmp + total, s);
     if (e == cudaSuccess && value_host)
         e = cudaMemcpyAsync(value_host, tmp, total * sizeof(int16_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && weight_host)
@@ -470,8 +511,7 @@ int tsdf_write(tsdf_map* map, const int64_t lo[3], const int64_t hi[3], const in
         e = cudaMemcpyAsync(tmp + total, weight_host, total * sizeof(int16_t), cudaMemcpyHostToDevice, s);
     const long long l[3] = {lo[0], lo[1], lo[2]};
     if (e == cudaSuccess)
-        e = launch_write_box(map->dev.grid, l, box, (uint32_t)map->p.dims[0], (uint32_t)map->p.dims[1],
-                             (uint32_t)map->p.dims[2], tmp, tmp + total, s);
+        e = launch_write_box(map->dev.grid, l, box, map->geom, tmp, tmp + total, s);
     cudaFreeAsync(tmp, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -483,6 +523,7 @@ int tsdf_stats(tsdf_map* map, tsdf_scan_stats* out, void* stream) {
     DeviceScope ds(map->device);
     cudaStream_t s = (cudaStream_t)stream;
     long long last[3] = {0, 0, 0};   // last_valid, last_hits, last_touched are contiguous
+    static_assert(offsetof(MapCounters, last_touched) == offsetof(MapCounters, last_valid) + 16, "layout");
     TSDF_CU(cudaMemcpyAsync(last, &map->dev.ctr->last_valid, sizeof(last), cudaMemcpyDeviceToHost, s));
     TSDF_CU(cudaStreamSynchronize(s));
     out->valid_rays = last[0];
@@ -521,6 +562,25 @@ int tsdf_profile_read(tsdf_map* map, tsdf_kernel_time* out, int32_t capacity, in
     }
     *count = c;
     return TSDF_OK;
+}
+
+int tsdf_set_option(tsdf_map* map, int32_t option, int64_t value) {
+    if (!map) return TSDF_ERR_INVALID;
+    switch (option) {
+        case TSDF_OPT_WARP_MERGE:
+            if (value != 0 && value != 1) return TSDF_ERR_INVALID;
+            map->merge = value != 0;
+            return TSDF_OK;
+        case TSDF_OPT_STEPS_PER_THREAD:
+            if (value != 1 && value != 2 && value != 4) return TSDF_ERR_INVALID;
+            map->kpt = (int)value;
+            return TSDF_OK;
+        case TSDF_OPT_PDL:
+            if (value != 0 && value != 1) return TSDF_ERR_INVALID;
+            map->pdl = value != 0;
+            return TSDF_OK;
+        default: return TSDF_ERR_INVALID;
+    }
 }
 
 int tsdf_get_origin(const tsdf_map* map, int64_t out[3]) {

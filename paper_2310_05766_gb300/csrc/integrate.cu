@@ -1,50 +1,86 @@
 // Per-scan TSDF integration kernels (FeatSense, Section "TSDF Map Generation").
 //
-// contrib: one thread per point. The thread transforms its point by the pose,
-//   sets up the ray (range, unit direction, unit interpolation direction
-//   int = d x (d x up), Eq. 3 / Eq. 4) and walks the steps k = -K..K and the
-//   fill samples j = -J..J in warp lock-step. Every sample that lands in the
-//   window yields (slot, q) with q the int16 code of the truncated projective
-//   distance of the voxel centre. Lanes of a warp that hit the same voxel in
-//   the same iteration are merged with match.any + redux.sync, and one lane
-//   per distinct voxel issues a single 64-bit atomic into the per-scan
-//   accumulator:
-//     WSUM    : acc += (count << 40) + sum(q)      (two's-complement packing;
-//               exact while count < 2^24 and |sum| < 2^39)
+// rays (K-A): one thread per point, coalesced float4 loads. Transforms the
+//   point by the pose, sets up the ray (range r, unit direction d, unit
+//   interpolation direction int = d x (d x up) with up the sensor z axis) and
+//   appends it (two float4) to a compacted list of live rays: a ray whose whole
+//   march (+-tau around the hit, widened by the fill height of Eq. 4 and a
+//   safety margin) stays outside the window box is dropped, since none of its
+//   samples could land in the window. Order is kept within a CTA, so
+//   neighbouring rays stay neighbours.
+// contrib (K-B): one thread per (live ray, group of KPT steps k), k = -K..K;
+//   lanes of a warp are 32 consecutive live rays. For each of its steps the
+//   thread walks the fill samples j = -J..J (Eq. 3 / Eq. 4) in warp lock-step.
+//   A sample inside the window yields (voxel, q), q the int16 code of the
+//   truncated projective distance of the voxel centre, and issues one
+//   fire-and-forget 64-bit reduction into the per-scan accumulator:
+//     WSUM    : acc += (count << 40) + sum(q)   (two's-complement packing; exact
+//               while count < 2^24 and |sum| < 2^39)
 //     MIN_ABS : acc = max(acc, 65536 - key), key = (|q| << 1) | (q < 0)
-//   so acc == 0 means "untouched". The lane that turned an accumulator from 0
-//   to non-zero appends the slot to the touched list (one list atomic per warp
-//   iteration). Integer accumulation makes the result independent of the
-//   order in which atomics land.
-// apply: one thread per touched voxel, grid-stride. Eq. 1 in exact integers
-//   with one rounding (half away from zero), Eq. 2 with the weight cap, and
-//   the accumulator is reset to 0. The last CTA to finish publishes the scan
-//   counters and clears the per-scan state.
+//   so acc == 0 means "untouched". Optionally (MERGE) lanes that hit the same
+//   voxel in the same iteration are first combined with match.any +
+//   redux.sync so that one lane per distinct voxel issues the reduction. The
+//   issuing lane marks the voxel's brick in a byte-per-brick flag array with
+//   a plain store (idempotent, nothing to wait for). Integer accumulation
+//   makes the result independent of the order of the atomics.
+// compact: turns the brick flags into a list of touched bricks (4 flags per
+//   thread, one list atomic per warp) and clears the flags.
+// apply (K-C): one warp per listed brick (grid-stride over the list), 16
+//   consecutive voxels per lane (64 B of grid, 128 B of accumulator): Eq. 1 in
+//   exact integers with one rounding (half away from zero) and Eq. 2 with the
+//   weight cap for every voxel whose accumulator is non-zero; the accumulator
+//   is reset. Touched voxels are counted, and in WSUM mode the contributions
+//   too (the sum of the decoded weights).
+// finish: one warp sums the per-scan counters into the published ones and
+//   clears the per-scan state.
+//
+// Kernels may be launched with programmatic stream serialisation: each may be
+// scheduled while its predecessor drains, and waits (griddepcontrol.wait) for
+// the predecessor's completion before touching its results.
 //
 // Every float operation on the geometry path is an explicit round-to-nearest
 // intrinsic (no contraction into FMA), in the same order as the CPU oracle, so
 // voxel indices and codes agree bit for bit.
+#include <utility>
+
 #include "tsdf_internal.cuh"
 
 namespace tsdf {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr unsigned kNoVoxel = 0xFFFFFFFFu;
 
 __device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
 
-template <int MODE>
-__global__ void __launch_bounds__(256) contrib_kernel(const ScanArgs a, const MapDev m) {
+// Programmatic dependent launch: wait for the preceding grid's completion
+// (and visibility of its writes) / let the next grid be scheduled early.
+// Both are no-ops for a grid launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Sum of a 64-bit value over the CTA (every thread must call it); the result
+// is valid in thread 0.
+template <int NWARPS>
+__device__ __forceinline__ unsigned long long cta_sum(unsigned long long v, unsigned long long* smem) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if ((threadIdx.x & 31u) == 0) smem[threadIdx.x >> 5] = v;
+    __syncthreads();
+    unsigned long long s = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < NWARPS; ++w) s += smem[w];
+    return s;
+}
+
+__global__ void __launch_bounds__(256) rays_kernel(const ScanArgs a, const MapDev m) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned lane = threadIdx.x & 31u;
-    const unsigned lt_mask = (1u << lane) - 1u;
-
-    // ---- transform + ray set-up (Section "TSDF Map Generation")
     float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
     const bool in = i < a.n;
-    if (in) p = __ldg(a.pts + i);
+    if (in) p = __ldg(a.pts + i);   // the caller's points: no dependency on earlier grids
+    pdl_trigger();
     const float tx = a.t[0], ty = a.t[1], tz = a.t[2];
     const float pwx = fa(fa(fa(fm(a.R[0], p.x), fm(a.R[1], p.y)), fm(a.R[2], p.z)), tx);
     const float pwy = fa(fa(fa(fm(a.R[3], p.x), fm(a.R[4], p.y)), fm(a.R[5], p.z)), ty);
@@ -53,15 +89,12 @@ __global__ void __launch_bounds__(256) contrib_kernel(const ScanArgs a, const Ma
     const float r2 = fa(fa(fm(vx, vx), fm(vy, vy)), fm(vz, vz));
     const float r = __fsqrt_rn(r2);
     const bool valid = in && (r >= a.rmin) && (r <= a.rmax);
-    const unsigned vmask = __ballot_sync(kFull, valid);
-    if (vmask == 0u) return;   // warp-uniform exit
 
-    float dx = 0.f, dy = 0.f, dz = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
-    bool fill = false;
+    float4 ra = make_float4(0.f, 0.f, 0.f, -1.f);
+    float4 rb = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool live = false;
     if (valid) {
-        dx = __fdiv_rn(vx, r);
-        dy = __fdiv_rn(vy, r);
-        dz = __fdiv_rn(vz, r);
+        const float dx = __fdiv_rn(vx, r), dy = __fdiv_rn(vy, r), dz = __fdiv_rn(vz, r);
         const float ux = a.R[2], uy = a.R[5], uz = a.R[8];   // sensor z axis in the world
         const float ax = fs(fm(dy, uz), fm(dz, uy));
         const float ay = fs(fm(dz, ux), fm(dx, uz));
@@ -70,153 +103,342 @@ __global__ void __launch_bounds__(256) contrib_kernel(const ScanArgs a, const Ma
         const float ivy = fs(fm(dz, ax), fm(dx, az));
         const float ivz = fs(fm(dx, ay), fm(dy, ax));
         const float n2 = fa(fa(fm(ivx, ivx), fm(ivy, ivy)), fm(ivz, ivz));
-        if (a.fill && n2 >= 1e-12f) {
+        const bool fill = a.fill && n2 >= 1e-12f;
+        if (fill) {
             const float nn = __fsqrt_rn(n2);
-            fill = true;
-            hx = __fdiv_rn(ivx, nn);
-            hy = __fdiv_rn(ivy, nn);
-            hz = __fdiv_rn(ivz, nn);
+            rb = make_float4(__fdiv_rn(ivx, nn), __fdiv_rn(ivy, nn), __fdiv_rn(ivz, nn), 1.f);
         }
+        // conservative culling: distance from the hit to the window box against
+        // the reach of the march (tau + fill height + margin)
+        const float hx = tx + dx * r, hy = ty + dy * r, hz = tz + dz * r;
+        const float ex = fmaxf(fmaxf(a.win_lo[0] - hx, hx - a.win_hi[0]), 0.f);
+        const float ey = fmaxf(fmaxf(a.win_lo[1] - hy, hy - a.win_hi[1]), 0.f);
+        const float ez = fmaxf(fmaxf(a.win_lo[2] - hz, hz - a.win_hi[2]), 0.f);
+        const float reach = a.tau + (fill ? a.dz * (r + a.tau) : 0.f) + 2.f * a.vs +
+                            1e-4f * (fabsf(tx) + fabsf(ty) + fabsf(tz) + r);
+        live = ex * ex + ey * ey + ez * ez <= reach * reach;
+        ra = make_float4(dx, dy, dz, r);
     }
+    // CTA-level compaction of the live rays: one list atomic per CTA
+    __shared__ unsigned wl[8], wv[8];
+    __shared__ unsigned cta_base;
+    const unsigned warp = threadIdx.x >> 5;
+    const unsigned lmask = __ballot_sync(kFull, live);
+    const unsigned vmask = __ballot_sync(kFull, valid);
+    if (lane == 0) {
+        wl[warp] = __popc(lmask);
+        wv[warp] = __popc(vmask);
+    }
+    __syncthreads();
+    pdl_wait();   // the previous scan's finish kernel resets live_count and the counters
+    if (threadIdx.x == 0) {
+        unsigned tl = 0, tv = 0;
+        for (int w = 0; w < 8; ++w) {
+            tl += wl[w];
+            tv += wv[w];
+        }
+        cta_base = tl ? atomicAdd(&m.ctr->live_count, tl) : 0u;
+        if (tv) atomicAdd(&m.ctr->part[blockIdx.x % kParts].valid, (unsigned long long)tv);
+    }
+    __syncthreads();
+    if (live) {
+        unsigned off = cta_base + __popc(lmask & ((1u << lane) - 1u));
+        for (unsigned w = 0; w < warp; ++w) off += wl[w];
+        m.ray_a[off] = ra;
+        m.ray_b[off] = rb;
+    }
+}
 
-    const unsigned mx = a.dimx - 1u, my = a.dimy - 1u, mz = a.dimz - 1u;
-    unsigned long long warp_hits = 0;
-
-    for (int k = -a.K; k <= a.K; ++k) {
+template <int MODE, bool MERGE, int KPT>
+__global__ void __launch_bounds__(256) contrib_kernel(const ScanArgs a, const MapDev m) {
+    __shared__ unsigned long long red[8];
+    const int ray = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k0 = (int)blockIdx.y * KPT - a.K;
+    const unsigned lane = threadIdx.x & 31u;
+    __shared__ unsigned s_nlive;
+    pdl_trigger();
+    pdl_wait();   // ray list and live count come from the rays kernel
+    // One load of the live count per CTA (a load per warp would make every
+    // warp of the grid hit the same L2 line).
+    if (threadIdx.x == 0) s_nlive = __ldcg(&m.ctr->live_count);
+    // The ray buffers hold a.n entries, so the loads are in bounds whatever
+    // the live count; entries at or beyond it are ignored.
+    float4 A = make_float4(0.f, 0.f, 0.f, -1.f);
+    float4 B = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ray < a.n) {
+        A = m.ray_a[ray];
+        B = m.ray_b[ray];
+    }
+    __syncthreads();
+    const unsigned nlive = s_nlive;
+    if ((unsigned)ray >= nlive) A.w = -1.f;
+    if (blockIdx.x * blockDim.x >= nlive) return;   // CTA-uniform: no live ray in this CTA
+    unsigned hits = 0;
+    const float r = A.w;
+    const float tx = a.t[0], ty = a.t[1], tz = a.t[2];
+#pragma unroll 1
+    for (int kk = 0; kk < KPT; ++kk) {
+        const int k = k0 + kk;
+        if (k > a.K) break;   // uniform
         const float l = fa(r, fm((float)k, a.vs));
-        const bool lv = valid && (l > 0.f);
-        int J = 0;
-        if (lv && fill) J = __float2int_rd(fm(fm(a.dz, l), a.inv_vs));
-        const int Jw = __reduce_max_sync(kFull, lv ? J : -1);
-        if (Jw < 0) continue;
-        const float bx = fa(tx, fm(dx, l));
-        const float by = fa(ty, fm(dy, l));
-        const float bz = fa(tz, fm(dz, l));
-        for (int j = -Jw; j <= Jw; ++j) {
-            unsigned slot = kEmptySlot;
-            int q = 0;
-            if (lv && j >= -J && j <= J) {
-                const float jd = fm((float)j, a.vs);
-                const float qx = fa(bx, fm(hx, jd));
-                const float qy = fa(by, fm(hy, jd));
-                const float qz = fa(bz, fm(hz, jd));
-                const long long gx = __float2ll_rd(fm(qx, a.inv_vs));
-                const long long gy = __float2ll_rd(fm(qy, a.inv_vs));
-                const long long gz = __float2ll_rd(fm(qz, a.inv_vs));
-                if ((unsigned long long)(gx - a.ox) < a.dimx && (unsigned long long)(gy - a.oy) < a.dimy &&
-                    (unsigned long long)(gz - a.oz) < a.dimz) {
-                    slot = ((unsigned)gz & mz) << a.shxy | ((unsigned)gy & my) << a.shx | ((unsigned)gx & mx);
-                    const float cx = fm(fa(__ll2float_rn(gx), 0.5f), a.vs);
-                    const float cy = fm(fa(__ll2float_rn(gy), 0.5f), a.vs);
-                    const float cz = fm(fa(__ll2float_rn(gz), 0.5f), a.vs);
-                    const float proj = fa(fa(fm(fs(cx, tx), dx), fm(fs(cy, ty), dy)), fm(fs(cz, tz), dz));
-                    float d = fs(r, proj);
-                    d = fminf(fmaxf(d, -a.tau), a.tau);
-                    q = __float2int_rn(fm(d, a.qs));
-                    q = max(-kQMax, min(kQMax, q));
-                }
-            }
-            const bool act = slot != kEmptySlot;
-            const unsigned amask = __ballot_sync(kFull, act);
-            if (amask == 0u) continue;
-            warp_hits += __popc(amask);
-            const unsigned peers = __match_any_sync(kFull, slot);
-            bool first = false;
-            if (act) {
-                const unsigned leader = __ffs(peers) - 1u;
+        const bool lv = (r >= 0.f) && (l > 0.f);   // dead lanes carry r = -1
+        const int J = (lv && B.w != 0.f) ? __float2int_rd(fm(fm(a.dz, l), a.inv_vs)) : 0;
+        const int Jw = __reduce_max_sync(kFull, lv ? J : -1);   // -1: no live lane
+        const float bx = fa(tx, fm(A.x, l));
+        const float by = fa(ty, fm(A.y, l));
+        const float bz = fa(tz, fm(A.z, l));
+        unsigned last_brick = kNoVoxel;
+        for (int j = -Jw; j <= Jw; ++j) {   // warp-uniform bounds
+            // every lane evaluates the sample; lanes outside their own fill
+            // range or outside the window are masked out (no divergent branches)
+            const float jd = fm((float)j, a.vs);
+            const float fx = floorf(fm(fa(bx, fm(B.x, jd)), a.inv_vs));
+            const float fy = floorf(fm(fa(by, fm(B.y, jd)), a.inv_vs));
+            const float fz = floorf(fm(fa(bz, fm(B.z, jd)), a.inv_vs));
+            const bool act = lv && j >= -J && j <= J && fx >= a.fo[0] && fx < a.fe[0] && fy >= a.fo[1] &&
+                             fy < a.fe[1] && fz >= a.fo[2] && fz < a.fe[2];
+            const int gx = (int)fx, gy = (int)fy, gz = (int)fz;
+            const unsigned brick = (((unsigned)(gz >> 3) & a.cmask[2]) << a.lcxy) |
+                                   (((unsigned)(gy >> 3) & a.cmask[1]) << a.lcx) |
+                                   ((unsigned)(gx >> 3) & a.cmask[0]);
+            const unsigned word = (brick << 9) | ((unsigned)(gz & 7) << 6) | ((unsigned)(gy & 7) << 3) |
+                                  (unsigned)(gx & 7);
+            // voxel centre: (float)g + 0.5 is fx + 0.5 exactly (|g| < 2^24)
+            const float cx = fm(fa(fx, 0.5f), a.vs);
+            const float cy = fm(fa(fy, 0.5f), a.vs);
+            const float cz = fm(fa(fz, 0.5f), a.vs);
+            const float proj = fa(fa(fm(fs(cx, tx), A.x), fm(fs(cy, ty), A.y)), fm(fs(cz, tz), A.z));
+            const float d = fminf(fmaxf(fs(r, proj), -a.tau), a.tau);
+            int q = __float2int_rn(fm(d, a.qs));
+            q = max(-kQMax, min(kQMax, q));
+            bool leader = act;
+            if (MERGE) {
+                if (__ballot_sync(kFull, act) == 0u) continue;   // warp-uniform
+                const unsigned peers = __match_any_sync(kFull, act ? word : kNoVoxel);
+                leader = act && lane == (unsigned)(__ffs(peers) - 1);
                 if (MODE == 0) {
                     const int s = __reduce_add_sync(peers, q);
-                    if (lane == leader) {
-                        const unsigned long long add =
-                            ((unsigned long long)__popc(peers) << 40) + (unsigned long long)(long long)s;
-                        first = atomicAdd(m.acc + slot, add) == 0ull;
-                    }
+                    if (leader)
+                        atomicAdd(m.acc + word,
+                                  ((unsigned long long)__popc(peers) << 40) + (unsigned long long)(long long)s);
                 } else {
                     const unsigned key = ((unsigned)abs(q) << 1) | (q < 0 ? 1u : 0u);
                     const unsigned kmin = __reduce_min_sync(peers, key);
-                    if (lane == leader) first = atomicMax(m.acc + slot, 65536ull - kmin) == 0ull;
+                    if (leader) atomicMax(m.acc + word, 65536ull - kmin);
+                }
+            } else {
+                if (MODE == 0) {
+                    if (act) atomicAdd(m.acc + word, (1ull << 40) + (unsigned long long)(long long)q);
+                } else {
+                    const unsigned key = ((unsigned)abs(q) << 1) | (q < 0 ? 1u : 0u);
+                    if (act) atomicMax(m.acc + word, 65536ull - key);
                 }
             }
-            const unsigned fmask = __ballot_sync(kFull, first);
-            if (fmask) {
-                unsigned base = 0;
-                if (lane == 0) base = atomicAdd(&m.ctr->touched_count, (unsigned)__popc(fmask));
-                base = __shfl_sync(kFull, base, 0);
-                if (first) m.touched[base + __popc(fmask & lt_mask)] = slot;
+            if (MODE == 1) hits += act ? 1u : 0u;
+            if (leader && brick != last_brick) {
+                last_brick = brick;
+                m.brick_flag[brick] = 1;
             }
         }
     }
-    if (lane == 0) {
-        atomicAdd(&m.ctr->cur_valid, (unsigned long long)__popc(vmask));
-        atomicAdd(&m.ctr->cur_hits, warp_hits);
+    (void)lane;
+    if (MODE == 1) {
+        // MIN_ABS keeps no contribution count per voxel: count them here
+        const unsigned long long total = cta_sum<8>((unsigned long long)hits, red);
+        if (threadIdx.x == 0 && total)
+            atomicAdd(&m.ctr->part[(blockIdx.x + blockIdx.y * gridDim.x) % kParts].hits, total);
+    }
+}
+
+// Eq. 1 / Eq. 2 for one voxel. Returns the new grid word.
+__device__ __forceinline__ uint32_t update_voxel(uint32_t word, long long S, long long W, int32_t w_max) {
+    const long long gv = (long long)(int16_t)(word & 0xFFFFu);
+    const long long gw = (long long)(int16_t)(word >> 16);
+    const long long num = gv * gw + S;
+    const long long den = gw + W;
+    const unsigned long long an = (unsigned long long)(num < 0 ? -num : num);
+    const unsigned long long top = 2ull * an + (unsigned long long)den;
+    const unsigned long long bot = 2ull * (unsigned long long)den;
+    unsigned long long qv;
+    if (top <= 0xFFFFFFFFull) qv = (unsigned)top / (unsigned)bot;   // common case: 32-bit divide
+    else qv = top / bot;
+    const long long nv = num < 0 ? -(long long)qv : (long long)qv;
+    const long long nw = den > w_max ? (long long)w_max : den;
+    return (uint32_t)(uint16_t)(int16_t)nv | ((uint32_t)nw << 16);
+}
+
+// Decode one accumulator and update its voxel; returns the voxel's number of
+// contributions (WSUM) or 1 (MIN_ABS), 0 if untouched.
+template <int MODE>
+__device__ __forceinline__ unsigned decode_apply(unsigned long long P, uint32_t& word, int32_t w_max) {
+    if (P == 0ull) return 0u;
+    long long S, W;
+    if (MODE == 0) {
+        S = ((long long)(P << 24)) >> 24;               // sign-extended low 40 bits
+        W = (long long)((P - (unsigned long long)S) >> 40);
+    } else {
+        const unsigned key = 65536u - (unsigned)P;
+        const int mag = (int)(key >> 1);
+        S = (key & 1u) ? -mag : mag;
+        W = 1;
+    }
+    word = update_voxel(word, S, W, w_max);
+    return (unsigned)W;
+}
+
+__global__ void __launch_bounds__(256) compact_kernel(const MapDev m, const uint32_t nwords) {
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned lane = threadIdx.x & 31u;
+    pdl_trigger();
+    pdl_wait();   // flags come from the contrib kernel
+    unsigned f = 0;
+    if (i < nwords) f = reinterpret_cast<const uint32_t*>(m.brick_flag)[i];
+    // bytes are 0 or 1: one bit per touched brick in bits 0, 8, 16, 24
+    const unsigned bits = (f & 1u) | ((f >> 7) & 2u) | ((f >> 14) & 4u) | ((f >> 21) & 8u);
+    const unsigned cnt = __popc(bits);
+    unsigned incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= (unsigned)o) incl += v;
+    }
+    const unsigned total = __shfl_sync(kFull, incl, 31);
+    if (total == 0u) return;   // warp-uniform
+    unsigned base = 0;
+    if (lane == 31) base = atomicAdd(&m.ctr->brick_count, total);
+    base = __shfl_sync(kFull, base, 31) + incl - cnt;
+    if (bits) {
+        reinterpret_cast<uint32_t*>(m.brick_flag)[i] = 0u;
+        for (unsigned b = 0; b < 4; ++b)
+            if (bits & (1u << b)) m.brick_list[base++] = 4u * i + b;
     }
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(256) apply_kernel(const MapDev m, const int32_t w_max) {
-    const unsigned U = *(volatile unsigned*)&m.ctr->touched_count;
-    const unsigned stride = gridDim.x * blockDim.x;
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < U; i += stride) {
-        const unsigned slot = m.touched[i];
-        const unsigned long long P = m.acc[slot];
-        m.acc[slot] = 0ull;
-        long long S, W;
-        if (MODE == 0) {
-            S = ((long long)(P << 24)) >> 24;               // sign-extended low 40 bits
-            W = (long long)((P - (unsigned long long)S) >> 40);
-        } else {
-            const unsigned key = 65536u - (unsigned)P;
-            const int mag = (int)(key >> 1);
-            S = (key & 1u) ? -mag : mag;
-            W = 1;
-        }
-        const uint32_t word = m.grid[slot];
-        const long long gv = (long long)(int16_t)(word & 0xFFFFu);
-        const long long gw = (long long)(int16_t)(word >> 16);
-        // Eq. 1: (gv*gw + S) / (gw + W), rounded half away from zero
-        const long long num = gv * gw + S;
-        const long long den = gw + W;
-        const long long an = num < 0 ? -num : num;
-        const long long qv = (2 * an + den) / (2 * den);
-        const long long nv = num < 0 ? -qv : qv;
-        // Eq. 2: min(w_max, gw + W)
-        const long long nw = den > w_max ? (long long)w_max : den;
-        m.grid[slot] = (uint32_t)(uint16_t)(int16_t)nv | ((uint32_t)nw << 16);
-    }
-    // The last CTA publishes the counters and clears the per-scan state.
+    __shared__ unsigned long long red_u[8], red_h[8];
+    __shared__ unsigned s_nb;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+    pdl_trigger();
+    pdl_wait();   // list and accumulators come from the earlier kernels
+    if (threadIdx.x == 0) s_nb = __ldcg(&m.ctr->brick_count);   // one load per CTA
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned done = atomicAdd(&m.ctr->apply_done, 1u);
-        if (done == gridDim.x - 1u) {
-            MapCounters* c = m.ctr;
-            c->last_valid = (long long)c->cur_valid;
-            c->last_hits = (long long)c->cur_hits;
-            c->last_touched = (long long)U;
-            c->cur_valid = 0ull;
-            c->cur_hits = 0ull;
-            c->touched_count = 0u;
-            c->apply_done = 0u;
-            __threadfence();
+    const unsigned nb = s_nb;
+    unsigned long long touched = 0, hits = 0;
+    for (unsigned i = gwarp; i < nb; i += nwarps) {
+        const unsigned brick = m.brick_list[i];
+        // the lane covers voxels [16 lane, 16 lane + 16) of the brick
+        uint4* gp = reinterpret_cast<uint4*>(m.grid + ((size_t)brick << 9)) + 4 * lane;
+        ulonglong2* ap = reinterpret_cast<ulonglong2*>(m.acc + ((size_t)brick << 9)) + 8 * lane;
+        ulonglong2 acc[8];
+        uint4 g[4];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[v] = ap[v];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) g[v] = gp[v];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const ulonglong2 a0 = acc[2 * v], a1 = acc[2 * v + 1];
+            if ((a0.x | a0.y | a1.x | a1.y) == 0ull) continue;
+            const unsigned w0 = decode_apply<MODE>(a0.x, g[v].x, w_max);
+            const unsigned w1 = decode_apply<MODE>(a0.y, g[v].y, w_max);
+            const unsigned w2 = decode_apply<MODE>(a1.x, g[v].z, w_max);
+            const unsigned w3 = decode_apply<MODE>(a1.y, g[v].w, w_max);
+            touched += (w0 != 0u) + (w1 != 0u) + (w2 != 0u) + (w3 != 0u);
+            hits += (unsigned long long)w0 + w1 + w2 + w3;
+            gp[v] = g[v];
+            ap[2 * v] = make_ulonglong2(0ull, 0ull);
+            ap[2 * v + 1] = make_ulonglong2(0ull, 0ull);
         }
+    }
+    const unsigned long long bu = cta_sum<8>(touched, red_u);
+    const unsigned long long bh = MODE == 0 ? cta_sum<8>(hits, red_h) : 0ull;
+    if (threadIdx.x == 0) {
+        if (bu) atomicAdd(&m.ctr->part[blockIdx.x % kParts].touched, bu);
+        if (MODE == 0 && bh) atomicAdd(&m.ctr->part[blockIdx.x % kParts].hits, bh);
+    }
+    (void)lane;
+}
+
+// One warp: publish the scan's counters and clear the per-scan state.
+__global__ void finish_kernel(const MapDev m) {
+    pdl_trigger();
+    pdl_wait();
+    MapCounters* c = m.ctr;
+    const unsigned lane = threadIdx.x;
+    unsigned long long v = c->part[lane].valid, h = c->part[lane].hits, u = c->part[lane].touched;
+    c->part[lane].valid = 0ull;
+    c->part[lane].hits = 0ull;
+    c->part[lane].touched = 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+        v += __shfl_xor_sync(kFull, v, o);
+        h += __shfl_xor_sync(kFull, h, o);
+        u += __shfl_xor_sync(kFull, u, o);
+    }
+    if (lane == 0) {
+        c->last_valid = (long long)v;
+        c->last_hits = (long long)h;
+        c->last_touched = (long long)u;
+        c->live_count = 0u;
+        c->brick_count = 0u;
+    }
+}
+
+// Launch with programmatic stream serialisation when `pdl` is set.
+template <typename... KArgs, typename... Args>
+cudaError_t launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, bool pdl, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+template <int MODE, bool MERGE>
+cudaError_t launch_contrib_k(const ScanArgs& a, const MapDev& m, int kpt, bool pdl, cudaStream_t s) {
+    const unsigned nk = (unsigned)(2 * a.K + 1);
+    const unsigned gx = (unsigned)((a.n + 255) / 256);
+    switch (kpt) {
+        case 2: return launch(contrib_kernel<MODE, MERGE, 2>, dim3(gx, (nk + 1) / 2), dim3(256), s, pdl, a, m);
+        case 4: return launch(contrib_kernel<MODE, MERGE, 4>, dim3(gx, (nk + 3) / 4), dim3(256), s, pdl, a, m);
+        default: return launch(contrib_kernel<MODE, MERGE, 1>, dim3(gx, nk), dim3(256), s, pdl, a, m);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_contrib(const ScanArgs& a, const MapDev& m, cudaStream_t s) {
+cudaError_t launch_rays(const ScanArgs& a, const MapDev& m, bool pdl, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
-    const int threads = 256;
-    const int blocks = (a.n + threads - 1) / threads;
-    if (a.reduce == 0) contrib_kernel<0><<<blocks, threads, 0, s>>>(a, m);
-    else contrib_kernel<1><<<blocks, threads, 0, s>>>(a, m);
-    return cudaGetLastError();
+    return launch(rays_kernel, dim3((unsigned)((a.n + 255) / 256)), dim3(256), s, pdl, a, m);
 }
 
-cudaError_t launch_apply(const MapDev& m, int32_t reduce, int32_t w_max, int num_ctas, cudaStream_t s) {
-    if (reduce == 0) apply_kernel<0><<<num_ctas, 256, 0, s>>>(m, w_max);
-    else apply_kernel<1><<<num_ctas, 256, 0, s>>>(m, w_max);
-    return cudaGetLastError();
+cudaError_t launch_contrib(const ScanArgs& a, const MapDev& m, int32_t reduce, bool merge, int kpt, bool pdl,
+                           cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    if (reduce == 0)
+        return merge ? launch_contrib_k<0, true>(a, m, kpt, pdl, s) : launch_contrib_k<0, false>(a, m, kpt, pdl, s);
+    return merge ? launch_contrib_k<1, true>(a, m, kpt, pdl, s) : launch_contrib_k<1, false>(a, m, kpt, pdl, s);
+}
+
+cudaError_t launch_compact(const MapDev& m, uint32_t bricks, bool pdl, cudaStream_t s) {
+    const uint32_t nwords = (bricks + 3u) / 4u;
+    return launch(compact_kernel, dim3((nwords + 255u) / 256u), dim3(256), s, pdl, m, nwords);
+}
+
+cudaError_t launch_apply(const MapDev& m, int32_t reduce, int32_t w_max, int num_ctas, bool pdl, cudaStream_t s) {
+    if (reduce == 0) return launch(apply_kernel<0>, dim3(num_ctas), dim3(256), s, pdl, m, w_max);
+    return launch(apply_kernel<1>, dim3(num_ctas), dim3(256), s, pdl, m, w_max);
+}
+
+cudaError_t launch_finish(const MapDev& m, bool pdl, cudaStream_t s) {
+    return launch(finish_kernel, dim3(1), dim3(kParts), s, pdl, m);
 }
 
 }  // namespace tsdf

@@ -7,30 +7,43 @@
 namespace tsdf {
 
 constexpr int32_t kQMax = 32767;
-constexpr unsigned kEmptySlot = 0xFFFFFFFFu;
+constexpr int kBrick = 8;                 // bricks are 8 x 8 x 8 voxels, stored contiguously
+constexpr int kBrickVoxels = 512;
 
-// Per-map device counters (one instance per map, in device memory).
+constexpr int kParts = 32;        // counters are spread over 32 slots, one 128-byte line each
+
+// Per-map device counters (one instance per map, in device memory). The
+// counters of the scan in flight are split over kParts slots so that CTAs
+// add to different L2 lines; the finish kernel sums them.
+struct CounterPart {
+    unsigned long long valid;       // valid rays
+    unsigned long long hits;        // in-window contributions
+    unsigned long long touched;     // voxels updated
+    unsigned long long pad[13];
+};
 struct MapCounters {
-    unsigned long long cur_valid;   // valid rays of the scan in flight
-    unsigned long long cur_hits;    // in-window contributions of the scan in flight
-    unsigned int touched_count;     // length of the touched list of the scan in flight
-    unsigned int apply_done;        // CTAs of the apply kernel that have finished
+    CounterPart part[kParts];
     long long last_valid;           // counters of the last completed scan
     long long last_hits;
     long long last_touched;
-    unsigned int error;             // sticky device-side error word (0 = none)
-    unsigned int pad;
+    unsigned int live_count;        // rays of the scan in flight that can reach the window (compacted)
+    unsigned int brick_count;       // length of the touched-brick list of the scan in flight
 };
 
-// Device-side view of one map.
+// Device-side view of one map. The window is bricked and ring addressed:
+// global voxel g lives in brick ((g >> 3) mod (dims / 8)) at offset
+// ((g.z & 7) * 8 + (g.y & 7)) * 8 + (g.x & 7).
 struct MapDev {
-    uint32_t* grid;                 // X*Y*Z words: value (low 16) | weight (high 16), ring addressed
-    unsigned long long* acc;        // X*Y*Z packed per-scan accumulators, all zero between scans
-    uint32_t* touched;              // slots touched by the scan in flight (first-touch order)
+    uint32_t* grid;                 // value (low 16) | weight (high 16), 512 words per brick
+    unsigned long long* acc;        // packed per-scan accumulators, same layout; all zero between scans
+    uint8_t* brick_flag;            // one byte per brick (padded to 4): 1 = touched by the scan in flight
+    uint32_t* brick_list;           // touched bricks of the scan in flight, built by the compaction kernel
+    float4* ray_a;                  // per live ray (compacted): (dir.x, dir.y, dir.z, r)
+    float4* ray_b;                  // per live ray (compacted): (int.x, int.y, int.z, fill ? 1 : 0)
     MapCounters* ctr;
 };
 
-// Everything the contribution kernel needs about one scan, passed by value.
+// Everything the kernels need about one scan, passed by value.
 struct ScanArgs {
     const float4* pts;
     int32_t n;
@@ -39,32 +52,39 @@ struct ScanArgs {
     float t[3];                     // sensor position in the world
     float vs, inv_vs, tau, qs, dz, rmin, rmax;
     int32_t fill;                   // delta_z > 0
-    int32_t reduce;                 // 0 = WSUM, 1 = MIN_ABS
-    long long ox, oy, oz;           // window origin (global voxel coordinates)
-    uint32_t dimx, dimy, dimz;      // powers of two
-    uint32_t shx, shxy;             // log2(dimx), log2(dimx*dimy)
-    int32_t w_max;
+    float win_lo[3], win_hi[3];     // window box in metres (rounded outward), for ray culling
+    float fo[3];                    // window origin as float (exact: |origin| <= 2^23)
+    float fe[3];                    // origin + dims as float (exact)
+    uint32_t cmask[3];              // dims / 8 - 1 per axis
+    uint32_t lcx, lcxy;             // log2(dims.x / 8), log2(dims.x / 8 * dims.y / 8)
 };
 
-// One 8^3 chunk slot that changes owner during a shift.
+// One brick slot that changes owner during a shift.
 struct ShiftItem {
-    uint32_t chunk_slot;            // (cz * CY + cy) * CX + cx in ring (slot) chunk coordinates
+    uint32_t brick;                 // ring brick index
     uint32_t pad0;
-    unsigned long long out_ptr;     // store address for the leaving chunk (2048 B), 0 = discard
-    unsigned long long in_ptr;      // store address of the entering chunk, 0 = zero fill
+    unsigned long long out_ptr;     // store address for the leaving brick (2048 B), 0 = discard
+    unsigned long long in_ptr;      // store address of the entering brick, 0 = zero fill
     unsigned long long pad1;
 };
 
+struct WindowGeom {
+    uint32_t dims[3];
+    uint32_t cmask[3];
+    uint32_t lcx, lcxy;
+};
+
 // Launchers (return the cudaError_t of the launch).
-cudaError_t launch_contrib(const ScanArgs& a, const MapDev& m, cudaStream_t s);
-cudaError_t launch_apply(const MapDev& m, int32_t reduce, int32_t w_max, int num_ctas, cudaStream_t s);
-cudaError_t launch_shift(uint32_t* grid, const ShiftItem* items, int count, uint32_t dimx, uint32_t dimy,
-                         cudaStream_t s);
+cudaError_t launch_rays(const ScanArgs& a, const MapDev& m, bool pdl, cudaStream_t s);
+cudaError_t launch_contrib(const ScanArgs& a, const MapDev& m, int32_t reduce, bool merge, int kpt, bool pdl,
+                           cudaStream_t s);
+cudaError_t launch_compact(const MapDev& m, uint32_t bricks, bool pdl, cudaStream_t s);
+cudaError_t launch_apply(const MapDev& m, int32_t reduce, int32_t w_max, int num_ctas, bool pdl, cudaStream_t s);
+cudaError_t launch_finish(const MapDev& m, bool pdl, cudaStream_t s);
+cudaError_t launch_shift(uint32_t* grid, const ShiftItem* items, int count, cudaStream_t s);
 cudaError_t launch_read_box(const uint32_t* grid, const long long lo[3], const uint32_t box[3],
-                            uint32_t dimx, uint32_t dimy, uint32_t dimz, int16_t* v, int16_t* w,
-                            cudaStream_t s);
-cudaError_t launch_write_box(uint32_t* grid, const long long lo[3], const uint32_t box[3], uint32_t dimx,
-                             uint32_t dimy, uint32_t dimz, const int16_t* v, const int16_t* w,
-                             cudaStream_t s);
+                            const WindowGeom& g, int16_t* v, int16_t* w, cudaStream_t s);
+cudaError_t launch_write_box(uint32_t* grid, const long long lo[3], const uint32_t box[3], const WindowGeom& g,
+                             const int16_t* v, const int16_t* w, cudaStream_t s);
 
 }  // namespace tsdf

@@ -5,12 +5,15 @@ import numpy as np
 import oracle
 
 
-def run_gpu(params, steps, torch, prefill=None, host=False):
-    """steps: list of ("scan", points(N,4) float32, pose[12]) or ("shift", origin3)."""
+def run_gpu(params, steps, torch, prefill=None, host=False, options=None):
+    """steps: list of ("scan", points(N,4) float32, pose[12]) or ("shift", origin3).
+    options: {tsdf option id: value} applied after creation."""
     from paper_2310_05766_gb300 import binding as b
     m = b.TsdfMap(params)
     stats = []
     try:
+        for opt, val in (options or {}).items():
+            b.tsdf_set_option(m.handle, opt, val)
         if prefill is not None:
             m.write(prefill[0], prefill[1])
         for st in steps:

@@ -25,8 +25,8 @@ def _lib():
     yield
 
 
-def both(params, steps, prefill=None, host=False, label=""):
-    g = run_gpu(params, steps, torch, prefill=prefill, host=host)
+def both(params, steps, prefill=None, host=False, label="", options=None):
+    g = run_gpu(params, steps, torch, prefill=prefill, host=host, options=options)
     o = run_oracle(params, steps, prefill=prefill)
     assert_same(g, o, label)
     return g, o
@@ -39,6 +39,34 @@ def test_room_scan_exact(reduce):
     w = synth.workload_room(reduce=reduce)
     g, o = both(w.params, workload_steps(w), label=f"room reduce={reduce}")
     assert g[2][0]["hits"] > 300000 and g[2][0]["valid_rays"] == 5760
+
+
+@pytest.mark.parametrize("reduce", [0, 1])
+@pytest.mark.parametrize("merge,kpt,pdl", [(1, 2, 1), (0, 1, 1), (0, 4, 1), (1, 4, 0), (0, 2, 0), (1, 1, 1)])
+def test_tuning_options_same_result(reduce, merge, kpt, pdl):
+    """Tuning options (warp match-merge, steps per thread, programmatic
+    dependent launch) change speed only: every setting is bit-identical to the
+    oracle."""
+    from paper_2310_05766_gb300 import binding as b
+    opts = {b.TSDF_OPT_WARP_MERGE: merge, b.TSDF_OPT_STEPS_PER_THREAD: kpt, b.TSDF_OPT_PDL: pdl}
+    w = synth.workload_room(reduce=reduce)
+    both(w.params, workload_steps(w), options=opts, label=f"room {opts}")
+    w2 = synth.workload_outdoor(n_scans=2, reduce=reduce)
+    both(w2.params, workload_steps(w2), options=opts, label=f"outdoor {opts}")
+    p, steps = _rand_case(7)
+    both(dict(p, reduce=reduce), steps, options=opts, label=f"random {opts}")
+
+
+def test_invalid_option_rejected():
+    from paper_2310_05766_gb300 import binding as b
+    w = synth.workload_room()
+    m = b.TsdfMap(w.params)
+    try:
+        for opt, val in [(b.TSDF_OPT_STEPS_PER_THREAD, 3), (b.TSDF_OPT_WARP_MERGE, 2), (b.TSDF_OPT_PDL, -1), (99, 0)]:
+            with pytest.raises(b.TsdfError):
+                b.tsdf_set_option(m.handle, opt, val)
+    finally:
+        m.close()
 
 
 def test_room_scan_into_prefilled_map():
