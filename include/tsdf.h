@@ -186,6 +186,46 @@ int tsdf_profile_enable(tsdf_map* map, int32_t enable);
  * Errors: INVALID, CUDA. */
 int tsdf_profile_read(tsdf_map* map, tsdf_kernel_time* out, int32_t capacity, int32_t* count);
 
+/* ---- integration without device allocation ---------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory once they run: for example a real-time
+ * mapping loop that reserves all of its memory at start-up (cudaMalloc may
+ * synchronise the device and take unbounded time), or a process whose device
+ * memory is owned by another allocator. It allocates nothing: it calls no
+ * cudaMalloc or cudaFree and no allocating library routine. Its working memory
+ * is one fixed file-scope device array of about 20 MiB (accumulators for up to
+ * TSDF_STATIC_MAX_VOXELS voxels, per-ray data for up to TSDF_STATIC_MAX_POINTS
+ * points, brick flags and list, counters) that every GPU which loads the
+ * library keeps until the process exits. */
+#define TSDF_STATIC_MAX_VOXELS  (1LL << 21)   /* window voxels (dims product) accepted */
+#define TSDF_STATIC_MAX_POINTS  (1LL << 17)   /* points per call accepted (one 128 x 1024 scan) */
+
+/* Integrate one scan into a caller-owned voxel grid, with the same result as
+ * tsdf_integrate on a map with these parameters and origin.
+ *   grid_dev   : device pointer, in/out, dims.x*dims.y*dims.z uint32 words in
+ *                the layout tsdf_grid_device_ptr describes (value low 16 bits,
+ *                weight high 16 bits, bricked, ring addressed); 16-byte
+ *                aligned. All zero for an empty map.
+ *   params     : window and method parameters; params->origin is the window
+ *                origin (this call never shifts). dims product must not exceed
+ *                TSDF_STATIC_MAX_VOXELS.
+ *   points_dev : n float4 points as for tsdf_integrate; n <= TSDF_STATIC_MAX_POINTS.
+ *   pose       : host, 12 floats, as for tsdf_integrate.
+ *   stats_host : if not NULL, receives the scan's counters; the call then
+ *                synchronises `stream`. If NULL the call is asynchronous.
+ * Set-up: the first call on each device looks up the device address of the
+ * scratch array (cudaGetSymbolAddress) with that device current, so make that
+ * first call before any stream capture.
+ * All calls share the one scratch array, and each call clears the parts that
+ * must start at zero: calls that overlap on the GPU (different streams, or
+ * different host threads, on one device) race and give undefined results;
+ * serialise them.
+ * Errors: INVALID (null or misaligned pointers, bad parameters, window larger
+ * than TSDF_STATIC_MAX_VOXELS voxels, n < 0 or n > TSDF_STATIC_MAX_POINTS),
+ * CUDA. */
+int tsdf_integrate_static(uint32_t* grid_dev, const tsdf_params* params, const float* points_dev, int64_t n,
+                          const float pose[12], tsdf_scan_stats* stats_host, void* stream);
+
 /* Static description of an error code. Never NULL. */
 const char* tsdf_error_string(int code);
 

@@ -27,6 +27,8 @@ TSDF_MAX_POINTS = 1 << 22
 TSDF_OPT_WARP_MERGE = 1
 TSDF_OPT_STEPS_PER_THREAD = 2
 TSDF_OPT_PDL = 3
+TSDF_STATIC_MAX_VOXELS = 1 << 21
+TSDF_STATIC_MAX_POINTS = 1 << 17
 
 
 class TsdfError(RuntimeError):
@@ -84,12 +86,14 @@ def lib():
     L.tsdf_set_option.argtypes = [vp, ctypes.c_int32, ctypes.c_int64]
     L.tsdf_profile_enable.argtypes = [vp, ctypes.c_int32]
     L.tsdf_profile_read.argtypes = [vp, P(tsdf_kernel_time), ctypes.c_int32, P(ctypes.c_int32)]
+    L.tsdf_integrate_static.argtypes = [vp, P(tsdf_params), vp, i64, f32p, P(tsdf_scan_stats), vp]
     L.tsdf_error_string.argtypes = [i32]
     L.tsdf_error_string.restype = ctypes.c_char_p
     L.tsdf_last_cuda_error.argtypes = []
     for name in ("tsdf_map_create", "tsdf_map_destroy", "tsdf_integrate", "tsdf_integrate_host", "tsdf_shift",
                  "tsdf_read", "tsdf_write", "tsdf_stats", "tsdf_get_origin", "tsdf_grid_device_ptr",
-                 "tsdf_last_cuda_error", "tsdf_profile_enable", "tsdf_profile_read", "tsdf_set_option"):
+                 "tsdf_last_cuda_error", "tsdf_profile_enable", "tsdf_profile_read", "tsdf_set_option",
+                 "tsdf_integrate_static"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -213,6 +217,24 @@ def tsdf_grid_device_ptr(handle: int) -> int:
     p = ctypes.c_void_p()
     _check(lib().tsdf_grid_device_ptr(handle, ctypes.byref(p)), "tsdf_grid_device_ptr")
     return p.value
+
+
+def tsdf_integrate_static(grid_dev, params, points_dev, n: int, pose, stream=None, want_stats: bool = True):
+    """Integrate one scan into a caller-owned grid without any device allocation.
+
+    grid_dev: CUDA int32/uint32 tensor (or device pointer) of dims product words;
+    points_dev: CUDA float32 (n, 4) tensor (or device pointer). Returns the
+    scan's counters (and synchronises the stream) when want_stats, else None.
+    """
+    gptr = grid_dev if isinstance(grid_dev, int) else grid_dev.data_ptr()
+    pptr = points_dev if isinstance(points_dev, int) else points_dev.data_ptr()
+    prm = params if isinstance(params, tsdf_params) else make_params(params)
+    pa, pp = _pose_arg(pose)
+    st = tsdf_scan_stats()
+    _check(lib().tsdf_integrate_static(gptr, ctypes.byref(prm), pptr, int(n), pp,
+                                       ctypes.byref(st) if want_stats else None, _stream_ptr(stream)),
+           "tsdf_integrate_static")
+    return dict(valid_rays=st.valid_rays, hits=st.hits, touched=st.touched) if want_stats else None
 
 
 def tsdf_set_option(handle: int, option: int, value: int) -> None:
