@@ -25,12 +25,15 @@
 //   makes the result independent of the order of the atomics.
 // compact: turns the brick flags into a list of touched bricks (4 flags per
 //   thread, one list atomic per warp) and clears the flags.
-// apply (K-C): one warp per listed brick (grid-stride over the list), 16
-//   consecutive voxels per lane (64 B of grid, 128 B of accumulator): Eq. 1 in
-//   exact integers with one rounding (half away from zero) and Eq. 2 with the
-//   weight cap for every voxel whose accumulator is non-zero; the accumulator
-//   is reset. Touched voxels are counted, and in WSUM mode the contributions
-//   too (the sum of the decoded weights).
+// apply (K-C): one warp per listed brick (grid-stride over the list). The
+//   warp copies the brick's grid words and accumulators into shared memory with
+//   coalesced 16-byte loads and compacts its
+//   touched voxels (non-zero accumulators) into a dense list with a warp scan,
+//   then applies Eq. 1 in exact integers with one rounding (half away from
+//   zero) and Eq. 2 with the weight cap one touched voxel per lane, writes the
+//   brick back with 16-byte stores and resets the accumulators. Touched voxels
+//   are counted, and in WSUM mode the contributions too (the sum of the decoded
+//   weights).
 // finish: one warp sums the per-scan counters into the published ones and
 //   clears the per-scan state.
 //
@@ -174,6 +177,7 @@ __global__ void __launch_bounds__(256) contrib_kernel(const ScanArgs a, const Ma
     if ((unsigned)ray >= nlive) A.w = -1.f;
     if (blockIdx.x * blockDim.x >= nlive) return;   // CTA-uniform: no live ray in this CTA
     unsigned hits = 0;
+    unsigned last_brick = kNoVoxel;
     const float r = A.w;
     const float tx = a.t[0], ty = a.t[1], tz = a.t[2];
 #pragma unroll 1
@@ -187,7 +191,6 @@ __global__ void __launch_bounds__(256) contrib_kernel(const ScanArgs a, const Ma
         const float bx = fa(tx, fm(A.x, l));
         const float by = fa(ty, fm(A.y, l));
         const float bz = fa(tz, fm(A.z, l));
-        unsigned last_brick = kNoVoxel;
         for (int j = -Jw; j <= Jw; ++j) {   // warp-uniform bounds
             // every lane evaluates the sample; lanes outside their own fill
             // range or outside the window are masked out (no divergent branches)
@@ -235,7 +238,10 @@ __global__ void __launch_bounds__(256) contrib_kernel(const ScanArgs a, const Ma
                 }
             }
             if (MODE == 1) hits += act ? 1u : 0u;
-            if (leader && brick != last_brick) {
+            // mark the brick; skip when this lane marked it last or the lane
+            // below (usually the neighbouring ray) marks the same brick now
+            const unsigned below = __shfl_up_sync(kFull, leader ? brick : kNoVoxel, 1);
+            if (leader && brick != last_brick && (lane == 0 || below != brick)) {
                 last_brick = brick;
                 m.brick_flag[brick] = 1;
             }
@@ -259,31 +265,47 @@ __device__ __forceinline__ uint32_t update_voxel(uint32_t word, long long S, lon
     const unsigned long long an = (unsigned long long)(num < 0 ? -num : num);
     const unsigned long long top = 2ull * an + (unsigned long long)den;
     const unsigned long long bot = 2ull * (unsigned long long)den;
-    unsigned long long qv;
-    if (top <= 0xFFFFFFFFull) qv = (unsigned)top / (unsigned)bot;   // common case: 32-bit divide
-    else qv = top / bot;
+    const unsigned long long qv = top / bot;
     const long long nv = num < 0 ? -(long long)qv : (long long)qv;
     const long long nw = den > w_max ? (long long)w_max : den;
     return (uint32_t)(uint16_t)(int16_t)nv | ((uint32_t)nw << 16);
 }
 
 // Decode one accumulator and update its voxel; returns the voxel's number of
-// contributions (WSUM) or 1 (MIN_ABS), 0 if untouched.
+// contributions (WSUM) or 1 (MIN_ABS), 0 if untouched. WSUM accumulators
+// whose sum fits 31 bits and count fits 15 bits (the common case) take an
+// all-32-bit path with the same result as the 64-bit one.
 template <int MODE>
 __device__ __forceinline__ unsigned decode_apply(unsigned long long P, uint32_t& word, int32_t w_max) {
     if (P == 0ull) return 0u;
-    long long S, W;
     if (MODE == 0) {
-        S = ((long long)(P << 24)) >> 24;               // sign-extended low 40 bits
-        W = (long long)((P - (unsigned long long)S) >> 40);
+        const unsigned lo = (unsigned)P, hi = (unsigned)(P >> 32);
+        const unsigned hb = hi & 0xFFu;   // bits 32..39 of the 40-bit sum
+        const bool small = ((hb == 0u) && (int)lo >= 0) || ((hb == 0xFFu) && (int)lo < 0);
+        const int S32 = (int)lo;
+        const unsigned W32 = (hi >> 8) + (S32 < 0 ? 1u : 0u);
+        const int gw = (int)(int16_t)(word >> 16);
+        if (small && W32 < 32768u && gw >= 0 && S32 > -(1 << 30) && S32 < (1 << 30)) {
+            const int gv = (int)(int16_t)(word & 0xFFFFu);
+            const int num = gv * gw + S32;                  // |gv gw| < 2^30, |S| < 2^30
+            const unsigned den = (unsigned)gw + W32;        // < 2^16
+            const unsigned an = (unsigned)(num < 0 ? -num : num);
+            const unsigned q = (2u * an + den) / (2u * den);   // < 2^32 by the bounds above
+            const int nv = num < 0 ? -(int)q : (int)q;
+            const unsigned nw = den > (unsigned)w_max ? (unsigned)w_max : den;
+            word = (uint32_t)(uint16_t)(int16_t)nv | (nw << 16);
+            return W32;
+        }
+        const long long S = ((long long)(P << 24)) >> 24;   // sign-extended low 40 bits
+        const long long W = (long long)((P - (unsigned long long)S) >> 40);
+        word = update_voxel(word, S, W, w_max);
+        return (unsigned)W;
     } else {
         const unsigned key = 65536u - (unsigned)P;
         const int mag = (int)(key >> 1);
-        S = (key & 1u) ? -mag : mag;
-        W = 1;
+        word = update_voxel(word, (key & 1u) ? -mag : mag, 1, w_max);
+        return 1u;
     }
-    word = update_voxel(word, S, W, w_max);
-    return (unsigned)W;
 }
 
 __global__ void __launch_bounds__(256) compact_kernel(const MapDev m, const uint32_t nwords) {
@@ -313,52 +335,95 @@ __global__ void __launch_bounds__(256) compact_kernel(const MapDev m, const uint
     }
 }
 
+constexpr int kApplyWarps = 4;
+
 template <int MODE>
-__global__ void __launch_bounds__(256) apply_kernel(const MapDev m, const int32_t w_max) {
-    __shared__ unsigned long long red_u[8], red_h[8];
+__global__ void __launch_bounds__(kApplyWarps * 32) apply_kernel(const MapDev m, const int32_t w_max) {
+    // per warp: the brick's grid words and accumulators, and the offsets of
+    // its touched voxels (compacted)
+    __shared__ uint32_t s_grid[kApplyWarps][kBrickVoxels];
+    __shared__ unsigned long long s_acc[kApplyWarps][kBrickVoxels];
+    __shared__ uint16_t s_off[kApplyWarps][kBrickVoxels];
+    __shared__ unsigned long long red_u[kApplyWarps], red_h[kApplyWarps];
     __shared__ unsigned s_nb;
     const unsigned lane = threadIdx.x & 31u;
-    const unsigned gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+    const unsigned w = threadIdx.x >> 5;
+    const unsigned gwarp = blockIdx.x * kApplyWarps + w;
+    const unsigned nwarps = gridDim.x * kApplyWarps;
     pdl_trigger();
     pdl_wait();   // list and accumulators come from the earlier kernels
     if (threadIdx.x == 0) s_nb = __ldcg(&m.ctr->brick_count);   // one load per CTA
     __syncthreads();
     const unsigned nb = s_nb;
     unsigned long long touched = 0, hits = 0;
+    uint4* sg4 = reinterpret_cast<uint4*>(s_grid[w]);
+    ulonglong2* sa2 = reinterpret_cast<ulonglong2*>(s_acc[w]);
     for (unsigned i = gwarp; i < nb; i += nwarps) {
         const unsigned brick = m.brick_list[i];
-        // the lane covers voxels [16 lane, 16 lane + 16) of the brick
-        uint4* gp = reinterpret_cast<uint4*>(m.grid + ((size_t)brick << 9)) + 4 * lane;
-        ulonglong2* ap = reinterpret_cast<ulonglong2*>(m.acc + ((size_t)brick << 9)) + 8 * lane;
-        ulonglong2 acc[8];
-        uint4 g[4];
+        // coalesced, bank-conflict-free 16-byte copies of the brick into shared
+        // memory: accumulator pair p = 32 v + lane holds voxels 2p and 2p + 1
+        const uint4* gp = reinterpret_cast<const uint4*>(m.grid + ((size_t)brick << 9));
+        ulonglong2* ap = reinterpret_cast<ulonglong2*>(m.acc + ((size_t)brick << 9));
+        unsigned nz = 0;   // bit 2v (2v+1): voxel 2(32 v + lane) (+1) has a non-zero accumulator
 #pragma unroll
-        for (int v = 0; v < 8; ++v) acc[v] = ap[v];
+        for (int v = 0; v < 4; ++v) sg4[32 * v + lane] = gp[32 * v + lane];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) g[v] = gp[v];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const ulonglong2 a0 = acc[2 * v], a1 = acc[2 * v + 1];
-            if ((a0.x | a0.y | a1.x | a1.y) == 0ull) continue;
-            const unsigned w0 = decode_apply<MODE>(a0.x, g[v].x, w_max);
-            const unsigned w1 = decode_apply<MODE>(a0.y, g[v].y, w_max);
-            const unsigned w2 = decode_apply<MODE>(a1.x, g[v].z, w_max);
-            const unsigned w3 = decode_apply<MODE>(a1.y, g[v].w, w_max);
-            touched += (w0 != 0u) + (w1 != 0u) + (w2 != 0u) + (w3 != 0u);
-            hits += (unsigned long long)w0 + w1 + w2 + w3;
-            gp[v] = g[v];
-            ap[2 * v] = make_ulonglong2(0ull, 0ull);
-            ap[2 * v + 1] = make_ulonglong2(0ull, 0ull);
+        for (int v = 0; v < 8; ++v) {
+            const ulonglong2 a2 = ap[32 * v + lane];
+            sa2[32 * v + lane] = a2;
+            nz |= (a2.x != 0ull ? 1u : 0u) << (2 * v);
+            nz |= (a2.y != 0ull ? 1u : 0u) << (2 * v + 1);
         }
+        const unsigned cnt = __popc(nz);
+        unsigned incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= (unsigned)o) incl += t;
+        }
+        const unsigned total = __shfl_sync(kFull, incl, 31);
+        unsigned pos = incl - cnt;
+        for (unsigned bits = nz; bits; bits &= bits - 1u) {
+            const unsigned b = __ffs(bits) - 1u;
+            s_off[w][pos++] = (uint16_t)(2u * (32u * (b >> 1) + lane) + (b & 1u));
+        }
+        __syncwarp();
+        // Eq. 1 / Eq. 2 over the touched voxels only, one per lane
+        for (unsigned e = lane; e < total; e += 32u) {
+            const unsigned off = s_off[w][e];
+            uint32_t word = s_grid[w][off];
+            hits += decode_apply<MODE>(s_acc[w][off], word, w_max);
+            s_grid[w][off] = word;
+        }
+        touched += lane == 0 ? total : 0u;
+        __syncwarp();
+        uint4* gpw = reinterpret_cast<uint4*>(m.grid + ((size_t)brick << 9));
+#pragma unroll
+        for (int v = 0; v < 4; ++v) gpw[32 * v + lane] = sg4[32 * v + lane];
+        if (nz) {
+#pragma unroll
+            for (int v = 0; v < 8; ++v)
+                if (nz & (3u << (2 * v))) ap[32 * v + lane] = make_ulonglong2(0ull, 0ull);
+        }
+        __syncwarp();
     }
-    const unsigned long long bu = cta_sum<8>(touched, red_u);
-    const unsigned long long bh = MODE == 0 ? cta_sum<8>(hits, red_h) : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+        touched += __shfl_xor_sync(kFull, touched, o);
+        hits += __shfl_xor_sync(kFull, hits, o);
+    }
+    if (lane == 0) {
+        red_u[w] = touched;
+        red_h[w] = hits;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
+        unsigned long long bu = 0, bh = 0;
+        for (int k = 0; k < kApplyWarps; ++k) {
+            bu += red_u[k];
+            bh += red_h[k];
+        }
         if (bu) atomicAdd(&m.ctr->part[blockIdx.x % kParts].touched, bu);
         if (MODE == 0 && bh) atomicAdd(&m.ctr->part[blockIdx.x % kParts].hits, bh);
     }
-    (void)lane;
 }
 
 // One warp: publish the scan's counters and clear the per-scan state.
@@ -433,8 +498,8 @@ cudaError_t launch_compact(const MapDev& m, uint32_t bricks, bool pdl, cudaStrea
 }
 
 cudaError_t launch_apply(const MapDev& m, int32_t reduce, int32_t w_max, int num_ctas, bool pdl, cudaStream_t s) {
-    if (reduce == 0) return launch(apply_kernel<0>, dim3(num_ctas), dim3(256), s, pdl, m, w_max);
-    return launch(apply_kernel<1>, dim3(num_ctas), dim3(256), s, pdl, m, w_max);
+    if (reduce == 0) return launch(apply_kernel<0>, dim3(num_ctas), dim3(kApplyWarps * 32), s, pdl, m, w_max);
+    return launch(apply_kernel<1>, dim3(num_ctas), dim3(kApplyWarps * 32), s, pdl, m, w_max);
 }
 
 cudaError_t launch_finish(const MapDev& m, bool pdl, cudaStream_t s) {
