@@ -149,7 +149,7 @@ int tsdf_stats(tsdf_map* map, tsdf_scan_stats* out, void* stream);
 #define TSDF_OPT_WARP_MERGE  1  /* 1: lanes of a warp that hit the same voxel in the same step are merged
                                    (match.any + redux) before one accumulator atomic; 0 (default): every
                                    contribution issues its own atomic */
-#define TSDF_OPT_STEPS_PER_THREAD 2  /* march steps k handled by one contribution thread: 1, 2 (default) or 4 */
+#define TSDF_OPT_STEPS_PER_THREAD 2  /* march steps k handled by one contribution work item: 1, 2 or 4 (default) */
 #define TSDF_OPT_PDL         3  /* 1 (default): the kernels of one integrate call use programmatic dependent
                                    launch, so each may be scheduled while the previous one drains; 0: plain
                                    stream order */

@@ -108,7 +108,7 @@ struct tsdf_map {
     size_t stage_cap = 0;
     // tuning options
     bool merge = false;             // warp match-merge before the accumulator atomics
-    int kpt = 2;                    // march steps per contribution thread (1, 2 or 4)
+    int kpt = 4;                    // march steps per contribution item (1, 2 or 4)
     bool pdl = true;                // programmatic dependent launch between the scan's kernels
     // optional per-kernel event timing
     bool prof = false;
@@ -343,6 +343,8 @@ static int integrate_dev(tsdf_map* map, const float* points_dev, int64_t n, cons
         a.fo[ax] = (float)map->origin[ax];
         a.fe[ax] = (float)(map->origin[ax] + map->p.dims[ax]);
         a.cmask[ax] = map->geom.cmask[ax];
+        a.dmask[ax] = (uint32_t)map->p.dims[ax] - 1u;
+        a.omod[ax] = (uint32_t)((unsigned long long)map->origin[ax] & (unsigned long long)(map->p.dims[ax] - 1));
     }
     a.lcx = map->geom.lcx;
     a.lcxy = map->geom.lcxy;

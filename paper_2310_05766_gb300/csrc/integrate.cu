@@ -8,8 +8,8 @@
 //   safety margin) stays outside the window box is dropped, since none of its
 //   samples could land in the window. Order is kept within a CTA, so
 //   neighbouring rays stay neighbours.
-// contrib (K-B): one thread per (live ray, group of KPT steps k), k = -K..K;
-//   lanes of a warp are 32 consecutive live rays. For each of its steps the
+// contrib (K-B): persistent; a warp takes work items (32 consecutive live
+//   rays, a group of KPT steps k of k = -K..K), one ray per lane. For each of its steps the
 //   thread walks the fill samples j = -J..J (Eq. 3 / Eq. 4) in warp lock-step.
 //   A sample inside the window yields (voxel, q), q the int16 code of the
 //   truncated projective distance of the voxel centre, and issues one
@@ -152,107 +152,123 @@ __global__ void __launch_bounds__(256) rays_kernel(const ScanArgs a, const MapDe
     }
 }
 
+// Exact integer value of an integer-valued float x with 0 <= x < 2^22 (and of
+// rint(x) for |x| < 2^22), via one float add and one integer subtract: the
+// add places the integer in the low mantissa bits.
+__device__ __forceinline__ int small_int(float x) { return __float_as_int(fa(x, 12582912.0f)) - 0x4B400000; }
+
+// Contribution work items: (block of 32 consecutive live rays, group of KPT
+// steps). The grid is persistent (it fills the GPU once); each warp walks the
+// items with a grid stride and loads the next item's rays while it processes
+// the current one.
 template <int MODE, bool MERGE, int KPT>
 __global__ void __launch_bounds__(256) contrib_kernel(const ScanArgs a, const MapDev m) {
     __shared__ unsigned long long red[8];
-    const int ray = blockIdx.x * blockDim.x + threadIdx.x;
-    const int k0 = (int)blockIdx.y * KPT - a.K;
     const unsigned lane = threadIdx.x & 31u;
-    __shared__ unsigned s_nlive;
+    const unsigned gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
     pdl_trigger();
     pdl_wait();   // ray list and live count come from the rays kernel
-    // One load of the live count per CTA (a load per warp would make every
-    // warp of the grid hit the same L2 line).
-    if (threadIdx.x == 0) s_nlive = __ldcg(&m.ctr->live_count);
-    // The ray buffers hold a.n entries, so the loads are in bounds whatever
-    // the live count; entries at or beyond it are ignored.
-    float4 A = make_float4(0.f, 0.f, 0.f, -1.f);
-    float4 B = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (ray < a.n) {
-        A = m.ray_a[ray];
-        B = m.ray_b[ray];
-    }
-    __syncthreads();
-    const unsigned nlive = s_nlive;
-    if ((unsigned)ray >= nlive) A.w = -1.f;
-    if (blockIdx.x * blockDim.x >= nlive) return;   // CTA-uniform: no live ray in this CTA
+    // The live count is read-only for this grid: the non-coherent load lets
+    // the warps of an SM share one L1 line instead of all hitting one L2 line.
+    const unsigned nlive = __ldg(&m.ctr->live_count);
+    const unsigned ngrp = (unsigned)(2 * a.K + KPT) / KPT;   // ceil((2K+1) / KPT)
+    const unsigned nitems = (nlive + 31u) / 32u * ngrp;
+    const float tx = a.t[0], ty = a.t[1], tz = a.t[2];
     unsigned hits = 0;
     unsigned last_brick = kNoVoxel;
-    const float r = A.w;
-    const float tx = a.t[0], ty = a.t[1], tz = a.t[2];
+
+    auto load_item = [&](unsigned item, float4& A, float4& B) {
+        const unsigned ray = (item / ngrp) * 32u + lane;
+        A = make_float4(0.f, 0.f, 0.f, -1.f);
+        B = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (item < nitems && ray < nlive) {
+            A = m.ray_a[ray];
+            B = m.ray_b[ray];
+        }
+    };
+    float4 A, B;
+    load_item(gwarp, A, B);
+    for (unsigned item = gwarp; item < nitems; item += nwarps) {   // warp-uniform
+        float4 An, Bn;
+        load_item(item + nwarps, An, Bn);   // prefetch the next item
+        const float r = A.w;                // dead lanes carry r = -1
+        const int k0 = (int)(item % ngrp) * KPT - a.K;
 #pragma unroll 1
-    for (int kk = 0; kk < KPT; ++kk) {
-        const int k = k0 + kk;
-        if (k > a.K) break;   // uniform
-        const float l = fa(r, fm((float)k, a.vs));
-        const bool lv = (r >= 0.f) && (l > 0.f);   // dead lanes carry r = -1
-        const int J = (lv && B.w != 0.f) ? __float2int_rd(fm(fm(a.dz, l), a.inv_vs)) : 0;
-        const int Jw = __reduce_max_sync(kFull, lv ? J : -1);   // -1: no live lane
-        const float bx = fa(tx, fm(A.x, l));
-        const float by = fa(ty, fm(A.y, l));
-        const float bz = fa(tz, fm(A.z, l));
-        for (int j = -Jw; j <= Jw; ++j) {   // warp-uniform bounds
-            // every lane evaluates the sample; lanes outside their own fill
-            // range or outside the window are masked out (no divergent branches)
-            const float jd = fm((float)j, a.vs);
-            const float fx = floorf(fm(fa(bx, fm(B.x, jd)), a.inv_vs));
-            const float fy = floorf(fm(fa(by, fm(B.y, jd)), a.inv_vs));
-            const float fz = floorf(fm(fa(bz, fm(B.z, jd)), a.inv_vs));
-            const bool act = lv && j >= -J && j <= J && fx >= a.fo[0] && fx < a.fe[0] && fy >= a.fo[1] &&
-                             fy < a.fe[1] && fz >= a.fo[2] && fz < a.fe[2];
-            const int gx = (int)fx, gy = (int)fy, gz = (int)fz;
-            const unsigned brick = (((unsigned)(gz >> 3) & a.cmask[2]) << a.lcxy) |
-                                   (((unsigned)(gy >> 3) & a.cmask[1]) << a.lcx) |
-                                   ((unsigned)(gx >> 3) & a.cmask[0]);
-            const unsigned word = (brick << 9) | ((unsigned)(gz & 7) << 6) | ((unsigned)(gy & 7) << 3) |
-                                  (unsigned)(gx & 7);
-            // voxel centre: (float)g + 0.5 is fx + 0.5 exactly (|g| < 2^24)
-            const float cx = fm(fa(fx, 0.5f), a.vs);
-            const float cy = fm(fa(fy, 0.5f), a.vs);
-            const float cz = fm(fa(fz, 0.5f), a.vs);
-            const float proj = fa(fa(fm(fs(cx, tx), A.x), fm(fs(cy, ty), A.y)), fm(fs(cz, tz), A.z));
-            const float d = fminf(fmaxf(fs(r, proj), -a.tau), a.tau);
-            int q = __float2int_rn(fm(d, a.qs));
-            q = max(-kQMax, min(kQMax, q));
-            bool leader = act;
-            if (MERGE) {
-                if (__ballot_sync(kFull, act) == 0u) continue;   // warp-uniform
-                const unsigned peers = __match_any_sync(kFull, act ? word : kNoVoxel);
-                leader = act && lane == (unsigned)(__ffs(peers) - 1);
-                if (MODE == 0) {
-                    const int s = __reduce_add_sync(peers, q);
-                    if (leader)
-                        atomicAdd(m.acc + word,
-                                  ((unsigned long long)__popc(peers) << 40) + (unsigned long long)(long long)s);
+        for (int kk = 0; kk < KPT; ++kk) {
+            const int k = k0 + kk;
+            if (k > a.K) break;   // uniform
+            const float l = fa(r, fm((float)k, a.vs));
+            const bool lv = (r >= 0.f) && (l > 0.f);
+            const int J = (lv && B.w != 0.f) ? __float2int_rd(fm(fm(a.dz, l), a.inv_vs)) : 0;
+            const int Jw = __reduce_max_sync(kFull, lv ? J : -1);   // -1: no live lane
+            const float bx = fa(tx, fm(A.x, l));
+            const float by = fa(ty, fm(A.y, l));
+            const float bz = fa(tz, fm(A.z, l));
+            for (int j = -Jw; j <= Jw; ++j) {   // warp-uniform bounds
+                // every lane evaluates the sample; lanes outside their own fill
+                // range or outside the window are masked out (no divergent branches)
+                const float jd = fm((float)j, a.vs);
+                const float fx = floorf(fm(fa(bx, fm(B.x, jd)), a.inv_vs));
+                const float fy = floorf(fm(fa(by, fm(B.y, jd)), a.inv_vs));
+                const float fz = floorf(fm(fa(bz, fm(B.z, jd)), a.inv_vs));
+                const bool act = lv && j >= -J && j <= J && fx >= a.fo[0] && fx < a.fe[0] && fy >= a.fo[1] &&
+                                 fy < a.fe[1] && fz >= a.fo[2] && fz < a.fe[2];
+                // window-relative index (exact: both integers below 2^24), then the ring slot
+                const unsigned rx = ((unsigned)small_int(fs(fx, a.fo[0])) + a.omod[0]) & a.dmask[0];
+                const unsigned ry = ((unsigned)small_int(fs(fy, a.fo[1])) + a.omod[1]) & a.dmask[1];
+                const unsigned rz = ((unsigned)small_int(fs(fz, a.fo[2])) + a.omod[2]) & a.dmask[2];
+                const unsigned brick = ((rz >> 3) << a.lcxy) | ((ry >> 3) << a.lcx) | (rx >> 3);
+                const unsigned word = (brick << 9) | ((rz & 7u) << 6) | ((ry & 7u) << 3) | (rx & 7u);
+                // voxel centre: (float)g + 0.5 is fx + 0.5 exactly (|g| < 2^24)
+                const float cx = fm(fa(fx, 0.5f), a.vs);
+                const float cy = fm(fa(fy, 0.5f), a.vs);
+                const float cz = fm(fa(fz, 0.5f), a.vs);
+                const float proj = fa(fa(fm(fs(cx, tx), A.x), fm(fs(cy, ty), A.y)), fm(fs(cz, tz), A.z));
+                const float d = fminf(fmaxf(fs(r, proj), -a.tau), a.tau);
+                // rint (ties to even) of |d qs| <= 32767.x < 2^22, as an exact float add
+                int q = small_int(fm(d, a.qs));
+                q = max(-kQMax, min(kQMax, q));
+                bool leader = act;
+                if (MERGE) {
+                    if (__ballot_sync(kFull, act) == 0u) continue;   // warp-uniform
+                    const unsigned peers = __match_any_sync(kFull, act ? word : kNoVoxel);
+                    leader = act && lane == (unsigned)(__ffs(peers) - 1);
+                    if (MODE == 0) {
+                        const int s = __reduce_add_sync(peers, q);
+                        if (leader)
+                            atomicAdd(m.acc + word,
+                                      ((unsigned long long)__popc(peers) << 40) + (unsigned long long)(long long)s);
+                    } else {
+                        const unsigned key = ((unsigned)abs(q) << 1) | (q < 0 ? 1u : 0u);
+                        const unsigned kmin = __reduce_min_sync(peers, key);
+                        if (leader) atomicMax(m.acc + word, 65536ull - kmin);
+                    }
                 } else {
-                    const unsigned key = ((unsigned)abs(q) << 1) | (q < 0 ? 1u : 0u);
-                    const unsigned kmin = __reduce_min_sync(peers, key);
-                    if (leader) atomicMax(m.acc + word, 65536ull - kmin);
+                    if (MODE == 0) {
+                        if (act) atomicAdd(m.acc + word, (1ull << 40) + (unsigned long long)(long long)q);
+                    } else {
+                        const unsigned key = ((unsigned)abs(q) << 1) | (q < 0 ? 1u : 0u);
+                        if (act) atomicMax(m.acc + word, 65536ull - key);
+                    }
                 }
-            } else {
-                if (MODE == 0) {
-                    if (act) atomicAdd(m.acc + word, (1ull << 40) + (unsigned long long)(long long)q);
-                } else {
-                    const unsigned key = ((unsigned)abs(q) << 1) | (q < 0 ? 1u : 0u);
-                    if (act) atomicMax(m.acc + word, 65536ull - key);
+                if (MODE == 1) hits += act ? 1u : 0u;
+                // mark the brick; skip when this lane marked it last or the lane
+                // below (usually the neighbouring ray) marks the same brick now
+                const unsigned below = __shfl_up_sync(kFull, leader ? brick : kNoVoxel, 1);
+                if (leader && brick != last_brick && (lane == 0 || below != brick)) {
+                    last_brick = brick;
+                    m.brick_flag[brick] = 1;
                 }
-            }
-            if (MODE == 1) hits += act ? 1u : 0u;
-            // mark the brick; skip when this lane marked it last or the lane
-            // below (usually the neighbouring ray) marks the same brick now
-            const unsigned below = __shfl_up_sync(kFull, leader ? brick : kNoVoxel, 1);
-            if (leader && brick != last_brick && (lane == 0 || below != brick)) {
-                last_brick = brick;
-                m.brick_flag[brick] = 1;
             }
         }
+        A = An;
+        B = Bn;
     }
-    (void)lane;
     if (MODE == 1) {
         // MIN_ABS keeps no contribution count per voxel: count them here
         const unsigned long long total = cta_sum<8>((unsigned long long)hits, red);
-        if (threadIdx.x == 0 && total)
-            atomicAdd(&m.ctr->part[(blockIdx.x + blockIdx.y * gridDim.x) % kParts].hits, total);
+        if (threadIdx.x == 0 && total) atomicAdd(&m.ctr->part[blockIdx.x % kParts].hits, total);
     }
 }
 
@@ -345,16 +361,13 @@ __global__ void __launch_bounds__(kApplyWarps * 32) apply_kernel(const MapDev m,
     __shared__ unsigned long long s_acc[kApplyWarps][kBrickVoxels];
     __shared__ uint16_t s_off[kApplyWarps][kBrickVoxels];
     __shared__ unsigned long long red_u[kApplyWarps], red_h[kApplyWarps];
-    __shared__ unsigned s_nb;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned w = threadIdx.x >> 5;
     const unsigned gwarp = blockIdx.x * kApplyWarps + w;
     const unsigned nwarps = gridDim.x * kApplyWarps;
     pdl_trigger();
     pdl_wait();   // list and accumulators come from the earlier kernels
-    if (threadIdx.x == 0) s_nb = __ldcg(&m.ctr->brick_count);   // one load per CTA
-    __syncthreads();
-    const unsigned nb = s_nb;
+    const unsigned nb = __ldg(&m.ctr->brick_count);   // read-only for this grid
     unsigned long long touched = 0, hits = 0;
     uint4* sg4 = reinterpret_cast<uint4*>(s_grid[w]);
     ulonglong2* sa2 = reinterpret_cast<ulonglong2*>(s_acc[w]);
@@ -466,14 +479,27 @@ cudaError_t launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+int persistent_ctas_256() {
+    // CTAs of 256 threads that fill every SM of the current device once (8 per SM)
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int slot = dev >= 0 && dev < 64 ? dev : 0;
+    if (cached[slot] == 0) {
+        int sms = 1;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cached[slot] = (sms > 0 ? sms : 1) * 8;
+    }
+    return cached[slot];
+}
+
 template <int MODE, bool MERGE>
 cudaError_t launch_contrib_k(const ScanArgs& a, const MapDev& m, int kpt, bool pdl, cudaStream_t s) {
-    const unsigned nk = (unsigned)(2 * a.K + 1);
-    const unsigned gx = (unsigned)((a.n + 255) / 256);
+    const dim3 grid((unsigned)persistent_ctas_256());
     switch (kpt) {
-        case 2: return launch(contrib_kernel<MODE, MERGE, 2>, dim3(gx, (nk + 1) / 2), dim3(256), s, pdl, a, m);
-        case 4: return launch(contrib_kernel<MODE, MERGE, 4>, dim3(gx, (nk + 3) / 4), dim3(256), s, pdl, a, m);
-        default: return launch(contrib_kernel<MODE, MERGE, 1>, dim3(gx, nk), dim3(256), s, pdl, a, m);
+        case 2: return launch(contrib_kernel<MODE, MERGE, 2>, grid, dim3(256), s, pdl, a, m);
+        case 4: return launch(contrib_kernel<MODE, MERGE, 4>, grid, dim3(256), s, pdl, a, m);
+        default: return launch(contrib_kernel<MODE, MERGE, 1>, grid, dim3(256), s, pdl, a, m);
     }
 }
 

@@ -151,6 +151,8 @@ extern "C" int tsdf_integrate_static(uint32_t* grid_dev, const tsdf_params* para
         a.fo[ax] = (float)params->origin[ax];
         a.fe[ax] = (float)(params->origin[ax] + params->dims[ax]);
         a.cmask[ax] = (uint32_t)params->dims[ax] / 8u - 1u;
+        a.dmask[ax] = (uint32_t)params->dims[ax] - 1u;
+        a.omod[ax] = (uint32_t)((unsigned long long)params->origin[ax] & (unsigned long long)(params->dims[ax] - 1));
     }
     a.lcx = ilog2((uint32_t)params->dims[0] / 8u);
     a.lcxy = a.lcx + ilog2((uint32_t)params->dims[1] / 8u);
@@ -160,7 +162,7 @@ extern "C" int tsdf_integrate_static(uint32_t* grid_dev, const tsdf_params* para
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = launch_rays(a, md, true, s);
-    if (e == cudaSuccess) e = launch_contrib(a, md, params->reduce, false, 2, true, s);
+    if (e == cudaSuccess) e = launch_contrib(a, md, params->reduce, false, 4, true, s);
     if (e == cudaSuccess) e = launch_compact(md, (uint32_t)bricks, true, s);
     if (e == cudaSuccess) e = launch_apply(md, params->reduce, params->w_max, num_sms * 8, true, s);
     if (e == cudaSuccess) e = launch_finish(md, true, s);

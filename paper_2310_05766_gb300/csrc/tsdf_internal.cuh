@@ -57,6 +57,8 @@ struct ScanArgs {
     float fe[3];                    // origin + dims as float (exact)
     uint32_t cmask[3];              // dims / 8 - 1 per axis
     uint32_t lcx, lcxy;             // log2(dims.x / 8), log2(dims.x / 8 * dims.y / 8)
+    uint32_t dmask[3];              // dims - 1 per axis
+    uint32_t omod[3];               // origin mod dims per axis (ring offset of the window origin)
 };
 
 // One brick slot that changes owner during a shift.
