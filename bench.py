@@ -39,6 +39,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "TSDF voxel updates/s (OS1-128-shaped scan)"
+# DRAM bytes (read + write) per launch from the committed ncu capture of these
+# kernels on this workload (profiles/contrib_apply_outdoor_128x1024.md). Reset
+# an entry to None whenever its kernel changes.
+NCU_DRAM_BYTES = {"contrib": 13.18e6 + 1.0e3, "apply": 27.36e6 + 0.07e6 + 3.0e3, "rays": 2.11e6}
 UNIT = "voxel_updates/s"
 N_SEQ = 100
 
@@ -317,7 +321,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                      "each kernel (that pass: %.1f us/scan; events serialise the kernels of a step)" %
                      (1e3 * float(sum(prof_step_ms)) / K),
         roofline=dict(kernel=kname, bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
-                      peak_source=f"{peak_kind} hbm_gbs", traffic=None,
+                      peak_source=f"{peak_kind} hbm_gbs", traffic=NCU_DRAM_BYTES.get(kname),
+                      alg_bytes_def=("16 B per point read + 8 B per touched voxel of the per-scan volume"
+                                     if kname == "contrib" else "16 B per touched voxel (volume read + grid RMW)"),
                       alg_bytes_per_launch=alg_bytes, avg_launch_us=k_avg_s * 1e6),
         e2e=dict(value=e2e_hits_all / t_e2e_max, unit=UNIT, h2d_bytes_per_step=int(16 * n_pts),
                  d2h_bytes_per_step=24, steps=n_e2e,
