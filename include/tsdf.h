@@ -186,6 +186,59 @@ int tsdf_profile_enable(tsdf_map* map, int32_t enable);
  * Errors: INVALID, CUDA. */
 int tsdf_profile_read(tsdf_map* map, tsdf_kernel_time* out, int32_t capacity, int32_t* count);
 
+/* ---- batched integration ---------------------------------------------------
+ * Integrates one scan into each of many maps in a single persistent
+ * cooperative launch: the phases of tsdf_integrate (ray set-up, contributions,
+ * brick compaction, Eq. 1 / Eq. 2 update, counters) run over all maps of the
+ * batch with a grid-wide barrier between phases, so maps of uneven size share
+ * the whole GPU and a batch costs one launch instead of five per map. Each map's
+ * result is bit-identical to tsdf_integrate of the same scan. The launch (a
+ * descriptor copy, a barrier reset and the kernel) is captured once into a CUDA
+ * graph and replayed; the descriptors are the only thing that changes. */
+typedef struct tsdf_batch tsdf_batch;   /* opaque; owns pinned and device descriptor buffers */
+
+#define TSDF_BATCH_OPT_GRAPH      1  /* 1 (default): replay a captured CUDA graph; 0: plain launches */
+#define TSDF_BATCH_OPT_AUTOTUNE   2  /* 1 (default): time every tuning configuration on the first calls and keep the fastest */
+#define TSDF_BATCH_OPT_CONFIG     3  /* fix the tuning configuration (0..5: {no merge, merge} x {4, 2, 1} steps per item); turns autotuning off */
+#define TSDF_BATCH_OPT_SPIN_LIMIT 4  /* polls before a grid-barrier wait gives up (default 2^24, about a second) */
+#define TSDF_BATCH_OPT_TEST_MISSING_ARRIVALS 5  /* test hook: the barrier waits for this many CTAs that do not exist (default 0) */
+
+/* Create a batch object for up to max_count (1..1024) maps per call, on the
+ * current device. Synchronous. Errors: INVALID, OOM, CUDA. */
+int tsdf_batch_create(int32_t max_count, tsdf_batch** out);
+
+/* Release a batch object (waits for the device). NULL is ignored. */
+int tsdf_batch_destroy(tsdf_batch* batch);
+
+/* Set an option (TSDF_BATCH_OPT_*). Host-side state. Errors: INVALID. */
+int tsdf_batch_set_option(tsdf_batch* batch, int32_t option, int64_t value);
+
+/* The tuning configuration in use: index, warp merge (0/1), steps per work
+ * item, and whether autotuning has finished (any pointer may be NULL). */
+int tsdf_batch_get_config(const tsdf_batch* batch, int32_t* config, int32_t* merge, int32_t* steps_per_item,
+                          int32_t* tuned);
+
+/* Integrate scan i (points_dev[i]: n[i] device float4 points, 16-byte
+ * aligned; poses + 12*i: host row-major 3x4 pose) into maps[i], for i <
+ * count (count <= max_count). The maps must be distinct and live on the batch's
+ * device; each keeps its own window (shift them separately). Asynchronous on
+ * `stream`; calls on one batch object must be serialised on one stream, and
+ * while a batch is in flight its maps must not be used on other streams.
+ * Per-map counters are available through tsdf_stats afterwards. A device-side
+ * barrier timeout is reported by tsdf_batch_sync; the maps of that batch are
+ * then in an undefined state. Errors: INVALID, OOM, CUDA. */
+int tsdf_batch_integrate(tsdf_batch* batch, tsdf_map* const* maps, const float* const* points_dev, const int64_t* n,
+                         const float* poses, int32_t count, void* stream);
+
+/* Convenience form of tsdf_batch_integrate with a batch object per host thread
+ * and device, created on first use (up to 1024 maps per call). */
+int tsdf_integrate_batch(tsdf_map* const* maps, const float* const* points_dev, const int64_t* n, const float* poses,
+                         int32_t count, void* stream);
+
+/* Wait for `stream` and report the last batch launch's status: TSDF_OK, or
+ * TSDF_ERR_TIMEOUT if a grid-barrier wait gave up. Errors: INVALID, CUDA. */
+int tsdf_batch_sync(tsdf_batch* batch, void* stream);
+
 /* ---- integration without device allocation ---------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory once they run: for example a real-time

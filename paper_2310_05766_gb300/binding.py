@@ -27,6 +27,11 @@ TSDF_MAX_POINTS = 1 << 22
 TSDF_OPT_WARP_MERGE = 1
 TSDF_OPT_STEPS_PER_THREAD = 2
 TSDF_OPT_PDL = 3
+TSDF_BATCH_OPT_GRAPH = 1
+TSDF_BATCH_OPT_AUTOTUNE = 2
+TSDF_BATCH_OPT_CONFIG = 3
+TSDF_BATCH_OPT_SPIN_LIMIT = 4
+TSDF_BATCH_OPT_TEST_MISSING_ARRIVALS = 5
 TSDF_STATIC_MAX_VOXELS = 1 << 21
 TSDF_STATIC_MAX_POINTS = 1 << 17
 
@@ -86,6 +91,13 @@ def lib():
     L.tsdf_set_option.argtypes = [vp, ctypes.c_int32, ctypes.c_int64]
     L.tsdf_profile_enable.argtypes = [vp, ctypes.c_int32]
     L.tsdf_profile_read.argtypes = [vp, P(tsdf_kernel_time), ctypes.c_int32, P(ctypes.c_int32)]
+    L.tsdf_batch_create.argtypes = [ctypes.c_int32, P(vp)]
+    L.tsdf_batch_destroy.argtypes = [vp]
+    L.tsdf_batch_set_option.argtypes = [vp, ctypes.c_int32, ctypes.c_int64]
+    L.tsdf_batch_get_config.argtypes = [vp] + [P(ctypes.c_int32)] * 4
+    L.tsdf_batch_integrate.argtypes = [vp, P(vp), P(vp), P(i64), f32p, ctypes.c_int32, vp]
+    L.tsdf_integrate_batch.argtypes = [P(vp), P(vp), P(i64), f32p, ctypes.c_int32, vp]
+    L.tsdf_batch_sync.argtypes = [vp, vp]
     L.tsdf_integrate_static.argtypes = [vp, P(tsdf_params), vp, i64, f32p, P(tsdf_scan_stats), vp]
     L.tsdf_error_string.argtypes = [i32]
     L.tsdf_error_string.restype = ctypes.c_char_p
@@ -93,7 +105,8 @@ def lib():
     for name in ("tsdf_map_create", "tsdf_map_destroy", "tsdf_integrate", "tsdf_integrate_host", "tsdf_shift",
                  "tsdf_read", "tsdf_write", "tsdf_stats", "tsdf_get_origin", "tsdf_grid_device_ptr",
                  "tsdf_last_cuda_error", "tsdf_profile_enable", "tsdf_profile_read", "tsdf_set_option",
-                 "tsdf_integrate_static"):
+                 "tsdf_integrate_static", "tsdf_batch_create", "tsdf_batch_destroy", "tsdf_batch_set_option",
+                 "tsdf_batch_get_config", "tsdf_batch_integrate", "tsdf_integrate_batch", "tsdf_batch_sync"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -235,6 +248,59 @@ def tsdf_integrate_static(grid_dev, params, points_dev, n: int, pose, stream=Non
                                        ctypes.byref(st) if want_stats else None, _stream_ptr(stream)),
            "tsdf_integrate_static")
     return dict(valid_rays=st.valid_rays, hits=st.hits, touched=st.touched) if want_stats else None
+
+
+def _batch_args(maps, points, poses):
+    count = len(maps)
+    assert len(points) == count and len(poses) == count
+    mh = (ctypes.c_void_p * count)(*[m if isinstance(m, int) else m.handle for m in maps])
+    ph = (ctypes.c_void_p * count)(*[p if isinstance(p, int) else p.data_ptr() for p in points])
+    nn = (ctypes.c_int64 * count)(*[0 if isinstance(p, int) else int(p.shape[0]) for p in points])
+    pa = np.ascontiguousarray(np.stack([np.asarray(x, np.float32).reshape(12) for x in poses]) if count else
+                              np.zeros((0, 12), np.float32))
+    return count, mh, ph, nn, pa
+
+
+def tsdf_batch_create(max_count: int) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().tsdf_batch_create(int(max_count), ctypes.byref(h)), "tsdf_batch_create")
+    return h.value
+
+
+def tsdf_batch_destroy(batch: int) -> None:
+    _check(lib().tsdf_batch_destroy(batch), "tsdf_batch_destroy")
+
+
+def tsdf_batch_set_option(batch: int, option: int, value: int) -> None:
+    _check(lib().tsdf_batch_set_option(batch, int(option), int(value)), "tsdf_batch_set_option")
+
+
+def tsdf_batch_get_config(batch: int) -> dict:
+    c, m, k, t = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().tsdf_batch_get_config(batch, ctypes.byref(c), ctypes.byref(m), ctypes.byref(k), ctypes.byref(t)),
+           "tsdf_batch_get_config")
+    return dict(config=c.value, merge=m.value, steps_per_item=k.value, tuned=bool(t.value))
+
+
+def tsdf_batch_integrate(batch: int, maps, points, poses, stream=None) -> None:
+    """maps: TsdfMap objects or handles; points: CUDA float32 (n_i, 4) tensors; poses: 12 floats each."""
+    count, mh, ph, nn, pa = _batch_args(maps, points, poses)
+    _check(lib().tsdf_batch_integrate(batch, mh, ph, nn, pa.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), count,
+                                      _stream_ptr(stream)), "tsdf_batch_integrate")
+
+
+def tsdf_integrate_batch(maps, points, poses, stream=None) -> None:
+    count, mh, ph, nn, pa = _batch_args(maps, points, poses)
+    _check(lib().tsdf_integrate_batch(mh, ph, nn, pa.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), count,
+                                      _stream_ptr(stream)), "tsdf_integrate_batch")
+
+
+def tsdf_batch_sync(batch: int, stream=None) -> int:
+    """Waits; returns TSDF_OK or TSDF_ERR_TIMEOUT (a device barrier gave up). Other errors raise."""
+    rc = lib().tsdf_batch_sync(batch, _stream_ptr(stream))
+    if rc not in (TSDF_OK, TSDF_ERR_TIMEOUT):
+        _check(rc, "tsdf_batch_sync")
+    return rc
 
 
 def tsdf_set_option(handle: int, option: int, value: int) -> None:

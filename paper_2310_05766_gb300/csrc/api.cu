@@ -315,11 +315,8 @@ static int ensure_rays(tsdf_map* map, int64_t n) {
     return TSDF_OK;
 }
 
-static int integrate_dev(tsdf_map* map, const float* points_dev, int64_t n, const float pose[12],
-                         cudaStream_t s) {
-    int rc = ensure_rays(map, n);
-    if (rc != TSDF_OK) return rc;
-    ScanArgs a{};
+static void fill_scan_args(const tsdf_map* map, const float* points_dev, int64_t n, const float pose[12], ScanArgs& a) {
+    a = ScanArgs{};
     a.pts = reinterpret_cast<const float4*>(points_dev);
     a.n = (int32_t)n;
     a.K = map->K;
@@ -348,6 +345,14 @@ static int integrate_dev(tsdf_map* map, const float* points_dev, int64_t n, cons
     }
     a.lcx = map->geom.lcx;
     a.lcxy = map->geom.lcxy;
+}
+
+static int integrate_dev(tsdf_map* map, const float* points_dev, int64_t n, const float pose[12],
+                         cudaStream_t s) {
+    int rc = ensure_rays(map, n);
+    if (rc != TSDF_OK) return rc;
+    ScanArgs a;
+    fill_scan_args(map, points_dev, n, pose, a);
     const bool pdl = map->pdl;
     cudaEvent_t e0 = n > 0 ? prof_mark(map, s) : nullptr;
     TSDF_CU(launch_rays(a, map->dev, pdl, s));
@@ -613,3 +618,25 @@ const char* tsdf_error_string(int code) {
 int tsdf_last_cuda_error(void) { return g_last_cuda_error; }
 
 }  // extern "C"
+
+namespace tsdf {
+
+int prepare_batch_item(::tsdf_map* map, const float* points_dev, int64_t n, const float pose[12], BatchItem* out) {
+    int rc = check_scan_args(map, points_dev, n, pose);
+    if (rc != TSDF_OK) return rc;
+    if (((uintptr_t)points_dev & 15u) != 0) return TSDF_ERR_INVALID;
+    DeviceScope ds(map->device);
+    rc = ensure_rays(map, n);
+    if (rc != TSDF_OK) return rc;
+    fill_scan_args(map, points_dev, n, pose, out->a);
+    out->m = map->dev;
+    out->reduce = map->p.reduce;
+    out->w_max = map->p.w_max;
+    out->bricks = (uint32_t)map->bricks;
+    out->pad = 0;
+    return TSDF_OK;
+}
+
+int map_device(const ::tsdf_map* map) { return map->device; }
+
+}  // namespace tsdf

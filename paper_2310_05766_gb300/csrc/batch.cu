@@ -1,0 +1,575 @@
+// Batched integration: one scan into each of many maps in ONE persistent
+// cooperative launch, optionally replayed from a captured CUDA graph.
+//
+// The kernel runs the five phases of the per-map path (rays, contrib,
+// compact, apply, finish; integrate_device.cuh) over all maps of the batch,
+// with a grid-wide barrier between phases. Work is spread over the whole GPU:
+// CTAs take ray blocks of any map, warps take (32-ray block, k-group) items of
+// any map, and so on, so maps of uneven size share the SMs. Per-map offsets
+// of the work known on the host (ray blocks, flag words) come with the
+// descriptors; those known only on the device (live rays, touched bricks) are
+// prefix-summed by every CTA after the barrier.
+//
+// The barrier is a counter plus generation word; each wait gives up after a
+// bounded number of polls, sets the batch's error word and makes every CTA
+// return, which the host reports as TSDF_ERR_TIMEOUT.
+//
+// Descriptors live in device memory, copied from a pinned host buffer by the
+// first node of the launch sequence, so one captured graph (copy, barrier
+// reset, kernel) serves every later batch: only the pinned buffer changes.
+// Two buffer sets alternate so the host can fill one while the GPU reads the
+// other.
+//
+// Tuning (warp merge, steps per work item) changes speed only: results are
+// bit-identical for every setting. With autotuning on, the first calls cycle
+// through the settings, timing each with events, and the fastest is kept.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "integrate_device.cuh"
+#include "../../include/tsdf.h"
+
+namespace tsdf {
+namespace {
+
+using namespace dev;
+
+constexpr int kBatchMax = 1024;               // maps per batch
+constexpr int kBatchThreads = 256;
+constexpr int kBatchWarps = kBatchThreads / 32;
+constexpr size_t kApplySmemPerWarp = kBrickVoxels * (4 + 8 + 2);   // grid, accumulator, offsets
+
+struct BatchHeader {
+    int32_t count;
+    uint32_t ray_tasks;                      // total CTA ray tasks (256 points each)
+    uint32_t word_tasks;                     // total warp compaction tasks (32 flag words each)
+    uint32_t extra_arrivals;                 // test hook: barrier arrivals that never come
+    long long spin_limit;                    // polls before a barrier wait gives up
+    uint32_t ray_prefix[kBatchMax + 1];      // exclusive prefix of ray tasks per map
+    uint32_t word_prefix[kBatchMax + 1];     // exclusive prefix of compaction tasks per map
+};
+
+struct BatchSync {
+    unsigned arrive;
+    unsigned generation;
+    unsigned error;
+    unsigned pad;
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier for a cooperative launch; false if the batch failed.
+__device__ bool grid_barrier(BatchSync* s, unsigned arrivals, long long spin_limit) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned gen = ld_acquire(&s->generation);
+        __threadfence();
+        const unsigned prev = atomicAdd(&s->arrive, 1u);
+        bool good = true;
+        if (prev == arrivals - 1u) {
+            atomicExch(&s->arrive, 0u);
+            __threadfence();
+            atomicAdd(&s->generation, 1u);
+        } else {
+            long long polls = 0;
+            while (ld_acquire(&s->generation) == gen) {
+                if (++polls > spin_limit || ld_acquire(&s->error) != 0u) {
+                    atomicOr(&s->error, 1u);
+                    good = false;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        ok = good && ld_acquire(&s->error) == 0u;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Index of the map whose segment [prefix[i], prefix[i+1]) holds t.
+__device__ __forceinline__ int find_segment(const uint32_t* prefix, int count, uint32_t t) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Block-wide exclusive prefix of per-map values v(i), written to out[0..count].
+template <typename F>
+__device__ void block_prefix(int count, F v, uint32_t* out) {
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const unsigned lane = threadIdx.x;
+        uint32_t carry = 0;
+        for (int base = 0; base < count; base += 32) {
+            const int i = base + (int)lane;
+            const uint32_t x = i < count ? v(i) : 0u;
+            uint32_t incl = x;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= (unsigned)o) incl += y;
+            }
+            if (i < count) out[i] = carry + incl - x;
+            carry += __shfl_sync(kFull, incl, 31);
+        }
+        if (lane == 0) out[count] = carry;
+    }
+    __syncthreads();
+}
+
+// Adds a warp's counter to the map's partial slot (lane 0 after a warp sum).
+__device__ __forceinline__ void warp_add(unsigned long long v, unsigned long long* dst) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if ((threadIdx.x & 31u) == 0 && v) atomicAdd(dst, v);
+}
+
+template <bool MERGE, int KPT>
+__global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem* __restrict__ items,
+                                                                  const BatchHeader* __restrict__ hdr,
+                                                                  BatchSync* sync) {
+    extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ uint32_t s_prefix[kBatchMax + 1];
+    __shared__ unsigned wl[8], wv[8], cta_base;
+    const int count = hdr->count;
+    const unsigned arrivals = gridDim.x + hdr->extra_arrivals;
+    const long long spin = hdr->spin_limit;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned w = threadIdx.x >> 5;
+    const unsigned gwarp = blockIdx.x * kBatchWarps + w;
+    const unsigned nwarps = gridDim.x * kBatchWarps;
+
+    // ---- phase 1: ray set-up and compaction, one CTA task = 256 points of a map
+    for (uint32_t t = blockIdx.x; t < hdr->ray_tasks; t += gridDim.x) {
+        const int i = find_segment(hdr->ray_prefix, count, t);
+        rays_task<false>(items[i].a, items[i].m, (int)((t - hdr->ray_prefix[i]) * 256u), t, wl, wv, &cta_base);
+        __syncthreads();
+    }
+    if (!grid_barrier(sync, arrivals, spin)) return;
+
+    // ---- phase 2: contributions; per map ceil(live / 32) * ceil((2K+1) / KPT) warp items
+    block_prefix(count, [&](int i) {
+        const unsigned nl = __ldcg(&items[i].m.ctr->live_count);
+        return (nl + 31u) / 32u * ((unsigned)(2 * items[i].a.K + KPT) / KPT);
+    }, s_prefix);
+    {
+        unsigned last_brick = kNoVoxel;
+        int cur = -1;
+        unsigned hits = 0;
+        for (uint32_t g = gwarp; g < s_prefix[count]; g += nwarps) {   // warp-uniform
+            const int i = find_segment(s_prefix, count, g);
+            if (i != cur) {
+                if (cur >= 0 && items[cur].reduce == 1)
+                    warp_add(hits, &items[cur].m.ctr->part[gwarp % kParts].hits);
+                hits = 0;
+                last_brick = kNoVoxel;
+                cur = i;
+            }
+            const BatchItem& it = items[i];
+            const unsigned ngrp = (unsigned)(2 * it.a.K + KPT) / KPT;
+            const unsigned local = g - s_prefix[i];
+            const unsigned nl = __ldcg(&it.m.ctr->live_count);
+            float4 A, B;
+            load_rays(it.m, nl, (local / ngrp) * 32u + lane, A, B);
+            if (it.reduce == 0) contrib_item<0, MERGE, KPT>(it.a, it.m, local % ngrp, A, B, hits, last_brick);
+            else contrib_item<1, MERGE, KPT>(it.a, it.m, local % ngrp, A, B, hits, last_brick);
+        }
+        if (cur >= 0 && items[cur].reduce == 1) warp_add(hits, &items[cur].m.ctr->part[gwarp % kParts].hits);
+    }
+    if (!grid_barrier(sync, arrivals, spin)) return;
+
+    // ---- phase 3: brick flags -> brick lists, one warp task = 32 flag words of a map
+    for (uint32_t t = gwarp; t < hdr->word_tasks; t += nwarps) {
+        const int i = find_segment(hdr->word_prefix, count, t);
+        const unsigned nwords = (items[i].bricks + 3u) / 4u;
+        compact_words(items[i].m, (t - hdr->word_prefix[i]) * 32u + lane, nwords);
+    }
+    if (!grid_barrier(sync, arrivals, spin)) return;
+
+    // ---- phase 4: Eq. 1 / Eq. 2 on the touched bricks, one warp per brick
+    block_prefix(count, [&](int i) { return __ldcg(&items[i].m.ctr->brick_count); }, s_prefix);
+    {
+        uint32_t* s_grid = reinterpret_cast<uint32_t*>(dyn + w * kApplySmemPerWarp);
+        unsigned long long* s_acc = reinterpret_cast<unsigned long long*>(dyn + w * kApplySmemPerWarp + 2048);
+        uint16_t* s_off = reinterpret_cast<uint16_t*>(dyn + w * kApplySmemPerWarp + 6144);
+        int cur = -1;
+        unsigned long long touched = 0, hits = 0;
+        for (uint32_t g = gwarp; g < s_prefix[count]; g += nwarps) {   // warp-uniform
+            const int i = find_segment(s_prefix, count, g);
+            if (i != cur) {
+                if (cur >= 0) {
+                    warp_add(touched, &items[cur].m.ctr->part[gwarp % kParts].touched);
+                    if (items[cur].reduce == 0) warp_add(hits, &items[cur].m.ctr->part[gwarp % kParts].hits);
+                }
+                touched = hits = 0;
+                cur = i;
+            }
+            const BatchItem& it = items[i];
+            if (it.reduce == 0) apply_brick<0>(it.m, it.w_max, g - s_prefix[i], s_grid, s_acc, s_off, touched, hits);
+            else apply_brick<1>(it.m, it.w_max, g - s_prefix[i], s_grid, s_acc, s_off, touched, hits);
+        }
+        if (cur >= 0) {
+            warp_add(touched, &items[cur].m.ctr->part[gwarp % kParts].touched);
+            if (items[cur].reduce == 0) warp_add(hits, &items[cur].m.ctr->part[gwarp % kParts].hits);
+        }
+    }
+    if (!grid_barrier(sync, arrivals, spin)) return;
+
+    // ---- phase 5: publish each map's counters
+    for (uint32_t i = gwarp; i < (uint32_t)count; i += nwarps) finish_warp(items[i].m);
+}
+
+constexpr size_t kDynSmem = kBatchWarps * kApplySmemPerWarp;
+
+using BatchKernel = void (*)(const BatchItem*, const BatchHeader*, BatchSync*);
+
+BatchKernel kernel_for(bool merge, int kpt) {
+    if (merge) return kpt == 1 ? batch_kernel<true, 1> : kpt == 2 ? batch_kernel<true, 2> : batch_kernel<true, 4>;
+    return kpt == 1 ? batch_kernel<false, 1> : kpt == 2 ? batch_kernel<false, 2> : batch_kernel<false, 4>;
+}
+
+struct Config {
+    bool merge;
+    int kpt;
+};
+const Config kConfigs[] = {{false, 4}, {false, 2}, {false, 1}, {true, 4}, {true, 2}, {true, 1}};
+constexpr int kNumConfigs = 6;
+
+}  // namespace
+}  // namespace tsdf
+
+using namespace tsdf;
+
+struct tsdf_batch {
+    int device = 0;
+    int max_count = 0;
+    int grid = 0;                          // co-resident CTAs of the cooperative launch
+    // two alternating descriptor sets
+    struct Slot {
+        unsigned char* host = nullptr;     // pinned: header + items
+        unsigned char* dev = nullptr;
+        cudaEvent_t done = nullptr;        // recorded after the set's launch
+        bool pending = false;
+        cudaGraphExec_t exec[kNumConfigs] = {};
+    } slot[2];
+    int next_slot = 0;
+    BatchSync* sync = nullptr;
+    size_t desc_bytes = 0;
+    // options
+    bool use_graph = true;
+    bool autotune = true;
+    int config = 0;                        // index into kConfigs
+    int extra_arrivals = 0;
+    long long spin_limit = 1LL << 24;
+    // autotuning state
+    int trials_per_config = 2;
+    int tuned = -1;                        // chosen config, -1 while tuning
+    struct Trial {
+        int config;
+        cudaEvent_t start, stop;
+    };
+    std::vector<Trial> trials;
+    float best_ms[kNumConfigs] = {};
+    int n_timed[kNumConfigs] = {};
+    cudaStream_t capture_stream = nullptr;
+};
+
+namespace {
+
+int cu_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? TSDF_ERR_OOM : TSDF_ERR_CUDA; }
+
+struct DevScope {
+    int prev = -1;
+    bool changed = false;
+    explicit DevScope(int d) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != d) changed = cudaSetDevice(d) == cudaSuccess;
+    }
+    ~DevScope() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+void free_batch(tsdf_batch* b) {
+    if (!b) return;
+    for (auto& s : b->slot) {
+        for (auto& e : s.exec)
+            if (e) cudaGraphExecDestroy(e);
+        if (s.host) cudaFreeHost(s.host);
+        cudaFree(s.dev);
+        if (s.done) cudaEventDestroy(s.done);
+    }
+    for (auto& t : b->trials) {
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
+    cudaFree(b->sync);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    delete b;
+}
+
+// Enqueue copy + barrier reset + cooperative kernel for descriptor slot `si`.
+cudaError_t enqueue(tsdf_batch* b, int si, int cfg, cudaStream_t s) {
+    tsdf_batch::Slot& sl = b->slot[si];
+    cudaError_t e = cudaMemcpyAsync(sl.dev, sl.host, b->desc_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->sync, 0, sizeof(BatchSync), s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)b->grid);
+    lc.blockDim = dim3(kBatchThreads);
+    lc.dynamicSmemBytes = kDynSmem;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    const BatchItem* items = reinterpret_cast<const BatchItem*>(sl.dev + sizeof(BatchHeader));
+    const BatchHeader* hdr = reinterpret_cast<const BatchHeader*>(sl.dev);
+    return cudaLaunchKernelEx(&lc, kernel_for(kConfigs[cfg].merge, kConfigs[cfg].kpt), items, hdr, b->sync);
+}
+
+// Collect finished autotuning trials; pick the fastest config once all have run.
+void harvest_trials(tsdf_batch* b) {
+    std::vector<tsdf_batch::Trial> keep;
+    for (auto& t : b->trials) {
+        if (cudaEventQuery(t.stop) != cudaSuccess) {
+            keep.push_back(t);
+            continue;
+        }
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.start, t.stop) == cudaSuccess) {
+            if (b->n_timed[t.config] == 0 || ms < b->best_ms[t.config]) b->best_ms[t.config] = ms;
+            b->n_timed[t.config]++;
+        }
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
+    b->trials.swap(keep);
+    bool all = true;
+    for (int c = 0; c < kNumConfigs; ++c) all = all && b->n_timed[c] >= b->trials_per_config;
+    if (all && b->tuned < 0) {
+        int best = 0;
+        for (int c = 1; c < kNumConfigs; ++c)
+            if (b->best_ms[c] < b->best_ms[best]) best = c;
+        b->tuned = best;
+        b->config = best;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int tsdf_batch_create(int32_t max_count, tsdf_batch** out) {
+    if (!out || max_count < 1 || max_count > kBatchMax) return TSDF_ERR_INVALID;
+    *out = nullptr;
+    tsdf_batch* b = new tsdf_batch();
+    b->max_count = max_count;
+    cudaError_t e = cudaGetDevice(&b->device);
+    int sms = 0, per_sm = 0;
+    for (int c = 0; c < kNumConfigs && e == cudaSuccess; ++c)
+        e = cudaFuncSetAttribute(kernel_for(kConfigs[c].merge, kConfigs[c].kpt),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    // the grid must be co-resident for every config: take the smallest occupancy
+    int occ = 1 << 30;
+    for (int c = 0; c < kNumConfigs && e == cudaSuccess; ++c) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(kConfigs[c].merge, kConfigs[c].kpt),
+                                                          kBatchThreads, kDynSmem);
+        occ = std::min(occ, per_sm);
+    }
+    if (e == cudaSuccess && occ < 1) e = cudaErrorInvalidConfiguration;
+    b->grid = sms * (occ > 0 ? occ : 1);
+    b->desc_bytes = sizeof(BatchHeader) + (size_t)max_count * sizeof(BatchItem);
+    for (auto& s : b->slot) {
+        if (e == cudaSuccess) e = cudaMallocHost(&s.host, b->desc_bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&s.dev, b->desc_bytes);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+        if (e == cudaSuccess) std::memset(s.host, 0, b->desc_bytes);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->sync, sizeof(BatchSync));
+    if (e == cudaSuccess) e = cudaMemset(b->sync, 0, sizeof(BatchSync));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_batch(b);
+        return cu_fail(e);
+    }
+    *out = b;
+    return TSDF_OK;
+}
+
+int tsdf_batch_destroy(tsdf_batch* b) {
+    if (!b) return TSDF_OK;
+    DevScope ds(b->device);
+    cudaDeviceSynchronize();
+    free_batch(b);
+    return TSDF_OK;
+}
+
+int tsdf_batch_set_option(tsdf_batch* b, int32_t option, int64_t value) {
+    if (!b) return TSDF_ERR_INVALID;
+    switch (option) {
+        case TSDF_BATCH_OPT_GRAPH:
+            if (value != 0 && value != 1) return TSDF_ERR_INVALID;
+            b->use_graph = value != 0;
+            return TSDF_OK;
+        case TSDF_BATCH_OPT_AUTOTUNE:
+            if (value != 0 && value != 1) return TSDF_ERR_INVALID;
+            b->autotune = value != 0;
+            return TSDF_OK;
+        case TSDF_BATCH_OPT_CONFIG:
+            if (value < 0 || value >= kNumConfigs) return TSDF_ERR_INVALID;
+            b->config = (int)value;
+            b->autotune = false;
+            return TSDF_OK;
+        case TSDF_BATCH_OPT_SPIN_LIMIT:
+            if (value < 1) return TSDF_ERR_INVALID;
+            b->spin_limit = value;
+            return TSDF_OK;
+        case TSDF_BATCH_OPT_TEST_MISSING_ARRIVALS:
+            if (value < 0 || value > 1024) return TSDF_ERR_INVALID;
+            b->extra_arrivals = (int)value;
+            return TSDF_OK;
+        default: return TSDF_ERR_INVALID;
+    }
+}
+
+int tsdf_batch_get_config(const tsdf_batch* b, int32_t* config, int32_t* merge, int32_t* steps_per_item,
+                          int32_t* tuned) {
+    if (!b) return TSDF_ERR_INVALID;
+    if (config) *config = b->config;
+    if (merge) *merge = kConfigs[b->config].merge ? 1 : 0;
+    if (steps_per_item) *steps_per_item = kConfigs[b->config].kpt;
+    if (tuned) *tuned = b->tuned >= 0 ? 1 : 0;
+    return TSDF_OK;
+}
+
+int tsdf_batch_integrate(tsdf_batch* b, tsdf_map* const* maps, const float* const* points_dev, const int64_t* n,
+                         const float* poses, int32_t count, void* stream) {
+    if (!b || !maps || !points_dev || !n || !poses || count < 0 || count > b->max_count) return TSDF_ERR_INVALID;
+    if (count == 0) return TSDF_OK;
+    for (int i = 0; i < count; ++i) {
+        if (!maps[i] || map_device(maps[i]) != b->device) return TSDF_ERR_INVALID;
+        for (int j = 0; j < i; ++j)
+            if (maps[j] == maps[i]) return TSDF_ERR_INVALID;   // one scan per map per batch
+    }
+    DevScope ds(b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int si = b->next_slot;
+    tsdf_batch::Slot& sl = b->slot[si];
+    if (sl.pending) {   // the GPU may still be reading this slot's host buffer
+        cudaError_t e = cudaEventSynchronize(sl.done);
+        if (e != cudaSuccess) return cu_fail(e);
+        sl.pending = false;
+    }
+    BatchHeader* hdr = reinterpret_cast<BatchHeader*>(sl.host);
+    BatchItem* items = reinterpret_cast<BatchItem*>(sl.host + sizeof(BatchHeader));
+    uint32_t rt = 0, wt = 0;
+    for (int i = 0; i < count; ++i) {
+        int rc = prepare_batch_item(maps[i], points_dev[i], n[i], poses + 12 * i, &items[i]);
+        if (rc != TSDF_OK) return rc;
+        hdr->ray_prefix[i] = rt;
+        hdr->word_prefix[i] = wt;
+        rt += (uint32_t)((n[i] + 255) / 256);
+        wt += ((items[i].bricks + 3u) / 4u + 31u) / 32u;
+    }
+    hdr->ray_prefix[count] = rt;
+    hdr->word_prefix[count] = wt;
+    hdr->count = count;
+    hdr->ray_tasks = rt;
+    hdr->word_tasks = wt;
+    hdr->extra_arrivals = (uint32_t)b->extra_arrivals;
+    hdr->spin_limit = b->spin_limit;
+
+    if (b->autotune && b->tuned < 0) harvest_trials(b);
+    int cfg = b->config;
+    bool timing = false;
+    if (b->autotune && b->tuned < 0) {
+        // cycle through the configurations until each has been timed enough
+        int pending_of[kNumConfigs] = {};
+        for (auto& t : b->trials) pending_of[t.config]++;
+        for (int c = 0; c < kNumConfigs; ++c) {
+            if (b->n_timed[c] + pending_of[c] < b->trials_per_config) {
+                cfg = c;
+                timing = true;
+                break;
+            }
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    tsdf_batch::Trial trial{cfg, nullptr, nullptr};
+    if (timing) {
+        e = cudaEventCreate(&trial.start);
+        if (e == cudaSuccess) e = cudaEventCreate(&trial.stop);
+        if (e == cudaSuccess) e = cudaEventRecord(trial.start, s);
+    }
+    if (e == cudaSuccess) {
+        if (b->use_graph) {
+            if (!sl.exec[cfg]) {
+                // capture copy + reset + kernel once for this slot and config
+                cudaGraph_t g = nullptr;
+                e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    cudaError_t e2 = enqueue(b, si, cfg, b->capture_stream);
+                    e = cudaStreamEndCapture(b->capture_stream, &g);
+                    if (e == cudaSuccess) e = e2;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&sl.exec[cfg], g, 0);
+                if (g) cudaGraphDestroy(g);
+            }
+            if (e == cudaSuccess) e = cudaGraphLaunch(sl.exec[cfg], s);
+        } else {
+            e = enqueue(b, si, cfg, s);
+        }
+    }
+    if (e == cudaSuccess && timing) {
+        e = cudaEventRecord(trial.stop, s);
+        if (e == cudaSuccess) b->trials.push_back(trial);
+    } else if (timing) {
+        if (trial.start) cudaEventDestroy(trial.start);
+        if (trial.stop) cudaEventDestroy(trial.stop);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(sl.done, s);
+    if (e != cudaSuccess) return cu_fail(e);
+    sl.pending = true;
+    b->next_slot ^= 1;
+    return TSDF_OK;
+}
+
+int tsdf_integrate_batch(tsdf_map* const* maps, const float* const* points_dev, const int64_t* n, const float* poses,
+                         int32_t count, void* stream) {
+    // one batch object per host thread and device, created on first use
+    static thread_local tsdf_batch* per_device[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TSDF_ERR_CUDA;
+    if (!per_device[dev]) {
+        int rc = tsdf_batch_create(kBatchMax, &per_device[dev]);
+        if (rc != TSDF_OK) return rc;
+    }
+    return tsdf_batch_integrate(per_device[dev], maps, points_dev, n, poses, count, stream);
+}
+
+int tsdf_batch_sync(tsdf_batch* b, void* stream) {
+    if (!b) return TSDF_ERR_INVALID;
+    DevScope ds(b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned err = 0;
+    cudaError_t e = cudaMemcpyAsync(&err, &b->sync->error, sizeof(err), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cu_fail(e);
+    return err ? TSDF_ERR_TIMEOUT : TSDF_OK;
+}
+
+}  // extern "C"

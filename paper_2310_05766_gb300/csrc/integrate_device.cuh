@@ -1,0 +1,368 @@
+// Device-side bodies of the integration phases, shared by the per-map kernels
+// (integrate.cu) and the batched persistent kernel (batch.cu), so that both
+// run the same arithmetic. See integrate.cu for the method.
+#pragma once
+
+#include "tsdf_internal.cuh"
+
+namespace tsdf {
+namespace dev {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr unsigned kNoVoxel = 0xFFFFFFFFu;
+
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+
+// Programmatic dependent launch: wait for the preceding grid's completion
+// (and visibility of its writes) / let the next grid be scheduled early.
+// Both are no-ops for a grid launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Sum of a 64-bit value over the CTA (every thread must call it); the result
+// is valid in thread 0.
+template <int NWARPS>
+__device__ __forceinline__ unsigned long long cta_sum(unsigned long long v, unsigned long long* smem) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if ((threadIdx.x & 31u) == 0) smem[threadIdx.x >> 5] = v;
+    __syncthreads();
+    unsigned long long s = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < NWARPS; ++w) s += smem[w];
+    return s;
+}
+
+// Exact integer value of an integer-valued float x with 0 <= x < 2^22 (and of
+// rint(x) for |x| < 2^22), via one float add and one integer subtract: the
+// add places the integer in the low mantissa bits.
+__device__ __forceinline__ int small_int(float x) { return __float_as_int(fa(x, 12582912.0f)) - 0x4B400000; }
+
+// ---- rays: the CTA's 256 threads set up points [base, base + 256) of a scan
+// and append the live ones to the map's ray list. smem: wl[8], wv[8], base.
+// With PDL the wait for the preceding grid comes before the first access to
+// the map's counters and ray list.
+template <bool PDL>
+__device__ __forceinline__ void rays_task(const ScanArgs& a, const MapDev& m, int base, unsigned part, unsigned* wl,
+                                          unsigned* wv, unsigned* cta_base) {
+    const int i = base + (int)threadIdx.x;
+    const unsigned lane = threadIdx.x & 31u;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool in = i < a.n;
+    if (in) p = __ldg(a.pts + i);   // the caller's points: no dependency on earlier grids
+    if (PDL) pdl_trigger();
+    const float tx = a.t[0], ty = a.t[1], tz = a.t[2];
+    const float pwx = fa(fa(fa(fm(a.R[0], p.x), fm(a.R[1], p.y)), fm(a.R[2], p.z)), tx);
+    const float pwy = fa(fa(fa(fm(a.R[3], p.x), fm(a.R[4], p.y)), fm(a.R[5], p.z)), ty);
+    const float pwz = fa(fa(fa(fm(a.R[6], p.x), fm(a.R[7], p.y)), fm(a.R[8], p.z)), tz);
+    const float vx = fs(pwx, tx), vy = fs(pwy, ty), vz = fs(pwz, tz);
+    const float r2 = fa(fa(fm(vx, vx), fm(vy, vy)), fm(vz, vz));
+    const float r = __fsqrt_rn(r2);
+    const bool valid = in && (r >= a.rmin) && (r <= a.rmax);
+
+    float4 ra = make_float4(0.f, 0.f, 0.f, -1.f);
+    float4 rb = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool live = false;
+    if (valid) {
+        const float dx = __fdiv_rn(vx, r), dy = __fdiv_rn(vy, r), dz = __fdiv_rn(vz, r);
+        const float ux = a.R[2], uy = a.R[5], uz = a.R[8];   // sensor z axis in the world
+        const float ax = fs(fm(dy, uz), fm(dz, uy));
+        const float ay = fs(fm(dz, ux), fm(dx, uz));
+        const float az = fs(fm(dx, uy), fm(dy, ux));
+        const float ivx = fs(fm(dy, az), fm(dz, ay));
+        const float ivy = fs(fm(dz, ax), fm(dx, az));
+        const float ivz = fs(fm(dx, ay), fm(dy, ax));
+        const float n2 = fa(fa(fm(ivx, ivx), fm(ivy, ivy)), fm(ivz, ivz));
+        const bool fill = a.fill && n2 >= 1e-12f;
+        if (fill) {
+            const float nn = __fsqrt_rn(n2);
+            rb = make_float4(__fdiv_rn(ivx, nn), __fdiv_rn(ivy, nn), __fdiv_rn(ivz, nn), 1.f);
+        }
+        // conservative culling: distance from the hit to the window box against
+        // the reach of the march (tau + fill height + margin)
+        const float hx = tx + dx * r, hy = ty + dy * r, hz = tz + dz * r;
+        const float ex = fmaxf(fmaxf(a.win_lo[0] - hx, hx - a.win_hi[0]), 0.f);
+        const float ey = fmaxf(fmaxf(a.win_lo[1] - hy, hy - a.win_hi[1]), 0.f);
+        const float ez = fmaxf(fmaxf(a.win_lo[2] - hz, hz - a.win_hi[2]), 0.f);
+        const float reach = a.tau + (fill ? a.dz * (r + a.tau) : 0.f) + 2.f * a.vs +
+                            1e-4f * (fabsf(tx) + fabsf(ty) + fabsf(tz) + r);
+        live = ex * ex + ey * ey + ez * ez <= reach * reach;
+        ra = make_float4(dx, dy, dz, r);
+    }
+    // CTA-level compaction of the live rays: one list atomic per CTA
+    const unsigned warp = threadIdx.x >> 5;
+    const unsigned lmask = __ballot_sync(kFull, live);
+    const unsigned vmask = __ballot_sync(kFull, valid);
+    if (lane == 0) {
+        wl[warp] = __popc(lmask);
+        wv[warp] = __popc(vmask);
+    }
+    __syncthreads();
+    if (PDL) pdl_wait();   // the previous scan's finish kernel resets live_count and the counters
+    if (threadIdx.x == 0) {
+        unsigned tl = 0, tv = 0;
+        for (int w = 0; w < 8; ++w) {
+            tl += wl[w];
+            tv += wv[w];
+        }
+        *cta_base = tl ? atomicAdd(&m.ctr->live_count, tl) : 0u;
+        if (tv) atomicAdd(&m.ctr->part[part % kParts].valid, (unsigned long long)tv);
+    }
+    __syncthreads();
+    if (live) {
+        unsigned off = *cta_base + __popc(lmask & ((1u << lane) - 1u));
+        for (unsigned w = 0; w < warp; ++w) off += wl[w];
+        m.ray_a[off] = ra;
+        m.ray_b[off] = rb;
+    }
+}
+
+// ---- contrib: rays of one 32-ray block (one per lane, dead lanes r = -1)
+__device__ __forceinline__ void load_rays(const MapDev& m, unsigned nlive, unsigned ray, float4& A, float4& B) {
+    A = make_float4(0.f, 0.f, 0.f, -1.f);
+    B = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ray < nlive) {
+        A = m.ray_a[ray];
+        B = m.ray_b[ray];
+    }
+}
+
+// One warp: the steps of k-group `grp` (KPT steps) of its 32 rays.
+template <int MODE, bool MERGE, int KPT>
+__device__ __forceinline__ void contrib_item(const ScanArgs& a, const MapDev& m, unsigned grp, const float4 A,
+                                             const float4 B, unsigned& hits, unsigned& last_brick) {
+    const unsigned lane = threadIdx.x & 31u;
+    const float tx = a.t[0], ty = a.t[1], tz = a.t[2];
+    const float r = A.w;                // dead lanes carry r = -1
+    const int k0 = (int)grp * KPT - a.K;
+#pragma unroll 1
+    for (int kk = 0; kk < KPT; ++kk) {
+        const int k = k0 + kk;
+        if (k > a.K) break;   // uniform
+        const float l = fa(r, fm((float)k, a.vs));
+        const bool lv = (r >= 0.f) && (l > 0.f);
+        const int J = (lv && B.w != 0.f) ? __float2int_rd(fm(fm(a.dz, l), a.inv_vs)) : 0;
+        const int Jw = __reduce_max_sync(kFull, lv ? J : -1);   // -1: no live lane
+        const float bx = fa(tx, fm(A.x, l));
+        const float by = fa(ty, fm(A.y, l));
+        const float bz = fa(tz, fm(A.z, l));
+        for (int j = -Jw; j <= Jw; ++j) {   // warp-uniform bounds
+            // every lane evaluates the sample; lanes outside their own fill
+            // range or outside the window are masked out (no divergent branches)
+            const float jd = fm((float)j, a.vs);
+            const float fx = floorf(fm(fa(bx, fm(B.x, jd)), a.inv_vs));
+            const float fy = floorf(fm(fa(by, fm(B.y, jd)), a.inv_vs));
+            const float fz = floorf(fm(fa(bz, fm(B.z, jd)), a.inv_vs));
+            const bool act = lv && j >= -J && j <= J && fx >= a.fo[0] && fx < a.fe[0] && fy >= a.fo[1] &&
+                             fy < a.fe[1] && fz >= a.fo[2] && fz < a.fe[2];
+            // window-relative index (exact: both integers below 2^24), then the ring slot
+            const unsigned rx = ((unsigned)small_int(fs(fx, a.fo[0])) + a.omod[0]) & a.dmask[0];
+            const unsigned ry = ((unsigned)small_int(fs(fy, a.fo[1])) + a.omod[1]) & a.dmask[1];
+            const unsigned rz = ((unsigned)small_int(fs(fz, a.fo[2])) + a.omod[2]) & a.dmask[2];
+            const unsigned brick = ((rz >> 3) << a.lcxy) | ((ry >> 3) << a.lcx) | (rx >> 3);
+            const unsigned word = (brick << 9) | ((rz & 7u) << 6) | ((ry & 7u) << 3) | (rx & 7u);
+            // voxel centre: (float)g + 0.5 is fx + 0.5 exactly (|g| < 2^24)
+            const float cx = fm(fa(fx, 0.5f), a.vs);
+            const float cy = fm(fa(fy, 0.5f), a.vs);
+            const float cz = fm(fa(fz, 0.5f), a.vs);
+            const float proj = fa(fa(fm(fs(cx, tx), A.x), fm(fs(cy, ty), A.y)), fm(fs(cz, tz), A.z));
+            const float d = fminf(fmaxf(fs(r, proj), -a.tau), a.tau);
+            // rint (ties to even) of |d qs| <= 32767.x < 2^22, as an exact float add
+            int q = small_int(fm(d, a.qs));
+            q = max(-kQMax, min(kQMax, q));
+            bool leader = act;
+            if (MERGE) {
+                if (__ballot_sync(kFull, act) == 0u) continue;   // warp-uniform
+                const unsigned peers = __match_any_sync(kFull, act ? word : kNoVoxel);
+                leader = act && lane == (unsigned)(__ffs(peers) - 1);
+                if (MODE == 0) {
+                    const int s = __reduce_add_sync(peers, q);
+                    if (leader)
+                        atomicAdd(m.acc + word,
+                                  ((unsigned long long)__popc(peers) << 40) + (unsigned long long)(long long)s);
+                } else {
+                    const unsigned key = ((unsigned)abs(q) << 1) | (q < 0 ? 1u : 0u);
+                    const unsigned kmin = __reduce_min_sync(peers, key);
+                    if (leader) atomicMax(m.acc + word, 65536ull - kmin);
+                }
+            } else {
+                if (MODE == 0) {
+                    if (act) atomicAdd(m.acc + word, (1ull << 40) + (unsigned long long)(long long)q);
+                } else {
+                    const unsigned key = ((unsigned)abs(q) << 1) | (q < 0 ? 1u : 0u);
+                    if (act) atomicMax(m.acc + word, 65536ull - key);
+                }
+            }
+            if (MODE == 1) hits += act ? 1u : 0u;
+            // mark the brick; skip when this lane marked it last or the lane
+            // below (usually the neighbouring ray) marks the same brick now
+            const unsigned below = __shfl_up_sync(kFull, leader ? brick : kNoVoxel, 1);
+            if (leader && brick != last_brick && (lane == 0 || below != brick)) {
+                last_brick = brick;
+                m.brick_flag[brick] = 1;
+            }
+        }
+    }
+}
+
+// Eq. 1 / Eq. 2 for one voxel. Returns the new grid word.
+__device__ __forceinline__ uint32_t update_voxel(uint32_t word, long long S, long long W, int32_t w_max) {
+    const long long gv = (long long)(int16_t)(word & 0xFFFFu);
+    const long long gw = (long long)(int16_t)(word >> 16);
+    const long long num = gv * gw + S;
+    const long long den = gw + W;
+    const unsigned long long an = (unsigned long long)(num < 0 ? -num : num);
+    const unsigned long long top = 2ull * an + (unsigned long long)den;
+    const unsigned long long bot = 2ull * (unsigned long long)den;
+    const unsigned long long qv = top / bot;
+    const long long nv = num < 0 ? -(long long)qv : (long long)qv;
+    const long long nw = den > w_max ? (long long)w_max : den;
+    return (uint32_t)(uint16_t)(int16_t)nv | ((uint32_t)nw << 16);
+}
+
+// Decode one accumulator and update its voxel; returns the voxel's number of
+// contributions (WSUM) or 1 (MIN_ABS), 0 if untouched. WSUM accumulators
+// whose sum fits 31 bits and count fits 15 bits (the common case) take an
+// all-32-bit path with the same result as the 64-bit one.
+template <int MODE>
+__device__ __forceinline__ unsigned decode_apply(unsigned long long P, uint32_t& word, int32_t w_max) {
+    if (P == 0ull) return 0u;
+    if (MODE == 0) {
+        const unsigned lo = (unsigned)P, hi = (unsigned)(P >> 32);
+        const unsigned hb = hi & 0xFFu;   // bits 32..39 of the 40-bit sum
+        const bool small = ((hb == 0u) && (int)lo >= 0) || ((hb == 0xFFu) && (int)lo < 0);
+        const int S32 = (int)lo;
+        const unsigned W32 = (hi >> 8) + (S32 < 0 ? 1u : 0u);
+        const int gw = (int)(int16_t)(word >> 16);
+        if (small && W32 < 32768u && gw >= 0 && S32 > -(1 << 30) && S32 < (1 << 30)) {
+            const int gv = (int)(int16_t)(word & 0xFFFFu);
+            const int num = gv * gw + S32;                  // |gv gw| < 2^30, |S| < 2^30
+            const unsigned den = (unsigned)gw + W32;        // < 2^16
+            const unsigned an = (unsigned)(num < 0 ? -num : num);
+            const unsigned q = (2u * an + den) / (2u * den);   // < 2^32 by the bounds above
+            const int nv = num < 0 ? -(int)q : (int)q;
+            const unsigned nw = den > (unsigned)w_max ? (unsigned)w_max : den;
+            word = (uint32_t)(uint16_t)(int16_t)nv | (nw << 16);
+            return W32;
+        }
+        const long long S = ((long long)(P << 24)) >> 24;   // sign-extended low 40 bits
+        const long long W = (long long)((P - (unsigned long long)S) >> 40);
+        word = update_voxel(word, S, W, w_max);
+        return (unsigned)W;
+    } else {
+        const unsigned key = 65536u - (unsigned)P;
+        const int mag = (int)(key >> 1);
+        word = update_voxel(word, (key & 1u) ? -mag : mag, 1, w_max);
+        return 1u;
+    }
+}
+
+// ---- compact: lane i of the warp turns flag word i (4 bricks) into list
+// entries and clears it; the warp takes one list atomic.
+__device__ __forceinline__ void compact_words(const MapDev& m, unsigned i, unsigned nwords) {
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned f = 0;
+    if (i < nwords) f = reinterpret_cast<const uint32_t*>(m.brick_flag)[i];
+    // bytes are 0 or 1: one bit per touched brick in bits 0, 8, 16, 24
+    const unsigned bits = (f & 1u) | ((f >> 7) & 2u) | ((f >> 14) & 4u) | ((f >> 21) & 8u);
+    const unsigned cnt = __popc(bits);
+    unsigned incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= (unsigned)o) incl += v;
+    }
+    const unsigned total = __shfl_sync(kFull, incl, 31);
+    if (total == 0u) return;   // warp-uniform
+    unsigned base = 0;
+    if (lane == 31) base = atomicAdd(&m.ctr->brick_count, total);
+    base = __shfl_sync(kFull, base, 31) + incl - cnt;
+    if (bits) {
+        reinterpret_cast<uint32_t*>(m.brick_flag)[i] = 0u;
+        for (unsigned b = 0; b < 4; ++b)
+            if (bits & (1u << b)) m.brick_list[base++] = 4u * i + b;
+    }
+}
+
+// ---- apply: one warp updates listed brick number i of the map. Shared
+// memory per warp: s_grid[512] words, s_acc[512] accumulators, s_off[512].
+template <int MODE>
+__device__ __forceinline__ void apply_brick(const MapDev& m, int32_t w_max, unsigned i, uint32_t* s_grid,
+                                            unsigned long long* s_acc, uint16_t* s_off, unsigned long long& touched,
+                                            unsigned long long& hits) {
+    const unsigned lane = threadIdx.x & 31u;
+    uint4* sg4 = reinterpret_cast<uint4*>(s_grid);
+    ulonglong2* sa2 = reinterpret_cast<ulonglong2*>(s_acc);
+    const unsigned brick = m.brick_list[i];
+    // coalesced, bank-conflict-free 16-byte copies of the brick into shared
+    // memory: accumulator pair p = 32 v + lane holds voxels 2p and 2p + 1
+    const uint4* gp = reinterpret_cast<const uint4*>(m.grid + ((size_t)brick << 9));
+    ulonglong2* ap = reinterpret_cast<ulonglong2*>(m.acc + ((size_t)brick << 9));
+    unsigned nz = 0;   // bit 2v (2v+1): voxel 2(32 v + lane) (+1) has a non-zero accumulator
+#pragma unroll
+    for (int v = 0; v < 4; ++v) sg4[32 * v + lane] = gp[32 * v + lane];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        const ulonglong2 a2 = ap[32 * v + lane];
+        sa2[32 * v + lane] = a2;
+        nz |= (a2.x != 0ull ? 1u : 0u) << (2 * v);
+        nz |= (a2.y != 0ull ? 1u : 0u) << (2 * v + 1);
+    }
+    const unsigned cnt = __popc(nz);
+    unsigned incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= (unsigned)o) incl += t;
+    }
+    const unsigned total = __shfl_sync(kFull, incl, 31);
+    unsigned pos = incl - cnt;
+    for (unsigned bits = nz; bits; bits &= bits - 1u) {
+        const unsigned b = __ffs(bits) - 1u;
+        s_off[pos++] = (uint16_t)(2u * (32u * (b >> 1) + lane) + (b & 1u));
+    }
+    __syncwarp();
+    // Eq. 1 / Eq. 2 over the touched voxels only, one per lane
+    for (unsigned e = lane; e < total; e += 32u) {
+        const unsigned off = s_off[e];
+        uint32_t word = s_grid[off];
+        hits += decode_apply<MODE>(s_acc[off], word, w_max);
+        s_grid[off] = word;
+    }
+    touched += lane == 0 ? total : 0u;
+    __syncwarp();
+    uint4* gpw = reinterpret_cast<uint4*>(m.grid + ((size_t)brick << 9));
+#pragma unroll
+    for (int v = 0; v < 4; ++v) gpw[32 * v + lane] = sg4[32 * v + lane];
+    if (nz) {
+#pragma unroll
+        for (int v = 0; v < 8; ++v)
+            if (nz & (3u << (2 * v))) ap[32 * v + lane] = make_ulonglong2(0ull, 0ull);
+    }
+    __syncwarp();
+}
+
+// ---- finish: one warp (lane = counter slot) publishes the scan's counters
+// and clears the per-scan state.
+__device__ __forceinline__ void finish_warp(const MapDev& m) {
+    MapCounters* c = m.ctr;
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned long long v = c->part[lane].valid, h = c->part[lane].hits, u = c->part[lane].touched;
+    c->part[lane].valid = 0ull;
+    c->part[lane].hits = 0ull;
+    c->part[lane].touched = 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+        v += __shfl_xor_sync(kFull, v, o);
+        h += __shfl_xor_sync(kFull, h, o);
+        u += __shfl_xor_sync(kFull, u, o);
+    }
+    if (lane == 0) {
+        c->last_valid = (long long)v;
+        c->last_hits = (long long)h;
+        c->last_touched = (long long)u;
+        c->live_count = 0u;
+        c->brick_count = 0u;
+    }
+}
+
+}  // namespace dev
+}  // namespace tsdf

@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+struct tsdf_map;   // host-side map object (defined in api.cu)
+
 namespace tsdf {
 
 constexpr int32_t kQMax = 32767;
@@ -75,6 +77,22 @@ struct WindowGeom {
     uint32_t cmask[3];
     uint32_t lcx, lcxy;
 };
+
+// One scan of a batch: everything the batched kernel needs about it.
+struct BatchItem {
+    ScanArgs a;
+    MapDev m;
+    int32_t reduce;
+    int32_t w_max;
+    uint32_t bricks;
+    uint32_t pad;
+};
+
+
+// Host helpers implemented in api.cu for the batched path: validate a scan for
+// `map`, grow its ray buffers if needed and fill the batch item.
+int prepare_batch_item(::tsdf_map* map, const float* points_dev, int64_t n, const float pose[12], BatchItem* out);
+int map_device(const ::tsdf_map* map);
 
 // Launchers (return the cudaError_t of the launch).
 cudaError_t launch_rays(const ScanArgs& a, const MapDev& m, bool pdl, cudaStream_t s);

@@ -1,0 +1,185 @@
+"""Batched integration (one persistent cooperative launch for many maps) against
+the per-map path and the oracle: every map's grid and counters bit-exact."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_05766_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+class _DevView:
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<u4", "data": (ptr, False), "version": 2}
+
+
+def _grid(b, m):
+    d = m.params["dims"]
+    return torch.as_tensor(_DevView(b.tsdf_grid_device_ptr(m.handle), d[0] * d[1] * d[2]), device="cuda")
+
+
+def _small_batch(n_maps, seed, reduce_mix=True):
+    ws = synth.workload_batch(n_maps=n_maps, seed=seed, dims_choices=[(128, 128, 64), (256, 256, 64), (64, 64, 64)])
+    if reduce_mix:
+        for i, w in enumerate(ws):
+            w.params["reduce"] = i % 2
+    return ws
+
+
+def _run_batch(b, ws, batch=None, prefill_steps=0, options=None):
+    maps = [b.TsdfMap(w.params) for w in ws]
+    pts = [torch.from_numpy(w.scans[0]).cuda() for w in ws]
+    poses = [w.poses[0] for w in ws]
+    own = batch is None
+    if own:
+        batch = b.tsdf_batch_create(len(ws))
+    for opt, val in (options or {}).items():
+        b.tsdf_batch_set_option(batch, opt, val)
+    for _ in range(1 + prefill_steps):
+        b.tsdf_batch_integrate(batch, maps, pts, poses)
+    assert b.tsdf_batch_sync(batch) == b.TSDF_OK
+    if own:
+        b.tsdf_batch_destroy(batch)
+    return maps
+
+
+def _run_single(b, ws, repeats=1):
+    maps = [b.TsdfMap(w.params) for w in ws]
+    for _ in range(repeats):
+        for m, w in zip(maps, ws):
+            m.integrate(torch.from_numpy(w.scans[0]).cuda(), w.poses[0])
+    torch.cuda.synchronize()
+    return maps
+
+
+def _same(b, ma, mb):
+    for x, y in zip(ma, mb):
+        assert torch.equal(_grid(b, x), _grid(b, y))
+        assert x.stats() == y.stats()
+
+
+def test_batch_matches_oracle_and_single():
+    from paper_2310_05766_gb300 import binding as b
+    ws = _small_batch(6, seed=5)
+    mb = _run_batch(b, ws)
+    ms = _run_single(b, ws)
+    _same(b, mb, ms)
+    for m, w in zip(mb[:3], ws[:3]):
+        om = oracle.OracleMap(w.params)
+        om.integrate(w.scans[0], w.poses[0])
+        vo, wo = om.read()
+        vg, wg = m.read()
+        assert np.array_equal(vg, vo) and np.array_equal(wg, wo)
+        assert m.stats() == om.stats()
+    for m in mb + ms:
+        m.close()
+
+
+@pytest.mark.parametrize("config", range(6))
+@pytest.mark.parametrize("graph", [0, 1])
+def test_batch_every_config_same_result(config, graph):
+    from paper_2310_05766_gb300 import binding as b
+    ws = _small_batch(5, seed=11)
+    mb = _run_batch(b, ws, prefill_steps=1,
+                    options={b.TSDF_BATCH_OPT_CONFIG: config, b.TSDF_BATCH_OPT_GRAPH: graph})
+    ms = _run_single(b, ws, repeats=2)
+    _same(b, mb, ms)
+    for m in mb + ms:
+        m.close()
+
+
+def test_batch_autotune_settles_and_is_exact():
+    from paper_2310_05766_gb300 import binding as b
+    ws = _small_batch(4, seed=13)
+    batch = b.tsdf_batch_create(8)
+    mb = _run_batch(b, ws, batch=batch, prefill_steps=15)
+    cfg = b.tsdf_batch_get_config(batch)
+    b.tsdf_batch_integrate(batch, mb, [torch.from_numpy(w.scans[0]).cuda() for w in ws], [w.poses[0] for w in ws])
+    assert b.tsdf_batch_sync(batch) == b.TSDF_OK
+    assert b.tsdf_batch_get_config(batch)["tuned"], cfg
+    ms = _run_single(b, ws, repeats=17)
+    _same(b, mb, ms)
+    b.tsdf_batch_destroy(batch)
+    for m in mb + ms:
+        m.close()
+
+
+def test_batch_uneven_sizes_and_empty_scans():
+    from paper_2310_05766_gb300 import binding as b
+    ws = _small_batch(5, seed=17)
+    ws[1].scans[0] = ws[1].scans[0][:0]           # empty scan
+    ws[3].scans[0] = ws[3].scans[0][:37]          # ragged tail
+    mb = _run_batch(b, ws)
+    ms = _run_single(b, ws)
+    _same(b, mb, ms)
+    assert mb[1].stats() == dict(valid_rays=0, hits=0, touched=0)
+    for m in mb + ms:
+        m.close()
+
+
+def test_batched_64_maps_full_size():
+    """64 maps, beams {16..128} x azimuths {512..2048}, grids 256^3 / 512x512x128 at
+    0.064 m: one batched launch equals 64 per-map calls, and three maps equal the oracle."""
+    from paper_2310_05766_gb300 import binding as b
+    ws = synth.workload_batch(n_maps=64, seed=3)
+    mb = _run_batch(b, ws)
+    ms = _run_single(b, ws)
+    _same(b, mb, ms)
+    for m in ms:
+        m.close()
+    for k in (0, 17, 63):
+        om = oracle.OracleMap(ws[k].params)
+        om.integrate(ws[k].scans[0], ws[k].poses[0])
+        assert mb[k].stats() == om.stats()
+        vo, wo = om.read()
+        vg, wg = mb[k].read()
+        assert np.array_equal(vg, vo) and np.array_equal(wg, wo)
+    for m in mb:
+        m.close()
+
+
+def test_batch_rejects_bad_arguments():
+    from paper_2310_05766_gb300 import binding as b
+    ws = _small_batch(2, seed=19)
+    maps = [b.TsdfMap(w.params) for w in ws]
+    pts = [torch.from_numpy(w.scans[0]).cuda() for w in ws]
+    batch = b.tsdf_batch_create(2)
+    try:
+        with pytest.raises(b.TsdfError):   # the same map twice
+            b.tsdf_batch_integrate(batch, [maps[0], maps[0]], pts, [ws[0].poses[0]] * 2)
+        with pytest.raises(b.TsdfError):   # more maps than the object holds
+            b.tsdf_batch_integrate(batch, maps + maps[:1], pts + pts[:1], [w.poses[0] for w in ws] + [ws[0].poses[0]])
+        with pytest.raises(b.TsdfError):
+            b.tsdf_batch_set_option(batch, b.TSDF_BATCH_OPT_CONFIG, 6)
+    finally:
+        b.tsdf_batch_destroy(batch)
+        for m in maps:
+            m.close()
+
+
+def test_barrier_timeout_is_reported_and_context_survives():
+    """A grid-barrier wait that can never complete (one arrival that does not
+    exist) gives up after its poll limit: the host sees TSDF_ERR_TIMEOUT and the
+    GPU context stays usable."""
+    from paper_2310_05766_gb300 import binding as b
+    ws = _small_batch(2, seed=23)
+    maps = [b.TsdfMap(w.params) for w in ws]
+    pts = [torch.from_numpy(w.scans[0]).cuda() for w in ws]
+    batch = b.tsdf_batch_create(2)
+    b.tsdf_batch_set_option(batch, b.TSDF_BATCH_OPT_GRAPH, 0)
+    b.tsdf_batch_set_option(batch, b.TSDF_BATCH_OPT_AUTOTUNE, 0)
+    b.tsdf_batch_set_option(batch, b.TSDF_BATCH_OPT_SPIN_LIMIT, 20000)
+    b.tsdf_batch_set_option(batch, b.TSDF_BATCH_OPT_TEST_MISSING_ARRIVALS, 1)
+    b.tsdf_batch_integrate(batch, maps, pts, [w.poses[0] for w in ws])
+    assert b.tsdf_batch_sync(batch) == b.TSDF_ERR_TIMEOUT
+    b.tsdf_batch_destroy(batch)
+    for m in maps:
+        m.close()
+    # the context still works: a fresh batch and fresh maps give exact results
+    mb = _run_batch(b, ws)
+    ms = _run_single(b, ws)
+    _same(b, mb, ms)
+    for m in mb + ms:
+        m.close()
