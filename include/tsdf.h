@@ -202,6 +202,8 @@ typedef struct tsdf_batch tsdf_batch;   /* opaque; owns pinned and device descri
 #define TSDF_BATCH_OPT_CONFIG     3  /* fix the tuning configuration (0..5: {no merge, merge} x {4, 2, 1} steps per item); turns autotuning off */
 #define TSDF_BATCH_OPT_SPIN_LIMIT 4  /* polls before a grid-barrier wait gives up (default 2^24, about a second) */
 #define TSDF_BATCH_OPT_TEST_MISSING_ARRIVALS 5  /* test hook: the barrier waits for this many CTAs that do not exist (default 0) */
+#define TSDF_BATCH_OPT_GRID_FRACTION 6  /* percent (1..100, default 100) of the device's co-resident CTAs the launch uses,
+                                           so that launches on several streams can be resident together */
 
 /* Create a batch object for up to max_count (1..1024) maps per call, on the
  * current device. Synchronous. Errors: INVALID, OOM, CUDA. */
@@ -238,6 +240,87 @@ int tsdf_integrate_batch(tsdf_map* const* maps, const float* const* points_dev, 
 /* Wait for `stream` and report the last batch launch's status: TSDF_OK, or
  * TSDF_ERR_TIMEOUT if a grid-barrier wait gave up. Errors: INVALID, CUDA. */
 int tsdf_batch_sync(tsdf_batch* batch, void* stream);
+
+/* ---- serving: continuous batching over many map sessions -------------------
+ * A server keeps every session's map resident on the device and admits
+ * sessions against a device-memory budget. Requests are queued per session;
+ * a worker thread forms batches from the requests that have arrived (at most
+ * one per session per batch, at most one batch per session in flight, so each
+ * map sees its scans in submission order) and runs each batch as one batched
+ * integration on one of several streams, so that batches overlap on the
+ * device. A session's map is bit-identical whether its scans ran alone or in
+ * any mix of sessions. */
+typedef struct tsdf_server tsdf_server;   /* opaque; owns its sessions' maps, streams and pinned slabs */
+
+typedef struct tsdf_server_config {
+    int64_t hbm_budget_bytes;   /* device memory the sessions may take (grid, accumulator, ray buffers) */
+    int64_t max_points;         /* largest scan accepted, 1..TSDF_MAX_POINTS */
+    int32_t max_batch;          /* most sessions in one batch, 1..1024 */
+    int32_t streams;            /* batches that may be in flight together, 1..8 */
+    int32_t max_outstanding;    /* submitted requests not yet waited for (pinned slabs of max_points points) */
+    int32_t reserved;           /* must be 0 */
+} tsdf_server_config;
+
+typedef struct tsdf_request_result {
+    uint64_t ticket;
+    int32_t session;
+    int32_t status;             /* TSDF_OK or the error of the request */
+    int32_t batch_size;         /* requests in the batch that carried it */
+    int32_t reserved;
+    tsdf_scan_stats stats;      /* counters of the scan */
+    double t_submit_us;         /* host steady-clock microseconds: submitted, */
+    double t_start_us;          /* launched on the GPU, */
+    double t_done_us;           /* and seen complete by the worker */
+} tsdf_request_result;
+
+typedef struct tsdf_server_stats {
+    int32_t sessions;
+    int32_t reserved;
+    int64_t used_bytes;         /* device memory reserved by the sessions */
+    int64_t completed;          /* requests completed */
+    int64_t batches;            /* batches launched */
+    int64_t queued;             /* requests waiting to be batched */
+    double mean_batch;          /* requests per batch */
+} tsdf_server_stats;
+
+/* Create a server on the current device and start its worker thread.
+ * Allocates per stream a batch object and a device staging buffer of
+ * max_batch x max_points points, and max_outstanding pinned host slabs.
+ * Errors: INVALID, OOM, CUDA. */
+int tsdf_server_create(const tsdf_server_config* config, tsdf_server** out);
+
+/* Stop the worker, wait for the device and free everything, including the
+ * sessions' maps. Outstanding requests are dropped. NULL is ignored. */
+int tsdf_server_destroy(tsdf_server* server);
+
+/* Admit a session with a new map (params as for tsdf_map_create) if its memory
+ * fits the remaining budget. Synchronous (allocates). Errors: ADMISSION (over
+ * budget; retry after a session closes), INVALID, OOM, CUDA. */
+int tsdf_server_open_session(tsdf_server* server, const tsdf_params* params, int32_t* session);
+
+/* Close a session and free its map and budget. Errors: BUSY (requests not yet
+ * waited for), INVALID. */
+int tsdf_server_close_session(tsdf_server* server, int32_t session);
+
+/* Queue a scan for a session: n <= max_points host float4 points (copied
+ * before the call returns), a host pose, and optionally a new window origin
+ * (multiples of 8; the window is shifted before the scan is integrated).
+ * Returns a ticket for tsdf_server_wait. Errors: BUSY (max_outstanding
+ * requests not yet waited for), INVALID, or a previous worker error. */
+int tsdf_server_submit(tsdf_server* server, int32_t session, const float* points_host, int64_t n,
+                       const float pose[12], const int64_t* new_origin, uint64_t* ticket);
+
+/* Wait up to timeout_us (negative: forever) for a request and take its
+ * result (each ticket can be waited for once). Returns the request's status,
+ * or TIMEOUT (the request is still pending), or INVALID (unknown ticket). */
+int tsdf_server_wait(tsdf_server* server, uint64_t ticket, tsdf_request_result* out, int64_t timeout_us);
+
+/* The session's map, for tsdf_read and tsdf_stats once all of its requests
+ * have been waited for. Errors: INVALID. */
+int tsdf_server_session_map(tsdf_server* server, int32_t session, tsdf_map** out);
+
+/* Server-wide counters. Errors: INVALID. */
+int tsdf_server_get_stats(tsdf_server* server, tsdf_server_stats* out);
 
 /* ---- integration without device allocation ---------------------------------
  * The paper has no counterpart to this entry point; it exists for callers

@@ -32,6 +32,7 @@ TSDF_BATCH_OPT_AUTOTUNE = 2
 TSDF_BATCH_OPT_CONFIG = 3
 TSDF_BATCH_OPT_SPIN_LIMIT = 4
 TSDF_BATCH_OPT_TEST_MISSING_ARRIVALS = 5
+TSDF_BATCH_OPT_GRID_FRACTION = 6
 TSDF_STATIC_MAX_VOXELS = 1 << 21
 TSDF_STATIC_MAX_POINTS = 1 << 17
 
@@ -56,6 +57,23 @@ class tsdf_scan_stats(ctypes.Structure):
 
 class tsdf_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+class tsdf_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_points", ctypes.c_int64), ("max_batch", ctypes.c_int32),
+                ("streams", ctypes.c_int32), ("max_outstanding", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class tsdf_request_result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("session", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("batch_size", ctypes.c_int32), ("reserved", ctypes.c_int32), ("stats", tsdf_scan_stats),
+                ("t_submit_us", ctypes.c_double), ("t_start_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
+
+
+class tsdf_server_stats(ctypes.Structure):
+    _fields_ = [("sessions", ctypes.c_int32), ("reserved", ctypes.c_int32), ("used_bytes", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("batches", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("mean_batch", ctypes.c_double)]
 
 
 _lib = None
@@ -98,6 +116,14 @@ def lib():
     L.tsdf_batch_integrate.argtypes = [vp, P(vp), P(vp), P(i64), f32p, ctypes.c_int32, vp]
     L.tsdf_integrate_batch.argtypes = [P(vp), P(vp), P(i64), f32p, ctypes.c_int32, vp]
     L.tsdf_batch_sync.argtypes = [vp, vp]
+    L.tsdf_server_create.argtypes = [P(tsdf_server_config), P(vp)]
+    L.tsdf_server_destroy.argtypes = [vp]
+    L.tsdf_server_open_session.argtypes = [vp, P(tsdf_params), P(ctypes.c_int32)]
+    L.tsdf_server_close_session.argtypes = [vp, ctypes.c_int32]
+    L.tsdf_server_submit.argtypes = [vp, ctypes.c_int32, vp, i64, f32p, P(i64), P(ctypes.c_uint64)]
+    L.tsdf_server_wait.argtypes = [vp, ctypes.c_uint64, P(tsdf_request_result), i64]
+    L.tsdf_server_session_map.argtypes = [vp, ctypes.c_int32, P(vp)]
+    L.tsdf_server_get_stats.argtypes = [vp, P(tsdf_server_stats)]
     L.tsdf_integrate_static.argtypes = [vp, P(tsdf_params), vp, i64, f32p, P(tsdf_scan_stats), vp]
     L.tsdf_error_string.argtypes = [i32]
     L.tsdf_error_string.restype = ctypes.c_char_p
@@ -106,7 +132,9 @@ def lib():
                  "tsdf_read", "tsdf_write", "tsdf_stats", "tsdf_get_origin", "tsdf_grid_device_ptr",
                  "tsdf_last_cuda_error", "tsdf_profile_enable", "tsdf_profile_read", "tsdf_set_option",
                  "tsdf_integrate_static", "tsdf_batch_create", "tsdf_batch_destroy", "tsdf_batch_set_option",
-                 "tsdf_batch_get_config", "tsdf_batch_integrate", "tsdf_integrate_batch", "tsdf_batch_sync"):
+                 "tsdf_batch_get_config", "tsdf_batch_integrate", "tsdf_integrate_batch", "tsdf_batch_sync",
+                 "tsdf_server_create", "tsdf_server_destroy", "tsdf_server_open_session", "tsdf_server_close_session",
+                 "tsdf_server_submit", "tsdf_server_wait", "tsdf_server_session_map", "tsdf_server_get_stats"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -301,6 +329,64 @@ def tsdf_batch_sync(batch: int, stream=None) -> int:
     if rc not in (TSDF_OK, TSDF_ERR_TIMEOUT):
         _check(rc, "tsdf_batch_sync")
     return rc
+
+
+def tsdf_server_create(hbm_budget_bytes: int, max_points: int = 1 << 18, max_batch: int = 32, streams: int = 2,
+                       max_outstanding: int = 64) -> int:
+    cfg = tsdf_server_config(int(hbm_budget_bytes), int(max_points), int(max_batch), int(streams),
+                             int(max_outstanding), 0)
+    h = ctypes.c_void_p()
+    _check(lib().tsdf_server_create(ctypes.byref(cfg), ctypes.byref(h)), "tsdf_server_create")
+    return h.value
+
+
+def tsdf_server_destroy(server: int) -> None:
+    _check(lib().tsdf_server_destroy(server), "tsdf_server_destroy")
+
+
+def tsdf_server_open_session(server: int, params) -> int:
+    prm = params if isinstance(params, tsdf_params) else make_params(params)
+    sid = ctypes.c_int32()
+    _check(lib().tsdf_server_open_session(server, ctypes.byref(prm), ctypes.byref(sid)), "tsdf_server_open_session")
+    return sid.value
+
+
+def tsdf_server_close_session(server: int, session: int) -> None:
+    _check(lib().tsdf_server_close_session(server, int(session)), "tsdf_server_close_session")
+
+
+def tsdf_server_submit(server: int, session: int, points_host, pose, new_origin=None) -> int:
+    """points_host: float32 (n, 4) host array (copied before returning). Returns a ticket."""
+    pts = np.ascontiguousarray(points_host, dtype=np.float32).reshape(-1, 4)
+    pa, pp = _pose_arg(pose)
+    org = _i64_3(new_origin) if new_origin is not None else None
+    t = ctypes.c_uint64()
+    _check(lib().tsdf_server_submit(server, int(session), pts.ctypes.data, pts.shape[0], pp, org, ctypes.byref(t)),
+           "tsdf_server_submit")
+    return t.value
+
+
+def tsdf_server_wait(server: int, ticket: int, timeout_us: int = -1) -> dict:
+    r = tsdf_request_result()
+    rc = lib().tsdf_server_wait(server, ctypes.c_uint64(ticket), ctypes.byref(r), int(timeout_us))
+    if rc != TSDF_OK:
+        raise TsdfError(rc, "tsdf_server_wait")
+    return dict(ticket=r.ticket, session=r.session, status=r.status, batch_size=r.batch_size,
+                stats=dict(valid_rays=r.stats.valid_rays, hits=r.stats.hits, touched=r.stats.touched),
+                t_submit_us=r.t_submit_us, t_start_us=r.t_start_us, t_done_us=r.t_done_us)
+
+
+def tsdf_server_session_map(server: int, session: int) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().tsdf_server_session_map(server, int(session), ctypes.byref(h)), "tsdf_server_session_map")
+    return h.value
+
+
+def tsdf_server_get_stats(server: int) -> dict:
+    st = tsdf_server_stats()
+    _check(lib().tsdf_server_get_stats(server, ctypes.byref(st)), "tsdf_server_get_stats")
+    return dict(sessions=st.sessions, used_bytes=st.used_bytes, completed=st.completed, batches=st.batches,
+                queued=st.queued, mean_batch=st.mean_batch)
 
 
 def tsdf_set_option(handle: int, option: int, value: int) -> None:

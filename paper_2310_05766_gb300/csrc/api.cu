@@ -639,4 +639,12 @@ int prepare_batch_item(::tsdf_map* map, const float* points_dev, int64_t n, cons
 
 int map_device(const ::tsdf_map* map) { return map->device; }
 
+const long long* map_last_counters(const ::tsdf_map* map) { return &map->dev.ctr->last_valid; }
+
+int map_reserve_points(::tsdf_map* map, int64_t n) {
+    if (!map || n < 0 || n > TSDF_MAX_POINTS) return TSDF_ERR_INVALID;
+    DeviceScope ds(map->device);
+    return ensure_rays(map, n);
+}
+
 }  // namespace tsdf

@@ -254,7 +254,8 @@ using namespace tsdf;
 struct tsdf_batch {
     int device = 0;
     int max_count = 0;
-    int grid = 0;                          // co-resident CTAs of the cooperative launch
+    int grid = 0;                          // CTAs of the cooperative launch (co-resident)
+    int grid_max = 0;                      // all co-resident CTAs of the device
     // two alternating descriptor sets
     struct Slot {
         unsigned char* host = nullptr;     // pinned: header + items
@@ -390,7 +391,7 @@ int tsdf_batch_create(int32_t max_count, tsdf_batch** out) {
         occ = std::min(occ, per_sm);
     }
     if (e == cudaSuccess && occ < 1) e = cudaErrorInvalidConfiguration;
-    b->grid = sms * (occ > 0 ? occ : 1);
+    b->grid = b->grid_max = sms * (occ > 0 ? occ : 1);
     b->desc_bytes = sizeof(BatchHeader) + (size_t)max_count * sizeof(BatchItem);
     for (auto& s : b->slot) {
         if (e == cudaSuccess) e = cudaMallocHost(&s.host, b->desc_bytes);
@@ -437,6 +438,28 @@ int tsdf_batch_set_option(tsdf_batch* b, int32_t option, int64_t value) {
         case TSDF_BATCH_OPT_SPIN_LIMIT:
             if (value < 1) return TSDF_ERR_INVALID;
             b->spin_limit = value;
+            return TSDF_OK;
+        case TSDF_BATCH_OPT_GRID_FRACTION:
+            // percentage of the co-resident CTAs the launch uses (1..100); the
+            // captured graphs are rebuilt for the new grid
+            if (value < 1 || value > 100) return TSDF_ERR_INVALID;
+            {
+                const int g = std::max(1, (int)((long long)b->grid_max * value / 100));
+                if (g != b->grid) {
+                    for (auto& sl : b->slot) {
+                        if (sl.pending) {
+                            cudaEventSynchronize(sl.done);
+                            sl.pending = false;
+                        }
+                        for (auto& e : sl.exec)
+                            if (e) {
+                                cudaGraphExecDestroy(e);
+                                e = nullptr;
+                            }
+                    }
+                    b->grid = g;
+                }
+            }
             return TSDF_OK;
         case TSDF_BATCH_OPT_TEST_MISSING_ARRIVALS:
             if (value < 0 || value > 1024) return TSDF_ERR_INVALID;

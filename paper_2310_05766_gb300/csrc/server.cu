@@ -1,0 +1,420 @@
+// Serving loop: scan-integration requests from many map sessions, with
+// continuous batching on the GPU.
+//
+// Every session owns a map that stays resident in device memory; sessions are
+// admitted against a device-memory budget. Requests (a host point cloud, a
+// pose and optionally a new window origin) are copied into pinned slabs at
+// submission and queued per session. A worker thread forms batches from the
+// requests that have arrived: at most one request per session per batch and
+// at most one batch per session in flight, so each map sees its scans in
+// submission order. Each batch goes to a free stream slot: host-to-device
+// copies of the points, the shifts, one batched integration launch
+// (tsdf_batch_integrate, a persistent cooperative kernel over all maps of the
+// batch), and device-to-host copies of each map's counters, then an event.
+// While one slot's batch runs, requests that arrive are formed into the next
+// batch on the other slot, so copies and kernels of consecutive batches
+// overlap on the device. Because each map's integration is bit-identical in
+// any batch composition, a session's result is the same alone and in the mix.
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "tsdf_internal.cuh"
+#include "../../include/tsdf.h"
+
+using namespace tsdf;
+
+namespace {
+
+double now_us() {
+    using namespace std::chrono;
+    return (double)duration_cast<nanoseconds>(steady_clock::now().time_since_epoch()).count() * 1e-3;
+}
+
+struct Request {
+    uint64_t ticket = 0;
+    int32_t session = 0;
+    int64_t n = 0;
+    float pose[12];
+    bool shift = false;
+    int64_t origin[3] = {0, 0, 0};
+    float4* host = nullptr;   // pinned slab
+    int slab = -1;
+    tsdf_request_result res{};
+    bool done = false;
+};
+
+struct Session {
+    tsdf_map* map = nullptr;
+    size_t bytes = 0;
+    std::deque<Request*> queue;
+    bool in_flight = false;
+    int outstanding = 0;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    tsdf_batch* batch = nullptr;
+    float4* dev_pts = nullptr;          // max_batch x max_points
+    long long* counters = nullptr;      // pinned, max_batch x 3
+    cudaEvent_t done = nullptr;
+    std::vector<Request*> reqs;
+    bool busy = false;
+};
+
+size_t session_bytes(const tsdf_params& p, int64_t max_points) {
+    const size_t voxels = (size_t)p.dims[0] * p.dims[1] * p.dims[2];
+    const size_t bricks = voxels / 512;
+    return voxels * (4 + 8) + bricks * (1 + 4) + (size_t)max_points * 32 + 8192;
+}
+
+}  // namespace
+
+struct tsdf_server {
+    tsdf_server_config cfg{};
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread worker;
+    bool stop = false;
+    int worker_error = TSDF_OK;
+    std::map<int32_t, Session> sessions;
+    int32_t next_session = 1;
+    std::unordered_map<uint64_t, Request*> requests;
+    uint64_t next_ticket = 1;
+    size_t used_bytes = 0;
+    std::vector<Slot> slots;
+    std::vector<float4*> slabs;
+    std::vector<int> free_slabs;
+    // totals for tsdf_server_get_stats
+    int64_t completed = 0, batches = 0, batched_requests = 0;
+};
+
+namespace {
+
+void release_request(tsdf_server* s, Request* r) {
+    if (r->slab >= 0) s->free_slabs.push_back(r->slab);
+    delete r;
+}
+
+// Launch a batch on slot `k`; called with the lock held.
+int launch_batch(tsdf_server* s, int k, std::vector<Request*>& reqs) {
+    Slot& sl = s->slots[k];
+    const int count = (int)reqs.size();
+    std::vector<tsdf_map*> maps(count);
+    std::vector<const float*> pts(count);
+    std::vector<int64_t> ns(count);
+    std::vector<float> poses(12 * (size_t)count);
+    cudaError_t e = cudaSuccess;
+    const double t0 = now_us();
+    for (int i = 0; i < count; ++i) {
+        Request* r = reqs[i];
+        Session& ss = s->sessions[r->session];
+        maps[i] = ss.map;
+        float4* dst = sl.dev_pts + (size_t)i * s->cfg.max_points;
+        if (r->n > 0 && e == cudaSuccess)
+            e = cudaMemcpyAsync(dst, r->host, (size_t)r->n * sizeof(float4), cudaMemcpyHostToDevice, sl.stream);
+        pts[i] = reinterpret_cast<const float*>(dst);
+        ns[i] = r->n;
+        std::memcpy(&poses[12 * (size_t)i], r->pose, sizeof(r->pose));
+        if (r->shift && e == cudaSuccess) {
+            int rc = tsdf_shift(ss.map, r->origin, sl.stream);
+            if (rc != TSDF_OK) return rc;
+        }
+        r->res.t_start_us = t0;
+    }
+    if (e != cudaSuccess) return TSDF_ERR_CUDA;
+    int rc = tsdf_batch_integrate(sl.batch, maps.data(), pts.data(), ns.data(), poses.data(), count, sl.stream);
+    if (rc != TSDF_OK) return rc;
+    for (int i = 0; i < count && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(sl.counters + 3 * i, map_last_counters(maps[i]), 3 * sizeof(long long),
+                            cudaMemcpyDeviceToHost, sl.stream);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
+    if (e != cudaSuccess) return TSDF_ERR_CUDA;
+    sl.reqs = reqs;
+    sl.busy = true;
+    s->batches++;
+    s->batched_requests += count;
+    return TSDF_OK;
+}
+
+void worker_loop(tsdf_server* s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (!s->stop) {
+        bool progress = false;
+        // 1. completions
+        for (Slot& sl : s->slots) {
+            if (!sl.busy || cudaEventQuery(sl.done) != cudaSuccess) continue;
+            const double t = now_us();
+            for (size_t i = 0; i < sl.reqs.size(); ++i) {
+                Request* r = sl.reqs[i];
+                r->res.stats.valid_rays = sl.counters[3 * i + 0];
+                r->res.stats.hits = sl.counters[3 * i + 1];
+                r->res.stats.touched = sl.counters[3 * i + 2];
+                r->res.t_done_us = t;
+                r->res.batch_size = (int32_t)sl.reqs.size();
+                r->res.status = TSDF_OK;
+                r->done = true;
+                s->sessions[r->session].in_flight = false;
+                s->completed++;
+            }
+            sl.reqs.clear();
+            sl.busy = false;
+            progress = true;
+        }
+        if (progress) s->cv_done.notify_all();
+        // 2. a new batch on a free slot from the requests that have arrived
+        for (size_t k = 0; k < s->slots.size(); ++k) {
+            if (s->slots[k].busy) continue;
+            std::vector<Request*> reqs;
+            for (auto& kv : s->sessions) {
+                Session& ss = kv.second;
+                if (ss.in_flight || ss.queue.empty()) continue;
+                reqs.push_back(ss.queue.front());
+                if ((int)reqs.size() >= s->cfg.max_batch) break;
+            }
+            if (reqs.empty()) break;
+            // oldest first is implicit in the per-session queues; mark and launch
+            for (Request* r : reqs) {
+                s->sessions[r->session].queue.pop_front();
+                s->sessions[r->session].in_flight = true;
+            }
+            int rc = launch_batch(s, (int)k, reqs);
+            if (rc != TSDF_OK) {
+                for (Request* r : reqs) {
+                    r->res.status = rc;
+                    r->res.t_done_us = now_us();
+                    r->done = true;
+                    s->sessions[r->session].in_flight = false;
+                }
+                s->worker_error = rc;
+                s->cv_done.notify_all();
+            }
+            progress = true;
+        }
+        bool any_busy = false;
+        for (Slot& sl : s->slots) any_busy = any_busy || sl.busy;
+        if (!progress) {
+            if (any_busy) s->cv_work.wait_for(lk, std::chrono::microseconds(20));
+            else s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+        }
+    }
+}
+
+void destroy_server(tsdf_server* s) {
+    for (Slot& sl : s->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.batch) tsdf_batch_destroy(sl.batch);
+        cudaFree(sl.dev_pts);
+        if (sl.counters) cudaFreeHost(sl.counters);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+    }
+    for (auto& kv : s->requests) delete kv.second;
+    for (auto& kv : s->sessions)
+        if (kv.second.map) tsdf_map_destroy(kv.second.map);
+    for (float4* p : s->slabs) cudaFreeHost(p);
+    delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tsdf_server_create(const tsdf_server_config* cfg, tsdf_server** out) {
+    if (!cfg || !out) return TSDF_ERR_INVALID;
+    *out = nullptr;
+    if (cfg->max_batch < 1 || cfg->max_batch > 1024 || cfg->streams < 1 || cfg->streams > 8 || cfg->max_points < 1 ||
+        cfg->max_points > TSDF_MAX_POINTS || cfg->max_outstanding < 1 || cfg->max_outstanding > 65536 ||
+        cfg->hbm_budget_bytes < 0)
+        return TSDF_ERR_INVALID;
+    tsdf_server* s = new tsdf_server();
+    s->cfg = *cfg;
+    cudaError_t e = cudaGetDevice(&s->device);
+    s->slots.resize((size_t)cfg->streams);
+    for (Slot& sl : s->slots) {
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaMalloc(&sl.dev_pts, (size_t)cfg->max_batch * cfg->max_points * sizeof(float4));
+        if (e == cudaSuccess) e = cudaMallocHost(&sl.counters, (size_t)cfg->max_batch * 3 * sizeof(long long));
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (e != cudaSuccess) break;
+        int rc = tsdf_batch_create(cfg->max_batch, &sl.batch);
+        if (rc != TSDF_OK) {
+            destroy_server(s);
+            return rc;
+        }
+        // each slot's launch uses its share of the GPU so that batches on
+        // different slots can be resident together
+        tsdf_batch_set_option(sl.batch, TSDF_BATCH_OPT_GRID_FRACTION, 100 / cfg->streams);
+    }
+    for (int i = 0; i < cfg->max_outstanding && e == cudaSuccess; ++i) {
+        float4* p = nullptr;
+        e = cudaMallocHost(&p, (size_t)cfg->max_points * sizeof(float4));
+        if (e == cudaSuccess) {
+            s->slabs.push_back(p);
+            s->free_slabs.push_back(i);
+        }
+    }
+    if (e != cudaSuccess) {
+        destroy_server(s);
+        return e == cudaErrorMemoryAllocation ? TSDF_ERR_OOM : TSDF_ERR_CUDA;
+    }
+    s->worker = std::thread(worker_loop, s);
+    *out = s;
+    return TSDF_OK;
+}
+
+int tsdf_server_destroy(tsdf_server* s) {
+    if (!s) return TSDF_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    destroy_server(s);
+    return TSDF_OK;
+}
+
+int tsdf_server_open_session(tsdf_server* s, const tsdf_params* params, int32_t* session) {
+    if (!s || !params || !session) return TSDF_ERR_INVALID;
+    const size_t bytes = session_bytes(*params, s->cfg.max_points);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if ((long long)(s->used_bytes + bytes) > s->cfg.hbm_budget_bytes) return TSDF_ERR_ADMISSION;
+        s->used_bytes += bytes;   // reserve before the (slow) allocation
+    }
+    tsdf_map* m = nullptr;
+    int rc = tsdf_map_create(params, &m);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (rc != TSDF_OK) {
+        s->used_bytes -= bytes;
+        return rc;
+    }
+    // size the per-ray buffers for the largest scan now, so that no request
+    // reallocates them (which would synchronise the device) while batches run
+    rc = map_reserve_points(m, s->cfg.max_points);
+    if (rc != TSDF_OK) {
+        tsdf_map_destroy(m);
+        s->used_bytes -= bytes;
+        return rc;
+    }
+    const int32_t id = s->next_session++;
+    Session& ss = s->sessions[id];
+    ss.map = m;
+    ss.bytes = bytes;
+    *session = id;
+    return TSDF_OK;
+}
+
+int tsdf_server_close_session(tsdf_server* s, int32_t session) {
+    if (!s) return TSDF_ERR_INVALID;
+    tsdf_map* m = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->sessions.find(session);
+        if (it == s->sessions.end()) return TSDF_ERR_INVALID;
+        if (it->second.outstanding > 0 || it->second.in_flight) return TSDF_ERR_BUSY;
+        m = it->second.map;
+        s->used_bytes -= it->second.bytes;
+        s->sessions.erase(it);
+    }
+    return tsdf_map_destroy(m);
+}
+
+int tsdf_server_submit(tsdf_server* s, int32_t session, const float* points_host, int64_t n, const float pose[12],
+                       const int64_t* new_origin, uint64_t* ticket) {
+    if (!s || !pose || !ticket || n < 0 || n > s->cfg.max_points || (n > 0 && !points_host)) return TSDF_ERR_INVALID;
+    for (int i = 0; i < 12; ++i)
+        if (!std::isfinite(pose[i])) return TSDF_ERR_INVALID;
+    if (new_origin)
+        for (int a = 0; a < 3; ++a)
+            if (new_origin[a] % 8 != 0) return TSDF_ERR_INVALID;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->sessions.find(session);
+    if (it == s->sessions.end()) return TSDF_ERR_INVALID;
+    if (s->worker_error != TSDF_OK) return s->worker_error;
+    if (s->free_slabs.empty()) return TSDF_ERR_BUSY;   // back-pressure: wait for results first
+    Request* r = new Request();
+    r->slab = s->free_slabs.back();
+    s->free_slabs.pop_back();
+    r->host = s->slabs[r->slab];
+    r->ticket = s->next_ticket++;
+    r->session = session;
+    r->n = n;
+    std::memcpy(r->pose, pose, sizeof(r->pose));
+    if (new_origin) {
+        r->shift = true;
+        for (int a = 0; a < 3; ++a) r->origin[a] = new_origin[a];
+    }
+    r->res.ticket = r->ticket;
+    r->res.session = session;
+    r->res.t_submit_us = now_us();
+    lk.unlock();
+    if (n > 0) std::memcpy(r->host, points_host, (size_t)n * sizeof(float4));   // slab is ours alone
+    lk.lock();
+    it = s->sessions.find(session);
+    if (it == s->sessions.end()) {
+        release_request(s, r);
+        return TSDF_ERR_INVALID;
+    }
+    it->second.queue.push_back(r);
+    it->second.outstanding++;
+    s->requests[r->ticket] = r;
+    *ticket = r->ticket;
+    lk.unlock();
+    s->cv_work.notify_one();
+    return TSDF_OK;
+}
+
+int tsdf_server_wait(tsdf_server* s, uint64_t ticket, tsdf_request_result* out, int64_t timeout_us) {
+    if (!s || !out) return TSDF_ERR_INVALID;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->requests.find(ticket);
+    if (it == s->requests.end()) return TSDF_ERR_INVALID;
+    Request* r = it->second;
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us < 0 ? 0 : timeout_us);
+    while (!r->done) {
+        if (timeout_us < 0) s->cv_done.wait(lk);
+        else if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !r->done) return TSDF_ERR_TIMEOUT;
+    }
+    *out = r->res;
+    auto sit = s->sessions.find(r->session);
+    if (sit != s->sessions.end()) sit->second.outstanding--;
+    s->requests.erase(it);
+    release_request(s, r);
+    return out->status;
+}
+
+int tsdf_server_session_map(tsdf_server* s, int32_t session, tsdf_map** out) {
+    if (!s || !out) return TSDF_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->sessions.find(session);
+    if (it == s->sessions.end()) return TSDF_ERR_INVALID;
+    *out = it->second.map;
+    return TSDF_OK;
+}
+
+int tsdf_server_get_stats(tsdf_server* s, tsdf_server_stats* out) {
+    if (!s || !out) return TSDF_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(s->mu);
+    out->sessions = (int32_t)s->sessions.size();
+    out->used_bytes = (int64_t)s->used_bytes;
+    out->completed = s->completed;
+    out->batches = s->batches;
+    out->mean_batch = s->batches ? (double)s->batched_requests / (double)s->batches : 0.0;
+    int64_t queued = 0;
+    for (auto& kv : s->sessions) queued += (int64_t)kv.second.queue.size();
+    out->queued = queued;
+    return TSDF_OK;
+}
+
+}  // extern "C"

@@ -93,6 +93,11 @@ struct BatchItem {
 // `map`, grow its ray buffers if needed and fill the batch item.
 int prepare_batch_item(::tsdf_map* map, const float* points_dev, int64_t n, const float pose[12], BatchItem* out);
 int map_device(const ::tsdf_map* map);
+// Device address of the map's published counters (last_valid, last_hits,
+// last_touched: three contiguous int64).
+const long long* map_last_counters(const ::tsdf_map* map);
+// Grow the map's per-ray buffers to hold n points (synchronous allocation).
+int map_reserve_points(::tsdf_map* map, int64_t n);
 
 // Launchers (return the cudaError_t of the launch).
 cudaError_t launch_rays(const ScanArgs& a, const MapDev& m, bool pdl, cudaStream_t s);

@@ -1,0 +1,127 @@
+"""Serving loop: many map sessions, requests arriving in any interleaving,
+continuous batching on two streams. Every session's map must be bit-identical
+to running its scans alone, in order, through tsdf_integrate / tsdf_shift."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_05766_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MiB = 1 << 20
+
+
+def _sessions(n, seed):
+    out = []
+    rng = np.random.default_rng(seed)
+    for i in range(n):
+        dims = [(128, 128, 64), (256, 256, 64), (128, 128, 128)][i % 3]
+        vs = [0.05, 0.064, 0.08, 0.1][int(rng.integers(0, 4))]
+        w = synth.workload_outdoor(n_scans=4, seed=500 + seed * 10 + i, reduce=i % 2, beams=[16, 32, 64][i % 3],
+                                   azimuths=[512, 1024][i % 2], dims=dims, voxel_size=vs, tau=max(0.2, 2.5 * vs))
+        # force a re-centring before the third scan to exercise shifts
+        o = w.origins[0]
+        w.origins = [o, o, (o[0] + 16, o[1] - 8, o[2]), (o[0] + 16, o[1] - 8, o[2])]
+        out.append(w)
+    return out
+
+
+def _alone(b, w):
+    m = b.TsdfMap(w.params)
+    cur = tuple(w.params["origin"])
+    stats = []
+    for pts, pose, org in zip(w.scans, w.poses, w.origins):
+        if tuple(org) != cur:
+            m.shift(org)
+            cur = tuple(org)
+        m.integrate(torch.from_numpy(pts).cuda(), pose)
+        stats.append(m.stats())
+    v, wt = m.read()
+    m.close()
+    return v, wt, stats
+
+
+def test_mixed_equals_alone():
+    from paper_2310_05766_gb300 import binding as b
+    ws = _sessions(6, seed=1)
+    srv = b.tsdf_server_create(hbm_budget_bytes=8 << 30, max_points=1 << 16, max_batch=4, streams=2,
+                               max_outstanding=64)
+    try:
+        sids = [b.tsdf_server_open_session(srv, w.params) for w in ws]
+        # interleave: round-robin over sessions, each session's scans in order
+        tickets = {i: [] for i in range(len(ws))}
+        cur = [tuple(w.params["origin"]) for w in ws]
+        order = [(i, k) for k in range(4) for i in np.random.default_rng(3).permutation(len(ws))]
+        for i, k in order:
+            w = ws[i]
+            org = tuple(w.origins[k])
+            shift = org if org != cur[i] else None
+            cur[i] = org
+            tickets[i].append(b.tsdf_server_submit(srv, sids[i], w.scans[k], w.poses[k], new_origin=shift))
+        results = {i: [b.tsdf_server_wait(srv, t) for t in tickets[i]] for i in tickets}
+        st = b.tsdf_server_get_stats(srv)
+        assert st["completed"] == 4 * len(ws)
+        for i, w in enumerate(ws):
+            for r in results[i]:
+                assert r["status"] == 0 and r["t_submit_us"] <= r["t_start_us"] <= r["t_done_us"]
+            mh = b.tsdf_server_session_map(srv, sids[i])
+            o = b.tsdf_get_origin(mh)
+            d = w.params["dims"]
+            vm, wm = b.tsdf_read(mh, o, tuple(o[a] + d[a] for a in range(3)))
+            va, wa, sa = _alone(b, w)
+            assert np.array_equal(vm, va) and np.array_equal(wm, wa), f"session {i}"
+            assert [r["stats"] for r in results[i]] == sa
+        # one session also against the oracle
+        w = ws[0]
+        om = oracle.OracleMap(w.params)
+        cur0 = tuple(w.params["origin"])
+        for pts, pose, org in zip(w.scans, w.poses, w.origins):
+            if tuple(org) != cur0:
+                om.shift(org)
+                cur0 = tuple(org)
+            om.integrate(pts, pose)
+        vo, wo = om.read()
+        mh = b.tsdf_server_session_map(srv, sids[0])
+        o = b.tsdf_get_origin(mh)
+        d = w.params["dims"]
+        vm, wm = b.tsdf_read(mh, o, tuple(o[a] + d[a] for a in range(3)))
+        assert np.array_equal(vm, vo) and np.array_equal(wm, wo)
+        assert st["mean_batch"] >= 1.0
+    finally:
+        b.tsdf_server_destroy(srv)
+
+
+def test_admission_by_budget_and_back_pressure():
+    from paper_2310_05766_gb300 import binding as b
+    p = synth.params_dict((256, 256, 128), 0.064, 0.3, 64, 0.006, 0.5, 50.0, 0, (-128, -128, -64))
+    # one session: 2^23 voxels * 12 B = 96 MiB + ray buffers; a 300 MiB budget admits 3
+    srv = b.tsdf_server_create(hbm_budget_bytes=300 * MiB, max_points=1 << 12, max_batch=4, streams=2,
+                               max_outstanding=2)
+    try:
+        sids = [b.tsdf_server_open_session(srv, p) for _ in range(3)]
+        with pytest.raises(b.TsdfError) as e:
+            b.tsdf_server_open_session(srv, p)
+        assert e.value.code == b.TSDF_ERR_ADMISSION
+        b.tsdf_server_close_session(srv, sids[0])
+        sids[0] = b.tsdf_server_open_session(srv, p)   # admitted once memory is free
+        pts = np.zeros((100, 4), np.float32)
+        pts[:, 0] = np.linspace(1.0, 5.0, 100)
+        pose = synth.pose12(np.eye(3), np.zeros(3))
+        t1 = b.tsdf_server_submit(srv, sids[1], pts, pose)
+        t2 = b.tsdf_server_submit(srv, sids[1], pts, pose)
+        with pytest.raises(b.TsdfError) as e:   # two outstanding: no pinned slab left
+            b.tsdf_server_submit(srv, sids[2], pts, pose)
+        assert e.value.code == b.TSDF_ERR_BUSY
+        with pytest.raises(b.TsdfError) as e:   # requests not yet waited for
+            b.tsdf_server_close_session(srv, sids[1])
+        assert e.value.code == b.TSDF_ERR_BUSY
+        r1 = b.tsdf_server_wait(srv, t1)
+        r2 = b.tsdf_server_wait(srv, t2)
+        assert r1["stats"]["valid_rays"] == 100 and r2["t_done_us"] >= r1["t_done_us"]
+        b.tsdf_server_close_session(srv, sids[1])
+        with pytest.raises(b.TsdfError):
+            b.tsdf_server_wait(srv, t1)   # each ticket is waited for once
+    finally:
+        b.tsdf_server_destroy(srv)
