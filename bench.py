@@ -42,7 +42,7 @@ METRIC = "TSDF voxel updates/s (OS1-128-shaped scan)"
 # DRAM bytes (read + write) per launch from the committed ncu capture of these
 # kernels on this workload (profiles/contrib_apply_outdoor_128x1024.md). Reset
 # an entry to None whenever its kernel changes.
-NCU_DRAM_BYTES = {"contrib": None, "apply": None, "rays": None}
+NCU_DRAM_BYTES = {"contrib": 13.18e6 + 0.3e3, "apply": 27.36e6 + 0.07e6 + 4.4e3, "rays": 2.11e6}
 UNIT = "voxel_updates/s"
 N_SEQ = 100
 
@@ -149,6 +149,23 @@ def oracle_sample(w, budget_s: float, stride: int = 1, order=None):
         if t_used >= budget_s:
             break
     return hits / max(t_used, 1e-9), n_used, hits, t_used
+
+
+# ---------------------------------------------------------------- multi-rank aggregation
+
+def aggregate_ranks(units, times, device=None):
+    """Whole-job figures over the ranks of the default process group: the sum
+    of each entry of `units` and the max of each entry of `times`. Without an
+    initialised group (one process) the inputs are returned unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(units), list(times)
+    u = torch.tensor(units, dtype=torch.float64, device=device)
+    t = torch.tensor(times, dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return u.cpu().tolist(), t.cpu().tolist()
 
 
 # ---------------------------------------------------------------- main GPU arm
@@ -259,17 +276,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     m.close()
 
     # ---- reduce over ranks: total units / slowest rank
-    tot = np.array([hits_timed, dev_ms, t_e2e, e2e_hits, t_wall], dtype=np.float64)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor(tot, dtype=torch.float64, device=dev)
-        sums = t.clone()
-        dist.all_reduce(sums, op=dist.ReduceOp.SUM)
-        maxs = t.clone()
-        dist.all_reduce(maxs, op=dist.ReduceOp.MAX)
-        hits_all, dev_ms_max, t_e2e_max, e2e_hits_all = sums[0].item(), maxs[1].item(), maxs[2].item(), sums[3].item()
-    else:
-        hits_all, dev_ms_max, t_e2e_max, e2e_hits_all = tot[0], tot[1], tot[2], tot[3]
+    (hits_all, e2e_hits_all), (dev_ms_max, t_e2e_max) = aggregate_ranks(
+        [float(hits_timed), float(e2e_hits)], [dev_ms, t_e2e], dev if world > 1 else None)
     clk = clocks.stop() if clocks else None
     if rank != 0:
         return None
@@ -383,6 +391,160 @@ def run_reference(args, rank: int, world: int):
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
 
 
+# ---------------------------------------------------------------- batched workload (64 maps)
+
+def run_batch_bench(args):
+    """64 maps, one scan each (beams {16,32,64,128} x azimuths {512,1024,2048},
+    grids 256^3 / 512x512x128 at 0.064 m, tau 0.6 m): one batched launch per step
+    (graph replay, autotuned) against 64 plain tsdf_integrate calls per step, with
+    L2 flushed before every step and excluded by per-step events."""
+    import torch
+    from paper_2310_05766_gb300 import binding as b, synth
+    torch.cuda.set_device(0)
+    b.lib()
+    ws = synth.workload_batch(n_maps=64, seed=3)
+    pts = [torch.from_numpy(w.scans[0]).cuda() for w in ws]
+    poses = [w.poses[0] for w in ws]
+    maps = [b.TsdfMap(w.params) for w in ws]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    batch = b.tsdf_batch_create(64)
+    hits = 0
+    for m, p_, pose in zip(maps, pts, poses):
+        m.integrate(p_, pose)
+        hits += m.stats()["hits"]
+
+    def timed(fn, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return [e0.elapsed_time(e1) for e0, e1 in ev]
+
+    def plain():
+        for m, p_, pose in zip(maps, pts, poses):
+            b.tsdf_integrate(m.handle, p_, p_.shape[0], pose, stream)
+
+    def batched():
+        b.tsdf_batch_integrate(batch, maps, pts, poses, stream)
+
+    for _ in range(max(args.warmup, 16)):   # includes the autotuner's trials
+        batched()
+    assert b.tsdf_batch_sync(batch, stream) == b.TSDF_OK
+    plain()
+    K = max(10, min(args.steps, 200))
+    t_plain = timed(plain, K)
+    t_batch = timed(batched, K)
+    cfg = b.tsdf_batch_get_config(batch)
+    b.tsdf_batch_destroy(batch)
+    for m in maps:
+        m.close()
+    ms_b = float(np.mean(t_batch))
+    ms_p = float(np.mean(t_plain))
+    return dict(metric="TSDF voxel updates/s, 64-map batch (one persistent launch, graph replay)",
+                value=hits / (ms_b / 1e3), unit=UNIT, n_gpus=1, steps=K, warmup=args.warmup, ms_per_step=ms_b,
+                higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32 geometry, int64 accumulation, int16 map", data="synthetic",
+                config=dict(workload="64 maps, beams {16,32,64,128} x azimuths {512,1024,2048}, grids 256^3 / "
+                                     "512x512x128 at 0.064 m, tau 0.6 m, one scan per map per step",
+                            l2="flushed before every step", tuned_config=cfg),
+                scans_per_s=64 / (ms_b / 1e3), plain_per_scan_launches=dict(ms_per_step=ms_p, value=hits / (ms_p / 1e3)),
+                batch_speedup_vs_plain=ms_p / ms_b, hits_per_step=hits)
+
+
+# ---------------------------------------------------------------- serving workload (32 sessions)
+
+def run_serving_bench(args):
+    """32 sessions (grids 256^3 / 512x512x128, voxel 0.05-0.1 m, tau 0.2-0.6 m),
+    Poisson arrivals at an aggregate 500 scans/s with scan sizes {16,32,64,128} x
+    {1024,2048}, 20 s, the first 2 s discarded; HBM budget 120 GB."""
+    import threading
+    import torch
+    from paper_2310_05766_gb300 import binding as b, synth
+    torch.cuda.set_device(0)
+    b.lib()
+    duration = args.serve_seconds
+    sess = synth.serving_sessions(32, seed=100)
+    rng = synth.SplitMix64(777)
+    scans = []
+    for i, sp in enumerate(sess):
+        beams = [16, 32, 64, 128][int(rng.integers(1, 0, 4)[0])]
+        az = [1024, 2048][int(rng.integers(1, 0, 2)[0])]
+        w = synth.workload_outdoor(n_scans=2, seed=sp["seed"], beams=beams, azimuths=az, dims=sp["dims"],
+                                   voxel_size=sp["voxel_size"], tau=sp["tau"])
+        scans.append(w)
+    srv = b.tsdf_server_create(hbm_budget_bytes=120 * 10**9, max_points=128 * 2048, max_batch=32, streams=2,
+                               max_outstanding=1024)
+    sids = [b.tsdf_server_open_session(srv, w.params) for w in scans]
+    times, who = synth.poisson_arrivals(500.0, duration, 32, seed=101)
+    tickets = []
+    lock = threading.Lock()
+    done_flag = [False]
+
+    def submitter():
+        t0 = time.perf_counter()
+        for k, (ta, si) in enumerate(zip(times, who)):
+            while True:
+                dt = ta - (time.perf_counter() - t0)
+                if dt <= 0:
+                    break
+                time.sleep(min(dt, 0.0005))
+            w = scans[si]
+            j = k % 2
+            t = b.tsdf_server_submit(srv, sids[si], w.scans[j], w.poses[j])
+            with lock:
+                tickets.append((ta, t))
+        done_flag[0] = True
+
+    results = []
+
+    def collector():
+        i = 0
+        while True:
+            with lock:
+                have = i < len(tickets)
+                item = tickets[i] if have else None
+            if not have:
+                if done_flag[0]:
+                    with lock:
+                        if i >= len(tickets):
+                            break
+                    continue
+                time.sleep(0.0002)
+                continue
+            r = b.tsdf_server_wait(srv, item[1])
+            results.append((item[0], r))
+            i += 1
+
+    th_s = threading.Thread(target=submitter)
+    th_c = threading.Thread(target=collector)
+    th_s.start()
+    th_c.start()
+    th_s.join()
+    th_c.join()
+    st = b.tsdf_server_get_stats(srv)
+    b.tsdf_server_destroy(srv)
+    keep = [r for ta, r in results if ta >= 2.0]
+    lat = np.array([r["t_done_us"] - r["t_submit_us"] for r in keep])
+    hits = sum(r["stats"]["hits"] for r in keep)
+    span = (max(r["t_done_us"] for r in keep) - min(r["t_submit_us"] for r in keep)) / 1e6
+    return dict(metric="served scan latency (p50 / p99) and throughput, 32 sessions, Poisson 500 scans/s",
+                value=len(keep) / span, unit="scans/s", n_gpus=1, steps=len(keep), warmup=0,
+                ms_per_step=float(np.mean(lat)) / 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32 geometry, int64 accumulation, int16 map", data="synthetic",
+                config=dict(workload="32 sessions, grids 256^3 / 512x512x128, voxel 0.05-0.1 m, tau 0.2-0.6 m, "
+                                     "Poisson 500 scans/s, scans {16,32,64,128} x {1024,2048}, %g s, first 2 s "
+                                     "discarded, HBM budget 120 GB, 2 streams, batches up to 32" % duration),
+                latency_ms=dict(p50=float(np.percentile(lat, 50)) / 1e3, p99=float(np.percentile(lat, 99)) / 1e3,
+                                mean=float(np.mean(lat)) / 1e3, max=float(np.max(lat)) / 1e3),
+                voxel_updates_per_s=hits / span, mean_batch=st["mean_batch"], batches=st["batches"],
+                sessions=st["sessions"], used_bytes=st["used_bytes"])
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -393,6 +555,9 @@ def main():
     ap.add_argument("--merge", type=int, default=None, help="tuning: warp match-merge (0/1)")
     ap.add_argument("--kpt", type=int, default=None, help="tuning: march steps per contribution thread (1/2/4)")
     ap.add_argument("--pdl", type=int, default=None, help="tuning: programmatic dependent launch (0/1)")
+    ap.add_argument("--workload", default="outdoor", choices=["outdoor", "batch", "serving"],
+                    help="outdoor: the headline sequence; batch / serving: the 64-map batch and 32-session serving runs")
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=120.0, help="seconds of oracle time for --impl reference")
     args = ap.parse_args()
@@ -403,6 +568,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.workload == "batch":
+        out = run_batch_bench(args) if rank == 0 else None
+    elif args.workload == "serving":
+        out = run_serving_bench(args) if rank == 0 else None
     else:
         if world > 1:
             import torch
