@@ -52,6 +52,14 @@ extern "C" {
 #define TSDF_REDUCE_WSUM     0  /* sum of weight * distance and sum of weights (weight 1 per contribution) */
 #define TSDF_REDUCE_MIN_ABS  1  /* the paper's "smallest distance of all rays": smallest |q|, ties -> positive; weight 1 */
 
+/* ---- alternative readings of the paper (tsdf_params.flags) ---------------- */
+#define TSDF_FLAG_STEP_VALUE   1  /* every sample of a march step (the step's voxel and its fill samples) gets the
+                                     step's own truncated distance r - l (the fill copies the step's value, Section
+                                     "TSDF Map Generation"); default: the projective distance of the voxel's centre */
+#define TSDF_FLAG_SCAN_WEIGHT  2  /* WSUM: a scan's averaged value S/W enters Eq. 1 / Eq. 2 as one observation of
+                                     weight 1: value (gv*gw*W + S) / ((gw + 1) * W), weight min(w_max, gw + 1);
+                                     default: weight W (its contribution count) */
+
 /* Largest number of points accepted by one integrate call. With weight 1 per
  * contribution, a voxel receives at most 4 contributions per ray, so the
  * per-scan weight sum of a voxel stays below 2^24 and its distance sum below
@@ -68,7 +76,7 @@ typedef struct tsdf_params {
     float   r_min;        /* points with range < r_min are skipped, >= 0 */
     float   r_max;        /* points with range > r_max are skipped, r_min <= r_max <= 1e5 */
     int32_t reduce;       /* TSDF_REDUCE_WSUM or TSDF_REDUCE_MIN_ABS */
-    int32_t reserved;     /* must be 0 */
+    int32_t flags;        /* TSDF_FLAG_* bits; 0 selects the default readings */
     int64_t origin[3];    /* initial window origin in global voxel coordinates; multiples of 8, |origin| <= 2^23 */
 } tsdf_params;
 

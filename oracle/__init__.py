@@ -43,7 +43,7 @@ def build(force: bool = False) -> str:
 class OrcParams(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int32 * 3), ("voxel_size", ctypes.c_float), ("tau", ctypes.c_float),
                 ("w_max", ctypes.c_int32), ("delta_z", ctypes.c_float), ("r_min", ctypes.c_float),
-                ("r_max", ctypes.c_float), ("reduce", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("r_max", ctypes.c_float), ("reduce", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("origin", ctypes.c_int64 * 3)]
 
 
@@ -59,6 +59,7 @@ def make_params(p: dict) -> OrcParams:
     o.r_min = p["r_min"]
     o.r_max = p["r_max"]
     o.reduce = int(p.get("reduce", 0))
+    o.flags = int(p.get("flags", 0))
     return o
 
 
@@ -78,12 +79,14 @@ def lib():
             fn.restype = ctypes.c_int
             fn.argtypes = [vp, f32p, i64, f32p]
         L.orc_hits.restype = i64
-        L.orc_hits.argtypes = [P(OrcParams), f32p, i64, f32p, P(i64), P(ctypes.c_int32), P(i64), i64]
+        L.orc_hits.argtypes = [P(OrcParams), f32p, i64, f32p, P(i64), P(ctypes.c_int32), P(i64),
+                               P(ctypes.c_int32), i64]
         L.orc_ray.argtypes = [f32p, f32p, ctypes.c_float, ctypes.c_float, ctypes.c_float, f32p]
         L.orc_quantize.restype = ctypes.c_int32
         L.orc_quantize.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_float]
-        L.orc_eq12.argtypes = [ctypes.c_int32, ctypes.c_int32, i64, i64, ctypes.c_int32,
-                               P(ctypes.c_int32), P(ctypes.c_int32)]
+        for name in ("orc_eq12", "orc_eq12_scan"):
+            getattr(L, name).argtypes = [ctypes.c_int32, ctypes.c_int32, i64, i64, ctypes.c_int32,
+                                         P(ctypes.c_int32), P(ctypes.c_int32)]
         L.orc_shift.restype = ctypes.c_int
         L.orc_shift.argtypes = [vp, P(i64)]
         L.orc_read.restype = ctypes.c_int
@@ -119,9 +122,11 @@ def quantize(d: float, tau: float, qs: float) -> int:
     return int(lib().orc_quantize(d, tau, qs))
 
 
-def eq12(gv, gw, S, W, w_max):
+def eq12(gv, gw, S, W, w_max, scan_weight=False):
+    """Eq. 1 / Eq. 2; scan_weight: the scan's average S/W as one observation."""
     nv, nw = ctypes.c_int32(), ctypes.c_int32()
-    lib().orc_eq12(gv, gw, S, W, w_max, ctypes.byref(nv), ctypes.byref(nw))
+    fn = lib().orc_eq12_scan if scan_weight else lib().orc_eq12
+    fn(gv, gw, S, W, w_max, ctypes.byref(nv), ctypes.byref(nw))
     return nv.value, nw.value
 
 
@@ -134,23 +139,28 @@ def ray(pose, pt, r_min, r_max, delta_z):
     return dict(valid=bool(out[0]), fill=bool(out[1]), r=out[2], dir=out[3:6].copy(), ih=out[6:9].copy())
 
 
-def hits(p: dict, points: np.ndarray, pose: np.ndarray, cap: int | None = None):
+def hits(p: dict, points: np.ndarray, pose: np.ndarray, cap: int | None = None, with_k: bool = False):
     """All contributions of a scan in enumeration order, in or out of the window.
 
-    Returns (g int64[H,3], q int32[H], ray int64[H])."""
+    Returns (g int64[H,3], q int32[H], ray int64[H]) and, with_k, also the
+    march step k int32[H] of each contribution."""
     pts_a, pts_p = _f32(points.reshape(-1, 4))
     pose_a, pose_p = _f32(pose)
     n = pts_a.shape[0]
     prm = make_params(p)
     P = ctypes.POINTER
     if cap is None:
-        cap = int(lib().orc_hits(ctypes.byref(prm), pts_p, n, pose_p, None, None, None, 0))
+        cap = int(lib().orc_hits(ctypes.byref(prm), pts_p, n, pose_p, None, None, None, None, 0))
     g = np.zeros((max(cap, 1), 3), dtype=np.int64)
     q = np.zeros(max(cap, 1), dtype=np.int32)
     r = np.zeros(max(cap, 1), dtype=np.int64)
+    k = np.zeros(max(cap, 1), dtype=np.int32)
     cnt = lib().orc_hits(ctypes.byref(prm), pts_p, n, pose_p, g.ctypes.data_as(P(ctypes.c_int64)),
-                         q.ctypes.data_as(P(ctypes.c_int32)), r.ctypes.data_as(P(ctypes.c_int64)), cap)
+                         q.ctypes.data_as(P(ctypes.c_int32)), r.ctypes.data_as(P(ctypes.c_int64)),
+                         k.ctypes.data_as(P(ctypes.c_int32)), cap)
     m = min(cnt, cap)
+    if with_k:
+        return g[:m], q[:m], r[:m], k[:m]
     return g[:m], q[:m], r[:m]
 
 

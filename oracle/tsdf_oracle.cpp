@@ -23,6 +23,10 @@
 //    all rays" with weight 1.
 //  * Eq. 1 is evaluated exactly in integers with one rounding, half away
 //    from zero. Eq. 2 clamps the summed weight at weight_max.
+//  * Two alternative readings selected by flags: bit 1, every sample of a
+//    march step takes that step's own distance r - l (the fill copies the
+//    step's value); bit 2, a WSUM scan's averaged
+//    value enters Eq. 1 / Eq. 2 as one observation of weight 1.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -44,7 +48,7 @@ struct orc_params {
     float r_min;
     float r_max;
     int32_t reduce;   // 0 = WSUM, 1 = MIN_ABS
-    int32_t pad_;
+    int32_t flags;    // 1: step-valued fill, 2: one observation per scan (WSUM)
     int64_t origin[3];
 };
 
@@ -137,6 +141,18 @@ int32_t quantize(float d, float tau, float qs) {
     return (int32_t)q;
 }
 
+// Eq. 1 and Eq. 2 with v.value = S / W and v.weight = 1 (one observation per
+// scan): value (gv*gw + S/W) / (gw + 1) = (gv*gw*W + S) / ((gw + 1) * W).
+void eq12_scan(int32_t gv, int32_t gw, int64_t S, int64_t W, int32_t w_max, int32_t* nv, int32_t* nw) {
+    int64_t num = (int64_t)gv * (int64_t)gw * W + S;
+    int64_t den = ((int64_t)gw + 1) * W;
+    int64_t a = num < 0 ? -num : num;
+    int64_t q = (2 * a + den) / (2 * den);
+    *nv = (int32_t)(num < 0 ? -q : q);
+    int64_t w = (int64_t)gw + 1;
+    *nw = (int32_t)(w > w_max ? w_max : w);
+}
+
 // Eq. 1 and Eq. 2 with v.value * v.weight = S and v.weight = W.
 void eq12(int32_t gv, int32_t gw, int64_t S, int64_t W, int32_t w_max, int32_t* nv, int32_t* nw) {
     int64_t num = (int64_t)gv * (int64_t)gw + S;
@@ -152,7 +168,8 @@ void eq12(int32_t gv, int32_t gw, int64_t S, int64_t W, int32_t w_max, int32_t* 
 // order (k outer, j inner). Eq. 3 gives delta_z; Eq. 4 the fill height
 // h = delta_z * l at step distance l; voxels are taken at spacing voxel_size
 // along +-int up to h. The distance of a voxel is the projective distance of
-// its centre along the ray: r - (c - s) . dir.
+// its centre along the ray: r - (c - s) . dir (or, with flag 1, the step's
+// own distance r - l).
 template <class F>
 void for_each_hit(const Ray& ry, const orc_params& p, const Derived& dv, F&& f) {
     if (!ry.valid) return;
@@ -182,8 +199,8 @@ void for_each_hit(const Ray& ry, const orc_params& p, const Derived& dv, F&& f) 
             float cy = ((float)g[1] + 0.5f) * vs;
             float cz = ((float)g[2] + 0.5f) * vs;
             float proj = (((cx - tx) * dx) + ((cy - ty) * dy)) + ((cz - tz) * dz);
-            float d = ry.r - proj;
-            f(g, quantize(d, p.tau, dv.qs));
+            float d = (p.flags & 1) ? ry.r - l : ry.r - proj;
+            f(g, quantize(d, p.tau, dv.qs), k);
         }
     }
 }
@@ -224,6 +241,7 @@ bool params_ok(const orc_params& p) {
     if (!(p.delta_z >= 0.f)) return false;
     if (!(p.r_min >= 0.f) || !(p.r_max >= p.r_min)) return false;
     if (p.reduce != 0 && p.reduce != 1) return false;
+    if ((p.flags & ~3) != 0) return false;
     return true;
 }
 
@@ -234,7 +252,8 @@ void apply_volume(OracleMap* m, const std::unordered_map<int64_t, Acc>& vol,
         for (const auto& kv : vol) {
             Cell& c = m->win[kv.first];
             int32_t nv, nw;
-            eq12(c.v, c.w, kv.second.S, kv.second.W, m->p.w_max, &nv, &nw);
+            if (m->p.flags & 2) eq12_scan(c.v, c.w, kv.second.S, kv.second.W, m->p.w_max, &nv, &nw);
+            else eq12(c.v, c.w, kv.second.S, kv.second.W, m->p.w_max, &nv, &nw);
             c.v = (int16_t)nv;
             c.w = (int16_t)nw;
         }
@@ -292,7 +311,7 @@ int orc_integrate(void* h, const float* pts, int64_t n, const float pose[12]) {
         Ray ry = ray_setup(pose, pts + 4 * i, m->p.r_min, m->p.r_max, m->p.delta_z);
         if (!ry.valid) continue;
         ++valid;
-        for_each_hit(ry, m->p, m->dv, [&](const int64_t g[3], int32_t q) {
+        for_each_hit(ry, m->p, m->dv, [&](const int64_t g[3], int32_t q, int) {
             if (!m->inside(g)) return;
             ++hits;
             int64_t key = m->lin(g);
@@ -352,8 +371,9 @@ int orc_integrate_bruteforce(void* h, const float* pts, int64_t n, const float p
                     float cx = ((float)gx + 0.5f) * vs;
                     float cy = ((float)gy + 0.5f) * vs;
                     float cz = ((float)gz + 0.5f) * vs;
-                    float d = ry.r - ((((cx - ry.t[0]) * ry.dir[0]) + ((cy - ry.t[1]) * ry.dir[1])) +
-                                      ((cz - ry.t[2]) * ry.dir[2]));
+                    float d = (m->p.flags & 1) ? ry.r - l
+                                               : ry.r - ((((cx - ry.t[0]) * ry.dir[0]) + ((cy - ry.t[1]) * ry.dir[1])) +
+                                                         ((cz - ry.t[2]) * ry.dir[2]));
                     int32_t q = quantize(d, m->p.tau, m->dv.qs);
                     S += q;
                     W += 1;
@@ -368,7 +388,8 @@ int orc_integrate_bruteforce(void* h, const float* pts, int64_t n, const float p
         int64_t g[3] = {gx, gy, gz};
         Cell& c = next[m->lin(g)];
         int32_t nv, nw;
-        if (m->p.reduce == 0) eq12(c.v, c.w, S, W, m->p.w_max, &nv, &nw);
+        if (m->p.reduce == 0 && (m->p.flags & 2)) eq12_scan(c.v, c.w, S, W, m->p.w_max, &nv, &nw);
+        else if (m->p.reduce == 0) eq12(c.v, c.w, S, W, m->p.w_max, &nv, &nw);
         else eq12(c.v, c.w, bq, 1, m->p.w_max, &nv, &nw);
         c.v = (int16_t)nv;
         c.w = (int16_t)nw;
@@ -384,18 +405,19 @@ int orc_integrate_bruteforce(void* h, const float* pts, int64_t n, const float p
 // in the window: out_g int64[cap][3], out_q int32[cap]. Returns the count
 // (which may exceed cap; only the first cap are written).
 int64_t orc_hits(const orc_params* p, const float* pts, int64_t n, const float pose[12],
-                 int64_t* out_g, int32_t* out_q, int64_t* out_ray, int64_t cap) {
+                 int64_t* out_g, int32_t* out_q, int64_t* out_ray, int32_t* out_k, int64_t cap) {
     Derived dv = derive(*p);
     int64_t cnt = 0;
     for (int64_t i = 0; i < n; ++i) {
         Ray ry = ray_setup(pose, pts + 4 * i, p->r_min, p->r_max, p->delta_z);
-        for_each_hit(ry, *p, dv, [&](const int64_t g[3], int32_t q) {
+        for_each_hit(ry, *p, dv, [&](const int64_t g[3], int32_t q, int k) {
             if (cnt < cap) {
                 out_g[3 * cnt + 0] = g[0];
                 out_g[3 * cnt + 1] = g[1];
                 out_g[3 * cnt + 2] = g[2];
                 out_q[cnt] = q;
                 if (out_ray) out_ray[cnt] = i;
+                if (out_k) out_k[cnt] = k;
             }
             ++cnt;
         });
@@ -420,6 +442,10 @@ int32_t orc_quantize(float d, float tau, float qs) { return quantize(d, tau, qs)
 
 void orc_eq12(int32_t gv, int32_t gw, int64_t S, int64_t W, int32_t w_max, int32_t* nv, int32_t* nw) {
     eq12(gv, gw, S, W, w_max, nv, nw);
+}
+
+void orc_eq12_scan(int32_t gv, int32_t gw, int64_t S, int64_t W, int32_t w_max, int32_t* nv, int32_t* nw) {
+    eq12_scan(gv, gw, S, W, w_max, nv, nw);
 }
 
 // Move the window to new_origin (multiples of 8). Chunks (8^3 voxels) that

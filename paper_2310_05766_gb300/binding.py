@@ -23,6 +23,8 @@ TSDF_ERR_ADMISSION = -5
 TSDF_ERR_BUSY = -6
 TSDF_REDUCE_WSUM = 0
 TSDF_REDUCE_MIN_ABS = 1
+TSDF_FLAG_STEP_VALUE = 1
+TSDF_FLAG_SCAN_WEIGHT = 2
 TSDF_MAX_POINTS = 1 << 22
 TSDF_OPT_WARP_MERGE = 1
 TSDF_OPT_STEPS_PER_THREAD = 2
@@ -47,7 +49,7 @@ class TsdfError(RuntimeError):
 class tsdf_params(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int32 * 3), ("voxel_size", ctypes.c_float), ("tau", ctypes.c_float),
                 ("w_max", ctypes.c_int32), ("delta_z", ctypes.c_float), ("r_min", ctypes.c_float),
-                ("r_max", ctypes.c_float), ("reduce", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("r_max", ctypes.c_float), ("reduce", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("origin", ctypes.c_int64 * 3)]
 
 
@@ -166,7 +168,7 @@ def make_params(p: dict) -> tsdf_params:
     s.r_min = float(p["r_min"])
     s.r_max = float(p["r_max"])
     s.reduce = int(p.get("reduce", 0))
-    s.reserved = 0
+    s.flags = int(p.get("flags", 0))
     return s
 
 

@@ -140,7 +140,7 @@ int validate_params(const tsdf_params* p) {
         return TSDF_ERR_INVALID;
     if ((double)p->delta_z * ((double)p->r_max + p->tau) / p->voxel_size > 1e6) return TSDF_ERR_INVALID;
     if (p->reduce != TSDF_REDUCE_WSUM && p->reduce != TSDF_REDUCE_MIN_ABS) return TSDF_ERR_INVALID;
-    if (p->reserved != 0) return TSDF_ERR_INVALID;
+    if ((p->flags & ~(TSDF_FLAG_STEP_VALUE | TSDF_FLAG_SCAN_WEIGHT)) != 0) return TSDF_ERR_INVALID;
     return TSDF_OK;
 }
 
@@ -345,6 +345,7 @@ static void fill_scan_args(const tsdf_map* map, const float* points_dev, int64_t
     }
     a.lcx = map->geom.lcx;
     a.lcxy = map->geom.lcxy;
+    a.flags = map->p.flags;
 }
 
 static int integrate_dev(tsdf_map* map, const float* points_dev, int64_t n, const float pose[12],
@@ -362,7 +363,7 @@ static int integrate_dev(tsdf_map* map, const float* points_dev, int64_t n, cons
     cudaEvent_t e3 = n > 0 ? prof_mark(map, s) : nullptr;
     cudaEvent_t e4 = prof_mark(map, s);
     TSDF_CU(launch_compact(map->dev, (uint32_t)map->bricks, pdl, s));
-    TSDF_CU(launch_apply(map->dev, map->p.reduce, map->p.w_max, map->num_sms * 8, pdl, s));
+    TSDF_CU(launch_apply(map->dev, map->p.reduce, map->p.w_max, map->p.flags, map->num_sms * 8, pdl, s));
     TSDF_CU(launch_finish(map->dev, pdl, s));
     cudaEvent_t e5 = prof_mark(map, s);
     prof_push(map, kRays, e0, e1);
@@ -633,7 +634,7 @@ int prepare_batch_item(::tsdf_map* map, const float* points_dev, int64_t n, cons
     out->reduce = map->p.reduce;
     out->w_max = map->p.w_max;
     out->bricks = (uint32_t)map->bricks;
-    out->pad = 0;
+    out->flags = map->p.flags;
     return TSDF_OK;
 }
 

@@ -216,8 +216,9 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem
                 cur = i;
             }
             const BatchItem& it = items[i];
-            if (it.reduce == 0) apply_brick<0>(it.m, it.w_max, g - s_prefix[i], s_grid, s_acc, s_off, touched, hits);
-            else apply_brick<1>(it.m, it.w_max, g - s_prefix[i], s_grid, s_acc, s_off, touched, hits);
+            if (it.reduce == 0)
+                apply_brick<0>(it.m, it.w_max, it.flags, g - s_prefix[i], s_grid, s_acc, s_off, touched, hits);
+            else apply_brick<1>(it.m, it.w_max, it.flags, g - s_prefix[i], s_grid, s_acc, s_off, touched, hits);
         }
         if (cur >= 0) {
             warp_add(touched, &items[cur].m.ctr->part[gwarp % kParts].touched);

@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(256) compact_kernel(const MapDev m, const uint
 constexpr int kApplyWarps = 4;
 
 template <int MODE>
-__global__ void __launch_bounds__(kApplyWarps * 32) apply_kernel(const MapDev m, const int32_t w_max) {
+__global__ void __launch_bounds__(kApplyWarps * 32) apply_kernel(const MapDev m, const int32_t w_max,
+                                                                  const int32_t flags) {
     // per warp: the brick's grid words and accumulators, and the offsets of
     // its touched voxels (compacted)
     __shared__ uint32_t s_grid[kApplyWarps][kBrickVoxels];
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(kApplyWarps * 32) apply_kernel(const MapDev m,
     nb = __shfl_sync(kFull, nb, 0);
     unsigned long long touched = 0, hits = 0;
     for (unsigned i = gwarp; i < nb; i += nwarps)
-        apply_brick<MODE>(m, w_max, i, s_grid[w], s_acc[w], s_off[w], touched, hits);
+        apply_brick<MODE>(m, w_max, flags, i, s_grid[w], s_acc[w], s_off[w], touched, hits);
     for (int o = 16; o > 0; o >>= 1) {
         touched += __shfl_xor_sync(kFull, touched, o);
         hits += __shfl_xor_sync(kFull, hits, o);
@@ -213,9 +214,10 @@ cudaError_t launch_compact(const MapDev& m, uint32_t bricks, bool pdl, cudaStrea
     return launch(compact_kernel, dim3((nwords + 255u) / 256u), dim3(256), s, pdl, m, nwords);
 }
 
-cudaError_t launch_apply(const MapDev& m, int32_t reduce, int32_t w_max, int num_ctas, bool pdl, cudaStream_t s) {
-    if (reduce == 0) return launch(apply_kernel<0>, dim3(num_ctas), dim3(kApplyWarps * 32), s, pdl, m, w_max);
-    return launch(apply_kernel<1>, dim3(num_ctas), dim3(kApplyWarps * 32), s, pdl, m, w_max);
+cudaError_t launch_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t flags, int num_ctas, bool pdl,
+                         cudaStream_t s) {
+    if (reduce == 0) return launch(apply_kernel<0>, dim3(num_ctas), dim3(kApplyWarps * 32), s, pdl, m, w_max, flags);
+    return launch(apply_kernel<1>, dim3(num_ctas), dim3(kApplyWarps * 32), s, pdl, m, w_max, flags);
 }
 
 cudaError_t launch_finish(const MapDev& m, bool pdl, cudaStream_t s) {

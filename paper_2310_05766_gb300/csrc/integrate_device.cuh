@@ -147,6 +147,7 @@ __device__ __forceinline__ void contrib_item(const ScanArgs& a, const MapDev& m,
         const float bx = fa(tx, fm(A.x, l));
         const float by = fa(ty, fm(A.y, l));
         const float bz = fa(tz, fm(A.z, l));
+        const float dstep = fs(r, l);   // the step's own distance (TSDF_FLAG_STEP_VALUE)
         for (int j = -Jw; j <= Jw; ++j) {   // warp-uniform bounds
             // every lane evaluates the sample; lanes outside their own fill
             // range or outside the window are masked out (no divergent branches)
@@ -167,7 +168,7 @@ __device__ __forceinline__ void contrib_item(const ScanArgs& a, const MapDev& m,
             const float cy = fm(fa(fy, 0.5f), a.vs);
             const float cz = fm(fa(fz, 0.5f), a.vs);
             const float proj = fa(fa(fm(fs(cx, tx), A.x), fm(fs(cy, ty), A.y)), fm(fs(cz, tz), A.z));
-            const float d = fminf(fmaxf(fs(r, proj), -a.tau), a.tau);
+            const float d = fminf(fmaxf((a.flags & kFlagStepValue) ? dstep : fs(r, proj), -a.tau), a.tau);
             // rint (ties to even) of |d qs| <= 32767.x < 2^22, as an exact float add
             int q = small_int(fm(d, a.qs));
             q = max(-kQMax, min(kQMax, q));
@@ -221,13 +222,34 @@ __device__ __forceinline__ uint32_t update_voxel(uint32_t word, long long S, lon
     return (uint32_t)(uint16_t)(int16_t)nv | ((uint32_t)nw << 16);
 }
 
+// Eq. 1 / Eq. 2 when the scan's average S/W counts as one observation of
+// weight 1 (TSDF_FLAG_SCAN_WEIGHT): (gv gw W + S) / ((gw + 1) W), one rounding.
+__device__ __forceinline__ uint32_t update_voxel_scan(uint32_t word, long long S, long long W, int32_t w_max) {
+    const long long gv = (long long)(int16_t)(word & 0xFFFFu);
+    const long long gw = (long long)(int16_t)(word >> 16);
+    const long long num = gv * gw * W + S;
+    const long long den = (gw + 1) * W;
+    const unsigned long long an = (unsigned long long)(num < 0 ? -num : num);
+    const unsigned long long qv = (2ull * an + (unsigned long long)den) / (2ull * (unsigned long long)den);
+    const long long nv = num < 0 ? -(long long)qv : (long long)qv;
+    const long long nw = gw + 1 > w_max ? (long long)w_max : gw + 1;
+    return (uint32_t)(uint16_t)(int16_t)nv | ((uint32_t)nw << 16);
+}
+
 // Decode one accumulator and update its voxel; returns the voxel's number of
 // contributions (WSUM) or 1 (MIN_ABS), 0 if untouched. WSUM accumulators
 // whose sum fits 31 bits and count fits 15 bits (the common case) take an
 // all-32-bit path with the same result as the 64-bit one.
 template <int MODE>
-__device__ __forceinline__ unsigned decode_apply(unsigned long long P, uint32_t& word, int32_t w_max) {
+__device__ __forceinline__ unsigned decode_apply(unsigned long long P, uint32_t& word, int32_t w_max,
+                                                 int32_t flags = 0) {
     if (P == 0ull) return 0u;
+    if (MODE == 0 && (flags & kFlagScanWeight)) {
+        const long long S = ((long long)(P << 24)) >> 24;
+        const long long W = (long long)((P - (unsigned long long)S) >> 40);
+        word = update_voxel_scan(word, S, W, w_max);
+        return (unsigned)W;
+    }
     if (MODE == 0) {
         const unsigned lo = (unsigned)P, hi = (unsigned)(P >> 32);
         const unsigned hb = hi & 0xFFu;   // bits 32..39 of the 40-bit sum
@@ -287,9 +309,9 @@ __device__ __forceinline__ void compact_words(const MapDev& m, unsigned i, unsig
 // ---- apply: one warp updates listed brick number i of the map. Shared
 // memory per warp: s_grid[512] words, s_acc[512] accumulators, s_off[512].
 template <int MODE>
-__device__ __forceinline__ void apply_brick(const MapDev& m, int32_t w_max, unsigned i, uint32_t* s_grid,
-                                            unsigned long long* s_acc, uint16_t* s_off, unsigned long long& touched,
-                                            unsigned long long& hits) {
+__device__ __forceinline__ void apply_brick(const MapDev& m, int32_t w_max, int32_t flags, unsigned i,
+                                            uint32_t* s_grid, unsigned long long* s_acc, uint16_t* s_off,
+                                            unsigned long long& touched, unsigned long long& hits) {
     const unsigned lane = threadIdx.x & 31u;
     uint4* sg4 = reinterpret_cast<uint4*>(s_grid);
     ulonglong2* sa2 = reinterpret_cast<ulonglong2*>(s_acc);
@@ -325,7 +347,7 @@ __device__ __forceinline__ void apply_brick(const MapDev& m, int32_t w_max, unsi
     for (unsigned e = lane; e < total; e += 32u) {
         const unsigned off = s_off[e];
         uint32_t word = s_grid[off];
-        hits += decode_apply<MODE>(s_acc[off], word, w_max);
+        hits += decode_apply<MODE>(s_acc[off], word, w_max, flags);
         s_grid[off] = word;
     }
     touched += lane == 0 ? total : 0u;

@@ -90,7 +90,7 @@ int check_params(const tsdf_params* p) {
         return TSDF_ERR_INVALID;
     if ((double)p->delta_z * ((double)p->r_max + p->tau) / p->voxel_size > 1e6) return TSDF_ERR_INVALID;
     if (p->reduce != TSDF_REDUCE_WSUM && p->reduce != TSDF_REDUCE_MIN_ABS) return TSDF_ERR_INVALID;
-    if (p->reserved != 0) return TSDF_ERR_INVALID;
+    if ((p->flags & ~(TSDF_FLAG_STEP_VALUE | TSDF_FLAG_SCAN_WEIGHT)) != 0) return TSDF_ERR_INVALID;
     return TSDF_OK;
 }
 
@@ -156,6 +156,7 @@ extern "C" int tsdf_integrate_static(uint32_t* grid_dev, const tsdf_params* para
     }
     a.lcx = ilog2((uint32_t)params->dims[0] / 8u);
     a.lcxy = a.lcx + ilog2((uint32_t)params->dims[1] / 8u);
+    a.flags = params->flags;
 
     int num_sms = 1;
     int dev = 0;
@@ -164,7 +165,7 @@ extern "C" int tsdf_integrate_static(uint32_t* grid_dev, const tsdf_params* para
     if (e == cudaSuccess) e = launch_rays(a, md, true, s);
     if (e == cudaSuccess) e = launch_contrib(a, md, params->reduce, false, 4, true, s);
     if (e == cudaSuccess) e = launch_compact(md, (uint32_t)bricks, true, s);
-    if (e == cudaSuccess) e = launch_apply(md, params->reduce, params->w_max, num_sms * 8, true, s);
+    if (e == cudaSuccess) e = launch_apply(md, params->reduce, params->w_max, params->flags, num_sms * 8, true, s);
     if (e == cudaSuccess) e = launch_finish(md, true, s);
     if (e == cudaSuccess && stats_host) {
         long long last[3] = {0, 0, 0};

@@ -12,6 +12,9 @@ constexpr int32_t kQMax = 32767;
 constexpr int kBrick = 8;                 // bricks are 8 x 8 x 8 voxels, stored contiguously
 constexpr int kBrickVoxels = 512;
 
+constexpr int32_t kFlagStepValue = 1;    // TSDF_FLAG_STEP_VALUE
+constexpr int32_t kFlagScanWeight = 2;   // TSDF_FLAG_SCAN_WEIGHT
+
 constexpr int kParts = 32;        // counters are spread over 32 slots, one 128-byte line each
 
 // Per-map device counters (one instance per map, in device memory). The
@@ -61,6 +64,7 @@ struct ScanArgs {
     uint32_t lcx, lcxy;             // log2(dims.x / 8), log2(dims.x / 8 * dims.y / 8)
     uint32_t dmask[3];              // dims - 1 per axis
     uint32_t omod[3];               // origin mod dims per axis (ring offset of the window origin)
+    int32_t flags;                  // TSDF_FLAG_* bits
 };
 
 // One brick slot that changes owner during a shift.
@@ -85,7 +89,7 @@ struct BatchItem {
     int32_t reduce;
     int32_t w_max;
     uint32_t bricks;
-    uint32_t pad;
+    int32_t flags;
 };
 
 
@@ -104,7 +108,8 @@ cudaError_t launch_rays(const ScanArgs& a, const MapDev& m, bool pdl, cudaStream
 cudaError_t launch_contrib(const ScanArgs& a, const MapDev& m, int32_t reduce, bool merge, int kpt, bool pdl,
                            cudaStream_t s);
 cudaError_t launch_compact(const MapDev& m, uint32_t bricks, bool pdl, cudaStream_t s);
-cudaError_t launch_apply(const MapDev& m, int32_t reduce, int32_t w_max, int num_ctas, bool pdl, cudaStream_t s);
+cudaError_t launch_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t flags, int num_ctas, bool pdl,
+                         cudaStream_t s);
 cudaError_t launch_finish(const MapDev& m, bool pdl, cudaStream_t s);
 cudaError_t launch_shift(uint32_t* grid, const ShiftItem* items, int count, cudaStream_t s);
 cudaError_t launch_read_box(const uint32_t* grid, const long long lo[3], const uint32_t box[3],

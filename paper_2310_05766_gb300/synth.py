@@ -288,11 +288,11 @@ def delta_z_for(vfov_deg: float, hlines: int) -> float:
     return float(np.float32(math.tan(math.radians(vfov_deg / hlines))))
 
 
-def params_dict(dims, voxel_size, tau, w_max, delta_z, r_min, r_max, reduce=0, origin=(0, 0, 0)):
+def params_dict(dims, voxel_size, tau, w_max, delta_z, r_min, r_max, reduce=0, origin=(0, 0, 0), flags=0):
     return dict(dims=tuple(int(x) for x in dims), voxel_size=float(np.float32(voxel_size)),
                 tau=float(np.float32(tau)), w_max=int(w_max), delta_z=float(np.float32(delta_z)),
                 r_min=float(np.float32(r_min)), r_max=float(np.float32(r_max)), reduce=int(reduce),
-                origin=tuple(int(x) for x in origin))
+                origin=tuple(int(x) for x in origin), flags=int(flags))
 
 
 def window_origin(center_xyz, dims, voxel_size) -> tuple:

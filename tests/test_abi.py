@@ -74,7 +74,8 @@ def test_host_side_validation_without_gpu():
            dict(base, w_max=0), dict(base, w_max=40000), dict(base, delta_z=-1.0), dict(base, delta_z=float("nan")),
            dict(base, r_max=0.1), dict(base, reduce=2), dict(base, origin=(-31, -32, -32)),
            dict(base, voxel_size=0.0), dict(base, dims=(32768, 32768, 8)),
-           dict(base, origin=((1 << 23) + 8, 0, 0)), dict(base, origin=(0, 0, -(1 << 23) - 8))]
+           dict(base, origin=((1 << 23) + 8, 0, 0)), dict(base, origin=(0, 0, -(1 << 23) - 8)),
+           dict(base, flags=4), dict(base, flags=-1)]
     for p in bad:
         h = ctypes.c_void_p()
         rc = b.lib().tsdf_map_create(ctypes.byref(b.make_params(p)), ctypes.byref(h))

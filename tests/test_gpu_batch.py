@@ -106,6 +106,28 @@ def test_batch_autotune_settles_and_is_exact():
         m.close()
 
 
+def test_batch_flags_match_single():
+    """Maps with different reading flags in one batched launch: each equals
+    its own per-map integration (and so the oracle, which the per-map path
+    matches)."""
+    from paper_2310_05766_gb300 import binding as b
+    ws = _small_batch(6, seed=19)
+    for i, w in enumerate(ws):
+        w.params["flags"] = i % 4
+    mb = _run_batch(b, ws, prefill_steps=1)
+    ms = _run_single(b, ws, repeats=2)
+    _same(b, mb, ms)
+    for m, w in zip(mb[1:4], ws[1:4]):
+        om = oracle.OracleMap(w.params)
+        om.integrate(w.scans[0], w.poses[0])
+        om.integrate(w.scans[0], w.poses[0])
+        vo, wo = om.read()
+        vg, wg = m.read()
+        assert np.array_equal(vg, vo) and np.array_equal(wg, wo)
+    for m in mb + ms:
+        m.close()
+
+
 def test_batch_uneven_sizes_and_empty_scans():
     from paper_2310_05766_gb300 import binding as b
     ws = _small_batch(5, seed=17)

@@ -130,6 +130,43 @@ def test_random_small_exact(seed):
     both(p, steps, label=f"random seed {seed}")
 
 
+# ---------------------------------------------------------------- alternative readings (map flags)
+
+@pytest.mark.parametrize("flags", [1, 2, 3])
+@pytest.mark.parametrize("reduce", [0, 1])
+def test_room_flags_exact(flags, reduce):
+    """Step-valued fill (flag 1) and one observation per scan (flag 2): two
+    scans (the second onto a map with weights) bit-exact against the oracle."""
+    w = synth.workload_room(reduce=reduce)
+    p = dict(w.params, flags=flags)
+    steps = workload_steps(w) + [("scan", w.scans[0], w.poses[0])]
+    g, o = both(p, steps, label=f"room flags={flags} reduce={reduce}")
+    assert g[2][0]["hits"] > 300000
+
+
+@pytest.mark.parametrize("flags", [1, 2, 3])
+def test_flags_with_tuning_options(flags):
+    from paper_2310_05766_gb300 import binding as b
+    w = synth.workload_outdoor(n_scans=2)
+    for merge, kpt in [(1, 2), (0, 1)]:
+        opts = {b.TSDF_OPT_WARP_MERGE: merge, b.TSDF_OPT_STEPS_PER_THREAD: kpt}
+        both(dict(w.params, flags=flags), workload_steps(w), options=opts, label=f"outdoor flags={flags} {opts}")
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_small_flags_exact(seed):
+    p, steps = _rand_case(seed)
+    both(dict(p, flags=seed % 3 + 1), steps, label=f"random seed {seed} flags {seed % 3 + 1}")
+
+
+def test_unknown_flag_bits_rejected():
+    from paper_2310_05766_gb300 import binding as b
+    w = synth.workload_room()
+    for fl in (4, 8, -1):
+        with pytest.raises(b.TsdfError):
+            b.TsdfMap(dict(w.params, flags=fl))
+
+
 # ---------------------------------------------------------------- edge cases
 
 def _edge_params(**kw):

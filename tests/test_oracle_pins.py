@@ -535,3 +535,148 @@ def test_integrate_after_shift_matches_bigger_window():
     a = m.read()
     b = big.read((-24, -40, -16), (40, 24, 16))
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+# ---------------------------------------------------------------- alternative readings (map flags)
+
+FLAG_STEP, FLAG_SCAN = 1, 2
+
+
+def test_eq12_scan_weight_golden_table():
+    """Eq. 1 / Eq. 2 with the scan's average as one observation, against the
+    hand-computed table (tests/golden/eq12_scan_table.txt)."""
+    rows = _table("eq12_scan_table.txt")
+    assert len(rows) >= 15
+    for r in rows:
+        gv, gw, S, W, wmax, ev, ew = (int(x) for x in r)
+        assert oracle.eq12(gv, gw, S, W, wmax, scan_weight=True) == (ev, ew), r
+
+
+def test_eq12_scan_weight_exact_rational():
+    """Random cases against exact rationals: value = (gv*gw + S/W)/(gw+1) rounded
+    half away from zero; with W = 1 it is plain Eq. 1."""
+    rng = np.random.default_rng(15)
+    for _ in range(3000):
+        gv = int(rng.integers(-32767, 32768))
+        gw = int(rng.integers(0, 65))
+        W = int(rng.integers(1, 300))
+        S = int(rng.integers(-32767, 32768)) * W // max(1, int(rng.integers(1, 4)))
+        wmax = int(rng.integers(1, 65))
+        x = (Fraction(gv * gw) + Fraction(S, W)) / (gw + 1)
+        mag = math.floor(abs(x) + Fraction(1, 2))
+        ev = mag if x >= 0 else -mag
+        assert oracle.eq12(gv, gw, S, W, wmax, scan_weight=True) == (ev, min(wmax, gw + 1))
+        if W == 1:
+            assert oracle.eq12(gv, gw, S, 1, wmax, scan_weight=True) == oracle.eq12(gv, gw, S, 1, wmax)
+
+
+def test_step_value_closed_form():
+    """Step-valued fill: every voxel of march step k, the ray voxel and all its
+    vertical fill voxels, carries the code of d = r - l = -k * voxel. With
+    r = 1.5, voxel 0.125 and tau 0.5 all of it is exact in binary32, so the
+    codes are rint(-k * 0.125 * 65534), ties to even:
+    k = -4..4 -> 32767, 24575, 16384, 8192, 0, -8192, -16384, -24575, -32767."""
+    expect = {-4: 32767, -3: 24575, -2: 16384, -1: 8192, 0: 0, 1: -8192, 2: -16384, 3: -24575, 4: -32767}
+    pose = synth.pose12(np.eye(3), np.array([0.25, -0.5, 0.125]))
+    pts = np.array([[0.5, 1.0, 1.0, 0.0]], np.float32)          # |p| = 1.5 exactly, oblique
+    for dz in (0.0, 0.1):
+        p = synth.params_dict((64, 64, 64), 0.125, 0.5, 64, dz, 0.1, 10.0, 0, (-32, -32, -32),
+                              flags=FLAG_STEP)
+        assert oracle.derived(p)[1] == np.float32(65534.0)
+        g, q, _, k = oracle.hits(p, pts, pose, with_k=True)
+        assert sorted(set(k.tolist())) == list(range(-4, 5))
+        for kk, qq in zip(k.tolist(), q.tolist()):
+            assert qq == expect[kk]
+        counts = np.bincount(k + 4)
+        if dz == 0.0:
+            assert np.all(counts == 1)
+        else:
+            # J = floor(0.1 * l / 0.125) per side at l = 1.5 + 0.125 k
+            J = [math.floor(0.1 * (1.5 + 0.125 * kk) / 0.125) for kk in range(-4, 5)]
+            assert counts.tolist() == [2 * j + 1 for j in J]
+        # the default projective reading differs off the ray's voxel centres
+        p0 = dict(p, flags=0)
+        _, q0, _ = oracle.hits(p0, pts, pose)
+        assert len(q0) == len(q) and not np.array_equal(q0, q)
+
+
+def test_step_value_vs_projective_on_axis():
+    """On an axis-aligned ray through voxel centres, the step's distance and the
+    projective distance of the ray voxel coincide: the codes of the j = 0 voxels
+    agree between the two readings (tests/golden/axis_ray_fill.json geometry)."""
+    gold = json.load(open(os.path.join(GOLD, "axis_ray_fill.json")))
+    gp = gold["params"]
+    p = synth.params_dict(gp["dims"], gp["voxel_size"], gp["tau"], gp["w_max"], gp["delta_z"], gp["r_min"],
+                          gp["r_max"], 0, gp["origin"])
+    pts = np.array([gold["point"]], np.float32)
+    pose = np.array(gold["pose"], np.float32)
+    g0, q0, _, k0 = oracle.hits(p, pts, pose, with_k=True)
+    g1, q1, _, k1 = oracle.hits(dict(p, flags=FLAG_STEP), pts, pose, with_k=True)
+    assert np.array_equal(g0, g1) and np.array_equal(k0, k1)
+    steps = {s["x"]: s["q"] for s in gold["steps"]}
+    for (x, y, z), qa, qb in zip(g0.tolist(), q0.tolist(), q1.tolist()):
+        assert qb == steps[x]            # every voxel of a step takes the step's code
+        if z == 0:
+            assert qa == qb
+
+
+@pytest.mark.parametrize("flags", [FLAG_STEP, FLAG_SCAN, FLAG_STEP | FLAG_SCAN])
+@pytest.mark.parametrize("reduce", [0, 1])
+@pytest.mark.parametrize("seed", range(3))
+def test_bruteforce_matches_ray_major_flags(flags, reduce, seed):
+    """Both readings through the voxel-major brute force, bit for bit."""
+    rng = np.random.default_rng(300 + seed)
+    vs = [0.1, 0.125, 0.08][seed]
+    origin = [(-8, -8, -8), (0, -16, 8), (-16, 0, -8)][seed]
+    p = synth.params_dict((16, 16, 16), vs, [0.2, 0.3, 0.25][seed], int(rng.integers(1, 20)),
+                          [0.05, 0.2, 0.1][seed], 0.05, 3.0, reduce, origin, flags=flags)
+    centre = np.array([(o + 8) * vs for o in origin])
+    pts, pose = _random_scan(rng, 48, (0.3, 1.0), (centre - 0.2, centre + 0.2), origin, vs)
+    v0 = rng.integers(-32767, 32768, size=(16, 16, 16)).astype(np.int16)
+    w0 = rng.integers(0, p["w_max"] + 1, size=(16, 16, 16)).astype(np.int16)
+    a, b = oracle.OracleMap(p), oracle.OracleMap(p)
+    a.load_window(v0, w0)
+    b.load_window(v0, w0)
+    a.integrate(pts, pose)
+    b.integrate(pts, pose, bruteforce=True)
+    assert a.stats()["hits"] > 100
+    va, wa = a.read()
+    vb, wb = b.read()
+    assert np.array_equal(va, vb) and np.array_equal(wa, wb)
+
+
+def test_scan_weight_relations():
+    """Per-scan weight reading on a room scan: on an empty map the values equal
+    the default reading's and every touched weight is 1; a second identical
+    scan leaves values within one code and raises each weight by exactly 1;
+    MIN_ABS (weight 1 per scan already) is unchanged by the flag."""
+    w = synth.workload_room(seed=9)
+    pts, pose, p = w.scans[0], w.poses[0], w.params
+    base = oracle.OracleMap(p)
+    scan = oracle.OracleMap(dict(p, flags=FLAG_SCAN))
+    base.integrate(pts, pose)
+    scan.integrate(pts, pose)
+    vb, wb = base.read()
+    vs_, ws = scan.read()
+    assert np.array_equal(vb, vs_)
+    assert np.array_equal(ws, (wb > 0).astype(np.int16))
+    assert int(wb.max()) > 1
+    scan.integrate(pts, pose)
+    v2, w2 = scan.read()
+    t = ws > 0
+    assert np.all(np.abs(v2[t].astype(int) - vs_[t].astype(int)) <= 1)
+    assert np.array_equal(w2[t], np.minimum(ws[t] + 1, p["w_max"]))
+    for fl in (0, FLAG_SCAN):
+        m = oracle.OracleMap(dict(p, reduce=1, flags=fl))
+        m.integrate(pts, pose)
+        if fl == 0:
+            ref = m.read()
+        else:
+            got = m.read()
+            assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1])
+
+
+def test_oracle_rejects_unknown_flag_bits():
+    p = synth.params_dict((16, 16, 16), 0.1, 0.2, 8, 0.0, 0.05, 3.0, 0, (0, 0, 0), flags=4)
+    with pytest.raises(ValueError):
+        oracle.OracleMap(p)

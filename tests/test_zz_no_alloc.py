@@ -38,17 +38,17 @@ def _two_scans():
     return out
 
 
-def _params(reduce=0):
+def _params(reduce=0, flags=0):
     # 128 x 128 x 64 = 2^20 voxels (inside the fixed scratch limit) at 0.1 m:
     # the window covers the whole 10 x 10 x 3 m room
     return synth.params_dict((128, 128, 64), 0.1, 0.3, 64, synth.delta_z_for(30.0, 16), 0.3, 20.0, reduce,
-                             (-64, -64, -32))
+                             (-64, -64, -32), flags=flags)
 
 
-@pytest.mark.parametrize("reduce", [0, 1])
-def test_static_entry_matches_allocating_path(reduce):
+@pytest.mark.parametrize("reduce,flags", [(0, 0), (1, 0), (0, 3)])
+def test_static_entry_matches_allocating_path(reduce, flags):
     from paper_2310_05766_gb300 import binding as b
-    p = _params(reduce)
+    p = _params(reduce, flags)
     voxels = p["dims"][0] * p["dims"][1] * p["dims"][2]
     scans = _two_scans()
     # reference: the allocating entry points
