@@ -186,8 +186,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
 
     m = b.TsdfMap(p)
     h = m.handle
+    sort = args.reduction == "sort"
     for opt, val in ((b.TSDF_OPT_WARP_MERGE, args.merge), (b.TSDF_OPT_STEPS_PER_THREAD, args.kpt),
-                     (b.TSDF_OPT_PDL, args.pdl)):
+                     (b.TSDF_OPT_PDL, args.pdl), (b.TSDF_OPT_REDUCTION, 1 if sort else None)):
         if val is not None:
             b.tsdf_set_option(h, opt, val)
     cur = tuple(p["origin"])
@@ -286,10 +287,12 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     K = len(timed)
     # roofline of the dominant kernel
     peak, peak_kind = peaks()
-    kern = max(prof.items(), key=lambda kv: kv[1][1])
+    # (the sort group -- compaction, count, prefix, scatter -- only reorders
+    # contributions and has no algorithmic bytes of its own)
+    kern = max(((k, v) for k, v in prof.items() if k in ("contrib", "emit", "apply")), key=lambda kv: kv[1][1])
     kname, (klaunch, kms) = kern
     n_pts = scans_dev[0].shape[0]
-    if kname == "contrib":
+    if kname in ("contrib", "emit"):
         # points in (16 B each) + the per-scan volume written once (8 B per touched voxel)
         alg_bytes = (16.0 * n_pts * K + 8.0 * touched_timed) / klaunch
     elif kname == "apply":
@@ -299,6 +302,19 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         alg_bytes = float("nan")
     k_avg_s = kms / klaunch / 1e3
     achieved = alg_bytes / k_avg_s / 1e9
+    # contribution kernel against the measured L2 reduction rate (one 64-bit
+    # reduction per in-window sample in the atomic reduction)
+    l2red = None
+    if "contrib" in prof:
+        rate_coal = b.tsdf_probe_reduction_rate(0, stream)
+        rate_scat = b.tsdf_probe_reduction_rate(1, stream)
+        c_launch, c_ms = prof["contrib"]
+        red_rate = hits_timed / (c_ms / 1e3) if c_launch == K else float("nan")
+        l2red = dict(kernel="contrib", achieved=red_rate, unit="reductions/s",
+                     peak_coalesced=rate_coal, peak_scattered=rate_scat,
+                     frac_coalesced=red_rate / rate_coal, frac_scattered=red_rate / rate_scat,
+                     peak_source="tsdf_probe_reduction_rate, measured in this run (64-bit red.add into a 64 MiB "
+                                 "L2-resident buffer, GPU-filling grid)")
     kernels = {k: dict(launches=v[0], total_ms=round(v[1], 4), avg_us=round(1e3 * v[1] / v[0], 3),
                        share=round(v[1] / sum(x[1] for x in prof.values()), 4)) for k, v in prof.items()}
 
@@ -317,7 +333,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         config=dict(workload="outdoor OS1-128 sequence: 128x1024 beams, 100 scans at 10 Hz, 1 m/s, "
                              "window 512x512x128 at 0.064 m, tau 0.6 m, shift every 1 m (ping-pong over the sequence)",
                     points_per_scan=int(n_pts), voxel_size=p["voxel_size"], tau=p["tau"], dims=list(p["dims"]),
-                    reduce="WSUM", l2="flushed (512 MiB write) before every timed step; flush excluded by per-step events",
+                    reduce="WSUM", reduction=args.reduction, l2="flushed (512 MiB write) before every timed step; flush excluded by per-step events",
                     parallelism=f"replicas x{world}"),
         scans_per_s=K * world / (dev_ms_max / 1e3),
         us_per_scan=dict(mean=1e3 * dev_ms_max / K, p50=1e3 * float(np.percentile(step_ms, 50)),
@@ -329,14 +345,17 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                      "each kernel (that pass: %.1f us/scan; events serialise the kernels of a step)" %
                      (1e3 * float(sum(prof_step_ms)) / K),
         roofline=dict(kernel=kname, bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
-                      peak_source=f"{peak_kind} hbm_gbs", traffic=NCU_DRAM_BYTES.get(kname),
+                      peak_source=f"{peak_kind} hbm_gbs", traffic=None if sort else NCU_DRAM_BYTES.get(kname),
                       alg_bytes_def=("16 B per point read + 8 B per touched voxel of the per-scan volume"
-                                     if kname == "contrib" else "16 B per touched voxel (volume read + grid RMW)"),
-                      alg_bytes_per_launch=alg_bytes, avg_launch_us=k_avg_s * 1e6),
+                                     if kname in ("contrib", "emit") else
+                                     "16 B per touched voxel (volume read + grid RMW)"),
+                      alg_bytes_per_launch=alg_bytes, avg_launch_us=k_avg_s * 1e6, l2_reductions=l2red),
         e2e=dict(value=e2e_hits_all / t_e2e_max, unit=UNIT, h2d_bytes_per_step=int(16 * n_pts),
                  d2h_bytes_per_step=24, steps=n_e2e,
                  note="tsdf_integrate_host from pinned memory + tsdf_stats read-back, host wall clock"),
-        gpu_launches=int(sum(v[0] for v in prof.values()) + 2 * K),   # + compact and finish per step
+        # library launches: one per profiled entry, plus compact + finish (atomic) or
+        # compact + count + prefix + scatter and finish (sort) that share an entry
+        gpu_launches=int(sum(v[0] for v in prof.values()) + (4 if sort else 2) * K),
         clocks=clk,
         wall_s_timed=t_wall,
         cpu_baseline=cpu,
@@ -555,6 +574,8 @@ def main():
     ap.add_argument("--merge", type=int, default=None, help="tuning: warp match-merge (0/1)")
     ap.add_argument("--kpt", type=int, default=None, help="tuning: march steps per contribution thread (1/2/4)")
     ap.add_argument("--pdl", type=int, default=None, help="tuning: programmatic dependent launch (0/1)")
+    ap.add_argument("--reduction", default="atomic", choices=["atomic", "sort"],
+                    help="per-scan reduction: accumulator atomics or counting sort by brick")
     ap.add_argument("--workload", default="outdoor", choices=["outdoor", "batch", "serving"],
                     help="outdoor: the headline sequence; batch / serving: the 64-map batch and 32-session serving runs")
     ap.add_argument("--serve-seconds", type=float, default=20.0)

@@ -161,9 +161,22 @@ int tsdf_stats(tsdf_map* map, tsdf_scan_stats* out, void* stream);
 #define TSDF_OPT_PDL         3  /* 1 (default): the kernels of one integrate call use programmatic dependent
                                    launch, so each may be scheduled while the previous one drains; 0: plain
                                    stream order */
+#define TSDF_OPT_REDUCTION   4  /* how a scan's contributions are combined per voxel (the per-scan volume of
+                                   Section "TSDF Map Generation"): TSDF_REDUCTION_ATOMIC (default) or
+                                   TSDF_REDUCTION_SORT. Both give bit-identical maps and counters. */
+#define TSDF_OPT_SORT_CAPACITY 5  /* sort reduction: pair slots held by the map (each 12 bytes of device
+                                   memory); 0 (default): 32 per point of the largest scan so far, at least
+                                   2^20; otherwise 1024 .. 2^28. Samples beyond the capacity are reduced
+                                   with accumulator atomics instead (same result, slower). */
+
+#define TSDF_REDUCTION_ATOMIC 0  /* each contribution is one 64-bit reduction into a per-voxel accumulator */
+#define TSDF_REDUCTION_SORT   1  /* contributions are written as (voxel, code) pairs, counting-sorted by brick
+                                   and reduced per voxel in shared memory; no per-contribution atomics. Buffers
+                                   are allocated on the first integrate call that uses it (synchronous). */
 
 /* Set a tuning option of a map; takes effect for later calls. Host-side
- * state only. Errors: INVALID (unknown option or value). */
+ * state only (the sort buffers are allocated by the next integrate call).
+ * Errors: INVALID (unknown option or value). */
 int tsdf_set_option(tsdf_map* map, int32_t option, int64_t value);
 
 /* Current window origin (host-side state; no synchronisation). */
@@ -194,6 +207,15 @@ int tsdf_profile_enable(tsdf_map* map, int32_t enable);
  * Errors: INVALID, CUDA. */
 int tsdf_profile_read(tsdf_map* map, tsdf_kernel_time* out, int32_t capacity, int32_t* count);
 
+/* ---- measurement ------------------------------------------------------------
+ * Sustained rate (operations per second) of fire-and-forget 64-bit integer
+ * reductions into L2-resident device memory on the current device, the
+ * operation the contribution kernel issues once per in-window sample:
+ * pattern 0 = each warp's lanes on 32 consecutive words, 1 = scattered words.
+ * Allocates and frees a 64 MiB scratch buffer; synchronises `stream`.
+ * Errors: INVALID, OOM, CUDA. */
+int tsdf_probe_reduction_rate(int32_t pattern, double* per_second, void* stream);
+
 /* ---- batched integration ---------------------------------------------------
  * Integrates one scan into each of many maps in a single persistent
  * cooperative launch: the phases of tsdf_integrate (ray set-up, contributions,
@@ -207,7 +229,9 @@ typedef struct tsdf_batch tsdf_batch;   /* opaque; owns pinned and device descri
 
 #define TSDF_BATCH_OPT_GRAPH      1  /* 1 (default): replay a captured CUDA graph; 0: plain launches */
 #define TSDF_BATCH_OPT_AUTOTUNE   2  /* 1 (default): time every tuning configuration on the first calls and keep the fastest */
-#define TSDF_BATCH_OPT_CONFIG     3  /* fix the tuning configuration (0..5: {no merge, merge} x {4, 2, 1} steps per item); turns autotuning off */
+#define TSDF_BATCH_OPT_CONFIG     3  /* fix the tuning configuration; turns autotuning off. 0..5: atomic reduction,
+                                        {no merge, merge} x {4, 2, 1} steps per item; 6, 7: sort reduction
+                                        (TSDF_REDUCTION_SORT) with 4, 2 steps per item */
 #define TSDF_BATCH_OPT_SPIN_LIMIT 4  /* polls before a grid-barrier wait gives up (default 2^24, about a second) */
 #define TSDF_BATCH_OPT_TEST_MISSING_ARRIVALS 5  /* test hook: the barrier waits for this many CTAs that do not exist (default 0) */
 #define TSDF_BATCH_OPT_GRID_FRACTION 6  /* percent (1..100, default 100) of the device's co-resident CTAs the launch uses,
@@ -224,9 +248,10 @@ int tsdf_batch_destroy(tsdf_batch* batch);
 int tsdf_batch_set_option(tsdf_batch* batch, int32_t option, int64_t value);
 
 /* The tuning configuration in use: index, warp merge (0/1), steps per work
- * item, and whether autotuning has finished (any pointer may be NULL). */
+ * item, reduction (TSDF_REDUCTION_*), and whether autotuning has finished
+ * (any pointer may be NULL). */
 int tsdf_batch_get_config(const tsdf_batch* batch, int32_t* config, int32_t* merge, int32_t* steps_per_item,
-                          int32_t* tuned);
+                          int32_t* reduction, int32_t* tuned);
 
 /* Integrate scan i (points_dev[i]: n[i] device float4 points, 16-byte
  * aligned; poses + 12*i: host row-major 3x4 pose) into maps[i], for i <

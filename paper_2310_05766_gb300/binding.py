@@ -29,6 +29,10 @@ TSDF_MAX_POINTS = 1 << 22
 TSDF_OPT_WARP_MERGE = 1
 TSDF_OPT_STEPS_PER_THREAD = 2
 TSDF_OPT_PDL = 3
+TSDF_OPT_REDUCTION = 4
+TSDF_OPT_SORT_CAPACITY = 5
+TSDF_REDUCTION_ATOMIC = 0
+TSDF_REDUCTION_SORT = 1
 TSDF_BATCH_OPT_GRAPH = 1
 TSDF_BATCH_OPT_AUTOTUNE = 2
 TSDF_BATCH_OPT_CONFIG = 3
@@ -111,10 +115,11 @@ def lib():
     L.tsdf_set_option.argtypes = [vp, ctypes.c_int32, ctypes.c_int64]
     L.tsdf_profile_enable.argtypes = [vp, ctypes.c_int32]
     L.tsdf_profile_read.argtypes = [vp, P(tsdf_kernel_time), ctypes.c_int32, P(ctypes.c_int32)]
+    L.tsdf_probe_reduction_rate.argtypes = [ctypes.c_int32, P(ctypes.c_double), vp]
     L.tsdf_batch_create.argtypes = [ctypes.c_int32, P(vp)]
     L.tsdf_batch_destroy.argtypes = [vp]
     L.tsdf_batch_set_option.argtypes = [vp, ctypes.c_int32, ctypes.c_int64]
-    L.tsdf_batch_get_config.argtypes = [vp] + [P(ctypes.c_int32)] * 4
+    L.tsdf_batch_get_config.argtypes = [vp] + [P(ctypes.c_int32)] * 5
     L.tsdf_batch_integrate.argtypes = [vp, P(vp), P(vp), P(i64), f32p, ctypes.c_int32, vp]
     L.tsdf_integrate_batch.argtypes = [P(vp), P(vp), P(i64), f32p, ctypes.c_int32, vp]
     L.tsdf_batch_sync.argtypes = [vp, vp]
@@ -133,7 +138,7 @@ def lib():
     for name in ("tsdf_map_create", "tsdf_map_destroy", "tsdf_integrate", "tsdf_integrate_host", "tsdf_shift",
                  "tsdf_read", "tsdf_write", "tsdf_stats", "tsdf_get_origin", "tsdf_grid_device_ptr",
                  "tsdf_last_cuda_error", "tsdf_profile_enable", "tsdf_profile_read", "tsdf_set_option",
-                 "tsdf_integrate_static", "tsdf_batch_create", "tsdf_batch_destroy", "tsdf_batch_set_option",
+                 "tsdf_integrate_static", "tsdf_probe_reduction_rate", "tsdf_batch_create", "tsdf_batch_destroy", "tsdf_batch_set_option",
                  "tsdf_batch_get_config", "tsdf_batch_integrate", "tsdf_integrate_batch", "tsdf_batch_sync",
                  "tsdf_server_create", "tsdf_server_destroy", "tsdf_server_open_session", "tsdf_server_close_session",
                  "tsdf_server_submit", "tsdf_server_wait", "tsdf_server_session_map", "tsdf_server_get_stats"):
@@ -306,10 +311,10 @@ def tsdf_batch_set_option(batch: int, option: int, value: int) -> None:
 
 
 def tsdf_batch_get_config(batch: int) -> dict:
-    c, m, k, t = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-    _check(lib().tsdf_batch_get_config(batch, ctypes.byref(c), ctypes.byref(m), ctypes.byref(k), ctypes.byref(t)),
-           "tsdf_batch_get_config")
-    return dict(config=c.value, merge=m.value, steps_per_item=k.value, tuned=bool(t.value))
+    c, m, k, r, t = (ctypes.c_int32() for _ in range(5))
+    _check(lib().tsdf_batch_get_config(batch, ctypes.byref(c), ctypes.byref(m), ctypes.byref(k), ctypes.byref(r),
+                                       ctypes.byref(t)), "tsdf_batch_get_config")
+    return dict(config=c.value, merge=m.value, steps_per_item=k.value, reduction=r.value, tuned=bool(t.value))
 
 
 def tsdf_batch_integrate(batch: int, maps, points, poses, stream=None) -> None:
@@ -405,6 +410,13 @@ def tsdf_profile_read(handle: int) -> dict:
     cnt = ctypes.c_int32()
     _check(lib().tsdf_profile_read(handle, buf, 8, ctypes.byref(cnt)), "tsdf_profile_read")
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(cnt.value)}
+
+
+def tsdf_probe_reduction_rate(pattern: int, stream=None) -> float:
+    """Measured 64-bit L2 reduction rate (ops/s): pattern 0 coalesced, 1 scattered."""
+    out = ctypes.c_double()
+    _check(lib().tsdf_probe_reduction_rate(pattern, ctypes.byref(out), _stream_ptr(stream)), "tsdf_probe_reduction_rate")
+    return out.value
 
 
 # ---- convenience wrapper ---------------------------------------------------

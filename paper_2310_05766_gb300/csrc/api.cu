@@ -71,8 +71,8 @@ long long floordiv8(long long v) { return v >= 0 ? v / 8 : -((-v + 7) / 8); }
 
 const long long kOriginLimit = 1LL << 23;   // window voxels stay below 2^24: exact as float
 
-enum KernelId { kRays = 0, kContrib = 1, kApply = 2, kShift = 3, kNumKernels = 4 };
-const char* const kKernelNames[kNumKernels] = {"rays", "contrib", "apply", "shift"};
+enum KernelId { kRays = 0, kContrib = 1, kApply = 2, kShift = 3, kEmit = 4, kSort = 5, kNumKernels = 6 };
+const char* const kKernelNames[kNumKernels] = {"rays", "contrib", "apply", "shift", "emit", "sort"};
 
 struct Pending {
     int kernel;
@@ -110,12 +110,15 @@ struct tsdf_map {
     bool merge = false;             // warp match-merge before the accumulator atomics
     int kpt = 4;                    // march steps per contribution item (1, 2 or 4)
     bool pdl = true;                // programmatic dependent launch between the scan's kernels
+    int reduction = TSDF_REDUCTION_ATOMIC;   // per-scan reduction: accumulator atomics or sort
+    size_t pair_cap_req = 0;        // sort reduction: requested pair capacity, 0 = from the scan size
+    size_t ray_slot_cap = 0;        // entries of dev.ray_slot
     // optional per-kernel event timing
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<Pending> pending;
-    int64_t prof_launches[kNumKernels] = {0, 0, 0, 0};
-    double prof_ms[kNumKernels] = {0.0, 0.0, 0.0, 0.0};
+    int64_t prof_launches[kNumKernels] = {};
+    double prof_ms[kNumKernels] = {};
 };
 
 namespace {
@@ -204,6 +207,12 @@ void free_map(tsdf_map* m) {
     cudaFree(m->dev.ray_a);
     cudaFree(m->dev.ray_b);
     cudaFree(m->dev.ctr);
+    cudaFree(m->dev.brick_slot);
+    cudaFree(m->dev.seg_count);
+    cudaFree(m->dev.seg_start);
+    cudaFree(m->dev.ray_slot);
+    cudaFree(m->dev.pairs);
+    cudaFree(m->dev.sorted);
     for (char* s : m->store_segments) cudaFree(s);
     cudaFree(m->items_dev);
     if (m->items_host) cudaFreeHost(m->items_host);
@@ -315,6 +324,41 @@ static int ensure_rays(tsdf_map* map, int64_t n) {
     return TSDF_OK;
 }
 
+// Sort-reduction buffers: per-brick arrays once, per-ray slots with the ray
+// buffers, pairs for `n` points (32 slots per point, at least 2^20, at most
+// kPairCapMax, unless a capacity was requested). Growing waits for the device.
+static int ensure_sort(tsdf_map* map, int64_t n) {
+    if (!map->dev.brick_slot) {
+        TSDF_CU(cudaMalloc(&map->dev.brick_slot, map->bricks * sizeof(uint32_t)));
+        TSDF_CU(cudaMalloc(&map->dev.seg_count, map->bricks * sizeof(uint32_t)));
+        TSDF_CU(cudaMalloc(&map->dev.seg_start, map->bricks * sizeof(uint32_t)));
+        TSDF_CU(cudaMemset(map->dev.seg_count, 0, map->bricks * sizeof(uint32_t)));
+    }
+    if (map->ray_slot_cap < map->ray_cap) {
+        cudaFree(map->dev.ray_slot);
+        map->dev.ray_slot = nullptr;
+        map->ray_slot_cap = 0;
+        TSDF_CU(cudaMalloc(&map->dev.ray_slot, map->ray_cap * sizeof(uint32_t)));
+        map->ray_slot_cap = map->ray_cap;
+    }
+    size_t want = map->pair_cap_req;
+    if (want == 0) {
+        want = (size_t)1 << 20;
+        while (want < 32 * (size_t)n && want < kPairCapMax) want *= 2;
+    }
+    if (want != map->dev.pair_cap && (map->pair_cap_req != 0 || want > map->dev.pair_cap)) {
+        cudaFree(map->dev.pairs);
+        cudaFree(map->dev.sorted);
+        map->dev.pairs = nullptr;
+        map->dev.sorted = nullptr;
+        map->dev.pair_cap = 0;
+        TSDF_CU(cudaMalloc(&map->dev.pairs, want * sizeof(uint2)));
+        TSDF_CU(cudaMalloc(&map->dev.sorted, want * sizeof(uint32_t)));
+        map->dev.pair_cap = (uint32_t)want;
+    }
+    return TSDF_OK;
+}
+
 static void fill_scan_args(const tsdf_map* map, const float* points_dev, int64_t n, const float pose[12], ScanArgs& a) {
     a = ScanArgs{};
     a.pts = reinterpret_cast<const float4*>(points_dev);
@@ -355,8 +399,34 @@ static int integrate_dev(tsdf_map* map, const float* points_dev, int64_t n, cons
     ScanArgs a;
     fill_scan_args(map, points_dev, n, pose, a);
     const bool pdl = map->pdl;
+    if (map->reduction == TSDF_REDUCTION_SORT) {
+        rc = ensure_sort(map, n);
+        if (rc != TSDF_OK) return rc;
+        const MapDev& d = map->dev;
+        cudaEvent_t e0 = n > 0 ? prof_mark(map, s) : nullptr;
+        TSDF_CU(launch_rays(a, d, true, pdl, s));
+        cudaEvent_t e1 = n > 0 ? prof_mark(map, s) : nullptr;
+        cudaEvent_t e2 = n > 0 ? prof_mark(map, s) : nullptr;
+        TSDF_CU(launch_emit(a, d, map->p.reduce, map->kpt, pdl, s));
+        cudaEvent_t e3 = n > 0 ? prof_mark(map, s) : nullptr;
+        cudaEvent_t e4 = prof_mark(map, s);
+        TSDF_CU(launch_compact(d, (uint32_t)map->bricks, pdl, s));
+        TSDF_CU(launch_sort_count(d, pdl, s));
+        TSDF_CU(launch_sort_scan(d, pdl, s));
+        TSDF_CU(launch_sort_scatter(d, pdl, s));
+        cudaEvent_t e5 = prof_mark(map, s);
+        cudaEvent_t e6 = prof_mark(map, s);
+        TSDF_CU(launch_sort_apply(d, map->p.reduce, map->p.w_max, map->p.flags, map->num_sms * 8, pdl, s));
+        TSDF_CU(launch_finish(d, pdl, s));
+        cudaEvent_t e7 = prof_mark(map, s);
+        prof_push(map, kRays, e0, e1);
+        prof_push(map, kEmit, e2, e3);
+        prof_push(map, kSort, e4, e5);
+        prof_push(map, kApply, e6, e7);
+        return TSDF_OK;
+    }
     cudaEvent_t e0 = n > 0 ? prof_mark(map, s) : nullptr;
-    TSDF_CU(launch_rays(a, map->dev, pdl, s));
+    TSDF_CU(launch_rays(a, map->dev, false, pdl, s));
     cudaEvent_t e1 = n > 0 ? prof_mark(map, s) : nullptr;
     cudaEvent_t e2 = n > 0 ? prof_mark(map, s) : nullptr;
     TSDF_CU(launch_contrib(a, map->dev, map->p.reduce, map->merge, map->kpt, pdl, s));
@@ -587,6 +657,14 @@ int tsdf_set_option(tsdf_map* map, int32_t option, int64_t value) {
             if (value != 0 && value != 1) return TSDF_ERR_INVALID;
             map->pdl = value != 0;
             return TSDF_OK;
+        case TSDF_OPT_REDUCTION:
+            if (value != TSDF_REDUCTION_ATOMIC && value != TSDF_REDUCTION_SORT) return TSDF_ERR_INVALID;
+            map->reduction = (int)value;
+            return TSDF_OK;
+        case TSDF_OPT_SORT_CAPACITY:
+            if (value != 0 && (value < 1024 || value > (int64_t)kPairCapMax)) return TSDF_ERR_INVALID;
+            map->pair_cap_req = (size_t)value;
+            return TSDF_OK;
         default: return TSDF_ERR_INVALID;
     }
 }
@@ -646,6 +724,14 @@ int map_reserve_points(::tsdf_map* map, int64_t n) {
     if (!map || n < 0 || n > TSDF_MAX_POINTS) return TSDF_ERR_INVALID;
     DeviceScope ds(map->device);
     return ensure_rays(map, n);
+}
+
+int map_reserve_sort(::tsdf_map* map, int64_t n) {
+    if (!map || n < 0 || n > TSDF_MAX_POINTS) return TSDF_ERR_INVALID;
+    DeviceScope ds(map->device);
+    int rc = ensure_rays(map, n);
+    if (rc != TSDF_OK) return rc;
+    return ensure_sort(map, n);
 }
 
 }  // namespace tsdf

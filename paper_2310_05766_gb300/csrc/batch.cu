@@ -20,9 +20,13 @@
 // Two buffer sets alternate so the host can fill one while the GPU reads the
 // other.
 //
-// Tuning (warp merge, steps per work item) changes speed only: results are
-// bit-identical for every setting. With autotuning on, the first calls cycle
-// through the settings, timing each with events, and the fastest is kept.
+// Tuning (per-scan reduction by accumulator atomics or by sort, warp merge,
+// steps per work item) changes speed only: results are bit-identical for every
+// setting. The sort configurations add three phases (count, prefix, scatter:
+// a counting sort of the emitted pairs by brick, see integrate.cu) and apply
+// each brick from its sorted segment. With autotuning on, the first calls
+// cycle through the settings, timing each with events, and the fastest is
+// kept.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -135,13 +139,19 @@ __device__ __forceinline__ void warp_add(unsigned long long v, unsigned long lon
     if ((threadIdx.x & 31u) == 0 && v) atomicAdd(dst, v);
 }
 
-template <bool MERGE, int KPT>
+// Pair slots written by map i's scan (sort configurations).
+__device__ __forceinline__ uint32_t written_slots(const MapDev& m) {
+    const unsigned long long n = __ldcg(&m.ctr->slot_count);
+    return (uint32_t)(n < m.pair_cap ? n : (unsigned long long)m.pair_cap);
+}
+
+template <bool MERGE, int KPT, bool SORT>
 __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem* __restrict__ items,
                                                                   const BatchHeader* __restrict__ hdr,
                                                                   BatchSync* sync) {
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ uint32_t s_prefix[kBatchMax + 1];
-    __shared__ unsigned wl[8], wv[8], cta_base;
+    __shared__ RaysSmem rsm;
     const int count = hdr->count;
     const unsigned arrivals = gridDim.x + hdr->extra_arrivals;
     const long long spin = hdr->spin_limit;
@@ -153,7 +163,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem
     // ---- phase 1: ray set-up and compaction, one CTA task = 256 points of a map
     for (uint32_t t = blockIdx.x; t < hdr->ray_tasks; t += gridDim.x) {
         const int i = find_segment(hdr->ray_prefix, count, t);
-        rays_task<false>(items[i].a, items[i].m, (int)((t - hdr->ray_prefix[i]) * 256u), t, wl, wv, &cta_base);
+        rays_task<false, SORT>(items[i].a, items[i].m, (int)((t - hdr->ray_prefix[i]) * 256u), t, &rsm);
         __syncthreads();
     }
     if (!grid_barrier(sync, arrivals, spin)) return;
@@ -167,12 +177,15 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem
         unsigned last_brick = kNoVoxel;
         int cur = -1;
         unsigned hits = 0;
+        bool ovf = false;
         for (uint32_t g = gwarp; g < s_prefix[count]; g += nwarps) {   // warp-uniform
             const int i = find_segment(s_prefix, count, g);
             if (i != cur) {
                 if (cur >= 0 && items[cur].reduce == 1)
                     warp_add(hits, &items[cur].m.ctr->part[gwarp % kParts].hits);
+                if (cur >= 0 && ovf) items[cur].m.ctr->overflow = 1u;
                 hits = 0;
+                ovf = false;
                 last_brick = kNoVoxel;
                 cur = i;
             }
@@ -180,12 +193,21 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem
             const unsigned ngrp = (unsigned)(2 * it.a.K + KPT) / KPT;
             const unsigned local = g - s_prefix[i];
             const unsigned nl = __ldcg(&it.m.ctr->live_count);
+            const unsigned ray = (local / ngrp) * 32u + lane;
             float4 A, B;
-            load_rays(it.m, nl, (local / ngrp) * 32u + lane, A, B);
-            if (it.reduce == 0) contrib_item<0, MERGE, KPT>(it.a, it.m, local % ngrp, A, B, hits, last_brick);
-            else contrib_item<1, MERGE, KPT>(it.a, it.m, local % ngrp, A, B, hits, last_brick);
+            load_rays(it.m, nl, ray, A, B);
+            if (SORT) {
+                const uint32_t sslot = ray < nl ? it.m.ray_slot[ray] : kNoSlot;
+                if (it.reduce == 0)
+                    contrib_item<0, false, KPT, true>(it.a, it.m, local % ngrp, A, B, hits, last_brick, sslot, &ovf);
+                else contrib_item<1, false, KPT, true>(it.a, it.m, local % ngrp, A, B, hits, last_brick, sslot, &ovf);
+            } else {
+                if (it.reduce == 0) contrib_item<0, MERGE, KPT>(it.a, it.m, local % ngrp, A, B, hits, last_brick);
+                else contrib_item<1, MERGE, KPT>(it.a, it.m, local % ngrp, A, B, hits, last_brick);
+            }
         }
         if (cur >= 0 && items[cur].reduce == 1) warp_add(hits, &items[cur].m.ctr->part[gwarp % kParts].hits);
+        if (cur >= 0 && ovf) items[cur].m.ctr->overflow = 1u;
     }
     if (!grid_barrier(sync, arrivals, spin)) return;
 
@@ -196,6 +218,27 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem
         compact_words(items[i].m, (t - hdr->word_prefix[i]) * 32u + lane, nwords);
     }
     if (!grid_barrier(sync, arrivals, spin)) return;
+
+    if (SORT) {
+        // ---- phase 3b: pair counts per brick, one warp task = 32 pair slots of a map
+        block_prefix(count, [&](int i) { return (written_slots(items[i].m) + 31u) / 32u; }, s_prefix);
+        for (uint32_t g = gwarp; g < s_prefix[count]; g += nwarps) {
+            const int i = find_segment(s_prefix, count, g);
+            sort_count_warp(items[i].m, (g - s_prefix[i]) * 32u, written_slots(items[i].m));
+        }
+        if (!grid_barrier(sync, arrivals, spin)) return;
+        // ---- phase 3c: segment starts, one CTA per map
+        for (int i = blockIdx.x; i < count; i += gridDim.x)
+            sort_scan_cta(items[i].m, __ldcg(&items[i].m.ctr->brick_count), s_prefix);
+        if (!grid_barrier(sync, arrivals, spin)) return;
+        // ---- phase 3d: scatter into the segments (same tasks as the count)
+        block_prefix(count, [&](int i) { return (written_slots(items[i].m) + 31u) / 32u; }, s_prefix);
+        for (uint32_t g = gwarp; g < s_prefix[count]; g += nwarps) {
+            const int i = find_segment(s_prefix, count, g);
+            sort_scatter_warp(items[i].m, (g - s_prefix[i]) * 32u, written_slots(items[i].m));
+        }
+        if (!grid_barrier(sync, arrivals, spin)) return;
+    }
 
     // ---- phase 4: Eq. 1 / Eq. 2 on the touched bricks, one warp per brick
     block_prefix(count, [&](int i) { return __ldcg(&items[i].m.ctr->brick_count); }, s_prefix);
@@ -210,19 +253,26 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem
             if (i != cur) {
                 if (cur >= 0) {
                     warp_add(touched, &items[cur].m.ctr->part[gwarp % kParts].touched);
-                    if (items[cur].reduce == 0) warp_add(hits, &items[cur].m.ctr->part[gwarp % kParts].hits);
+                    if (SORT || items[cur].reduce == 0) warp_add(hits, &items[cur].m.ctr->part[gwarp % kParts].hits);
                 }
                 touched = hits = 0;
                 cur = i;
             }
             const BatchItem& it = items[i];
-            if (it.reduce == 0)
-                apply_brick<0>(it.m, it.w_max, it.flags, g - s_prefix[i], s_grid, s_acc, s_off, touched, hits);
-            else apply_brick<1>(it.m, it.w_max, it.flags, g - s_prefix[i], s_grid, s_acc, s_off, touched, hits);
+            const unsigned local = g - s_prefix[i];
+            if (SORT) {
+                const bool ovf = __ldcg(&it.m.ctr->overflow) != 0u;
+                if (it.reduce == 0)
+                    sort_apply_brick<0>(it.m, it.w_max, it.flags, local, ovf, s_grid, s_acc, s_off, touched, hits);
+                else sort_apply_brick<1>(it.m, it.w_max, it.flags, local, ovf, s_grid, s_acc, s_off, touched, hits);
+            } else {
+                if (it.reduce == 0) apply_brick<0>(it.m, it.w_max, it.flags, local, s_grid, s_acc, s_off, touched, hits);
+                else apply_brick<1>(it.m, it.w_max, it.flags, local, s_grid, s_acc, s_off, touched, hits);
+            }
         }
         if (cur >= 0) {
             warp_add(touched, &items[cur].m.ctr->part[gwarp % kParts].touched);
-            if (items[cur].reduce == 0) warp_add(hits, &items[cur].m.ctr->part[gwarp % kParts].hits);
+            if (SORT || items[cur].reduce == 0) warp_add(hits, &items[cur].m.ctr->part[gwarp % kParts].hits);
         }
     }
     if (!grid_barrier(sync, arrivals, spin)) return;
@@ -235,17 +285,23 @@ constexpr size_t kDynSmem = kBatchWarps * kApplySmemPerWarp;
 
 using BatchKernel = void (*)(const BatchItem*, const BatchHeader*, BatchSync*);
 
-BatchKernel kernel_for(bool merge, int kpt) {
-    if (merge) return kpt == 1 ? batch_kernel<true, 1> : kpt == 2 ? batch_kernel<true, 2> : batch_kernel<true, 4>;
-    return kpt == 1 ? batch_kernel<false, 1> : kpt == 2 ? batch_kernel<false, 2> : batch_kernel<false, 4>;
-}
-
 struct Config {
     bool merge;
     int kpt;
+    bool sort;
 };
-const Config kConfigs[] = {{false, 4}, {false, 2}, {false, 1}, {true, 4}, {true, 2}, {true, 1}};
-constexpr int kNumConfigs = 6;
+const Config kConfigs[] = {{false, 4, false}, {false, 2, false}, {false, 1, false}, {true, 4, false},
+                           {true, 2, false},  {true, 1, false},  {false, 4, true},  {false, 2, true}};
+constexpr int kNumConfigs = 8;
+
+BatchKernel kernel_for(const Config& c) {
+    if (c.sort) return c.kpt == 2 ? batch_kernel<false, 2, true> : batch_kernel<false, 4, true>;
+    if (c.merge)
+        return c.kpt == 1 ? batch_kernel<true, 1, false> : c.kpt == 2 ? batch_kernel<true, 2, false>
+                                                                       : batch_kernel<true, 4, false>;
+    return c.kpt == 1 ? batch_kernel<false, 1, false> : c.kpt == 2 ? batch_kernel<false, 2, false>
+                                                                    : batch_kernel<false, 4, false>;
+}
 
 }  // namespace
 }  // namespace tsdf
@@ -338,7 +394,7 @@ cudaError_t enqueue(tsdf_batch* b, int si, int cfg, cudaStream_t s) {
     lc.numAttrs = 1;
     const BatchItem* items = reinterpret_cast<const BatchItem*>(sl.dev + sizeof(BatchHeader));
     const BatchHeader* hdr = reinterpret_cast<const BatchHeader*>(sl.dev);
-    return cudaLaunchKernelEx(&lc, kernel_for(kConfigs[cfg].merge, kConfigs[cfg].kpt), items, hdr, b->sync);
+    return cudaLaunchKernelEx(&lc, kernel_for(kConfigs[cfg]), items, hdr, b->sync);
 }
 
 // Collect finished autotuning trials; pick the fastest config once all have run.
@@ -381,13 +437,13 @@ int tsdf_batch_create(int32_t max_count, tsdf_batch** out) {
     cudaError_t e = cudaGetDevice(&b->device);
     int sms = 0, per_sm = 0;
     for (int c = 0; c < kNumConfigs && e == cudaSuccess; ++c)
-        e = cudaFuncSetAttribute(kernel_for(kConfigs[c].merge, kConfigs[c].kpt),
+        e = cudaFuncSetAttribute(kernel_for(kConfigs[c]),
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     // the grid must be co-resident for every config: take the smallest occupancy
     int occ = 1 << 30;
     for (int c = 0; c < kNumConfigs && e == cudaSuccess; ++c) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(kConfigs[c].merge, kConfigs[c].kpt),
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(kConfigs[c]),
                                                           kBatchThreads, kDynSmem);
         occ = std::min(occ, per_sm);
     }
@@ -471,9 +527,10 @@ int tsdf_batch_set_option(tsdf_batch* b, int32_t option, int64_t value) {
 }
 
 int tsdf_batch_get_config(const tsdf_batch* b, int32_t* config, int32_t* merge, int32_t* steps_per_item,
-                          int32_t* tuned) {
+                          int32_t* reduction, int32_t* tuned) {
     if (!b) return TSDF_ERR_INVALID;
     if (config) *config = b->config;
+    if (reduction) *reduction = kConfigs[b->config].sort ? TSDF_REDUCTION_SORT : TSDF_REDUCTION_ATOMIC;
     if (merge) *merge = kConfigs[b->config].merge ? 1 : 0;
     if (steps_per_item) *steps_per_item = kConfigs[b->config].kpt;
     if (tuned) *tuned = b->tuned >= 0 ? 1 : 0;
@@ -498,25 +555,6 @@ int tsdf_batch_integrate(tsdf_batch* b, tsdf_map* const* maps, const float* cons
         if (e != cudaSuccess) return cu_fail(e);
         sl.pending = false;
     }
-    BatchHeader* hdr = reinterpret_cast<BatchHeader*>(sl.host);
-    BatchItem* items = reinterpret_cast<BatchItem*>(sl.host + sizeof(BatchHeader));
-    uint32_t rt = 0, wt = 0;
-    for (int i = 0; i < count; ++i) {
-        int rc = prepare_batch_item(maps[i], points_dev[i], n[i], poses + 12 * i, &items[i]);
-        if (rc != TSDF_OK) return rc;
-        hdr->ray_prefix[i] = rt;
-        hdr->word_prefix[i] = wt;
-        rt += (uint32_t)((n[i] + 255) / 256);
-        wt += ((items[i].bricks + 3u) / 4u + 31u) / 32u;
-    }
-    hdr->ray_prefix[count] = rt;
-    hdr->word_prefix[count] = wt;
-    hdr->count = count;
-    hdr->ray_tasks = rt;
-    hdr->word_tasks = wt;
-    hdr->extra_arrivals = (uint32_t)b->extra_arrivals;
-    hdr->spin_limit = b->spin_limit;
-
     if (b->autotune && b->tuned < 0) harvest_trials(b);
     int cfg = b->config;
     bool timing = false;
@@ -532,6 +570,29 @@ int tsdf_batch_integrate(tsdf_batch* b, tsdf_map* const* maps, const float* cons
             }
         }
     }
+    BatchHeader* hdr = reinterpret_cast<BatchHeader*>(sl.host);
+    BatchItem* items = reinterpret_cast<BatchItem*>(sl.host + sizeof(BatchHeader));
+    uint32_t rt = 0, wt = 0;
+    for (int i = 0; i < count; ++i) {
+        if (kConfigs[cfg].sort) {   // the sort buffers must exist before the descriptors are taken
+            int rc = map_reserve_sort(maps[i], n[i]);
+            if (rc != TSDF_OK) return rc;
+        }
+        int rc = prepare_batch_item(maps[i], points_dev[i], n[i], poses + 12 * i, &items[i]);
+        if (rc != TSDF_OK) return rc;
+        hdr->ray_prefix[i] = rt;
+        hdr->word_prefix[i] = wt;
+        rt += (uint32_t)((n[i] + 255) / 256);
+        wt += ((items[i].bricks + 3u) / 4u + 31u) / 32u;
+    }
+    hdr->ray_prefix[count] = rt;
+    hdr->word_prefix[count] = wt;
+    hdr->count = count;
+    hdr->ray_tasks = rt;
+    hdr->word_tasks = wt;
+    hdr->extra_arrivals = (uint32_t)b->extra_arrivals;
+    hdr->spin_limit = b->spin_limit;
+
     cudaError_t e = cudaSuccess;
     tsdf_batch::Trial trial{cfg, nullptr, nullptr};
     if (timing) {

@@ -37,6 +37,16 @@
 // finish: one warp sums the per-scan counters into the published ones and
 //   clears the per-scan state.
 //
+// Sort reduction (an alternative to the accumulator atomics, same results):
+// rays also reserve each live ray's pair slots (one per march sample); emit is
+// the contrib march writing (voxel word, code) to the sample's slot instead of
+// reducing it (no atomics; samples beyond the capacity fall back to the
+// accumulators); count adds each brick's pairs (warp-merged per brick);
+// scan turns counts into segment starts; scatter moves every pair to its
+// brick's segment as a 32-bit (offset, code); sort_apply reduces each brick's
+// segment per voxel in shared memory and applies Eq. 1 / Eq. 2. Together
+// count, scan and scatter are a counting sort of the contributions by brick.
+//
 // Kernels may be launched with programmatic stream serialisation: each may be
 // scheduled while its predecessor drains, and waits (griddepcontrol.wait) for
 // the predecessor's completion before touching its results.
@@ -53,10 +63,10 @@ namespace {
 
 using namespace dev;
 
+template <bool SORT>
 __global__ void __launch_bounds__(256) rays_kernel(const ScanArgs a, const MapDev m) {
-    __shared__ unsigned wl[8], wv[8];
-    __shared__ unsigned cta_base;
-    rays_task<true>(a, m, (int)(blockIdx.x * blockDim.x), blockIdx.x, wl, wv, &cta_base);
+    __shared__ RaysSmem sm;
+    rays_task<true, SORT>(a, m, (int)(blockIdx.x * blockDim.x), blockIdx.x, &sm);
 }
 
 // Contribution work items: (block of 32 consecutive live rays, group of KPT
@@ -95,6 +105,65 @@ __global__ void __launch_bounds__(256) contrib_kernel(const ScanArgs a, const Ma
         const unsigned long long total = cta_sum<8>((unsigned long long)hits, red);
         if (threadIdx.x == 0 && total) atomicAdd(&m.ctr->part[blockIdx.x % kParts].hits, total);
     }
+}
+
+// Sort reduction: the contribution march writing pairs (same work items).
+template <int MODE, int KPT>
+__global__ void __launch_bounds__(256) emit_kernel(const ScanArgs a, const MapDev m) {
+    __shared__ unsigned long long red[8];
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+    pdl_trigger();
+    pdl_wait();
+    unsigned nlive = 0;
+    if (lane == 0) nlive = __ldcg(&m.ctr->live_count);
+    nlive = __shfl_sync(kFull, nlive, 0);
+    const unsigned ngrp = (unsigned)(2 * a.K + KPT) / KPT;
+    const unsigned nitems = (nlive + 31u) / 32u * ngrp;
+    unsigned hits = 0;
+    unsigned last_brick = kNoVoxel;
+    bool ovf = false;
+    for (unsigned item = gwarp; item < nitems; item += nwarps) {   // warp-uniform
+        const unsigned ray = (item / ngrp) * 32u + lane;
+        float4 A, B;
+        load_rays(m, nlive, ray, A, B);
+        const uint32_t sslot = ray < nlive ? m.ray_slot[ray] : kNoSlot;
+        contrib_item<MODE, false, KPT, true>(a, m, item % ngrp, A, B, hits, last_brick, sslot, &ovf);
+    }
+    if (ovf) m.ctr->overflow = 1u;
+    if (MODE == 1) {
+        const unsigned long long total = cta_sum<8>((unsigned long long)hits, red);
+        if (threadIdx.x == 0 && total) atomicAdd(&m.ctr->part[blockIdx.x % kParts].hits, total);
+    }
+}
+
+__global__ void __launch_bounds__(256) sort_count_kernel(const MapDev m) {
+    pdl_trigger();
+    pdl_wait();   // pairs come from emit, brick slots from compact
+    const uint32_t n = sort_nslots(m);
+    const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t w = w0; w * 32u < n; w += nw) sort_count_warp(m, w * 32u, n);
+}
+
+__global__ void __launch_bounds__(1024) sort_scan_kernel(const MapDev m) {
+    __shared__ uint32_t smem[33];
+    __shared__ uint32_t nb;
+    pdl_trigger();
+    pdl_wait();
+    if (threadIdx.x == 0) nb = __ldcg(&m.ctr->brick_count);
+    __syncthreads();
+    sort_scan_cta(m, nb, smem);
+}
+
+__global__ void __launch_bounds__(256) sort_scatter_kernel(const MapDev m) {
+    pdl_trigger();
+    pdl_wait();
+    const uint32_t n = sort_nslots(m);
+    const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t w = w0; w * 32u < n; w += nw) sort_scatter_warp(m, w * 32u, n);
 }
 
 __global__ void __launch_bounds__(256) compact_kernel(const MapDev m, const uint32_t nwords) {
@@ -147,6 +216,50 @@ __global__ void __launch_bounds__(kApplyWarps * 32) apply_kernel(const MapDev m,
     }
 }
 
+// Sort reduction: one warp per listed brick (as apply_kernel).
+template <int MODE>
+__global__ void __launch_bounds__(kApplyWarps * 32) sort_apply_kernel(const MapDev m, const int32_t w_max,
+                                                                       const int32_t flags) {
+    __shared__ uint32_t s_grid[kApplyWarps][kBrickVoxels];
+    __shared__ unsigned long long s_acc[kApplyWarps][kBrickVoxels];
+    __shared__ uint16_t s_off[kApplyWarps][kBrickVoxels];
+    __shared__ unsigned long long red_u[kApplyWarps], red_h[kApplyWarps];
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned w = threadIdx.x >> 5;
+    const unsigned gwarp = blockIdx.x * kApplyWarps + w;
+    const unsigned nwarps = gridDim.x * kApplyWarps;
+    pdl_trigger();
+    pdl_wait();
+    unsigned nb = 0, ovf = 0;
+    if (lane == 0) {
+        nb = __ldcg(&m.ctr->brick_count);
+        ovf = __ldcg(&m.ctr->overflow);
+    }
+    nb = __shfl_sync(kFull, nb, 0);
+    ovf = __shfl_sync(kFull, ovf, 0);
+    unsigned long long touched = 0, hits = 0;
+    for (unsigned i = gwarp; i < nb; i += nwarps)
+        sort_apply_brick<MODE>(m, w_max, flags, i, ovf != 0u, s_grid[w], s_acc[w], s_off[w], touched, hits);
+    for (int o = 16; o > 0; o >>= 1) {
+        touched += __shfl_xor_sync(kFull, touched, o);
+        hits += __shfl_xor_sync(kFull, hits, o);
+    }
+    if (lane == 0) {
+        red_u[w] = touched;
+        red_h[w] = hits;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long bu = 0, bh = 0;
+        for (int k = 0; k < kApplyWarps; ++k) {
+            bu += red_u[k];
+            bh += red_h[k];
+        }
+        if (bu) atomicAdd(&m.ctr->part[blockIdx.x % kParts].touched, bu);
+        if (bh) atomicAdd(&m.ctr->part[blockIdx.x % kParts].hits, bh);
+    }
+}
+
 // One warp: publish the scan's counters and clear the per-scan state.
 __global__ void finish_kernel(const MapDev m) {
     pdl_trigger();
@@ -196,9 +309,47 @@ cudaError_t launch_contrib_k(const ScanArgs& a, const MapDev& m, int kpt, bool p
 
 }  // namespace
 
-cudaError_t launch_rays(const ScanArgs& a, const MapDev& m, bool pdl, cudaStream_t s) {
+cudaError_t launch_rays(const ScanArgs& a, const MapDev& m, bool sort, bool pdl, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
-    return launch(rays_kernel, dim3((unsigned)((a.n + 255) / 256)), dim3(256), s, pdl, a, m);
+    const dim3 grid((unsigned)((a.n + 255) / 256));
+    return sort ? launch(rays_kernel<true>, grid, dim3(256), s, pdl, a, m)
+                : launch(rays_kernel<false>, grid, dim3(256), s, pdl, a, m);
+}
+
+cudaError_t launch_emit(const ScanArgs& a, const MapDev& m, int32_t reduce, int kpt, bool pdl, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)persistent_ctas_256());
+    if (reduce == 0) {
+        switch (kpt) {
+            case 2: return launch(emit_kernel<0, 2>, grid, dim3(256), s, pdl, a, m);
+            case 4: return launch(emit_kernel<0, 4>, grid, dim3(256), s, pdl, a, m);
+            default: return launch(emit_kernel<0, 1>, grid, dim3(256), s, pdl, a, m);
+        }
+    }
+    switch (kpt) {
+        case 2: return launch(emit_kernel<1, 2>, grid, dim3(256), s, pdl, a, m);
+        case 4: return launch(emit_kernel<1, 4>, grid, dim3(256), s, pdl, a, m);
+        default: return launch(emit_kernel<1, 1>, grid, dim3(256), s, pdl, a, m);
+    }
+}
+
+cudaError_t launch_sort_count(const MapDev& m, bool pdl, cudaStream_t s) {
+    return launch(sort_count_kernel, dim3((unsigned)persistent_ctas_256()), dim3(256), s, pdl, m);
+}
+
+cudaError_t launch_sort_scan(const MapDev& m, bool pdl, cudaStream_t s) {
+    return launch(sort_scan_kernel, dim3(1), dim3(1024), s, pdl, m);
+}
+
+cudaError_t launch_sort_scatter(const MapDev& m, bool pdl, cudaStream_t s) {
+    return launch(sort_scatter_kernel, dim3((unsigned)persistent_ctas_256()), dim3(256), s, pdl, m);
+}
+
+cudaError_t launch_sort_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t flags, int num_ctas, bool pdl,
+                              cudaStream_t s) {
+    if (reduce == 0)
+        return launch(sort_apply_kernel<0>, dim3(num_ctas), dim3(kApplyWarps * 32), s, pdl, m, w_max, flags);
+    return launch(sort_apply_kernel<1>, dim3(num_ctas), dim3(kApplyWarps * 32), s, pdl, m, w_max, flags);
 }
 
 cudaError_t launch_contrib(const ScanArgs& a, const MapDev& m, int32_t reduce, bool merge, int kpt, bool pdl,

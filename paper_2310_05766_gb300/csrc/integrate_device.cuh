@@ -39,13 +39,46 @@ __device__ __forceinline__ unsigned long long cta_sum(unsigned long long v, unsi
 // add places the integer in the low mantissa bits.
 __device__ __forceinline__ int small_int(float x) { return __float_as_int(fa(x, 12582912.0f)) - 0x4B400000; }
 
+// Fill half-height J of march step k of a ray of range r (Eq. 3 / Eq. 4):
+// J = floor(delta_z * l / vs) at l = r + k vs; -1 when the step is skipped
+// (l <= 0 or a dead ray). The contribution march and the slot count of the
+// sort reduction both use exactly this arithmetic.
+__device__ __forceinline__ int step_fill(const ScanArgs& a, float r, bool fill, int k, float& l) {
+    l = fa(r, fm((float)k, a.vs));
+    const bool lv = (r >= 0.f) && (l > 0.f);
+    if (!lv) return -1;
+    return fill ? __float2int_rd(fm(fm(a.dz, l), a.inv_vs)) : 0;
+}
+
+// Sort reduction: pair slots of one ray, one per (k, j) sample of its march,
+// or kNoSlot when it has more than kRaySlotLimit (its samples then overflow).
+__device__ __forceinline__ uint32_t ray_slots(const ScanArgs& a, float r, bool fill) {
+    uint32_t n = 0;
+    for (int k = -a.K; k <= a.K; ++k) {
+        float l;
+        const int J = step_fill(a, r, fill, k, l);
+        if (J < 0) continue;
+        if ((uint32_t)J >= kRaySlotLimit) return kNoSlot;
+        n += 2u * (uint32_t)J + 1u;
+        if (n > kRaySlotLimit) return kNoSlot;
+    }
+    return n;
+}
+
+struct RaysSmem {
+    unsigned wl[8], wv[8], ws[8];   // per warp: live rays, valid rays, pair slots
+    unsigned base;                  // the CTA's first ray-list entry
+    unsigned long long sbase;       // the CTA's first pair slot (sort reduction)
+};
+
 // ---- rays: the CTA's 256 threads set up points [base, base + 256) of a scan
-// and append the live ones to the map's ray list. smem: wl[8], wv[8], base.
-// With PDL the wait for the preceding grid comes before the first access to
-// the map's counters and ray list.
-template <bool PDL>
-__device__ __forceinline__ void rays_task(const ScanArgs& a, const MapDev& m, int base, unsigned part, unsigned* wl,
-                                          unsigned* wv, unsigned* cta_base) {
+// and append the live ones to the map's ray list. With SORT each live ray also
+// reserves its pair slots (one 64-bit atomic per CTA). With PDL the wait for
+// the preceding grid comes before the first access to the map's counters and
+// ray list.
+template <bool PDL, bool SORT>
+__device__ __forceinline__ void rays_task(const ScanArgs& a, const MapDev& m, int base, unsigned part,
+                                          RaysSmem* sm) {
     const int i = base + (int)threadIdx.x;
     const unsigned lane = threadIdx.x & 31u;
     float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -90,31 +123,53 @@ __device__ __forceinline__ void rays_task(const ScanArgs& a, const MapDev& m, in
         live = ex * ex + ey * ey + ez * ez <= reach * reach;
         ra = make_float4(dx, dy, dz, r);
     }
+    // pair slots of this ray (sort reduction): an inclusive warp scan
+    uint32_t nslot = 0, sincl = 0;
+    if (SORT) {
+        nslot = live ? ray_slots(a, r, rb.w != 0.f) : 0u;
+        const uint32_t own = nslot == kNoSlot ? 0u : nslot;
+        sincl = own;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, sincl, o);
+            if (lane >= (unsigned)o) sincl += y;
+        }
+    }
     // CTA-level compaction of the live rays: one list atomic per CTA
     const unsigned warp = threadIdx.x >> 5;
     const unsigned lmask = __ballot_sync(kFull, live);
     const unsigned vmask = __ballot_sync(kFull, valid);
     if (lane == 0) {
-        wl[warp] = __popc(lmask);
-        wv[warp] = __popc(vmask);
+        sm->wl[warp] = __popc(lmask);
+        sm->wv[warp] = __popc(vmask);
     }
+    if (SORT && lane == 31) sm->ws[warp] = sincl;
     __syncthreads();
     if (PDL) pdl_wait();   // the previous scan's finish kernel resets live_count and the counters
     if (threadIdx.x == 0) {
         unsigned tl = 0, tv = 0;
+        unsigned long long ts = 0;
         for (int w = 0; w < 8; ++w) {
-            tl += wl[w];
-            tv += wv[w];
+            tl += sm->wl[w];
+            tv += sm->wv[w];
+            if (SORT) ts += sm->ws[w];
         }
-        *cta_base = tl ? atomicAdd(&m.ctr->live_count, tl) : 0u;
+        sm->base = tl ? atomicAdd(&m.ctr->live_count, tl) : 0u;
         if (tv) atomicAdd(&m.ctr->part[part % kParts].valid, (unsigned long long)tv);
+        if (SORT) sm->sbase = ts ? atomicAdd(&m.ctr->slot_count, ts) : 0ull;
     }
     __syncthreads();
     if (live) {
-        unsigned off = *cta_base + __popc(lmask & ((1u << lane) - 1u));
-        for (unsigned w = 0; w < warp; ++w) off += wl[w];
+        unsigned off = sm->base + __popc(lmask & ((1u << lane) - 1u));
+        for (unsigned w = 0; w < warp; ++w) off += sm->wl[w];
         m.ray_a[off] = ra;
         m.ray_b[off] = rb;
+        if (SORT) {
+            unsigned long long first = sm->sbase + (sincl - (nslot == kNoSlot ? 0u : nslot));
+            for (unsigned w = 0; w < warp; ++w) first += sm->ws[w];
+            // slots at or beyond the capacity overflow, sample by sample
+            m.ray_slot[off] = nslot == kNoSlot ? kNoSlot
+                                                : (uint32_t)(first < m.pair_cap ? first : (unsigned long long)m.pair_cap);
+        }
     }
 }
 
@@ -129,20 +184,37 @@ __device__ __forceinline__ void load_rays(const MapDev& m, unsigned nlive, unsig
 }
 
 // One warp: the steps of k-group `grp` (KPT steps) of its 32 rays.
-template <int MODE, bool MERGE, int KPT>
+// SORT (sort reduction, MERGE off): each sample of a lane's ray is written to
+// the ray's pair slot sslot + (its index in the ray's march) instead of being
+// reduced: (voxel word, code) inside the window, kNoVoxel outside. Samples
+// whose slot is at or beyond the capacity (or whose ray has none) take the
+// accumulator reduction instead and set `ovf`.
+template <int MODE, bool MERGE, int KPT, bool SORT = false>
 __device__ __forceinline__ void contrib_item(const ScanArgs& a, const MapDev& m, unsigned grp, const float4 A,
-                                             const float4 B, unsigned& hits, unsigned& last_brick) {
+                                             const float4 B, unsigned& hits, unsigned& last_brick,
+                                             uint32_t sslot = kNoSlot, bool* ovf = nullptr) {
+    static_assert(!(SORT && MERGE), "the sort reduction emits every sample");
     const unsigned lane = threadIdx.x & 31u;
     const float tx = a.t[0], ty = a.t[1], tz = a.t[2];
     const float r = A.w;                // dead lanes carry r = -1
+    const bool rfill = B.w != 0.f;
     const int k0 = (int)grp * KPT - a.K;
+    uint32_t sidx = 0;                  // SORT: index of the step's first sample in the ray's march
+    if (SORT && sslot != kNoSlot) {
+        for (int k = -a.K; k < k0; ++k) {
+            float l;
+            const int J = step_fill(a, r, rfill, k, l);
+            if (J >= 0) sidx += 2u * (uint32_t)J + 1u;
+        }
+    }
 #pragma unroll 1
     for (int kk = 0; kk < KPT; ++kk) {
         const int k = k0 + kk;
         if (k > a.K) break;   // uniform
-        const float l = fa(r, fm((float)k, a.vs));
-        const bool lv = (r >= 0.f) && (l > 0.f);
-        const int J = (lv && B.w != 0.f) ? __float2int_rd(fm(fm(a.dz, l), a.inv_vs)) : 0;
+        float l;
+        const int Jr = step_fill(a, r, rfill, k, l);
+        const bool lv = Jr >= 0;
+        const int J = lv ? Jr : 0;
         const int Jw = __reduce_max_sync(kFull, lv ? J : -1);   // -1: no live lane
         const float bx = fa(tx, fm(A.x, l));
         const float by = fa(ty, fm(A.y, l));
@@ -173,7 +245,18 @@ __device__ __forceinline__ void contrib_item(const ScanArgs& a, const MapDev& m,
             int q = small_int(fm(d, a.qs));
             q = max(-kQMax, min(kQMax, q));
             bool leader = act;
-            if (MERGE) {
+            if (SORT) {
+                const bool mine = lv && j >= -J && j <= J;
+                const uint32_t slot = sslot + sidx + (uint32_t)(j + J);   // no wrap: sslot <= cap, sidx < 2^21
+                if (mine && sslot != kNoSlot && slot < m.pair_cap) {
+                    m.pairs[slot] = act ? make_uint2(word, (uint32_t)q) : make_uint2(kNoVoxel, 0u);
+                } else if (act) {
+                    if (MODE == 0) atomicAdd(m.acc + word, (1ull << 40) + (unsigned long long)(long long)q);
+                    else atomicMax(m.acc + word, 65536ull - (((unsigned)abs(q) << 1) | (q < 0 ? 1u : 0u)));
+                    if (MODE == 1) ++hits;
+                    *ovf = true;
+                }
+            } else if (MERGE) {
                 if (__ballot_sync(kFull, act) == 0u) continue;   // warp-uniform
                 const unsigned peers = __match_any_sync(kFull, act ? word : kNoVoxel);
                 leader = act && lane == (unsigned)(__ffs(peers) - 1);
@@ -195,7 +278,7 @@ __device__ __forceinline__ void contrib_item(const ScanArgs& a, const MapDev& m,
                     if (act) atomicMax(m.acc + word, 65536ull - key);
                 }
             }
-            if (MODE == 1) hits += act ? 1u : 0u;
+            if (MODE == 1 && !SORT) hits += act ? 1u : 0u;
             // mark the brick; skip when this lane marked it last or the lane
             // below (usually the neighbouring ray) marks the same brick now
             const unsigned below = __shfl_up_sync(kFull, leader ? brick : kNoVoxel, 1);
@@ -204,6 +287,7 @@ __device__ __forceinline__ void contrib_item(const ScanArgs& a, const MapDev& m,
                 m.brick_flag[brick] = 1;
             }
         }
+        if (SORT && lv) sidx += 2u * (uint32_t)J + 1u;
     }
 }
 
@@ -301,9 +385,51 @@ __device__ __forceinline__ void compact_words(const MapDev& m, unsigned i, unsig
     base = __shfl_sync(kFull, base, 31) + incl - cnt;
     if (bits) {
         reinterpret_cast<uint32_t*>(m.brick_flag)[i] = 0u;
-        for (unsigned b = 0; b < 4; ++b)
-            if (bits & (1u << b)) m.brick_list[base++] = 4u * i + b;
+        for (unsigned b = 0; b < 4; ++b) {
+            if (bits & (1u << b)) {
+                if (m.brick_slot) m.brick_slot[4u * i + b] = base;
+                m.brick_list[base++] = 4u * i + b;
+            }
+        }
     }
+}
+
+// Apply part shared by both reductions: the brick's grid words and per-scan
+// accumulators are staged in shared memory; nz (bit 2v / 2v+1 of lane l) marks
+// voxel 2(32 v + l) / +1 as touched. Compacts the touched voxels, applies
+// Eq. 1 / Eq. 2 to each (one per lane) and writes the brick back.
+template <int MODE>
+__device__ __forceinline__ void apply_staged(const MapDev& m, int32_t w_max, int32_t flags, unsigned brick,
+                                             unsigned nz, uint32_t* s_grid, const unsigned long long* s_acc,
+                                             uint16_t* s_off, unsigned long long& touched,
+                                             unsigned long long& hits) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned cnt = __popc(nz);
+    unsigned incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= (unsigned)o) incl += t;
+    }
+    const unsigned total = __shfl_sync(kFull, incl, 31);
+    unsigned pos = incl - cnt;
+    for (unsigned bits = nz; bits; bits &= bits - 1u) {
+        const unsigned b = __ffs(bits) - 1u;
+        s_off[pos++] = (uint16_t)(2u * (32u * (b >> 1) + lane) + (b & 1u));
+    }
+    __syncwarp();
+    // Eq. 1 / Eq. 2 over the touched voxels only, one per lane
+    for (unsigned e = lane; e < total; e += 32u) {
+        const unsigned off = s_off[e];
+        uint32_t word = s_grid[off];
+        hits += decode_apply<MODE>(s_acc[off], word, w_max, flags);
+        s_grid[off] = word;
+    }
+    touched += lane == 0 ? total : 0u;
+    __syncwarp();
+    uint4* gpw = reinterpret_cast<uint4*>(m.grid + ((size_t)brick << 9));
+    const uint4* sg4 = reinterpret_cast<const uint4*>(s_grid);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) gpw[32 * v + lane] = sg4[32 * v + lane];
 }
 
 // ---- apply: one warp updates listed brick number i of the map. Shared
@@ -330,35 +456,155 @@ __device__ __forceinline__ void apply_brick(const MapDev& m, int32_t w_max, int3
         nz |= (a2.x != 0ull ? 1u : 0u) << (2 * v);
         nz |= (a2.y != 0ull ? 1u : 0u) << (2 * v + 1);
     }
-    const unsigned cnt = __popc(nz);
-    unsigned incl = cnt;
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned t = __shfl_up_sync(kFull, incl, o);
-        if (lane >= (unsigned)o) incl += t;
-    }
-    const unsigned total = __shfl_sync(kFull, incl, 31);
-    unsigned pos = incl - cnt;
-    for (unsigned bits = nz; bits; bits &= bits - 1u) {
-        const unsigned b = __ffs(bits) - 1u;
-        s_off[pos++] = (uint16_t)(2u * (32u * (b >> 1) + lane) + (b & 1u));
-    }
-    __syncwarp();
-    // Eq. 1 / Eq. 2 over the touched voxels only, one per lane
-    for (unsigned e = lane; e < total; e += 32u) {
-        const unsigned off = s_off[e];
-        uint32_t word = s_grid[off];
-        hits += decode_apply<MODE>(s_acc[off], word, w_max, flags);
-        s_grid[off] = word;
-    }
-    touched += lane == 0 ? total : 0u;
-    __syncwarp();
-    uint4* gpw = reinterpret_cast<uint4*>(m.grid + ((size_t)brick << 9));
-#pragma unroll
-    for (int v = 0; v < 4; ++v) gpw[32 * v + lane] = sg4[32 * v + lane];
+    apply_staged<MODE>(m, w_max, flags, brick, nz, s_grid, s_acc, s_off, touched, hits);
     if (nz) {
 #pragma unroll
         for (int v = 0; v < 8; ++v)
             if (nz & (3u << (2 * v))) ap[32 * v + lane] = make_ulonglong2(0ull, 0ull);
+    }
+    __syncwarp();
+}
+
+// ---- sort reduction (counting sort of the emitted pairs by touched brick,
+// then a per-brick segmented reduction in shared memory)
+
+// Pair slots of the scan in flight that were written: min(reserved, capacity).
+// A coherent load (see the per-map kernels), lane 0 then broadcast.
+__device__ __forceinline__ uint32_t sort_nslots(const MapDev& m) {
+    unsigned long long n = 0;
+    if ((threadIdx.x & 31u) == 0) n = __ldcg(&m.ctr->slot_count);
+    n = __shfl_sync(kFull, n, 0);
+    return (uint32_t)(n < m.pair_cap ? n : (unsigned long long)m.pair_cap);
+}
+
+// One warp: pairs [s, s + 32) add to their bricks' counts. Lanes holding the
+// same brick (usually neighbouring samples of one ray) are merged first.
+__device__ __forceinline__ void sort_count_warp(const MapDev& m, uint32_t s, uint32_t nslots) {
+    const unsigned lane = threadIdx.x & 31u;
+    const uint32_t slot = s + lane;
+    uint32_t seg = kNoVoxel;
+    if (slot < nslots) {
+        const uint32_t word = m.pairs[slot].x;
+        if (word != kNoVoxel) seg = m.brick_slot[word >> 9];
+    }
+    if (__ballot_sync(kFull, seg != kNoVoxel) == 0u) return;   // warp-uniform
+    const unsigned peers = __match_any_sync(kFull, seg);
+    if (seg != kNoVoxel && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(m.seg_count + seg, (uint32_t)__popc(peers));
+}
+
+// The CTA turns the per-brick counts of the map's nb listed bricks into
+// segment starts (exclusive prefix) and scatter cursors (seg_count := start).
+// blockDim.x must be a multiple of 32, at most 1024. smem: 33 words.
+__device__ __forceinline__ void sort_scan_cta(const MapDev& m, uint32_t nb, uint32_t* smem) {
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const unsigned nw = blockDim.x >> 5;
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < nb; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t x = i < nb ? m.seg_count[i] : 0u;
+        uint32_t incl = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= (unsigned)o) incl += y;
+        }
+        if (lane == 31) smem[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t t = lane < nw ? smem[lane] : 0u, ti = t;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, ti, o);
+                if (lane >= (unsigned)o) ti += y;
+            }
+            if (lane < nw) smem[lane] = ti - t;        // exclusive prefix of the warp totals
+            if (lane == 31) smem[32] = ti;             // block total
+        }
+        __syncthreads();
+        if (i < nb) {
+            const uint32_t start = carry + smem[warp] + incl - x;
+            m.seg_start[i] = start;
+            m.seg_count[i] = start;
+        }
+        carry += smem[32];
+        __syncthreads();
+    }
+}
+
+// One warp: pairs [s, s + 32) go to their bricks' segments as
+// (offset in brick << 16) | (code & 0xFFFF); one returning atomic per
+// distinct brick in the warp.
+__device__ __forceinline__ void sort_scatter_warp(const MapDev& m, uint32_t s, uint32_t nslots) {
+    const unsigned lane = threadIdx.x & 31u;
+    const uint32_t slot = s + lane;
+    uint32_t seg = kNoVoxel;
+    uint2 p = make_uint2(kNoVoxel, 0u);
+    if (slot < nslots) {
+        p = m.pairs[slot];
+        if (p.x != kNoVoxel) seg = m.brick_slot[p.x >> 9];
+    }
+    if (__ballot_sync(kFull, seg != kNoVoxel) == 0u) return;   // warp-uniform
+    const unsigned peers = __match_any_sync(kFull, seg);
+    const unsigned leader = (unsigned)(__ffs(peers) - 1);
+    uint32_t pos = 0;
+    if (seg != kNoVoxel && lane == leader) pos = atomicAdd(m.seg_count + seg, (uint32_t)__popc(peers));
+    pos = __shfl_sync(kFull, pos, leader);
+    if (seg != kNoVoxel) m.sorted[pos + __popc(peers & ((1u << lane) - 1u))] = ((p.x & 511u) << 16) | (p.y & 0xFFFFu);
+}
+
+// One warp: listed brick i. Its segment of `sorted` is reduced per voxel in
+// shared memory (the same packed accumulators as the atomic reduction), the
+// accumulators of overflowed samples are merged when `ovf`, and Eq. 1 / Eq. 2
+// are applied as in apply_brick. Resets the brick's count for the next scan.
+template <int MODE>
+__device__ __forceinline__ void sort_apply_brick(const MapDev& m, int32_t w_max, int32_t flags, unsigned i, bool ovf,
+                                                 uint32_t* s_grid, unsigned long long* s_acc, uint16_t* s_off,
+                                                 unsigned long long& touched, unsigned long long& hits) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned brick = m.brick_list[i];
+    const uint32_t start = m.seg_start[i], end = m.seg_count[i];
+    uint4* sg4 = reinterpret_cast<uint4*>(s_grid);
+    ulonglong2* sa2 = reinterpret_cast<ulonglong2*>(s_acc);
+    const uint4* gp = reinterpret_cast<const uint4*>(m.grid + ((size_t)brick << 9));
+    ulonglong2* ap = reinterpret_cast<ulonglong2*>(m.acc + ((size_t)brick << 9));
+    unsigned onz = 0;   // global accumulators that held overflowed samples
+#pragma unroll
+    for (int v = 0; v < 4; ++v) sg4[32 * v + lane] = gp[32 * v + lane];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        ulonglong2 a2 = make_ulonglong2(0ull, 0ull);
+        if (ovf) {
+            a2 = ap[32 * v + lane];
+            onz |= (a2.x != 0ull || a2.y != 0ull ? 1u : 0u) << v;
+        }
+        sa2[32 * v + lane] = a2;
+    }
+    __syncwarp();
+    for (uint32_t e = start + lane; e < end; e += 32u) {
+        const uint32_t val = m.sorted[e];
+        const unsigned off = val >> 16;
+        const int q = (int)(int16_t)(val & 0xFFFFu);
+        if (MODE == 0) atomicAdd(s_acc + off, (1ull << 40) + (unsigned long long)(long long)q);
+        else atomicMax(s_acc + off, 65536ull - (((unsigned)abs(q) << 1) | (q < 0 ? 1u : 0u)));
+    }
+    if (MODE == 1 && lane == 0) hits += end - start;
+    if (lane == 0) m.seg_count[i] = 0u;
+    __syncwarp();
+    unsigned nz = 0;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        const ulonglong2 a2 = sa2[32 * v + lane];
+        nz |= (a2.x != 0ull ? 1u : 0u) << (2 * v);
+        nz |= (a2.y != 0ull ? 1u : 0u) << (2 * v + 1);
+    }
+    if (MODE == 0) {
+        apply_staged<MODE>(m, w_max, flags, brick, nz, s_grid, s_acc, s_off, touched, hits);
+    } else {
+        unsigned long long voxels = 0;   // MIN_ABS decode counts voxels, not contributions
+        apply_staged<MODE>(m, w_max, flags, brick, nz, s_grid, s_acc, s_off, touched, voxels);
+    }
+    if (onz) {
+#pragma unroll
+        for (int v = 0; v < 8; ++v)
+            if (onz & (1u << v)) ap[32 * v + lane] = make_ulonglong2(0ull, 0ull);
     }
     __syncwarp();
 }
@@ -383,6 +629,8 @@ __device__ __forceinline__ void finish_warp(const MapDev& m) {
         c->last_touched = (long long)u;
         c->live_count = 0u;
         c->brick_count = 0u;
+        c->slot_count = 0ull;
+        c->overflow = 0u;
     }
 }
 

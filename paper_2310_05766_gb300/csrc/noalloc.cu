@@ -162,7 +162,7 @@ extern "C" int tsdf_integrate_static(uint32_t* grid_dev, const tsdf_params* para
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = launch_rays(a, md, true, s);
+    if (e == cudaSuccess) e = launch_rays(a, md, false, true, s);
     if (e == cudaSuccess) e = launch_contrib(a, md, params->reduce, false, 4, true, s);
     if (e == cudaSuccess) e = launch_compact(md, (uint32_t)bricks, true, s);
     if (e == cudaSuccess) e = launch_apply(md, params->reduce, params->w_max, params->flags, num_sms * 8, true, s);

@@ -33,7 +33,14 @@ struct MapCounters {
     long long last_touched;
     unsigned int live_count;        // rays of the scan in flight that can reach the window (compacted)
     unsigned int brick_count;       // length of the touched-brick list of the scan in flight
+    unsigned long long slot_count;  // sort reduction: pair slots reserved by the scan in flight
+    unsigned int overflow;          // sort reduction: 1 if some contribution went to the accumulators
+    unsigned int pad_;
 };
+
+constexpr uint32_t kNoSlot = 0xFFFFFFFFu;        // ray without pair slots (all its samples overflow)
+constexpr uint32_t kRaySlotLimit = 1u << 20;      // rays with more samples than this overflow
+constexpr uint32_t kPairCapMax = 1u << 28;        // largest pair capacity of a map
 
 // Device-side view of one map. The window is bricked and ring addressed:
 // global voxel g lives in brick ((g >> 3) mod (dims / 8)) at offset
@@ -46,6 +53,14 @@ struct MapDev {
     float4* ray_a;                  // per live ray (compacted): (dir.x, dir.y, dir.z, r)
     float4* ray_b;                  // per live ray (compacted): (int.x, int.y, int.z, fill ? 1 : 0)
     MapCounters* ctr;
+    // sort reduction (null / 0 when the map has no sort buffers)
+    uint32_t* brick_slot;           // per brick: its position in the brick list (touched bricks only)
+    uint32_t* seg_count;            // per list position: pair count, then the scatter cursor; zero between scans
+    uint32_t* seg_start;            // per list position: first entry of the brick's segment in `sorted`
+    uint32_t* ray_slot;             // per live ray: first pair slot, or kNoSlot
+    uint2* pairs;                   // emitted (voxel word, code) per sample; word kNoVoxel = outside the window
+    uint32_t* sorted;               // (offset in brick << 16) | (code & 0xFFFF), grouped by brick
+    uint32_t pair_cap;              // capacity of `pairs` and `sorted`
 };
 
 // Everything the kernels need about one scan, passed by value.
@@ -103,14 +118,25 @@ const long long* map_last_counters(const ::tsdf_map* map);
 // Grow the map's per-ray buffers to hold n points (synchronous allocation).
 int map_reserve_points(::tsdf_map* map, int64_t n);
 
+// Grow the map's ray and sort-reduction buffers for scans of n points
+// (synchronous allocation on first use or growth).
+int map_reserve_sort(::tsdf_map* map, int64_t n);
+
 // Launchers (return the cudaError_t of the launch).
-cudaError_t launch_rays(const ScanArgs& a, const MapDev& m, bool pdl, cudaStream_t s);
+cudaError_t launch_rays(const ScanArgs& a, const MapDev& m, bool sort, bool pdl, cudaStream_t s);
 cudaError_t launch_contrib(const ScanArgs& a, const MapDev& m, int32_t reduce, bool merge, int kpt, bool pdl,
                            cudaStream_t s);
 cudaError_t launch_compact(const MapDev& m, uint32_t bricks, bool pdl, cudaStream_t s);
 cudaError_t launch_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t flags, int num_ctas, bool pdl,
                          cudaStream_t s);
 cudaError_t launch_finish(const MapDev& m, bool pdl, cudaStream_t s);
+// Sort reduction: emit pairs, count per brick, prefix, scatter, reduce + apply.
+cudaError_t launch_emit(const ScanArgs& a, const MapDev& m, int32_t reduce, int kpt, bool pdl, cudaStream_t s);
+cudaError_t launch_sort_count(const MapDev& m, bool pdl, cudaStream_t s);
+cudaError_t launch_sort_scan(const MapDev& m, bool pdl, cudaStream_t s);
+cudaError_t launch_sort_scatter(const MapDev& m, bool pdl, cudaStream_t s);
+cudaError_t launch_sort_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t flags, int num_ctas, bool pdl,
+                              cudaStream_t s);
 cudaError_t launch_shift(uint32_t* grid, const ShiftItem* items, int count, cudaStream_t s);
 cudaError_t launch_read_box(const uint32_t* grid, const long long lo[3], const uint32_t box[3],
                             const WindowGeom& g, int16_t* v, int16_t* w, cudaStream_t s);

@@ -77,7 +77,7 @@ def test_batch_matches_oracle_and_single():
         m.close()
 
 
-@pytest.mark.parametrize("config", range(6))
+@pytest.mark.parametrize("config", range(8))
 @pytest.mark.parametrize("graph", [0, 1])
 def test_batch_every_config_same_result(config, graph):
     from paper_2310_05766_gb300 import binding as b
@@ -103,6 +103,28 @@ def test_batch_autotune_settles_and_is_exact():
     _same(b, mb, ms)
     b.tsdf_batch_destroy(batch)
     for m in mb + ms:
+        m.close()
+
+
+def test_batch_sort_overflow_matches_single():
+    """Sort configuration with a pair capacity far below the scans' samples
+    (the overflow path) in one batched launch: equal to the per-map path."""
+    from paper_2310_05766_gb300 import binding as b
+    ws = _small_batch(4, seed=23)
+    maps = [b.TsdfMap(w.params) for w in ws]
+    for m in maps:
+        b.tsdf_set_option(m.handle, b.TSDF_OPT_SORT_CAPACITY, 4096)
+    batch = b.tsdf_batch_create(8)
+    b.tsdf_batch_set_option(batch, b.TSDF_BATCH_OPT_CONFIG, 6)
+    pts = [torch.from_numpy(w.scans[0]).cuda() for w in ws]
+    for _ in range(2):
+        b.tsdf_batch_integrate(batch, maps, pts, [w.poses[0] for w in ws])
+    assert b.tsdf_batch_sync(batch) == b.TSDF_OK
+    assert b.tsdf_batch_get_config(batch)["reduction"] == b.TSDF_REDUCTION_SORT
+    b.tsdf_batch_destroy(batch)
+    ms = _run_single(b, ws, repeats=2)
+    _same(b, maps, ms)
+    for m in maps + ms:
         m.close()
 
 
@@ -174,7 +196,7 @@ def test_batch_rejects_bad_arguments():
         with pytest.raises(b.TsdfError):   # more maps than the object holds
             b.tsdf_batch_integrate(batch, maps + maps[:1], pts + pts[:1], [w.poses[0] for w in ws] + [ws[0].poses[0]])
         with pytest.raises(b.TsdfError):
-            b.tsdf_batch_set_option(batch, b.TSDF_BATCH_OPT_CONFIG, 6)
+            b.tsdf_batch_set_option(batch, b.TSDF_BATCH_OPT_CONFIG, 8)
     finally:
         b.tsdf_batch_destroy(batch)
         for m in maps:

@@ -130,6 +130,93 @@ def test_random_small_exact(seed):
     both(p, steps, label=f"random seed {seed}")
 
 
+# ---------------------------------------------------------------- sort reduction
+
+def _sort_opts(b, kpt=4, cap=0):
+    return {b.TSDF_OPT_REDUCTION: b.TSDF_REDUCTION_SORT, b.TSDF_OPT_STEPS_PER_THREAD: kpt,
+            b.TSDF_OPT_SORT_CAPACITY: cap}
+
+
+@pytest.mark.parametrize("reduce", [0, 1])
+@pytest.mark.parametrize("kpt", [4, 2, 1])
+def test_sort_reduction_exact(reduce, kpt):
+    """The counting-sort reduction gives the same maps and counters as the
+    oracle (and so as the atomic reduction): room, two outdoor scans with a
+    shift, a random case with shifts."""
+    from paper_2310_05766_gb300 import binding as b
+    opts = _sort_opts(b, kpt)
+    w = synth.workload_room(reduce=reduce)
+    both(w.params, workload_steps(w) + [("scan", w.scans[0], w.poses[0])], options=opts, label=f"room sort {kpt}")
+    w2 = synth.workload_outdoor(n_scans=12, reduce=reduce)
+    both(w2.params, workload_steps(w2)[:4], options=opts, label=f"outdoor sort {kpt}")
+    p, steps = _rand_case(7)
+    both(dict(p, reduce=reduce), steps, options=opts, label=f"random sort {kpt}")
+
+
+@pytest.mark.parametrize("cap", [1024, 65536, 250000])
+@pytest.mark.parametrize("reduce", [0, 1])
+def test_sort_reduction_overflow_exact(cap, reduce):
+    """Pair capacities far below the scan's samples: the samples beyond it go
+    to the accumulator atomics and are merged per brick; still exact."""
+    from paper_2310_05766_gb300 import binding as b
+    w = synth.workload_room(reduce=reduce)
+    steps = workload_steps(w) + [("scan", w.scans[0], w.poses[0])]
+    g, o = both(w.params, steps, options=_sort_opts(b, 4, cap), label=f"room sort cap {cap}")
+    assert g[2][0]["hits"] > cap
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_random_small_sort_exact(seed):
+    from paper_2310_05766_gb300 import binding as b
+    p, steps = _rand_case(seed)
+    both(dict(p, flags=seed % 4), steps, options=_sort_opts(b, [4, 2, 1][seed % 3], [0, 0, 1024, 4096][seed % 4]),
+         label=f"random sort seed {seed}")
+
+
+def test_sort_reduction_edge_cases():
+    """Empty and all-invalid scans, many rays through the same voxels, the
+    weight cap and a switch between reductions on one map."""
+    from paper_2310_05766_gb300 import binding as b
+    p = _edge_params()
+    rng = np.random.default_rng(21)
+    empty = np.zeros((0, 4), np.float32)
+    nan = np.full((100, 4), np.nan, np.float32)
+    pose = synth.pose12(np.eye(3), np.zeros(3))
+    same = np.tile(np.array([[1.0, 0.2, 0.1, 0.0]], np.float32), (4096, 1))
+    pts = np.zeros((2000, 4), np.float32)
+    d = rng.normal(size=(2000, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    pts[:, :3] = d * rng.uniform(0.3, 1.5, (2000, 1))
+    steps = [("scan", empty, pose), ("scan", nan, pose), ("scan", same, pose), ("scan", pts, pose)]
+    steps += [("scan", pts, pose)] * 3
+    for reduce in (0, 1):
+        both(dict(p, reduce=reduce, w_max=3), steps, options=_sort_opts(b), label=f"sort edges {reduce}")
+    # switching the reduction between scans of one map
+    m = b.TsdfMap(p)
+    try:
+        for i, st in enumerate(steps[2:]):
+            b.tsdf_set_option(m.handle, b.TSDF_OPT_REDUCTION, i % 2)
+            m.integrate(torch.from_numpy(st[1]).cuda(), st[2])
+        vg, wg = m.read()
+    finally:
+        m.close()
+    vo, wo, _, _ = run_oracle(p, steps[2:])
+    assert np.array_equal(vg, vo) and np.array_equal(wg, wo)
+
+
+def test_sort_options_rejected():
+    from paper_2310_05766_gb300 import binding as b
+    w = synth.workload_room()
+    m = b.TsdfMap(w.params)
+    try:
+        for opt, val in [(b.TSDF_OPT_REDUCTION, 2), (b.TSDF_OPT_REDUCTION, -1), (b.TSDF_OPT_SORT_CAPACITY, 5),
+                         (b.TSDF_OPT_SORT_CAPACITY, (1 << 28) + 1)]:
+            with pytest.raises(b.TsdfError):
+                b.tsdf_set_option(m.handle, opt, val)
+    finally:
+        m.close()
+
+
 # ---------------------------------------------------------------- alternative readings (map flags)
 
 @pytest.mark.parametrize("flags", [1, 2, 3])
