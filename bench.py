@@ -353,9 +353,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         e2e=dict(value=e2e_hits_all / t_e2e_max, unit=UNIT, h2d_bytes_per_step=int(16 * n_pts),
                  d2h_bytes_per_step=24, steps=n_e2e,
                  note="tsdf_integrate_host from pinned memory + tsdf_stats read-back, host wall clock"),
-        # library launches: one per profiled entry, plus compact + finish (atomic) or
-        # compact + count + prefix + scatter and finish (sort) that share an entry
-        gpu_launches=int(sum(v[0] for v in prof.values()) + (4 if sort else 2) * K),
+        # library launches: one per profiled entry, plus the compaction that shares
+        # the apply entry (atomic) or compact + count + prefix + scatter sharing
+        # the sort entry (sort)
+        gpu_launches=int(sum(v[0] for v in prof.values()) + (3 if sort else 1) * K),
         clocks=clk,
         wall_s_timed=t_wall,
         cpu_baseline=cpu,

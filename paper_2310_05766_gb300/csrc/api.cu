@@ -416,8 +416,7 @@ static int integrate_dev(tsdf_map* map, const float* points_dev, int64_t n, cons
         TSDF_CU(launch_sort_scatter(d, pdl, s));
         cudaEvent_t e5 = prof_mark(map, s);
         cudaEvent_t e6 = prof_mark(map, s);
-        TSDF_CU(launch_sort_apply(d, map->p.reduce, map->p.w_max, map->p.flags, map->num_sms * 8, pdl, s));
-        TSDF_CU(launch_finish(d, pdl, s));
+        TSDF_CU(launch_sort_apply(d, map->p.reduce, map->p.w_max, map->p.flags, pdl, s));   // + counters
         cudaEvent_t e7 = prof_mark(map, s);
         prof_push(map, kRays, e0, e1);
         prof_push(map, kEmit, e2, e3);
@@ -433,8 +432,7 @@ static int integrate_dev(tsdf_map* map, const float* points_dev, int64_t n, cons
     cudaEvent_t e3 = n > 0 ? prof_mark(map, s) : nullptr;
     cudaEvent_t e4 = prof_mark(map, s);
     TSDF_CU(launch_compact(map->dev, (uint32_t)map->bricks, pdl, s));
-    TSDF_CU(launch_apply(map->dev, map->p.reduce, map->p.w_max, map->p.flags, map->num_sms * 8, pdl, s));
-    TSDF_CU(launch_finish(map->dev, pdl, s));
+    TSDF_CU(launch_apply(map->dev, map->p.reduce, map->p.w_max, map->p.flags, pdl, s));   // + counters
     cudaEvent_t e5 = prof_mark(map, s);
     prof_push(map, kRays, e0, e1);
     prof_push(map, kContrib, e2, e3);

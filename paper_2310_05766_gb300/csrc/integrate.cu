@@ -34,8 +34,8 @@
 //   brick back with 16-byte stores and resets the accumulators. Touched voxels
 //   are counted, and in WSUM mode the contributions too (the sum of the decoded
 //   weights).
-// finish: one warp sums the per-scan counters into the published ones and
-//   clears the per-scan state.
+// finish: the last apply CTA to retire sums the per-scan counters into the
+//   published ones and clears the per-scan state (one warp).
 //
 // Sort reduction (an alternative to the accumulator atomics, same results):
 // rays also reserve each live ray's pair slots (one per march sample); emit is
@@ -54,9 +54,34 @@
 // Every float operation on the geometry path is an explicit round-to-nearest
 // intrinsic (no contraction into FMA), in the same order as the CPU oracle, so
 // voxel indices and codes agree bit for bit.
+#include <mutex>
+#include <unordered_map>
 #include <utility>
 
 #include "integrate_device.cuh"
+
+// Minimum resident CTAs per SM requested for the contribution kernels (caps
+// their registers; 6 CTAs of 256 threads fit without the cap).
+#ifndef TSDF_CONTRIB_MIN_CTAS
+#define TSDF_CONTRIB_MIN_CTAS 1
+#endif
+// CTAs per SM launched by the persistent contribution and apply kernels;
+// 0 = as many as are resident at once.
+#ifndef TSDF_CONTRIB_CTAS_PER_SM
+#define TSDF_CONTRIB_CTAS_PER_SM 8
+#endif
+#ifndef TSDF_APPLY_CTAS_PER_SM
+#define TSDF_APPLY_CTAS_PER_SM 0
+#endif
+// Minimum resident CTAs per SM requested for the apply kernel.
+#ifndef TSDF_APPLY_MIN_CTAS
+#define TSDF_APPLY_MIN_CTAS 1
+#endif
+// 1: the apply kernel keeps each lane's voxels in registers (apply_brick_reg);
+// 0: it stages the brick in shared memory and compacts the touched voxels.
+#ifndef TSDF_APPLY_REG
+#define TSDF_APPLY_REG 1
+#endif
 
 namespace tsdf {
 namespace {
@@ -74,7 +99,7 @@ __global__ void __launch_bounds__(256) rays_kernel(const ScanArgs a, const MapDe
 // items with a grid stride and loads the next item's rays while it processes
 // the current one.
 template <int MODE, bool MERGE, int KPT>
-__global__ void __launch_bounds__(256) contrib_kernel(const ScanArgs a, const MapDev m) {
+__global__ void __launch_bounds__(256, TSDF_CONTRIB_MIN_CTAS) contrib_kernel(const ScanArgs a, const MapDev m) {
     __shared__ unsigned long long red[8];
     const unsigned lane = threadIdx.x & 31u;
     const unsigned gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -109,7 +134,7 @@ __global__ void __launch_bounds__(256) contrib_kernel(const ScanArgs a, const Ma
 
 // Sort reduction: the contribution march writing pairs (same work items).
 template <int MODE, int KPT>
-__global__ void __launch_bounds__(256) emit_kernel(const ScanArgs a, const MapDev m) {
+__global__ void __launch_bounds__(256, TSDF_CONTRIB_MIN_CTAS) emit_kernel(const ScanArgs a, const MapDev m) {
     __shared__ unsigned long long red[8];
     const unsigned lane = threadIdx.x & 31u;
     const unsigned gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -174,15 +199,19 @@ __global__ void __launch_bounds__(256) compact_kernel(const MapDev m, const uint
 
 constexpr int kApplyWarps = 4;
 
+// The last CTA to finish also publishes the scan's counters (finish_if_last).
 template <int MODE>
-__global__ void __launch_bounds__(kApplyWarps * 32) apply_kernel(const MapDev m, const int32_t w_max,
+__global__ void __launch_bounds__(kApplyWarps * 32, TSDF_APPLY_MIN_CTAS) apply_kernel(const MapDev m, const int32_t w_max,
                                                                   const int32_t flags) {
+#if !TSDF_APPLY_REG
     // per warp: the brick's grid words and accumulators, and the offsets of
     // its touched voxels (compacted)
     __shared__ uint32_t s_grid[kApplyWarps][kBrickVoxels];
     __shared__ unsigned long long s_acc[kApplyWarps][kBrickVoxels];
     __shared__ uint16_t s_off[kApplyWarps][kBrickVoxels];
+#endif
     __shared__ unsigned long long red_u[kApplyWarps], red_h[kApplyWarps];
+    __shared__ unsigned s_last;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned w = threadIdx.x >> 5;
     const unsigned gwarp = blockIdx.x * kApplyWarps + w;
@@ -194,8 +223,13 @@ __global__ void __launch_bounds__(kApplyWarps * 32) apply_kernel(const MapDev m,
     if (lane == 0) nb = __ldcg(&m.ctr->brick_count);
     nb = __shfl_sync(kFull, nb, 0);
     unsigned long long touched = 0, hits = 0;
-    for (unsigned i = gwarp; i < nb; i += nwarps)
+    for (unsigned i = gwarp; i < nb; i += nwarps) {
+#if TSDF_APPLY_REG
+        apply_brick_reg<MODE>(m, w_max, flags, i, touched, hits);
+#else
         apply_brick<MODE>(m, w_max, flags, i, s_grid[w], s_acc[w], s_off[w], touched, hits);
+#endif
+    }
     for (int o = 16; o > 0; o >>= 1) {
         touched += __shfl_xor_sync(kFull, touched, o);
         hits += __shfl_xor_sync(kFull, hits, o);
@@ -214,9 +248,11 @@ __global__ void __launch_bounds__(kApplyWarps * 32) apply_kernel(const MapDev m,
         if (bu) atomicAdd(&m.ctr->part[blockIdx.x % kParts].touched, bu);
         if (MODE == 0 && bh) atomicAdd(&m.ctr->part[blockIdx.x % kParts].hits, bh);
     }
+    finish_if_last(m, &s_last);
 }
 
-// Sort reduction: one warp per listed brick (as apply_kernel).
+// Sort reduction: one warp per listed brick (as apply_kernel, and likewise
+// the last CTA publishes the counters).
 template <int MODE>
 __global__ void __launch_bounds__(kApplyWarps * 32) sort_apply_kernel(const MapDev m, const int32_t w_max,
                                                                        const int32_t flags) {
@@ -224,6 +260,7 @@ __global__ void __launch_bounds__(kApplyWarps * 32) sort_apply_kernel(const MapD
     __shared__ unsigned long long s_acc[kApplyWarps][kBrickVoxels];
     __shared__ uint16_t s_off[kApplyWarps][kBrickVoxels];
     __shared__ unsigned long long red_u[kApplyWarps], red_h[kApplyWarps];
+    __shared__ unsigned s_last;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned w = threadIdx.x >> 5;
     const unsigned gwarp = blockIdx.x * kApplyWarps + w;
@@ -258,14 +295,9 @@ __global__ void __launch_bounds__(kApplyWarps * 32) sort_apply_kernel(const MapD
         if (bu) atomicAdd(&m.ctr->part[blockIdx.x % kParts].touched, bu);
         if (bh) atomicAdd(&m.ctr->part[blockIdx.x % kParts].hits, bh);
     }
+    finish_if_last(m, &s_last);
 }
 
-// One warp: publish the scan's counters and clear the per-scan state.
-__global__ void finish_kernel(const MapDev m) {
-    pdl_trigger();
-    pdl_wait();
-    finish_warp(m);
-}
 
 // Launch with programmatic stream serialisation when `pdl` is set.
 template <typename... KArgs, typename... Args>
@@ -283,28 +315,64 @@ cudaError_t launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-int persistent_ctas_256() {
-    // CTAs of 256 threads that fill every SM of the current device once (8 per SM)
-    static int cached[64] = {0};
+// CTAs of `kernel` (launched with `threads` threads and static shared memory
+// only) that the current device holds at once: SMs x resident CTAs per SM.
+// Persistent kernels launch exactly this many, so no CTA waits for a second
+// wave. Cached per kernel and device.
+int resident_ctas(const void* kernel, int threads) {
+    static std::mutex mu;
+    static std::unordered_map<unsigned long long, int> cache;
     int dev = 0;
     cudaGetDevice(&dev);
-    const int slot = dev >= 0 && dev < 64 ? dev : 0;
-    if (cached[slot] == 0) {
-        int sms = 1;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cached[slot] = (sms > 0 ? sms : 1) * 8;
+    const unsigned long long key = (unsigned long long)(uintptr_t)kernel * 1024ull + (unsigned long long)dev;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int sms = 1, per_sm = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int n = (sms > 0 ? sms : 1) * per_sm;
+    cache[key] = n;
+    return n;
+}
+
+template <typename... KArgs>
+dim3 resident_grid(void (*kernel)(KArgs...), int threads, int per_sm = 0) {
+    if (per_sm > 0) {
+        static int sms[64] = {};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const int d = dev >= 0 && dev < 64 ? dev : 0;
+        if (sms[d] == 0) {
+            int v = 1;
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+            sms[d] = v > 0 ? v : 1;
+        }
+        return dim3((unsigned)(sms[d] * per_sm));
     }
-    return cached[slot];
+    return dim3((unsigned)resident_ctas(reinterpret_cast<const void*>(kernel), threads));
+}
+
+template <int MODE, bool MERGE, int KPT>
+cudaError_t launch_contrib_kk(const ScanArgs& a, const MapDev& m, bool pdl, cudaStream_t s) {
+    auto* k = contrib_kernel<MODE, MERGE, KPT>;
+    return launch(k, resident_grid(k, 256, TSDF_CONTRIB_CTAS_PER_SM), dim3(256), s, pdl, a, m);
 }
 
 template <int MODE, bool MERGE>
 cudaError_t launch_contrib_k(const ScanArgs& a, const MapDev& m, int kpt, bool pdl, cudaStream_t s) {
-    const dim3 grid((unsigned)persistent_ctas_256());
     switch (kpt) {
-        case 2: return launch(contrib_kernel<MODE, MERGE, 2>, grid, dim3(256), s, pdl, a, m);
-        case 4: return launch(contrib_kernel<MODE, MERGE, 4>, grid, dim3(256), s, pdl, a, m);
-        default: return launch(contrib_kernel<MODE, MERGE, 1>, grid, dim3(256), s, pdl, a, m);
+        case 2: return launch_contrib_kk<MODE, MERGE, 2>(a, m, pdl, s);
+        case 4: return launch_contrib_kk<MODE, MERGE, 4>(a, m, pdl, s);
+        default: return launch_contrib_kk<MODE, MERGE, 1>(a, m, pdl, s);
     }
+}
+
+template <int MODE, int KPT>
+cudaError_t launch_emit_k(const ScanArgs& a, const MapDev& m, bool pdl, cudaStream_t s) {
+    auto* k = emit_kernel<MODE, KPT>;
+    return launch(k, resident_grid(k, 256, TSDF_CONTRIB_CTAS_PER_SM), dim3(256), s, pdl, a, m);
 }
 
 }  // namespace
@@ -318,23 +386,22 @@ cudaError_t launch_rays(const ScanArgs& a, const MapDev& m, bool sort, bool pdl,
 
 cudaError_t launch_emit(const ScanArgs& a, const MapDev& m, int32_t reduce, int kpt, bool pdl, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
-    const dim3 grid((unsigned)persistent_ctas_256());
     if (reduce == 0) {
         switch (kpt) {
-            case 2: return launch(emit_kernel<0, 2>, grid, dim3(256), s, pdl, a, m);
-            case 4: return launch(emit_kernel<0, 4>, grid, dim3(256), s, pdl, a, m);
-            default: return launch(emit_kernel<0, 1>, grid, dim3(256), s, pdl, a, m);
+            case 2: return launch_emit_k<0, 2>(a, m, pdl, s);
+            case 4: return launch_emit_k<0, 4>(a, m, pdl, s);
+            default: return launch_emit_k<0, 1>(a, m, pdl, s);
         }
     }
     switch (kpt) {
-        case 2: return launch(emit_kernel<1, 2>, grid, dim3(256), s, pdl, a, m);
-        case 4: return launch(emit_kernel<1, 4>, grid, dim3(256), s, pdl, a, m);
-        default: return launch(emit_kernel<1, 1>, grid, dim3(256), s, pdl, a, m);
+        case 2: return launch_emit_k<1, 2>(a, m, pdl, s);
+        case 4: return launch_emit_k<1, 4>(a, m, pdl, s);
+        default: return launch_emit_k<1, 1>(a, m, pdl, s);
     }
 }
 
 cudaError_t launch_sort_count(const MapDev& m, bool pdl, cudaStream_t s) {
-    return launch(sort_count_kernel, dim3((unsigned)persistent_ctas_256()), dim3(256), s, pdl, m);
+    return launch(sort_count_kernel, resident_grid(sort_count_kernel, 256), dim3(256), s, pdl, m);
 }
 
 cudaError_t launch_sort_scan(const MapDev& m, bool pdl, cudaStream_t s) {
@@ -342,14 +409,14 @@ cudaError_t launch_sort_scan(const MapDev& m, bool pdl, cudaStream_t s) {
 }
 
 cudaError_t launch_sort_scatter(const MapDev& m, bool pdl, cudaStream_t s) {
-    return launch(sort_scatter_kernel, dim3((unsigned)persistent_ctas_256()), dim3(256), s, pdl, m);
+    return launch(sort_scatter_kernel, resident_grid(sort_scatter_kernel, 256), dim3(256), s, pdl, m);
 }
 
-cudaError_t launch_sort_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t flags, int num_ctas, bool pdl,
+cudaError_t launch_sort_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t flags, bool pdl,
                               cudaStream_t s) {
-    if (reduce == 0)
-        return launch(sort_apply_kernel<0>, dim3(num_ctas), dim3(kApplyWarps * 32), s, pdl, m, w_max, flags);
-    return launch(sort_apply_kernel<1>, dim3(num_ctas), dim3(kApplyWarps * 32), s, pdl, m, w_max, flags);
+    auto* k = reduce == 0 ? sort_apply_kernel<0> : sort_apply_kernel<1>;
+    return launch(k, resident_grid(k, kApplyWarps * 32, TSDF_APPLY_CTAS_PER_SM), dim3(kApplyWarps * 32), s, pdl, m,
+                  w_max, flags);
 }
 
 cudaError_t launch_contrib(const ScanArgs& a, const MapDev& m, int32_t reduce, bool merge, int kpt, bool pdl,
@@ -365,14 +432,10 @@ cudaError_t launch_compact(const MapDev& m, uint32_t bricks, bool pdl, cudaStrea
     return launch(compact_kernel, dim3((nwords + 255u) / 256u), dim3(256), s, pdl, m, nwords);
 }
 
-cudaError_t launch_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t flags, int num_ctas, bool pdl,
-                         cudaStream_t s) {
-    if (reduce == 0) return launch(apply_kernel<0>, dim3(num_ctas), dim3(kApplyWarps * 32), s, pdl, m, w_max, flags);
-    return launch(apply_kernel<1>, dim3(num_ctas), dim3(kApplyWarps * 32), s, pdl, m, w_max, flags);
-}
-
-cudaError_t launch_finish(const MapDev& m, bool pdl, cudaStream_t s) {
-    return launch(finish_kernel, dim3(1), dim3(kParts), s, pdl, m);
+cudaError_t launch_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t flags, bool pdl, cudaStream_t s) {
+    auto* k = reduce == 0 ? apply_kernel<0> : apply_kernel<1>;
+    return launch(k, resident_grid(k, kApplyWarps * 32, TSDF_APPLY_CTAS_PER_SM), dim3(kApplyWarps * 32), s, pdl, m,
+                  w_max, flags);
 }
 
 }  // namespace tsdf

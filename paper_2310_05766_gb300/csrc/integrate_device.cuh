@@ -11,6 +11,10 @@ namespace dev {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr unsigned kNoVoxel = 0xFFFFFFFFu;
 
+#ifndef TSDF_MARK_SHFL
+#define TSDF_MARK_SHFL 0
+#endif
+
 __device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
@@ -279,10 +283,15 @@ __device__ __forceinline__ void contrib_item(const ScanArgs& a, const MapDev& m,
                 }
             }
             if (MODE == 1 && !SORT) hits += act ? 1u : 0u;
-            // mark the brick; skip when this lane marked it last or the lane
-            // below (usually the neighbouring ray) marks the same brick now
+            // mark the brick unless this lane marked it last (same-address
+            // byte stores of a warp merge into one transaction); optionally
+            // also skip when the lane below marks the same brick now
+#if TSDF_MARK_SHFL
             const unsigned below = __shfl_up_sync(kFull, leader ? brick : kNoVoxel, 1);
             if (leader && brick != last_brick && (lane == 0 || below != brick)) {
+#else
+            if (leader && brick != last_brick) {
+#endif
                 last_brick = brick;
                 m.brick_flag[brick] = 1;
             }
@@ -324,42 +333,53 @@ __device__ __forceinline__ uint32_t update_voxel_scan(uint32_t word, long long S
 // contributions (WSUM) or 1 (MIN_ABS), 0 if untouched. WSUM accumulators
 // whose sum fits 31 bits and count fits 15 bits (the common case) take an
 // all-32-bit path with the same result as the 64-bit one.
+// Eq. 1 / Eq. 2 in 32-bit integers, exact while |gv gw + S| < 2^31 - 2^17
+// and gw + W < 2^16 (then 2 |num| + den < 2^32).
+__device__ __forceinline__ uint32_t eq12_small(uint32_t word, int S, unsigned W, int32_t w_max) {
+    const int gv = (int)(int16_t)(word & 0xFFFFu);
+    const int gw = (int)(int16_t)(word >> 16);
+    const int num = gv * gw + S;
+    const unsigned den = (unsigned)gw + W;
+    const unsigned an = (unsigned)(num < 0 ? -num : num);
+    const unsigned q = (2u * an + den) / (2u * den);
+    const int nv = num < 0 ? -(int)q : (int)q;
+    const unsigned nw = den > (unsigned)w_max ? (unsigned)w_max : den;
+    return (uint32_t)(uint16_t)(int16_t)nv | (nw << 16);
+}
+
+// WSUM cases outside the 32-bit range, and the per-scan weight reading, in
+// 64-bit integers; rare, so kept out of line (fewer registers in the callers).
+static __device__ __noinline__ uint32_t decode_apply_wide(unsigned long long P, uint32_t word, int32_t w_max,
+                                                   int32_t flags) {
+    const long long S = ((long long)(P << 24)) >> 24;   // sign-extended low 40 bits
+    const long long W = (long long)((P - (unsigned long long)S) >> 40);
+    return (flags & kFlagScanWeight) ? update_voxel_scan(word, S, W, w_max) : update_voxel(word, S, W, w_max);
+}
+
 template <int MODE>
 __device__ __forceinline__ unsigned decode_apply(unsigned long long P, uint32_t& word, int32_t w_max,
                                                  int32_t flags = 0) {
     if (P == 0ull) return 0u;
-    if (MODE == 0 && (flags & kFlagScanWeight)) {
-        const long long S = ((long long)(P << 24)) >> 24;
-        const long long W = (long long)((P - (unsigned long long)S) >> 40);
-        word = update_voxel_scan(word, S, W, w_max);
-        return (unsigned)W;
-    }
     if (MODE == 0) {
         const unsigned lo = (unsigned)P, hi = (unsigned)(P >> 32);
         const unsigned hb = hi & 0xFFu;   // bits 32..39 of the 40-bit sum
         const bool small = ((hb == 0u) && (int)lo >= 0) || ((hb == 0xFFu) && (int)lo < 0);
         const int S32 = (int)lo;
-        const unsigned W32 = (hi >> 8) + (S32 < 0 ? 1u : 0u);
+        const unsigned W32 = (hi >> 8) + (S32 < 0 ? 1u : 0u);   // exact when `small`
         const int gw = (int)(int16_t)(word >> 16);
-        if (small && W32 < 32768u && gw >= 0 && S32 > -(1 << 30) && S32 < (1 << 30)) {
-            const int gv = (int)(int16_t)(word & 0xFFFFu);
-            const int num = gv * gw + S32;                  // |gv gw| < 2^30, |S| < 2^30
-            const unsigned den = (unsigned)gw + W32;        // < 2^16
-            const unsigned an = (unsigned)(num < 0 ? -num : num);
-            const unsigned q = (2u * an + den) / (2u * den);   // < 2^32 by the bounds above
-            const int nv = num < 0 ? -(int)q : (int)q;
-            const unsigned nw = den > (unsigned)w_max ? (unsigned)w_max : den;
-            word = (uint32_t)(uint16_t)(int16_t)nv | (nw << 16);
+        if (!(flags & kFlagScanWeight) && small && W32 < 32768u && gw >= 0 && S32 > -(1 << 30) &&
+            S32 < (1 << 30)) {
+            word = eq12_small(word, S32, W32, w_max);   // |gv gw| < 2^30, |S| < 2^30
             return W32;
         }
-        const long long S = ((long long)(P << 24)) >> 24;   // sign-extended low 40 bits
-        const long long W = (long long)((P - (unsigned long long)S) >> 40);
-        word = update_voxel(word, S, W, w_max);
-        return (unsigned)W;
+        word = decode_apply_wide(P, word, w_max, flags);
+        const long long S = ((long long)(P << 24)) >> 24;
+        return (unsigned)((P - (unsigned long long)S) >> 40);
     } else {
+        // |S| <= 32767 and W = 1: always inside the 32-bit range
         const unsigned key = 65536u - (unsigned)P;
         const int mag = (int)(key >> 1);
-        word = update_voxel(word, (key & 1u) ? -mag : mag, 1, w_max);
+        word = eq12_small(word, (key & 1u) ? -mag : mag, 1u, w_max);
         return 1u;
     }
 }
@@ -430,6 +450,48 @@ __device__ __forceinline__ void apply_staged(const MapDev& m, int32_t w_max, int
     const uint4* sg4 = reinterpret_cast<const uint4*>(s_grid);
 #pragma unroll
     for (int v = 0; v < 4; ++v) gpw[32 * v + lane] = sg4[32 * v + lane];
+}
+
+// ---- apply, register form: one warp updates listed brick number i. Lane l
+// holds voxels 2(32 v + l) and +1 (v = 0..7) as eight 8-byte grid pairs and
+// eight 16-byte accumulator pairs, all loaded at once; every touched voxel is
+// decoded in place (16 independent updates per lane), and only changed pairs
+// are written back and reset.
+template <int MODE>
+__device__ __forceinline__ void apply_brick_reg(const MapDev& m, int32_t w_max, int32_t flags, unsigned i,
+                                                unsigned long long& touched, unsigned long long& hits) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned brick = m.brick_list[i];
+    uint2* gp = reinterpret_cast<uint2*>(m.grid + ((size_t)brick << 9));
+    ulonglong2* ap = reinterpret_cast<ulonglong2*>(m.acc + ((size_t)brick << 9));
+    ulonglong2 acc[8];
+    uint2 g[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) acc[v] = ap[32 * v + lane];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) g[v] = gp[32 * v + lane];
+    unsigned cnt = 0;
+    unsigned long long h = 0;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        if (acc[v].x != 0ull) {
+            h += decode_apply<MODE>(acc[v].x, g[v].x, w_max, flags);
+            ++cnt;
+        }
+        if (acc[v].y != 0ull) {
+            h += decode_apply<MODE>(acc[v].y, g[v].y, w_max, flags);
+            ++cnt;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        if ((acc[v].x | acc[v].y) != 0ull) {
+            gp[32 * v + lane] = g[v];
+            ap[32 * v + lane] = make_ulonglong2(0ull, 0ull);
+        }
+    }
+    touched += cnt;
+    hits += h;
 }
 
 // ---- apply: one warp updates listed brick number i of the map. Shared
@@ -614,7 +676,9 @@ __device__ __forceinline__ void sort_apply_brick(const MapDev& m, int32_t w_max,
 __device__ __forceinline__ void finish_warp(const MapDev& m) {
     MapCounters* c = m.ctr;
     const unsigned lane = threadIdx.x & 31u;
-    unsigned long long v = c->part[lane].valid, h = c->part[lane].hits, u = c->part[lane].touched;
+    // coherent loads: the partial counters were added by other CTAs' atomics
+    unsigned long long v = __ldcg(&c->part[lane].valid), h = __ldcg(&c->part[lane].hits),
+                       u = __ldcg(&c->part[lane].touched);
     c->part[lane].valid = 0ull;
     c->part[lane].hits = 0ull;
     c->part[lane].touched = 0ull;
@@ -631,6 +695,23 @@ __device__ __forceinline__ void finish_warp(const MapDev& m) {
         c->brick_count = 0u;
         c->slot_count = 0ull;
         c->overflow = 0u;
+        c->apply_done = 0u;
+    }
+}
+
+// The calling CTA (all threads) counts itself done; the last CTA of the grid
+// then publishes the scan's counters with its first warp (finish_warp). The
+// caller must have added its partial counters before the call.
+__device__ __forceinline__ void finish_if_last(const MapDev& m, unsigned* s_last) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        *s_last = atomicAdd(&m.ctr->apply_done, 1u) == gridDim.x - 1u ? 1u : 0u;
+    }
+    __syncthreads();
+    if (*s_last && threadIdx.x < 32) {
+        __threadfence();
+        finish_warp(m);
     }
 }
 

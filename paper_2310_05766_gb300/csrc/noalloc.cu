@@ -158,15 +158,10 @@ extern "C" int tsdf_integrate_static(uint32_t* grid_dev, const tsdf_params* para
     a.lcxy = a.lcx + ilog2((uint32_t)params->dims[1] / 8u);
     a.flags = params->flags;
 
-    int num_sms = 1;
-    int dev = 0;
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = launch_rays(a, md, false, true, s);
     if (e == cudaSuccess) e = launch_contrib(a, md, params->reduce, false, 4, true, s);
     if (e == cudaSuccess) e = launch_compact(md, (uint32_t)bricks, true, s);
-    if (e == cudaSuccess) e = launch_apply(md, params->reduce, params->w_max, params->flags, num_sms * 8, true, s);
-    if (e == cudaSuccess) e = launch_finish(md, true, s);
+    if (e == cudaSuccess) e = launch_apply(md, params->reduce, params->w_max, params->flags, true, s);
     if (e == cudaSuccess && stats_host) {
         long long last[3] = {0, 0, 0};
         e = cudaMemcpyAsync(last, &md.ctr->last_valid, sizeof(last), cudaMemcpyDeviceToHost, s);

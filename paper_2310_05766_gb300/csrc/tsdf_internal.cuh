@@ -35,7 +35,7 @@ struct MapCounters {
     unsigned int brick_count;       // length of the touched-brick list of the scan in flight
     unsigned long long slot_count;  // sort reduction: pair slots reserved by the scan in flight
     unsigned int overflow;          // sort reduction: 1 if some contribution went to the accumulators
-    unsigned int pad_;
+    unsigned int apply_done;        // CTAs of the apply kernel that have finished (the last one publishes)
 };
 
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;        // ray without pair slots (all its samples overflow)
@@ -127,15 +127,13 @@ cudaError_t launch_rays(const ScanArgs& a, const MapDev& m, bool sort, bool pdl,
 cudaError_t launch_contrib(const ScanArgs& a, const MapDev& m, int32_t reduce, bool merge, int kpt, bool pdl,
                            cudaStream_t s);
 cudaError_t launch_compact(const MapDev& m, uint32_t bricks, bool pdl, cudaStream_t s);
-cudaError_t launch_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t flags, int num_ctas, bool pdl,
-                         cudaStream_t s);
-cudaError_t launch_finish(const MapDev& m, bool pdl, cudaStream_t s);
+cudaError_t launch_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t flags, bool pdl, cudaStream_t s);
 // Sort reduction: emit pairs, count per brick, prefix, scatter, reduce + apply.
 cudaError_t launch_emit(const ScanArgs& a, const MapDev& m, int32_t reduce, int kpt, bool pdl, cudaStream_t s);
 cudaError_t launch_sort_count(const MapDev& m, bool pdl, cudaStream_t s);
 cudaError_t launch_sort_scan(const MapDev& m, bool pdl, cudaStream_t s);
 cudaError_t launch_sort_scatter(const MapDev& m, bool pdl, cudaStream_t s);
-cudaError_t launch_sort_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t flags, int num_ctas, bool pdl,
+cudaError_t launch_sort_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t flags, bool pdl,
                               cudaStream_t s);
 cudaError_t launch_shift(uint32_t* grid, const ShiftItem* items, int count, cudaStream_t s);
 cudaError_t launch_read_box(const uint32_t* grid, const long long lo[3], const uint32_t box[3],
