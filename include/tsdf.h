@@ -47,6 +47,7 @@ extern "C" {
 #define TSDF_ERR_TIMEOUT    -4  /* a bounded device-side wait expired */
 #define TSDF_ERR_ADMISSION  -5  /* a session would exceed the device-memory budget */
 #define TSDF_ERR_BUSY       -6  /* the resource is in use (e.g. an outstanding request) */
+#define TSDF_ERR_IO         -7  /* a file could not be opened, read or written, or is not a map file */
 
 /* ---- per-scan reduction of the contributions to one voxel ----------------- */
 #define TSDF_REDUCE_WSUM     0  /* sum of weight * distance and sum of weights (weight 1 per contribution) */
@@ -206,6 +207,38 @@ int tsdf_profile_enable(tsdf_map* map, int32_t enable);
  * events (host blocks until the profiled launches have finished).
  * Errors: INVALID, CUDA. */
 int tsdf_profile_read(tsdf_map* map, tsdf_kernel_time* out, int32_t capacity, int32_t* count);
+
+/* ---- persistence (checkpoint / resume of the whole global map) --------------
+ * The paper keeps the local map small and writes map parts that leave it to
+ * storage, reading them back when the sensor returns (Introduction). Here the
+ * parts live in a device-resident store while the process runs; these calls
+ * write the whole global map (window + store) to a file and rebuild a map from
+ * one, bit for bit.
+ *
+ * File format (little-endian): a 128-byte header, then one 2072-byte record
+ * per non-empty 8^3 chunk.
+ *   header: char magic[8] = "TSDFMAP1"; uint32 version = 1; uint32 header_bytes
+ *           = 128; tsdf_params params (72 bytes; origin = the window origin at
+ *           save time); int64 chunk_count; 32 zero bytes.
+ *   record: int64 chunk[3] (the chunk's first voxel in global coordinates,
+ *           divided by 8); uint32 word[512], word (z * 8 + y) * 8 + x holding
+ *           voxel chunk * 8 + (x, y, z) as value (low 16 bits, int16) and
+ *           weight (high 16 bits, int16).
+ * A chunk is non-empty when any of its words is non-zero. */
+#define TSDF_FILE_HEADER_BYTES 128
+#define TSDF_FILE_RECORD_BYTES 2072
+
+/* Write `map` to `path` (created or truncated). Synchronises `stream` first
+ * (all earlier work on the map must be on it); uses a pinned staging buffer.
+ * Errors: INVALID, IO, OOM, CUDA. */
+int tsdf_map_save(tsdf_map* map, const char* path, void* stream);
+
+/* Create a map from a file written by tsdf_map_save: same parameters, window
+ * at the saved origin, every chunk back in the window or the store. The new
+ * map is ready when the call returns (it synchronises `stream`). The file is
+ * checked (magic, version, sizes, parameters) before any device memory is
+ * allocated. Errors: INVALID, IO, OOM, CUDA. */
+int tsdf_map_load(const char* path, tsdf_map** out, void* stream);
 
 /* ---- measurement ------------------------------------------------------------
  * Sustained rate (operations per second) of fire-and-forget 64-bit integer

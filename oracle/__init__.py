@@ -97,6 +97,8 @@ def lib():
         L.orc_stats.argtypes = [vp, P(i64)]
         L.orc_store_chunks.restype = i64
         L.orc_store_chunks.argtypes = [vp]
+        L.orc_global_chunks.restype = i64
+        L.orc_global_chunks.argtypes = [vp, P(i64), P(ctypes.c_int16), P(ctypes.c_int16), i64]
         _lib = L
     return _lib
 
@@ -234,3 +236,16 @@ class OracleMap:
 
     def store_chunks(self) -> int:
         return int(lib().orc_store_chunks(self.h))
+
+    def global_chunks(self):
+        """Non-empty 8^3 chunks of the global map (window + store):
+        {chunk key (x, y, z): (value int16[512], weight int16[512])}, cells in
+        (z * 8 + y) * 8 + x order."""
+        P = ctypes.POINTER
+        n = int(lib().orc_global_chunks(self.h, None, None, None, 0))
+        keys = np.zeros((max(n, 1), 3), np.int64)
+        v = np.zeros((max(n, 1), 512), np.int16)
+        w = np.zeros((max(n, 1), 512), np.int16)
+        lib().orc_global_chunks(self.h, keys.ctypes.data_as(P(ctypes.c_int64)), v.ctypes.data_as(P(ctypes.c_int16)),
+                                w.ctypes.data_as(P(ctypes.c_int16)), n)
+        return {tuple(int(x) for x in keys[i]): (v[i], w[i]) for i in range(n)}

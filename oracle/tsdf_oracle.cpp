@@ -543,4 +543,45 @@ void orc_stats(void* h, int64_t out[3]) {
 
 int64_t orc_store_chunks(void* h) { return (int64_t)((OracleMap*)h)->store.size(); }
 
+// The global map as non-empty 8^3 chunks: every window chunk with a non-zero
+// cell, then every stored chunk outside the window (a stored copy of a chunk
+// that is back in the window is stale). Writes up to `cap` chunks: key (the
+// chunk's first voxel / 8) and 512 values and weights in (z * 8 + y) * 8 + x
+// order. Returns the number of chunks.
+int64_t orc_global_chunks(void* h, int64_t* keys, int16_t* v, int16_t* w, int64_t cap) {
+    OracleMap* m = (OracleMap*)h;
+    int64_t n = 0;
+    auto emit = [&](const std::array<int64_t, 3>& key, const std::vector<Cell>& cells) {
+        if (n < cap) {
+            for (int a = 0; a < 3; ++a) keys[3 * n + a] = key[a];
+            for (int i = 0; i < 512; ++i) {
+                v[512 * n + i] = cells[i].v;
+                w[512 * n + i] = cells[i].w;
+            }
+        }
+        ++n;
+    };
+    for (int64_t cz = m->origin[2]; cz < m->origin[2] + m->Z(); cz += 8)
+    for (int64_t cy = m->origin[1]; cy < m->origin[1] + m->Y(); cy += 8)
+    for (int64_t cx = m->origin[0]; cx < m->origin[0] + m->X(); cx += 8) {
+        std::vector<Cell> cells(512);
+        bool nonzero = false;
+        for (int z = 0; z < 8; ++z)
+        for (int y = 0; y < 8; ++y)
+        for (int x = 0; x < 8; ++x) {
+            int64_t g[3] = {cx + x, cy + y, cz + z};
+            Cell c = m->win[m->lin(g)];
+            cells[(z * 8 + y) * 8 + x] = c;
+            if (c.v != 0 || c.w != 0) nonzero = true;
+        }
+        if (nonzero) emit({cx / 8, cy / 8, cz / 8}, cells);
+    }
+    for (const auto& kv : m->store) {
+        const int64_t g[3] = {kv.first[0] * 8, kv.first[1] * 8, kv.first[2] * 8};
+        if (m->inside(g)) continue;
+        emit(kv.first, kv.second);
+    }
+    return n;
+}
+
 }  // extern "C"

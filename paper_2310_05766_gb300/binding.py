@@ -21,6 +21,7 @@ TSDF_ERR_CUDA = -3
 TSDF_ERR_TIMEOUT = -4
 TSDF_ERR_ADMISSION = -5
 TSDF_ERR_BUSY = -6
+TSDF_ERR_IO = -7
 TSDF_REDUCE_WSUM = 0
 TSDF_REDUCE_MIN_ABS = 1
 TSDF_FLAG_STEP_VALUE = 1
@@ -116,6 +117,8 @@ def lib():
     L.tsdf_profile_enable.argtypes = [vp, ctypes.c_int32]
     L.tsdf_profile_read.argtypes = [vp, P(tsdf_kernel_time), ctypes.c_int32, P(ctypes.c_int32)]
     L.tsdf_probe_reduction_rate.argtypes = [ctypes.c_int32, P(ctypes.c_double), vp]
+    L.tsdf_map_save.argtypes = [vp, ctypes.c_char_p, vp]
+    L.tsdf_map_load.argtypes = [ctypes.c_char_p, P(vp), vp]
     L.tsdf_batch_create.argtypes = [ctypes.c_int32, P(vp)]
     L.tsdf_batch_destroy.argtypes = [vp]
     L.tsdf_batch_set_option.argtypes = [vp, ctypes.c_int32, ctypes.c_int64]
@@ -138,7 +141,7 @@ def lib():
     for name in ("tsdf_map_create", "tsdf_map_destroy", "tsdf_integrate", "tsdf_integrate_host", "tsdf_shift",
                  "tsdf_read", "tsdf_write", "tsdf_stats", "tsdf_get_origin", "tsdf_grid_device_ptr",
                  "tsdf_last_cuda_error", "tsdf_profile_enable", "tsdf_profile_read", "tsdf_set_option",
-                 "tsdf_integrate_static", "tsdf_probe_reduction_rate", "tsdf_batch_create", "tsdf_batch_destroy", "tsdf_batch_set_option",
+                 "tsdf_integrate_static", "tsdf_probe_reduction_rate", "tsdf_map_save", "tsdf_map_load", "tsdf_batch_create", "tsdf_batch_destroy", "tsdf_batch_set_option",
                  "tsdf_batch_get_config", "tsdf_batch_integrate", "tsdf_integrate_batch", "tsdf_batch_sync",
                  "tsdf_server_create", "tsdf_server_destroy", "tsdf_server_open_session", "tsdf_server_close_session",
                  "tsdf_server_submit", "tsdf_server_wait", "tsdf_server_session_map", "tsdf_server_get_stats"):
@@ -412,6 +415,40 @@ def tsdf_profile_read(handle: int) -> dict:
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(cnt.value)}
 
 
+def tsdf_map_save(handle: int, path: str, stream=None) -> None:
+    _check(lib().tsdf_map_save(handle, os.fsencode(path), _stream_ptr(stream)), "tsdf_map_save")
+
+
+def tsdf_map_load(path: str, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().tsdf_map_load(os.fsencode(path), ctypes.byref(h), _stream_ptr(stream)), "tsdf_map_load")
+    return h.value
+
+
+FILE_HEADER_BYTES = 128
+FILE_RECORD_BYTES = 2072
+
+
+def _header_params(raw: np.ndarray) -> dict:
+    if raw.size < FILE_HEADER_BYTES or bytes(raw[:8]) != b"TSDFMAP1":
+        raise ValueError("not a map file")
+    prm = tsdf_params.from_buffer_copy(raw[16:16 + ctypes.sizeof(tsdf_params)].tobytes())
+    return dict(dims=tuple(prm.dims), voxel_size=prm.voxel_size, tau=prm.tau, w_max=prm.w_max,
+                delta_z=prm.delta_z, r_min=prm.r_min, r_max=prm.r_max, reduce=prm.reduce, flags=prm.flags,
+                origin=tuple(prm.origin))
+
+
+def read_map_file(path: str):
+    """Parse a map file (host only): (params dict, {chunk key: uint32[512] words})."""
+    raw = np.fromfile(path, dtype=np.uint8)
+    params = _header_params(raw)
+    count = int(raw[88:96].view(np.int64)[0])
+    recs = raw[FILE_HEADER_BYTES:].reshape(count, FILE_RECORD_BYTES)
+    keys = recs[:, :24].copy().view(np.int64).reshape(count, 3)
+    words = recs[:, 24:].copy().view(np.uint32).reshape(count, 512)
+    return params, {tuple(int(x) for x in keys[i]): words[i] for i in range(count)}
+
+
 def tsdf_probe_reduction_rate(pattern: int, stream=None) -> float:
     """Measured 64-bit L2 reduction rate (ops/s): pattern 0 coalesced, 1 scattered."""
     out = ctypes.c_double()
@@ -468,3 +505,14 @@ class TsdfMap:
 
     def stats(self, stream=None):
         return tsdf_stats(self.handle, stream)
+
+    def save(self, path: str, stream=None):
+        tsdf_map_save(self.handle, path, stream)
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "TsdfMap":
+        """A new map from a file written by save()."""
+        m = cls.__new__(cls)
+        m.handle = tsdf_map_load(path, stream)
+        m.params = _header_params(np.fromfile(path, dtype=np.uint8, count=FILE_HEADER_BYTES))
+        return m

@@ -667,6 +667,215 @@ int tsdf_set_option(tsdf_map* map, int32_t option, int64_t value) {
     }
 }
 
+// ---- persistence ------------------------------------------------------------
+
+namespace {
+
+constexpr char kFileMagic[8] = {'T', 'S', 'D', 'F', 'M', 'A', 'P', '1'};
+
+struct FileHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t header_bytes;
+    tsdf_params params;
+    int64_t chunk_count;
+    unsigned char zero[32];
+};
+static_assert(sizeof(tsdf_params) == 72, "tsdf_params layout");
+static_assert(sizeof(FileHeader) == TSDF_FILE_HEADER_BYTES, "file header layout");
+
+struct FileRecord {
+    int64_t chunk[3];
+    uint32_t word[512];
+};
+static_assert(sizeof(FileRecord) == TSDF_FILE_RECORD_BYTES, "file record layout");
+
+struct FileCloser {
+    FILE* f = nullptr;
+    ~FileCloser() {
+        if (f) fclose(f);
+    }
+};
+
+struct PinnedBuffer {
+    void* p = nullptr;
+    ~PinnedBuffer() {
+        if (p) cudaFreeHost(p);
+    }
+};
+
+bool all_zero(const uint32_t* w) {
+    for (int i = 0; i < 512; ++i)
+        if (w[i] != 0u) return false;
+    return true;
+}
+
+// Chunk coordinate of window ring slot s along one axis (C chunks per axis).
+long long slot_chunk(long long origin, long long C, long long s) {
+    const long long co = floordiv8(origin);
+    return co + (((s - co) % C) + C) % C;
+}
+
+}  // namespace
+
+int tsdf_map_save(tsdf_map* map, const char* path, void* stream) {
+    if (!map || !path) return TSDF_ERR_INVALID;
+    DeviceScope ds(map->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    TSDF_CU(cudaStreamSynchronize(s));
+    FileCloser fc;
+    fc.f = std::fopen(path, "wb");
+    if (!fc.f) return TSDF_ERR_IO;
+    FileHeader h{};
+    std::memcpy(h.magic, kFileMagic, 8);
+    h.version = 1;
+    h.header_bytes = TSDF_FILE_HEADER_BYTES;
+    h.params = map->p;
+    for (int a = 0; a < 3; ++a) h.params.origin[a] = map->origin[a];
+    h.chunk_count = 0;
+    if (std::fwrite(&h, sizeof(h), 1, fc.f) != 1) return TSDF_ERR_IO;
+
+    // staging: up to 4096 chunks (8 MiB) at a time
+    const size_t kStage = kSegChunks;
+    PinnedBuffer stage;
+    TSDF_CU(cudaMallocHost(&stage.p, kStage * kChunkBytes));
+    const uint32_t* sw = static_cast<const uint32_t*>(stage.p);
+    FileRecord rec;
+    int64_t count = 0;
+    const long long C[3] = {map->p.dims[0] / 8, map->p.dims[1] / 8, map->p.dims[2] / 8};
+    // 1. the window, brick by brick (ring slot order)
+    for (size_t b0 = 0; b0 < map->bricks; b0 += kStage) {
+        const size_t nb = map->bricks - b0 < kStage ? map->bricks - b0 : kStage;
+        TSDF_CU(cudaMemcpyAsync(stage.p, map->dev.grid + b0 * kBrickVoxels, nb * kChunkBytes, cudaMemcpyDeviceToHost, s));
+        TSDF_CU(cudaStreamSynchronize(s));
+        for (size_t k = 0; k < nb; ++k) {
+            const uint32_t* w = sw + k * kBrickVoxels;
+            if (all_zero(w)) continue;
+            const long long b = (long long)(b0 + k);
+            rec.chunk[0] = slot_chunk(map->origin[0], C[0], b % C[0]);
+            rec.chunk[1] = slot_chunk(map->origin[1], C[1], (b / C[0]) % C[1]);
+            rec.chunk[2] = slot_chunk(map->origin[2], C[2], b / (C[0] * C[1]));
+            std::memcpy(rec.word, w, kChunkBytes);
+            if (std::fwrite(&rec, sizeof(rec), 1, fc.f) != 1) return TSDF_ERR_IO;
+            ++count;
+        }
+    }
+    // 2. stored chunks outside the window (a stored copy of a chunk that is
+    //    back in the window is stale), segment by segment
+    std::vector<std::vector<std::pair<uint32_t, ChunkKey>>> by_seg(map->store_segments.size());
+    for (const auto& kv : map->store_index) {
+        const ChunkKey& k = kv.first;
+        const long long kc[3] = {k.x, k.y, k.z};
+        bool inside = true;
+        for (int a = 0; a < 3; ++a) {
+            const long long co = floordiv8(map->origin[a]);
+            inside = inside && kc[a] >= co && kc[a] < co + C[a];
+        }
+        if (!inside) by_seg[kv.second / kSegChunks].push_back({kv.second % kSegChunks, k});
+    }
+    for (size_t sg = 0; sg < by_seg.size(); ++sg) {
+        if (by_seg[sg].empty()) continue;
+        TSDF_CU(cudaMemcpyAsync(stage.p, map->store_segments[sg], (size_t)kSegChunks * kChunkBytes,
+                                cudaMemcpyDeviceToHost, s));
+        TSDF_CU(cudaStreamSynchronize(s));
+        for (const auto& e : by_seg[sg]) {
+            const uint32_t* w = sw + (size_t)e.first * kBrickVoxels;
+            if (all_zero(w)) continue;
+            rec.chunk[0] = e.second.x;
+            rec.chunk[1] = e.second.y;
+            rec.chunk[2] = e.second.z;
+            std::memcpy(rec.word, w, kChunkBytes);
+            if (std::fwrite(&rec, sizeof(rec), 1, fc.f) != 1) return TSDF_ERR_IO;
+            ++count;
+        }
+    }
+    h.chunk_count = count;
+    if (std::fseek(fc.f, 0, SEEK_SET) != 0 || std::fwrite(&h, sizeof(h), 1, fc.f) != 1) return TSDF_ERR_IO;
+    if (std::fclose(fc.f) != 0) {
+        fc.f = nullptr;
+        return TSDF_ERR_IO;
+    }
+    fc.f = nullptr;
+    return TSDF_OK;
+}
+
+int tsdf_map_load(const char* path, tsdf_map** out, void* stream) {
+    if (!path || !out) return TSDF_ERR_INVALID;
+    *out = nullptr;
+    FileCloser fc;
+    fc.f = std::fopen(path, "rb");
+    if (!fc.f) return TSDF_ERR_IO;
+    FileHeader h{};
+    if (std::fread(&h, sizeof(h), 1, fc.f) != 1) return TSDF_ERR_IO;
+    if (std::memcmp(h.magic, kFileMagic, 8) != 0 || h.version != 1 || h.header_bytes != TSDF_FILE_HEADER_BYTES ||
+        h.chunk_count < 0)
+        return TSDF_ERR_IO;
+    if (std::fseek(fc.f, 0, SEEK_END) != 0) return TSDF_ERR_IO;
+    const long long size = std::ftell(fc.f);
+    if (size != (long long)TSDF_FILE_HEADER_BYTES + h.chunk_count * (long long)TSDF_FILE_RECORD_BYTES)
+        return TSDF_ERR_IO;
+    if (std::fseek(fc.f, TSDF_FILE_HEADER_BYTES, SEEK_SET) != 0) return TSDF_ERR_IO;
+    if (validate_params(&h.params) != TSDF_OK) return TSDF_ERR_IO;
+
+    tsdf_map* map = nullptr;
+    int rc = tsdf_map_create(&h.params, &map);
+    if (rc != TSDF_OK) return rc;
+    DeviceScope ds(map->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t kStage = kSegChunks;
+    PinnedBuffer stage, items_h;
+    void* stage_d = nullptr;
+    ChunkCopy* items_d = nullptr;
+    auto fail = [&](int code) {
+        cudaFree(stage_d);
+        cudaFree(items_d);
+        tsdf_map_destroy(map);
+        return code;
+    };
+    cudaError_t e = cudaMallocHost(&stage.p, kStage * kChunkBytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&items_h.p, kStage * sizeof(ChunkCopy));
+    if (e == cudaSuccess) e = cudaMalloc(&stage_d, kStage * kChunkBytes);
+    if (e == cudaSuccess) e = cudaMalloc(&items_d, kStage * sizeof(ChunkCopy));
+    if (e != cudaSuccess) return fail(cuda_fail(e));
+    const long long C[3] = {map->p.dims[0] / 8, map->p.dims[1] / 8, map->p.dims[2] / 8};
+    ChunkCopy* items = static_cast<ChunkCopy*>(items_h.p);
+    FileRecord rec;
+    for (int64_t done = 0; done < h.chunk_count;) {
+        const int64_t nb = h.chunk_count - done < (int64_t)kStage ? h.chunk_count - done : (int64_t)kStage;
+        for (int64_t k = 0; k < nb; ++k) {
+            if (std::fread(&rec, sizeof(rec), 1, fc.f) != 1) return fail(TSDF_ERR_IO);
+            std::memcpy(static_cast<char*>(stage.p) + k * kChunkBytes, rec.word, kChunkBytes);
+            bool inside = true;
+            long long slot[3];
+            for (int a = 0; a < 3; ++a) {
+                const long long co = floordiv8(map->origin[a]);
+                inside = inside && rec.chunk[a] >= co && rec.chunk[a] < co + C[a];
+                slot[a] = ((rec.chunk[a] % C[a]) + C[a]) % C[a];
+            }
+            unsigned long long dst = 0;
+            if (inside) {
+                const size_t brick = (size_t)((slot[2] * C[1] + slot[1]) * C[0] + slot[0]);
+                dst = (unsigned long long)(map->dev.grid + brick * kBrickVoxels);
+            } else {
+                rc = store_lookup(map, ChunkKey{rec.chunk[0], rec.chunk[1], rec.chunk[2]}, true, &dst);
+                if (rc != TSDF_OK) return fail(rc);
+            }
+            items[k].dst = dst;
+            items[k].src = (unsigned long long)(static_cast<char*>(stage_d) + k * kChunkBytes);
+        }
+        e = cudaMemcpyAsync(stage_d, stage.p, (size_t)nb * kChunkBytes, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(items_d, items, (size_t)nb * sizeof(ChunkCopy), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = launch_copy_chunks(items_d, (int)nb, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the staging buffers are reused
+        if (e != cudaSuccess) return fail(cuda_fail(e));
+        done += nb;
+    }
+    cudaFree(stage_d);
+    cudaFree(items_d);
+    *out = map;
+    return TSDF_OK;
+}
+
 int tsdf_get_origin(const tsdf_map* map, int64_t out[3]) {
     if (!map || !out) return TSDF_ERR_INVALID;
     for (int a = 0; a < 3; ++a) out[a] = map->origin[a];
@@ -688,6 +897,7 @@ const char* tsdf_error_string(int code) {
         case TSDF_ERR_TIMEOUT: return "device wait timed out";
         case TSDF_ERR_ADMISSION: return "device-memory budget exceeded";
         case TSDF_ERR_BUSY: return "resource busy";
+        case TSDF_ERR_IO: return "file error or not a map file";
         default: return "unknown error";
     }
 }

@@ -91,6 +91,12 @@ struct ShiftItem {
     unsigned long long pad1;
 };
 
+// One 2048-byte chunk copy (device addresses).
+struct ChunkCopy {
+    unsigned long long dst;
+    unsigned long long src;
+};
+
 struct WindowGeom {
     uint32_t dims[3];
     uint32_t cmask[3];
@@ -136,6 +142,7 @@ cudaError_t launch_sort_scatter(const MapDev& m, bool pdl, cudaStream_t s);
 cudaError_t launch_sort_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t flags, bool pdl,
                               cudaStream_t s);
 cudaError_t launch_shift(uint32_t* grid, const ShiftItem* items, int count, cudaStream_t s);
+cudaError_t launch_copy_chunks(const ChunkCopy* items, int count, cudaStream_t s);
 cudaError_t launch_read_box(const uint32_t* grid, const long long lo[3], const uint32_t box[3],
                             const WindowGeom& g, int16_t* v, int16_t* w, cudaStream_t s);
 cudaError_t launch_write_box(uint32_t* grid, const long long lo[3], const uint32_t box[3], const WindowGeom& g,

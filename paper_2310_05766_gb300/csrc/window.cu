@@ -29,6 +29,15 @@ __global__ void __launch_bounds__(128) shift_kernel(uint32_t* __restrict__ grid,
     }
 }
 
+// One CTA of 128 threads per chunk: copies 2048 bytes from src to dst.
+__global__ void __launch_bounds__(128) copy_chunks_kernel(const ChunkCopy* __restrict__ items, int count) {
+    const int t = threadIdx.x;
+    for (int it = blockIdx.x; it < count; it += gridDim.x) {
+        const ChunkCopy c = items[it];
+        reinterpret_cast<uint4*>(c.dst)[t] = reinterpret_cast<const uint4*>(c.src)[t];
+    }
+}
+
 __device__ __forceinline__ size_t word_of(long long gx, long long gy, long long gz, const WindowGeom& g) {
     const size_t bx = (size_t)((unsigned long long)(gx >> 3) & g.cmask[0]);
     const size_t by = (size_t)((unsigned long long)(gy >> 3) & g.cmask[1]);
@@ -66,6 +75,12 @@ int grid_for(size_t total) {
 }
 
 }  // namespace
+
+cudaError_t launch_copy_chunks(const ChunkCopy* items, int count, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    copy_chunks_kernel<<<count < 4096 ? count : 4096, 128, 0, s>>>(items, count);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_shift(uint32_t* grid, const ShiftItem* items, int count, cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
