@@ -240,6 +240,20 @@ int tsdf_map_save(tsdf_map* map, const char* path, void* stream);
  * allocated. Errors: INVALID, IO, OOM, CUDA. */
 int tsdf_map_load(const char* path, tsdf_map** out, void* stream);
 
+/* ---- map consumers ------------------------------------------------------------
+ * Surface points: one per pair of 6-connected window voxels a, b = a + e_axis
+ * (axis 0, 1, 2 = x, y, z) whose weights are both >= min_weight and whose
+ * values differ in sign ((v_a < 0) != (v_b < 0)), placed where the linear
+ * interpolation of the two codes between the voxel centres is zero:
+ * t = v_a / (v_a - v_b) (IEEE binary32 division), coordinate along the axis
+ * ((float)g_a + 0.5 + t) * voxel_size, the other two ((float)g + 0.5) *
+ * voxel_size, in world metres. out_dev: device float4 array (x, y, z, axis),
+ * 16-byte aligned, `capacity` points; the order is unspecified. *count gets
+ * the number of points found (those beyond capacity are not written).
+ * Synchronises `stream`. Errors: INVALID, CUDA. */
+int tsdf_extract_surface(tsdf_map* map, int32_t min_weight, float* out_dev, int64_t capacity, int64_t* count,
+                         void* stream);
+
 /* ---- measurement ------------------------------------------------------------
  * Sustained rate (operations per second) of fire-and-forget 64-bit integer
  * reductions into L2-resident device memory on the current device, the

@@ -97,6 +97,8 @@ def lib():
         L.orc_stats.argtypes = [vp, P(i64)]
         L.orc_store_chunks.restype = i64
         L.orc_store_chunks.argtypes = [vp]
+        L.orc_surface.restype = i64
+        L.orc_surface.argtypes = [vp, ctypes.c_int32, f32p, i64]
         L.orc_global_chunks.restype = i64
         L.orc_global_chunks.argtypes = [vp, P(i64), P(ctypes.c_int16), P(ctypes.c_int16), i64]
         _lib = L
@@ -236,6 +238,13 @@ class OracleMap:
 
     def store_chunks(self) -> int:
         return int(lib().orc_store_chunks(self.h))
+
+    def surface(self, min_weight: int = 1) -> np.ndarray:
+        """Zero-crossing points of the window: float32 (n, 4) = (x, y, z, axis), z-y-x-axis order."""
+        n = int(lib().orc_surface(self.h, min_weight, None, 0))
+        out = np.zeros((max(n, 1), 4), np.float32)
+        lib().orc_surface(self.h, min_weight, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n)
+        return out[:n]
 
     def global_chunks(self):
         """Non-empty 8^3 chunks of the global map (window + store):

@@ -543,6 +543,44 @@ void orc_stats(void* h, int64_t out[3]) {
 
 int64_t orc_store_chunks(void* h) { return (int64_t)((OracleMap*)h)->store.size(); }
 
+// Zero crossings of the window (a consumer of the map): for each voxel a (z,
+// y, x order) and each axis x, y, z with b = a + e_axis inside the window,
+// both weights >= min_w and (v_a < 0) != (v_b < 0): the point where the
+// linear interpolation of v between the centres is zero, t = v_a / (v_a -
+// v_b), coordinate along the axis ((float)g_a + 0.5 + t) * vs. Writes up to
+// cap points as (x, y, z, axis); returns the number found.
+int64_t orc_surface(void* h, int32_t min_w, float* out, int64_t cap) {
+    OracleMap* m = (OracleMap*)h;
+    const float vs = m->p.voxel_size;
+    int64_t n = 0;
+    for (int64_t z = 0; z < m->Z(); ++z)
+    for (int64_t y = 0; y < m->Y(); ++y)
+    for (int64_t x = 0; x < m->X(); ++x) {
+        const int64_t ga[3] = {m->origin[0] + x, m->origin[1] + y, m->origin[2] + z};
+        const Cell a = m->win[m->lin(ga)];
+        if (a.w < min_w) continue;
+        for (int ax = 0; ax < 3; ++ax) {
+            int64_t gb[3] = {ga[0], ga[1], ga[2]};
+            gb[ax] += 1;
+            if (!m->inside(gb)) continue;
+            const Cell b = m->win[m->lin(gb)];
+            if (b.w < min_w || ((a.v < 0) == (b.v < 0))) continue;
+            const float t = (float)a.v / (float)(a.v - b.v);
+            float p[3];
+            for (int k = 0; k < 3; ++k) p[k] = ((float)ga[k] + 0.5f) * vs;
+            p[ax] = (((float)ga[ax] + 0.5f) + t) * vs;
+            if (n < cap) {
+                out[4 * n + 0] = p[0];
+                out[4 * n + 1] = p[1];
+                out[4 * n + 2] = p[2];
+                out[4 * n + 3] = (float)ax;
+            }
+            ++n;
+        }
+    }
+    return n;
+}
+
 // The global map as non-empty 8^3 chunks: every window chunk with a non-zero
 // cell, then every stored chunk outside the window (a stored copy of a chunk
 // that is back in the window is stale). Writes up to `cap` chunks: key (the

@@ -118,6 +118,7 @@ def lib():
     L.tsdf_profile_read.argtypes = [vp, P(tsdf_kernel_time), ctypes.c_int32, P(ctypes.c_int32)]
     L.tsdf_probe_reduction_rate.argtypes = [ctypes.c_int32, P(ctypes.c_double), vp]
     L.tsdf_map_save.argtypes = [vp, ctypes.c_char_p, vp]
+    L.tsdf_extract_surface.argtypes = [vp, ctypes.c_int32, vp, i64, P(i64), vp]
     L.tsdf_map_load.argtypes = [ctypes.c_char_p, P(vp), vp]
     L.tsdf_batch_create.argtypes = [ctypes.c_int32, P(vp)]
     L.tsdf_batch_destroy.argtypes = [vp]
@@ -141,7 +142,7 @@ def lib():
     for name in ("tsdf_map_create", "tsdf_map_destroy", "tsdf_integrate", "tsdf_integrate_host", "tsdf_shift",
                  "tsdf_read", "tsdf_write", "tsdf_stats", "tsdf_get_origin", "tsdf_grid_device_ptr",
                  "tsdf_last_cuda_error", "tsdf_profile_enable", "tsdf_profile_read", "tsdf_set_option",
-                 "tsdf_integrate_static", "tsdf_probe_reduction_rate", "tsdf_map_save", "tsdf_map_load", "tsdf_batch_create", "tsdf_batch_destroy", "tsdf_batch_set_option",
+                 "tsdf_integrate_static", "tsdf_probe_reduction_rate", "tsdf_map_save", "tsdf_map_load", "tsdf_extract_surface", "tsdf_batch_create", "tsdf_batch_destroy", "tsdf_batch_set_option",
                  "tsdf_batch_get_config", "tsdf_batch_integrate", "tsdf_integrate_batch", "tsdf_batch_sync",
                  "tsdf_server_create", "tsdf_server_destroy", "tsdf_server_open_session", "tsdf_server_close_session",
                  "tsdf_server_submit", "tsdf_server_wait", "tsdf_server_session_map", "tsdf_server_get_stats"):
@@ -415,6 +416,22 @@ def tsdf_profile_read(handle: int) -> dict:
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(cnt.value)}
 
 
+def tsdf_extract_surface(handle: int, min_weight: int = 1, out=None, stream=None):
+    """Zero-crossing points of the window. out: CUDA float32 (cap, 4) tensor or
+    None (sized automatically with a second call). Returns (points view, count)."""
+    import torch
+    cnt = ctypes.c_int64()
+    if out is None:
+        _check(lib().tsdf_extract_surface(handle, min_weight, None, 0, ctypes.byref(cnt), _stream_ptr(stream)),
+               "tsdf_extract_surface")
+        out = torch.empty((max(int(cnt.value), 1), 4), dtype=torch.float32, device="cuda")
+    assert out.dtype == torch.float32 and out.is_contiguous() and out.shape[1] == 4
+    _check(lib().tsdf_extract_surface(handle, min_weight, out.data_ptr(), out.shape[0], ctypes.byref(cnt),
+                                      _stream_ptr(stream)), "tsdf_extract_surface")
+    n = int(cnt.value)
+    return out[:min(n, out.shape[0])], n
+
+
 def tsdf_map_save(handle: int, path: str, stream=None) -> None:
     _check(lib().tsdf_map_save(handle, os.fsencode(path), _stream_ptr(stream)), "tsdf_map_save")
 
@@ -505,6 +522,10 @@ class TsdfMap:
 
     def stats(self, stream=None):
         return tsdf_stats(self.handle, stream)
+
+    def surface(self, min_weight: int = 1, stream=None):
+        """Zero-crossing points (x, y, z, axis) as a CUDA float32 tensor."""
+        return tsdf_extract_surface(self.handle, min_weight, None, stream)[0]
 
     def save(self, path: str, stream=None):
         tsdf_map_save(self.handle, path, stream)

@@ -36,6 +36,7 @@ struct MapCounters {
     unsigned long long slot_count;  // sort reduction: pair slots reserved by the scan in flight
     unsigned int overflow;          // sort reduction: 1 if some contribution went to the accumulators
     unsigned int apply_done;        // CTAs of the apply kernel that have finished (the last one publishes)
+    unsigned long long surface_count;   // points found by the last surface extraction
 };
 
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;        // ray without pair slots (all its samples overflow)
@@ -143,6 +144,8 @@ cudaError_t launch_sort_apply(const MapDev& m, int32_t reduce, int32_t w_max, in
                               cudaStream_t s);
 cudaError_t launch_shift(uint32_t* grid, const ShiftItem* items, int count, cudaStream_t s);
 cudaError_t launch_copy_chunks(const ChunkCopy* items, int count, cudaStream_t s);
+cudaError_t launch_surface(const uint32_t* grid, const WindowGeom& geo, const long long origin[3], int min_w, float vs,
+                           float4* out, unsigned long long cap, unsigned long long* count, cudaStream_t s);
 cudaError_t launch_read_box(const uint32_t* grid, const long long lo[3], const uint32_t box[3],
                             const WindowGeom& g, int16_t* v, int16_t* w, cudaStream_t s);
 cudaError_t launch_write_box(uint32_t* grid, const long long lo[3], const uint32_t box[3], const WindowGeom& g,

@@ -680,3 +680,74 @@ def test_oracle_rejects_unknown_flag_bits():
     p = synth.params_dict((16, 16, 16), 0.1, 0.2, 8, 0.0, 0.05, 3.0, 0, (0, 0, 0), flags=4)
     with pytest.raises(ValueError):
         oracle.OracleMap(p)
+
+
+# ---------------------------------------------------------------- zero-crossing surface (map consumer)
+
+def _surface_map(v, w, vs=0.25):
+    Z, Y, X = v.shape
+    p = synth.params_dict((X, Y, Z), vs, 4 * vs, 64, 0.0, 0.1, 10.0, 0, (0, 0, 0))
+    m = oracle.OracleMap(p)
+    m.load_window(v.astype(np.int16), w.astype(np.int16))
+    return m
+
+
+def _sign_changes(v, w, min_w):
+    """Numpy brute force: crossings per axis (x, y, z) of a (z, y, x) field."""
+    ok = w >= min_w
+    neg = v < 0
+    out = []
+    for ax, sl_a, sl_b in ((0, np.s_[:, :, :-1], np.s_[:, :, 1:]), (1, np.s_[:, :-1, :], np.s_[:, 1:, :]),
+                           (2, np.s_[:-1, :, :], np.s_[1:, :, :])):
+        out.append(int(np.sum(ok[sl_a] & ok[sl_b] & (neg[sl_a] != neg[sl_b]))))
+    return out
+
+
+def test_surface_axis_plane_closed_form():
+    """A field linear in x with its zero at x = 7.3 voxels gives one point per
+    (y, z) row at exactly ((6 + 0.5) + 0.8) * 0.25 = 1.825 m."""
+    xs = np.arange(16)
+    v = np.broadcast_to(np.rint(1000 * (xs + 0.5 - 7.3)), (16, 16, 16)).astype(np.int16)
+    m = _surface_map(v, np.ones_like(v))
+    pts = m.surface()
+    assert pts.shape == (256, 4)
+    assert np.all(pts[:, 3] == 0)
+    assert np.all(np.abs(pts[:, 0] - 1.825) < 1e-6)
+    assert sorted(set(np.round(pts[:, 1] / 0.25 - 0.5).astype(int))) == list(range(16))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_surface_tilted_plane_and_counts(seed):
+    """A linear field of a tilted plane: every point lies on the plane within
+    the rounding of the codes, and the number of points per axis equals a
+    numpy count of sign changes between observed neighbours."""
+    rng = np.random.default_rng(40 + seed)
+    n = rng.normal(size=3)
+    n /= np.linalg.norm(n)
+    c0 = rng.uniform(6, 10, 3)
+    s = 1000.0
+    zz, yy, xx = np.meshgrid(np.arange(16), np.arange(16), np.arange(16), indexing="ij")
+    cen = np.stack([xx + 0.5, yy + 0.5, zz + 0.5], axis=-1)
+    v = np.rint(s * ((cen - c0) @ n)).clip(-32767, 32767).astype(np.int16)
+    w = (rng.uniform(size=v.shape) < 0.8).astype(np.int16) * rng.integers(1, 5, size=v.shape).astype(np.int16)
+    for min_w in (1, 3):
+        m = _surface_map(v, w, vs=0.25)
+        pts = m.surface(min_w)
+        per_axis = [int(np.sum(pts[:, 3] == a)) for a in range(3)]
+        assert per_axis == _sign_changes(v, w, min_w)
+        d = (pts[:, :3].astype(np.float64) / 0.25 - c0) @ n
+        ax = pts[:, 3].astype(int)
+        tol = 0.5 / (s * np.abs(n[ax])) + 1e-4
+        assert np.all(np.abs(d) <= tol)
+
+
+def test_surface_of_room_scan_near_walls():
+    """Points extracted from the box-room scan lie near the room's surfaces
+    (FP64 analytic distance, one voxel + 3 sigma)."""
+    w = synth.workload_room(seed=3)
+    m = oracle.OracleMap(w.params)
+    m.integrate(w.scans[0], w.poses[0])
+    pts = m.surface(1)
+    assert len(pts) > 10000
+    dist = np.abs(w.scene.sdf(pts[:, :3].astype(np.float64)))
+    assert np.mean(dist <= w.params["voxel_size"] + 0.03) > 0.95
