@@ -220,11 +220,11 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem
     if (!grid_barrier(sync, arrivals, spin)) return;
 
     if (SORT) {
-        // ---- phase 3b: pair counts per brick, one warp task = 32 pair slots of a map
-        block_prefix(count, [&](int i) { return (written_slots(items[i].m) + 31u) / 32u; }, s_prefix);
+        // ---- phase 3b: pair counts per brick, one warp task = 128 pair slots of a map
+        block_prefix(count, [&](int i) { return (written_slots(items[i].m) + 127u) / 128u; }, s_prefix);
         for (uint32_t g = gwarp; g < s_prefix[count]; g += nwarps) {
             const int i = find_segment(s_prefix, count, g);
-            sort_count_warp(items[i].m, (g - s_prefix[i]) * 32u, written_slots(items[i].m));
+            sort_count_warp(items[i].m, (g - s_prefix[i]) * 128u, written_slots(items[i].m));
         }
         if (!grid_barrier(sync, arrivals, spin)) return;
         // ---- phase 3c: segment starts, one CTA per map
@@ -232,10 +232,10 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem
             sort_scan_cta(items[i].m, __ldcg(&items[i].m.ctr->brick_count), s_prefix);
         if (!grid_barrier(sync, arrivals, spin)) return;
         // ---- phase 3d: scatter into the segments (same tasks as the count)
-        block_prefix(count, [&](int i) { return (written_slots(items[i].m) + 31u) / 32u; }, s_prefix);
+        block_prefix(count, [&](int i) { return (written_slots(items[i].m) + 127u) / 128u; }, s_prefix);
         for (uint32_t g = gwarp; g < s_prefix[count]; g += nwarps) {
             const int i = find_segment(s_prefix, count, g);
-            sort_scatter_warp(items[i].m, (g - s_prefix[i]) * 32u, written_slots(items[i].m));
+            sort_scatter_warp(items[i].m, (g - s_prefix[i]) * 128u, written_slots(items[i].m));
         }
         if (!grid_barrier(sync, arrivals, spin)) return;
     }

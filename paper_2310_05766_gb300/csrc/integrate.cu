@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(256) sort_count_kernel(const MapDev m) {
     const uint32_t n = sort_nslots(m);
     const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t w = w0; w * 32u < n; w += nw) sort_count_warp(m, w * 32u, n);
+    for (uint32_t w = w0; w * 128u < n; w += nw) sort_count_warp(m, w * 128u, n);
 }
 
 __global__ void __launch_bounds__(1024) sort_scan_kernel(const MapDev m) {
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256) sort_scatter_kernel(const MapDev m) {
     const uint32_t n = sort_nslots(m);
     const uint32_t w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t w = w0; w * 32u < n; w += nw) sort_scatter_warp(m, w * 32u, n);
+    for (uint32_t w = w0; w * 128u < n; w += nw) sort_scatter_warp(m, w * 128u, n);
 }
 
 __global__ void __launch_bounds__(256) compact_kernel(const MapDev m, const uint32_t nwords) {

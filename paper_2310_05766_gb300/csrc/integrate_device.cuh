@@ -539,19 +539,27 @@ __device__ __forceinline__ uint32_t sort_nslots(const MapDev& m) {
     return (uint32_t)(n < m.pair_cap ? n : (unsigned long long)m.pair_cap);
 }
 
-// One warp: pairs [s, s + 32) add to their bricks' counts. Lanes holding the
-// same brick (usually neighbouring samples of one ray) are merged first.
+// One warp: pairs [s, s + 128) add to their bricks' counts; each lane loads
+// four pairs and their brick slots before any warp operation, so the loads
+// overlap. Lanes holding the same brick (usually neighbouring samples of one
+// ray) are merged first.
 __device__ __forceinline__ void sort_count_warp(const MapDev& m, uint32_t s, uint32_t nslots) {
     const unsigned lane = threadIdx.x & 31u;
-    const uint32_t slot = s + lane;
-    uint32_t seg = kNoVoxel;
-    if (slot < nslots) {
-        const uint32_t word = m.pairs[slot].x;
-        if (word != kNoVoxel) seg = m.brick_slot[word >> 9];
+    uint32_t word[4], seg[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const uint32_t slot = s + 32u * u + lane;
+        word[u] = slot < nslots ? m.pairs[slot].x : kNoVoxel;
     }
-    if (__ballot_sync(kFull, seg != kNoVoxel) == 0u) return;   // warp-uniform
-    const unsigned peers = __match_any_sync(kFull, seg);
-    if (seg != kNoVoxel && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(m.seg_count + seg, (uint32_t)__popc(peers));
+#pragma unroll
+    for (int u = 0; u < 4; ++u) seg[u] = word[u] != kNoVoxel ? m.brick_slot[word[u] >> 9] : kNoVoxel;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        if (__ballot_sync(kFull, seg[u] != kNoVoxel) == 0u) continue;   // warp-uniform
+        const unsigned peers = __match_any_sync(kFull, seg[u]);
+        if (seg[u] != kNoVoxel && lane == (unsigned)(__ffs(peers) - 1))
+            atomicAdd(m.seg_count + seg[u], (uint32_t)__popc(peers));
+    }
 }
 
 // The CTA turns the per-brick counts of the map's nb listed bricks into
@@ -591,25 +599,35 @@ __device__ __forceinline__ void sort_scan_cta(const MapDev& m, uint32_t nb, uint
     }
 }
 
-// One warp: pairs [s, s + 32) go to their bricks' segments as
-// (offset in brick << 16) | (code & 0xFFFF); one returning atomic per
-// distinct brick in the warp.
+// One warp: pairs [s, s + 128) go to their bricks' segments as
+// (offset in brick << 16) | (code & 0xFFFF); loads first (four per lane),
+// then one returning atomic per distinct brick of each 32-pair group, the
+// four groups' atomics in flight together.
 __device__ __forceinline__ void sort_scatter_warp(const MapDev& m, uint32_t s, uint32_t nslots) {
     const unsigned lane = threadIdx.x & 31u;
-    const uint32_t slot = s + lane;
-    uint32_t seg = kNoVoxel;
-    uint2 p = make_uint2(kNoVoxel, 0u);
-    if (slot < nslots) {
-        p = m.pairs[slot];
-        if (p.x != kNoVoxel) seg = m.brick_slot[p.x >> 9];
+    uint2 p[4];
+    uint32_t seg[4], pos[4];
+    unsigned peers[4], leader[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const uint32_t slot = s + 32u * u + lane;
+        p[u] = slot < nslots ? m.pairs[slot] : make_uint2(kNoVoxel, 0u);
     }
-    if (__ballot_sync(kFull, seg != kNoVoxel) == 0u) return;   // warp-uniform
-    const unsigned peers = __match_any_sync(kFull, seg);
-    const unsigned leader = (unsigned)(__ffs(peers) - 1);
-    uint32_t pos = 0;
-    if (seg != kNoVoxel && lane == leader) pos = atomicAdd(m.seg_count + seg, (uint32_t)__popc(peers));
-    pos = __shfl_sync(kFull, pos, leader);
-    if (seg != kNoVoxel) m.sorted[pos + __popc(peers & ((1u << lane) - 1u))] = ((p.x & 511u) << 16) | (p.y & 0xFFFFu);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) seg[u] = p[u].x != kNoVoxel ? m.brick_slot[p[u].x >> 9] : kNoVoxel;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        peers[u] = __match_any_sync(kFull, seg[u]);
+        leader[u] = (unsigned)(__ffs(peers[u]) - 1);
+        pos[u] = 0u;
+        if (seg[u] != kNoVoxel && lane == leader[u]) pos[u] = atomicAdd(m.seg_count + seg[u], (uint32_t)__popc(peers[u]));
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const uint32_t b = __shfl_sync(kFull, pos[u], leader[u]);
+        if (seg[u] != kNoVoxel)
+            m.sorted[b + __popc(peers[u] & ((1u << lane) - 1u))] = ((p[u].x & 511u) << 16) | (p[u].y & 0xFFFFu);
+    }
 }
 
 // One warp: listed brick i. Its segment of `sorted` is reduced per voxel in
@@ -640,12 +658,22 @@ __device__ __forceinline__ void sort_apply_brick(const MapDev& m, int32_t w_max,
         sa2[32 * v + lane] = a2;
     }
     __syncwarp();
-    for (uint32_t e = start + lane; e < end; e += 32u) {
-        const uint32_t val = m.sorted[e];
-        const unsigned off = val >> 16;
-        const int q = (int)(int16_t)(val & 0xFFFFu);
-        if (MODE == 0) atomicAdd(s_acc + off, (1ull << 40) + (unsigned long long)(long long)q);
-        else atomicMax(s_acc + off, 65536ull - (((unsigned)abs(q) << 1) | (q < 0 ? 1u : 0u)));
+    // four entries per lane in flight per round
+    for (uint32_t e0 = start; e0 < end; e0 += 128u) {
+        uint32_t val[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t e = e0 + 32u * u + lane;
+            val[u] = e < end ? m.sorted[e] : kNoVoxel;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (val[u] == kNoVoxel) continue;
+            const unsigned off = val[u] >> 16;
+            const int q = (int)(int16_t)(val[u] & 0xFFFFu);
+            if (MODE == 0) atomicAdd(s_acc + off, (1ull << 40) + (unsigned long long)(long long)q);
+            else atomicMax(s_acc + off, 65536ull - (((unsigned)abs(q) << 1) | (q < 0 ? 1u : 0u)));
+        }
     }
     if (MODE == 1 && lane == 0) hits += end - start;
     if (lane == 0) m.seg_count[i] = 0u;
