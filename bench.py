@@ -188,7 +188,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     h = m.handle
     sort = args.reduction == "sort"
     for opt, val in ((b.TSDF_OPT_WARP_MERGE, args.merge), (b.TSDF_OPT_STEPS_PER_THREAD, args.kpt),
-                     (b.TSDF_OPT_PDL, args.pdl), (b.TSDF_OPT_REDUCTION, 1 if sort else None)):
+                     (b.TSDF_OPT_PDL, args.pdl), (b.TSDF_OPT_REDUCTION, 1 if sort else None),
+                     (b.TSDF_OPT_HOST_ZERO_COPY, args.zero_copy)):
         if val is not None:
             b.tsdf_set_option(h, opt, val)
     cur = tuple(p["origin"])
@@ -352,7 +353,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                       alg_bytes_per_launch=alg_bytes, avg_launch_us=k_avg_s * 1e6, l2_reductions=l2red),
         e2e=dict(value=e2e_hits_all / t_e2e_max, unit=UNIT, h2d_bytes_per_step=int(16 * n_pts),
                  d2h_bytes_per_step=24, steps=n_e2e,
-                 note="tsdf_integrate_host from pinned memory + tsdf_stats read-back, host wall clock"),
+                 zero_copy=args.zero_copy != 0,
+                 note="tsdf_integrate_host from pinned memory (read in place by the first kernel over the host "
+                      "link unless --zero-copy 0) + tsdf_stats read-back, host wall clock"),
         # library launches: one per profiled entry, plus the compaction that shares
         # the apply entry (atomic) or compact + count + prefix + scatter sharing
         # the sort entry (sort)
@@ -575,6 +578,8 @@ def main():
     ap.add_argument("--merge", type=int, default=None, help="tuning: warp match-merge (0/1)")
     ap.add_argument("--kpt", type=int, default=None, help="tuning: march steps per contribution thread (1/2/4)")
     ap.add_argument("--pdl", type=int, default=None, help="tuning: programmatic dependent launch (0/1)")
+    ap.add_argument("--zero-copy", type=int, default=None,
+                    help="e2e: pinned host points read in place (1, library default) or staged (0)")
     ap.add_argument("--reduction", default="atomic", choices=["atomic", "sort"],
                     help="per-scan reduction: accumulator atomics or counting sort by brick")
     ap.add_argument("--workload", default="outdoor", choices=["outdoor", "batch", "serving"],

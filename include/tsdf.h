@@ -121,10 +121,13 @@ int tsdf_map_destroy(tsdf_map* map);
 int tsdf_integrate(tsdf_map* map, const float* points_dev, int64_t n, const float pose[12], void* stream);
 
 /* As tsdf_integrate, but points_host is a HOST pointer (pinned or pageable)
- * to n float4 values. The points are copied into a map-owned device buffer on
- * `stream` and integrated. Returns once the copy has been enqueued (for
- * pageable memory the CUDA runtime may wait for the copy). Errors: INVALID,
- * OOM, CUDA. */
+ * to n float4 values. Pinned memory that is mapped into the device (16-byte
+ * aligned) is read in place by the first kernel over the host link
+ * (TSDF_OPT_HOST_ZERO_COPY); otherwise the points are copied into a map-owned
+ * device buffer on `stream` first. Either way the buffer must stay valid and
+ * unchanged until the stream has passed the call. Returns once the work has
+ * been enqueued (for pageable memory the CUDA runtime may wait for the copy).
+ * Errors: INVALID, OOM, CUDA. */
 int tsdf_integrate_host(tsdf_map* map, const float* points_host, int64_t n, const float pose[12], void* stream);
 
 /* Move the window to new_origin (global voxel coordinates, multiples of 8,
@@ -169,6 +172,10 @@ int tsdf_stats(tsdf_map* map, tsdf_scan_stats* out, void* stream);
                                    memory); 0 (default): 32 per point of the largest scan so far, at least
                                    2^20; otherwise 1024 .. 2^28. Samples beyond the capacity are reduced
                                    with accumulator atomics instead (same result, slower). */
+
+#define TSDF_OPT_HOST_ZERO_COPY 6  /* 1 (default): tsdf_integrate_host reads points that lie in pinned host memory
+                                     mapped into the device (cudaHostAlloc / cudaHostRegister) in place over
+                                     the host link instead of copying them first; 0: always stage a copy */
 
 #define TSDF_REDUCTION_ATOMIC 0  /* each contribution is one 64-bit reduction into a per-voxel accumulator */
 #define TSDF_REDUCTION_SORT   1  /* contributions are written as (voxel, code) pairs, counting-sorted by brick

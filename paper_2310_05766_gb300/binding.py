@@ -32,6 +32,7 @@ TSDF_OPT_STEPS_PER_THREAD = 2
 TSDF_OPT_PDL = 3
 TSDF_OPT_REDUCTION = 4
 TSDF_OPT_SORT_CAPACITY = 5
+TSDF_OPT_HOST_ZERO_COPY = 6
 TSDF_REDUCTION_ATOMIC = 0
 TSDF_REDUCTION_SORT = 1
 TSDF_BATCH_OPT_GRAPH = 1

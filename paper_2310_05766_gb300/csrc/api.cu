@@ -111,6 +111,8 @@ struct tsdf_map {
     int kpt = 4;                    // march steps per contribution item (1, 2 or 4)
     bool pdl = true;                // programmatic dependent launch between the scan's kernels
     int reduction = TSDF_REDUCTION_ATOMIC;   // per-scan reduction: accumulator atomics or sort
+    bool zero_copy = true;          // tsdf_integrate_host reads device-mapped pinned points in place
+    long long* host_last = nullptr; // mapped pinned copy of the published counters (host address)
     size_t pair_cap_req = 0;        // sort reduction: requested pair capacity, 0 = from the scan size
     size_t ray_slot_cap = 0;        // entries of dev.ray_slot
     // optional per-kernel event timing
@@ -207,6 +209,7 @@ void free_map(tsdf_map* m) {
     cudaFree(m->dev.ray_a);
     cudaFree(m->dev.ray_b);
     cudaFree(m->dev.ctr);
+    if (m->host_last) cudaFreeHost(m->host_last);
     cudaFree(m->dev.brick_slot);
     cudaFree(m->dev.seg_count);
     cudaFree(m->dev.seg_start);
@@ -291,6 +294,21 @@ int tsdf_map_create(const tsdf_params* params, tsdf_map** out) {
     if (e == cudaSuccess) e = cudaMemset(m->dev.acc, 0, m->voxels * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(m->dev.brick_flag, 0, flag_bytes);
     if (e == cudaSuccess) e = cudaMemset(m->dev.ctr, 0, sizeof(MapCounters));
+    // published counters mirrored into mapped pinned memory (falls back to a
+    // device-to-host copy in tsdf_stats when the mapping is unavailable)
+    if (e == cudaSuccess && cudaHostAlloc(&m->host_last, 3 * sizeof(long long), cudaHostAllocMapped) == cudaSuccess) {
+        std::memset(m->host_last, 0, 3 * sizeof(long long));
+        void* dp = nullptr;
+        if (cudaHostGetDevicePointer(&dp, m->host_last, 0) == cudaSuccess) {
+            m->dev.host_last = static_cast<long long*>(dp);
+        } else {
+            cudaFreeHost(m->host_last);
+            m->host_last = nullptr;
+        }
+    } else {
+        m->host_last = nullptr;
+        cudaGetLastError();   // clear a failed mapping request
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->items_event, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -461,6 +479,15 @@ int tsdf_integrate_host(tsdf_map* map, const float* points_host, int64_t n, cons
     if (rc != TSDF_OK) return rc;
     DeviceScope ds(map->device);
     cudaStream_t s = (cudaStream_t)stream;
+    if (map->zero_copy && n > 0 && ((uintptr_t)points_host & 15u) == 0) {
+        // pinned host memory mapped into the device's address space: the rays
+        // kernel reads the points in place (over the host link), no staging copy
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, points_host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+            at.devicePointer != nullptr && ((uintptr_t)at.devicePointer & 15u) == 0)
+            return integrate_dev(map, static_cast<const float*>(at.devicePointer), n, pose, s);
+        cudaGetLastError();
+    }
     if ((size_t)n > map->stage_cap) {
         // a previous call may still read the old buffer: cudaFree waits for the device
         cudaFree(map->stage_dev);
@@ -600,8 +627,14 @@ int tsdf_stats(tsdf_map* map, tsdf_scan_stats* out, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     long long last[3] = {0, 0, 0};   // last_valid, last_hits, last_touched are contiguous
     static_assert(offsetof(MapCounters, last_touched) == offsetof(MapCounters, last_valid) + 16, "layout");
-    TSDF_CU(cudaMemcpyAsync(last, &map->dev.ctr->last_valid, sizeof(last), cudaMemcpyDeviceToHost, s));
-    TSDF_CU(cudaStreamSynchronize(s));
+    if (map->host_last) {
+        // the last apply CTA of each scan also wrote them to mapped host memory
+        TSDF_CU(cudaStreamSynchronize(s));
+        std::memcpy(last, (const void*)map->host_last, sizeof(last));
+    } else {
+        TSDF_CU(cudaMemcpyAsync(last, &map->dev.ctr->last_valid, sizeof(last), cudaMemcpyDeviceToHost, s));
+        TSDF_CU(cudaStreamSynchronize(s));
+    }
     out->valid_rays = last[0];
     out->hits = last[1];
     out->touched = last[2];
@@ -658,6 +691,10 @@ int tsdf_set_option(tsdf_map* map, int32_t option, int64_t value) {
         case TSDF_OPT_REDUCTION:
             if (value != TSDF_REDUCTION_ATOMIC && value != TSDF_REDUCTION_SORT) return TSDF_ERR_INVALID;
             map->reduction = (int)value;
+            return TSDF_OK;
+        case TSDF_OPT_HOST_ZERO_COPY:
+            if (value != 0 && value != 1) return TSDF_ERR_INVALID;
+            map->zero_copy = value != 0;
             return TSDF_OK;
         case TSDF_OPT_SORT_CAPACITY:
             if (value != 0 && (value < 1024 || value > (int64_t)kPairCapMax)) return TSDF_ERR_INVALID;

@@ -719,6 +719,11 @@ __device__ __forceinline__ void finish_warp(const MapDev& m) {
         c->last_valid = (long long)v;
         c->last_hits = (long long)h;
         c->last_touched = (long long)u;
+        if (m.host_last) {   // also into host memory: reading them needs no copy
+            m.host_last[0] = (long long)v;
+            m.host_last[1] = (long long)h;
+            m.host_last[2] = (long long)u;
+        }
         c->live_count = 0u;
         c->brick_count = 0u;
         c->slot_count = 0ull;

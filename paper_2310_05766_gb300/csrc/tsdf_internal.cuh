@@ -54,6 +54,7 @@ struct MapDev {
     float4* ray_a;                  // per live ray (compacted): (dir.x, dir.y, dir.z, r)
     float4* ray_b;                  // per live ray (compacted): (int.x, int.y, int.z, fill ? 1 : 0)
     MapCounters* ctr;
+    long long* host_last;           // mapped pinned host copy of last_valid / last_hits / last_touched, or null
     // sort reduction (null / 0 when the map has no sort buffers)
     uint32_t* brick_slot;           // per brick: its position in the brick list (touched bricks only)
     uint32_t* seg_count;            // per list position: pair count, then the scatter cursor; zero between scans

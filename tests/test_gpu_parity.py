@@ -84,6 +84,39 @@ def test_room_host_points_path():
     both(w.params, workload_steps(w), host=True, label="host points")
 
 
+@pytest.mark.parametrize("zero_copy", [1, 0])
+def test_host_pinned_points_path(zero_copy):
+    """Pinned host points: read in place by the rays kernel (zero copy) or
+    staged; both exact, counters read back through the mapped copy. A pinned
+    buffer that is not 16-byte aligned takes the staging copy."""
+    from paper_2310_05766_gb300 import binding as b
+    w = synth.workload_outdoor(n_scans=3)
+    steps = workload_steps(w)
+    m = b.TsdfMap(w.params)
+    stats = []
+    try:
+        b.tsdf_set_option(m.handle, b.TSDF_OPT_HOST_ZERO_COPY, zero_copy)
+        for k, st in enumerate(steps):
+            if st[0] == "shift":
+                m.shift(st[1])
+                continue
+            n = st[1].shape[0]
+            if k % 2 == 0:
+                pinned = torch.from_numpy(np.ascontiguousarray(st[1], np.float32)).pin_memory()
+                m.integrate_host(pinned, st[2])
+            else:   # 4 bytes past a 16-byte boundary
+                buf = torch.empty(4 * n + 1, dtype=torch.float32).pin_memory()
+                buf[1:] = torch.from_numpy(np.ascontiguousarray(st[1], np.float32).reshape(-1))
+                b.tsdf_integrate_host(m.handle, buf.data_ptr() + 4, n, st[2])
+            stats.append(m.stats())   # synchronises: the buffers may go now
+        v, wt = m.read()
+    finally:
+        m.close()
+    vo, wo, so, _ = run_oracle(w.params, steps)
+    assert np.array_equal(v, vo) and np.array_equal(wt, wo)
+    assert stats == so
+
+
 def test_point_order_does_not_matter():
     w = synth.workload_room()
     perm = np.random.default_rng(2).permutation(w.scans[0].shape[0])
