@@ -35,6 +35,12 @@
 #include "integrate_device.cuh"
 #include "../../include/tsdf.h"
 
+// 1: the atomic configurations apply each brick from registers
+// (apply_brick_reg); 0: through shared memory (apply_brick).
+#ifndef TSDF_BATCH_APPLY_REG
+#define TSDF_BATCH_APPLY_REG 1
+#endif
+
 namespace tsdf {
 namespace {
 
@@ -266,8 +272,13 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem
                     sort_apply_brick<0>(it.m, it.w_max, it.flags, local, ovf, s_grid, s_acc, s_off, touched, hits);
                 else sort_apply_brick<1>(it.m, it.w_max, it.flags, local, ovf, s_grid, s_acc, s_off, touched, hits);
             } else {
+#if TSDF_BATCH_APPLY_REG
+                if (it.reduce == 0) apply_brick_reg<0>(it.m, it.w_max, it.flags, local, touched, hits);
+                else apply_brick_reg<1>(it.m, it.w_max, it.flags, local, touched, hits);
+#else
                 if (it.reduce == 0) apply_brick<0>(it.m, it.w_max, it.flags, local, s_grid, s_acc, s_off, touched, hits);
                 else apply_brick<1>(it.m, it.w_max, it.flags, local, s_grid, s_acc, s_off, touched, hits);
+#endif
             }
         }
         if (cur >= 0) {
