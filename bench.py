@@ -170,6 +170,18 @@ def aggregate_ranks(units, times, device=None):
 
 # ---------------------------------------------------------------- main GPU arm
 
+def sequence_workload(name: str):
+    """The scan sequence of a per-map workload and its description."""
+    from paper_2310_05766_gb300 import synth
+    if name == "corridor":
+        w = synth.workload_corridor(n_scans=50)
+        return w, ("high-resolution corridor: 128x2048 beams, 50 scans at 10 Hz, 0.5 m/s, window 1024x1024x256 "
+                   "at 0.02 m (1 GiB grid), tau 0.1 m, shift every 0.5 m (ping-pong over the sequence)")
+    w = synth.workload_outdoor(n_scans=N_SEQ)
+    return w, ("outdoor OS1-128 sequence: 128x1024 beams, 100 scans at 10 Hz, 1 m/s, window 512x512x128 at "
+               "0.064 m, tau 0.6 m, shift every 1 m (ping-pong over the sequence)")
+
+
 def run_gpu(args, rank: int, world: int, local_rank: int):
     import torch
     from paper_2310_05766_gb300 import binding as b, synth
@@ -177,7 +189,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     b.lib()
-    w = synth.workload_outdoor(n_scans=N_SEQ)
+    w, wdesc = sequence_workload(args.workload)
+    n_seq = len(w.scans)
     p = w.params
     scans_dev = [torch.from_numpy(s).to(dev) for s in w.scans]
     scans_pin = [torch.from_numpy(s).pin_memory() for s in w.scans]
@@ -206,14 +219,14 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
             b.tsdf_integrate(h, scans_dev[i], scans_dev[i].shape[0], w.poses[i], stream)
 
     # per-scan counters (they depend only on the scan, its pose and the window origin)
-    hits = np.zeros(N_SEQ, np.int64)
-    touched = np.zeros(N_SEQ, np.int64)
-    for i in range(N_SEQ):
+    hits = np.zeros(n_seq, np.int64)
+    touched = np.zeros(n_seq, np.int64)
+    for i in range(n_seq):
         step(i)
         st = b.tsdf_stats(h, stream)
         hits[i], touched[i] = st["hits"], st["touched"]
 
-    schedule = ping_pong(args.warmup + args.steps)
+    schedule = ping_pong(args.warmup + args.steps, n_seq)
     for i in schedule[:args.warmup]:
         step(i)
     torch.cuda.synchronize()
@@ -323,7 +336,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     if world == 1 and not args.no_cpu_baseline:
         rate, n_used, h_used, t_used = oracle_sample(w, args.cpu_budget)
         cpu = dict(value=rate, unit=UNIT, cores=1, kind="oracle",
-                   sample=f"first {n_used} scans of the 100-scan sequence, all 131072 points each, "
+                   sample=f"first {n_used} scans of the {n_seq}-scan sequence, all {n_pts} points each, "
                           f"{h_used} voxel updates in {t_used:.1f} s, single-threaded C++ oracle; "
                           f"window re-centring by pre-placed oracle windows (shift not timed)")
 
@@ -331,8 +344,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=K, warmup=args.warmup,
         ms_per_step=dev_ms_max / K, higher_is_better=True, scaling="weak", vs_baseline=None,
         dtype="f32 geometry, int64 accumulation, int16 map", data="synthetic",
-        config=dict(workload="outdoor OS1-128 sequence: 128x1024 beams, 100 scans at 10 Hz, 1 m/s, "
-                             "window 512x512x128 at 0.064 m, tau 0.6 m, shift every 1 m (ping-pong over the sequence)",
+        config=dict(workload=wdesc,
                     points_per_scan=int(n_pts), voxel_size=p["voxel_size"], tau=p["tau"], dims=list(p["dims"]),
                     reduce="WSUM", reduction=args.reduction, l2="flushed (512 MiB write) before every timed step; flush excluded by per-step events",
                     parallelism=f"replicas x{world}"),
@@ -582,7 +594,7 @@ def main():
                     help="e2e: pinned host points read in place (1, library default) or staged (0)")
     ap.add_argument("--reduction", default="atomic", choices=["atomic", "sort"],
                     help="per-scan reduction: accumulator atomics or counting sort by brick")
-    ap.add_argument("--workload", default="outdoor", choices=["outdoor", "batch", "serving"],
+    ap.add_argument("--workload", default="outdoor", choices=["outdoor", "corridor", "batch", "serving"],
                     help="outdoor: the headline sequence; batch / serving: the 64-map batch and 32-session serving runs")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle time for cpu_baseline")
