@@ -25,7 +25,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-CXXFLAGS = ["-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+CXXFLAGS = ["-O2", "-std=c++17", "-fPIC", "-shared", "-pthread", "-ffp-contract=off", "-fno-fast-math",
             "-fno-finite-math-only", "-fsigned-char"]
 
 
@@ -78,6 +78,8 @@ def lib():
             fn = getattr(L, name)
             fn.restype = ctypes.c_int
             fn.argtypes = [vp, f32p, i64, f32p]
+        L.orc_integrate_parallel.restype = ctypes.c_int
+        L.orc_integrate_parallel.argtypes = [vp, f32p, i64, f32p, ctypes.c_int32]
         L.orc_hits.restype = i64
         L.orc_hits.argtypes = [P(OrcParams), f32p, i64, f32p, P(i64), P(ctypes.c_int32), P(i64),
                                P(ctypes.c_int32), i64]
@@ -189,9 +191,16 @@ class OracleMap:
         except Exception:
             pass
 
-    def integrate(self, points: np.ndarray, pose: np.ndarray, bruteforce: bool = False):
+    def integrate(self, points: np.ndarray, pose: np.ndarray, bruteforce: bool = False, threads: int = 0):
+        """One scan. threads > 0: the rays split over that many host threads
+        (identical result); bruteforce: the voxel-major enumeration."""
         pts_a, pts_p = _f32(points.reshape(-1, 4))
         pose_a, pose_p = _f32(pose)
+        if threads > 0:
+            rc = lib().orc_integrate_parallel(self.h, pts_p, pts_a.shape[0], pose_p, threads)
+            if rc != 0:
+                raise ValueError("oracle integrate failed")
+            return
         fn = lib().orc_integrate_bruteforce if bruteforce else lib().orc_integrate
         rc = fn(self.h, pts_p, pts_a.shape[0], pose_p)
         if rc != 0:

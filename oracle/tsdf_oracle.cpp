@@ -31,6 +31,7 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <thread>
 #include <array>
 #include <unordered_map>
 #include <vector>
@@ -245,9 +246,10 @@ bool params_ok(const orc_params& p) {
     return true;
 }
 
-// Apply a per-scan volume to the window: Eq. 1 / Eq. 2 for every touched voxel.
-void apply_volume(OracleMap* m, const std::unordered_map<int64_t, Acc>& vol,
-                  const std::unordered_map<int64_t, int32_t>& best) {
+// Apply a per-scan volume to the window: Eq. 1 / Eq. 2 for every touched
+// voxel. Returns the number of voxels updated.
+int64_t apply_volume(OracleMap* m, const std::unordered_map<int64_t, Acc>& vol,
+                     const std::unordered_map<int64_t, int32_t>& best) {
     if (m->p.reduce == 0) {
         for (const auto& kv : vol) {
             Cell& c = m->win[kv.first];
@@ -257,7 +259,7 @@ void apply_volume(OracleMap* m, const std::unordered_map<int64_t, Acc>& vol,
             c.v = (int16_t)nv;
             c.w = (int16_t)nw;
         }
-        m->st_touched = (int64_t)vol.size();
+        return (int64_t)vol.size();
     } else {
         for (const auto& kv : best) {
             Cell& c = m->win[kv.first];
@@ -266,7 +268,7 @@ void apply_volume(OracleMap* m, const std::unordered_map<int64_t, Acc>& vol,
             c.v = (int16_t)nv;
             c.w = (int16_t)nw;
         }
-        m->st_touched = (int64_t)best.size();
+        return (int64_t)best.size();
     }
 }
 
@@ -326,9 +328,62 @@ int orc_integrate(void* h, const float* pts, int64_t n, const float pose[12]) {
             }
         });
     }
-    apply_volume(m, vol, best);
+    m->st_touched = apply_volume(m, vol, best);
     m->st_valid = valid;
     m->st_hits = hits;
+    return 0;
+}
+
+// The same scan on `threads` host threads, partitioned by voxel: every
+// thread enumerates all rays (the cheap part) but keeps only the
+// contributions to the voxels it owns (a hash of the window index), then
+// applies Eq. 1 / Eq. 2 to those voxels. Owners are disjoint, so nothing is
+// merged and the result is identical to orc_integrate. Used to time the
+// oracle on all host cores (the paper's CPU baseline is multithreaded).
+int orc_integrate_parallel(void* h, const float* pts, int64_t n, const float pose[12], int32_t threads) {
+    OracleMap* m = (OracleMap*)h;
+    if (!m || n < 0 || (n > 0 && !pts) || !pose || threads < 1) return -1;
+    std::vector<int64_t> valid((size_t)threads, 0), hits((size_t)threads, 0), touched((size_t)threads, 0);
+    auto owner = [threads](int64_t key) {
+        return (int)(((uint64_t)key * 0x9E3779B97F4A7C15ull) >> 40) % threads;
+    };
+    auto work = [&](int t) {
+        std::unordered_map<int64_t, Acc> vol;
+        std::unordered_map<int64_t, int32_t> best;
+        for (int64_t i = 0; i < n; ++i) {
+            Ray ry = ray_setup(pose, pts + 4 * i, m->p.r_min, m->p.r_max, m->p.delta_z);
+            if (!ry.valid) continue;
+            if (t == 0) ++valid[0];
+            for_each_hit(ry, m->p, m->dv, [&](const int64_t g[3], int32_t q, int) {
+                if (!m->inside(g)) return;
+                const int64_t key = m->lin(g);
+                if (owner(key) != t) return;
+                ++hits[(size_t)t];
+                if (m->p.reduce == 0) {
+                    Acc& a = vol[key];
+                    a.S += q;
+                    a.W += 1;
+                } else {
+                    auto it = best.find(key);
+                    if (it == best.end()) best.emplace(key, q);
+                    else if (min_abs_better(q, it->second)) it->second = q;
+                }
+            });
+        }
+        touched[(size_t)t] = apply_volume(m, vol, best);   // disjoint cells per thread
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < threads; ++t) pool.emplace_back(work, t);
+    work(0);
+    for (auto& th : pool) th.join();
+    int64_t h_all = 0, u_all = 0;
+    for (int t = 0; t < threads; ++t) {
+        h_all += hits[(size_t)t];
+        u_all += touched[(size_t)t];
+    }
+    m->st_valid = valid[0];
+    m->st_hits = h_all;
+    m->st_touched = u_all;
     return 0;
 }
 

@@ -751,3 +751,25 @@ def test_surface_of_room_scan_near_walls():
     assert len(pts) > 10000
     dist = np.abs(w.scene.sdf(pts[:, :3].astype(np.float64)))
     assert np.mean(dist <= w.params["voxel_size"] + 0.03) > 0.95
+
+
+# ---------------------------------------------------------------- parallel oracle (host-core timing)
+
+@pytest.mark.parametrize("reduce", [0, 1])
+def test_parallel_oracle_identical(reduce):
+    """The ray-split, multithreaded oracle merges integer per-scan volumes, so
+    it equals the serial oracle bit for bit (with a pre-filled window)."""
+    w = synth.workload_room(reduce=reduce, seed=6)
+    rng = np.random.default_rng(7)
+    d = w.params["dims"]
+    v0 = rng.integers(-32767, 32768, size=(d[2], d[1], d[0])).astype(np.int16)
+    w0 = rng.integers(0, 65, size=v0.shape).astype(np.int16)
+    a, b = oracle.OracleMap(w.params), oracle.OracleMap(w.params)
+    a.load_window(v0, w0)
+    b.load_window(v0, w0)
+    a.integrate(w.scans[0], w.poses[0])
+    b.integrate(w.scans[0], w.poses[0], threads=5)
+    va, wa = a.read()
+    vb, wb = b.read()
+    assert np.array_equal(va, vb) and np.array_equal(wa, wb)
+    assert a.stats() == b.stats()
