@@ -201,8 +201,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     m = b.TsdfMap(p)
     h = m.handle
     sort = args.reduction == "sort"
+    red_opt = {"atomic": None, "sort": b.TSDF_REDUCTION_SORT, "pool": b.TSDF_REDUCTION_POOL}[args.reduction]
     for opt, val in ((b.TSDF_OPT_WARP_MERGE, args.merge), (b.TSDF_OPT_STEPS_PER_THREAD, args.kpt),
-                     (b.TSDF_OPT_PDL, args.pdl), (b.TSDF_OPT_REDUCTION, 1 if sort else None),
+                     (b.TSDF_OPT_PDL, args.pdl), (b.TSDF_OPT_REDUCTION, red_opt),
                      (b.TSDF_OPT_HOST_ZERO_COPY, args.zero_copy)):
         if val is not None:
             b.tsdf_set_option(h, opt, val)
@@ -289,6 +290,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         b.tsdf_stats(h, stream)
         t_e2e += time.perf_counter() - t0
     e2e_hits = int(sum(hits[i] for i in e2e_sched))
+    map_bytes = b.tsdf_map_device_bytes(h)
     m.close()
 
     # ---- reduce over ranks: total units / slowest rank
@@ -352,7 +354,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         dtype="f32 geometry, int64 accumulation, int16 map", data="synthetic",
         config=dict(workload=wdesc,
                     points_per_scan=int(n_pts), voxel_size=p["voxel_size"], tau=p["tau"], dims=list(p["dims"]),
-                    reduce="WSUM", reduction=args.reduction, l2="flushed (512 MiB write) before every timed step; flush excluded by per-step events",
+                    reduce="WSUM", reduction=args.reduction, map_device_bytes=map_bytes, l2="flushed (512 MiB write) before every timed step; flush excluded by per-step events",
                     parallelism=f"replicas x{world}"),
         scans_per_s=K * world / (dev_ms_max / 1e3),
         us_per_scan=dict(mean=1e3 * dev_ms_max / K, p50=1e3 * float(np.percentile(step_ms, 50)),
@@ -364,7 +366,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                      "each kernel (that pass: %.1f us/scan; events serialise the kernels of a step)" %
                      (1e3 * float(sum(prof_step_ms)) / K),
         roofline=dict(kernel=kname, bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
-                      peak_source=f"{peak_kind} hbm_gbs", traffic=None if sort else NCU_DRAM_BYTES.get(kname),
+                      peak_source=f"{peak_kind} hbm_gbs",
+                      traffic=NCU_DRAM_BYTES.get(kname) if args.reduction == "atomic" else None,
                       alg_bytes_def=("16 B per point read + 8 B per touched voxel of the per-scan volume"
                                      if kname in ("contrib", "emit") else
                                      "16 B per touched voxel (volume read + grid RMW)"),
@@ -376,8 +379,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                       "link unless --zero-copy 0) + tsdf_stats read-back, host wall clock"),
         # library launches: one per profiled entry, plus the compaction that shares
         # the apply entry (atomic) or compact + count + prefix + scatter sharing
-        # the sort entry (sort)
-        gpu_launches=int(sum(v[0] for v in prof.values()) + (3 if sort else 1) * K),
+        # the sort entry (sort); the pool reduction has no compaction
+        gpu_launches=int(sum(v[0] for v in prof.values()) +
+                         {"atomic": 1, "sort": 3, "pool": 0}[args.reduction] * K),
         clocks=clk,
         wall_s_timed=t_wall,
         cpu_baseline=cpu,
@@ -599,7 +603,7 @@ def main():
     ap.add_argument("--pdl", type=int, default=None, help="tuning: programmatic dependent launch (0/1)")
     ap.add_argument("--zero-copy", type=int, default=None,
                     help="e2e: pinned host points read in place (1, library default) or staged (0)")
-    ap.add_argument("--reduction", default="atomic", choices=["atomic", "sort"],
+    ap.add_argument("--reduction", default="atomic", choices=["atomic", "sort", "pool"],
                     help="per-scan reduction: accumulator atomics or counting sort by brick")
     ap.add_argument("--workload", default="outdoor", choices=["outdoor", "corridor", "batch", "serving"],
                     help="outdoor: the headline sequence; batch / serving: the 64-map batch and 32-session serving runs")

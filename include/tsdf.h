@@ -48,6 +48,8 @@ extern "C" {
 #define TSDF_ERR_ADMISSION  -5  /* a session would exceed the device-memory budget */
 #define TSDF_ERR_BUSY       -6  /* the resource is in use (e.g. an outstanding request) */
 #define TSDF_ERR_IO         -7  /* a file could not be opened, read or written, or is not a map file */
+#define TSDF_ERR_CAPACITY   -8  /* the last scan needed more accumulator bricks than the pool holds; it was
+                                   dropped whole (the map is unchanged) */
 
 /* ---- per-scan reduction of the contributions to one voxel ----------------- */
 #define TSDF_REDUCE_WSUM     0  /* sum of weight * distance and sum of weights (weight 1 per contribution) */
@@ -153,7 +155,8 @@ int tsdf_write(tsdf_map* map, const int64_t lo[3], const int64_t hi[3], const in
                const int16_t* weight_host, void* stream);
 
 /* Counters of the most recent integrate call (zero before the first).
- * Synchronises `stream`. Errors: INVALID, CUDA. */
+ * Synchronises `stream`. Returns TSDF_ERR_CAPACITY (hits and touched 0) when
+ * that scan was dropped by the pool reduction. Errors: INVALID, CUDA. */
 int tsdf_stats(tsdf_map* map, tsdf_scan_stats* out, void* stream);
 
 /* Tuning options (no effect on results, which are bit-identical for every
@@ -181,6 +184,19 @@ int tsdf_stats(tsdf_map* map, tsdf_scan_stats* out, void* stream);
 #define TSDF_REDUCTION_SORT   1  /* contributions are written as (voxel, code) pairs, counting-sorted by brick
                                    and reduced per voxel in shared memory; no per-contribution atomics. Buffers
                                    are allocated on the first integrate call that uses it (synchronous). */
+#define TSDF_REDUCTION_POOL   2  /* sparse per-scan accumulator: a brick gets a 4 KiB accumulator slot from a
+                                   pool on its first contribution of the scan (brick -> slot table, 4 B per
+                                   brick) and the apply walks the claimed slots; the dense 8 B/voxel
+                                   accumulator is never allocated for a map used only this way. A scan that
+                                   needs more bricks than the pool holds is dropped whole and tsdf_stats
+                                   returns TSDF_ERR_CAPACITY. Same results as the other reductions. */
+#define TSDF_OPT_POOL_BRICKS  7  /* pool reduction: slots of the pool (64 .. bricks of the window); 0 (default):
+                                   an eighth of the window's bricks, at least 16384 */
+
+/* Device memory held by the map (grid, per-scan buffers of the reductions
+ * that have been used, ray buffers, global store) in bytes. Host-side.
+ * Errors: INVALID. */
+int tsdf_map_device_bytes(const tsdf_map* map, int64_t* out);
 
 /* Set a tuning option of a map; takes effect for later calls. Host-side
  * state only (the sort buffers are allocated by the next integrate call).

@@ -22,6 +22,7 @@ TSDF_ERR_TIMEOUT = -4
 TSDF_ERR_ADMISSION = -5
 TSDF_ERR_BUSY = -6
 TSDF_ERR_IO = -7
+TSDF_ERR_CAPACITY = -8
 TSDF_REDUCE_WSUM = 0
 TSDF_REDUCE_MIN_ABS = 1
 TSDF_FLAG_STEP_VALUE = 1
@@ -35,6 +36,8 @@ TSDF_OPT_SORT_CAPACITY = 5
 TSDF_OPT_HOST_ZERO_COPY = 6
 TSDF_REDUCTION_ATOMIC = 0
 TSDF_REDUCTION_SORT = 1
+TSDF_REDUCTION_POOL = 2
+TSDF_OPT_POOL_BRICKS = 7
 TSDF_BATCH_OPT_GRAPH = 1
 TSDF_BATCH_OPT_AUTOTUNE = 2
 TSDF_BATCH_OPT_CONFIG = 3
@@ -119,6 +122,7 @@ def lib():
     L.tsdf_profile_read.argtypes = [vp, P(tsdf_kernel_time), ctypes.c_int32, P(ctypes.c_int32)]
     L.tsdf_probe_reduction_rate.argtypes = [ctypes.c_int32, P(ctypes.c_double), vp]
     L.tsdf_map_save.argtypes = [vp, ctypes.c_char_p, vp]
+    L.tsdf_map_device_bytes.argtypes = [vp, P(i64)]
     L.tsdf_extract_surface.argtypes = [vp, ctypes.c_int32, vp, i64, P(i64), vp]
     L.tsdf_map_load.argtypes = [ctypes.c_char_p, P(vp), vp]
     L.tsdf_batch_create.argtypes = [ctypes.c_int32, P(vp)]
@@ -143,7 +147,7 @@ def lib():
     for name in ("tsdf_map_create", "tsdf_map_destroy", "tsdf_integrate", "tsdf_integrate_host", "tsdf_shift",
                  "tsdf_read", "tsdf_write", "tsdf_stats", "tsdf_get_origin", "tsdf_grid_device_ptr",
                  "tsdf_last_cuda_error", "tsdf_profile_enable", "tsdf_profile_read", "tsdf_set_option",
-                 "tsdf_integrate_static", "tsdf_probe_reduction_rate", "tsdf_map_save", "tsdf_map_load", "tsdf_extract_surface", "tsdf_batch_create", "tsdf_batch_destroy", "tsdf_batch_set_option",
+                 "tsdf_integrate_static", "tsdf_probe_reduction_rate", "tsdf_map_save", "tsdf_map_load", "tsdf_extract_surface", "tsdf_map_device_bytes", "tsdf_batch_create", "tsdf_batch_destroy", "tsdf_batch_set_option",
                  "tsdf_batch_get_config", "tsdf_batch_integrate", "tsdf_integrate_batch", "tsdf_batch_sync",
                  "tsdf_server_create", "tsdf_server_destroy", "tsdf_server_open_session", "tsdf_server_close_session",
                  "tsdf_server_submit", "tsdf_server_wait", "tsdf_server_session_map", "tsdf_server_get_stats"):
@@ -431,6 +435,12 @@ def tsdf_extract_surface(handle: int, min_weight: int = 1, out=None, stream=None
                                       _stream_ptr(stream)), "tsdf_extract_surface")
     n = int(cnt.value)
     return out[:min(n, out.shape[0])], n
+
+
+def tsdf_map_device_bytes(handle: int) -> int:
+    out = ctypes.c_int64()
+    _check(lib().tsdf_map_device_bytes(handle, ctypes.byref(out)), "tsdf_map_device_bytes")
+    return int(out.value)
 
 
 def tsdf_map_save(handle: int, path: str, stream=None) -> None:

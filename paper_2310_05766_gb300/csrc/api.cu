@@ -114,6 +114,7 @@ struct tsdf_map {
     bool zero_copy = true;          // tsdf_integrate_host reads device-mapped pinned points in place
     long long* host_last = nullptr; // mapped pinned copy of the published counters (host address)
     size_t pair_cap_req = 0;        // sort reduction: requested pair capacity, 0 = from the scan size
+    size_t pool_req = 0;            // pool reduction: requested slots, 0 = default
     size_t ray_slot_cap = 0;        // entries of dev.ray_slot
     // optional per-kernel event timing
     bool prof = false;
@@ -210,6 +211,9 @@ void free_map(tsdf_map* m) {
     cudaFree(m->dev.ray_b);
     cudaFree(m->dev.ctr);
     if (m->host_last) cudaFreeHost(m->host_last);
+    cudaFree(m->dev.pool_table);
+    cudaFree(m->dev.pool_brick);
+    cudaFree(m->dev.pool_acc);
     cudaFree(m->dev.brick_slot);
     cudaFree(m->dev.seg_count);
     cudaFree(m->dev.seg_start);
@@ -285,19 +289,17 @@ int tsdf_map_create(const tsdf_params* params, tsdf_map** out) {
     m->bricks = m->voxels / kBrickVoxels;
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&m->dev.grid, m->voxels * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&m->dev.acc, m->voxels * sizeof(unsigned long long));
     const size_t flag_bytes = (m->bricks + 3) / 4 * 4;
     if (e == cudaSuccess) e = cudaMalloc(&m->dev.brick_flag, flag_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&m->dev.brick_list, m->bricks * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&m->dev.ctr, sizeof(MapCounters));
     if (e == cudaSuccess) e = cudaMemset(m->dev.grid, 0, m->voxels * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMemset(m->dev.acc, 0, m->voxels * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(m->dev.brick_flag, 0, flag_bytes);
     if (e == cudaSuccess) e = cudaMemset(m->dev.ctr, 0, sizeof(MapCounters));
     // published counters mirrored into mapped pinned memory (falls back to a
     // device-to-host copy in tsdf_stats when the mapping is unavailable)
-    if (e == cudaSuccess && cudaHostAlloc(&m->host_last, 3 * sizeof(long long), cudaHostAllocMapped) == cudaSuccess) {
-        std::memset(m->host_last, 0, 3 * sizeof(long long));
+    if (e == cudaSuccess && cudaHostAlloc(&m->host_last, 4 * sizeof(long long), cudaHostAllocMapped) == cudaSuccess) {
+        std::memset(m->host_last, 0, 4 * sizeof(long long));
         void* dp = nullptr;
         if (cudaHostGetDevicePointer(&dp, m->host_last, 0) == cudaSuccess) {
             m->dev.host_last = static_cast<long long*>(dp);
@@ -324,6 +326,50 @@ int tsdf_map_destroy(tsdf_map* map) {
     DeviceScope ds(map->device);
     cudaDeviceSynchronize();
     free_map(map);
+    return TSDF_OK;
+}
+
+// The dense per-scan accumulator (8 B per voxel, all zero between scans) is
+// allocated on the first call that needs it: the atomic and sort reductions,
+// batches and sessions. A map used only with the pool reduction never holds it.
+static int ensure_acc(tsdf_map* map) {
+    if (map->dev.acc) return TSDF_OK;
+    unsigned long long* a = nullptr;
+    TSDF_CU(cudaMalloc(&a, map->voxels * sizeof(unsigned long long)));
+    cudaError_t e = cudaMemset(a, 0, map->voxels * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaFree(a);
+        return cuda_fail(e);
+    }
+    map->dev.acc = a;
+    return TSDF_OK;
+}
+
+// Pool reduction: the brick -> slot table (all empty), the per-slot brick ids
+// and the slot accumulators (all zero). Default capacity: an eighth of the
+// window's bricks, at least 16384 and at most all of them.
+static int ensure_pool(tsdf_map* map) {
+    size_t want = map->pool_req;
+    if (want == 0) {
+        want = map->bricks / 8;
+        if (want < 16384) want = 16384;
+    }
+    if (want > map->bricks) want = map->bricks;
+    if (map->dev.pool_table && want == map->dev.pool_cap) return TSDF_OK;
+    TSDF_CU(cudaDeviceSynchronize());   // an earlier scan may still use the old pool
+    cudaFree(map->dev.pool_table);
+    cudaFree(map->dev.pool_brick);
+    cudaFree(map->dev.pool_acc);
+    map->dev.pool_table = nullptr;
+    map->dev.pool_brick = nullptr;
+    map->dev.pool_acc = nullptr;
+    map->dev.pool_cap = 0;
+    TSDF_CU(cudaMalloc(&map->dev.pool_table, map->bricks * sizeof(uint32_t)));
+    TSDF_CU(cudaMemset(map->dev.pool_table, 0xFF, map->bricks * sizeof(uint32_t)));
+    TSDF_CU(cudaMalloc(&map->dev.pool_brick, want * sizeof(uint32_t)));
+    TSDF_CU(cudaMalloc(&map->dev.pool_acc, want * kBrickVoxels * sizeof(unsigned long long)));
+    TSDF_CU(cudaMemset(map->dev.pool_acc, 0, want * kBrickVoxels * sizeof(unsigned long long)));
+    map->dev.pool_cap = (uint32_t)want;
     return TSDF_OK;
 }
 
@@ -417,6 +463,26 @@ static int integrate_dev(tsdf_map* map, const float* points_dev, int64_t n, cons
     ScanArgs a;
     fill_scan_args(map, points_dev, n, pose, a);
     const bool pdl = map->pdl;
+    if (map->reduction == TSDF_REDUCTION_POOL) {
+        rc = ensure_pool(map);
+        if (rc != TSDF_OK) return rc;
+        const MapDev& d = map->dev;
+        cudaEvent_t e0 = n > 0 ? prof_mark(map, s) : nullptr;
+        TSDF_CU(launch_rays(a, d, false, pdl, s));
+        cudaEvent_t e1 = n > 0 ? prof_mark(map, s) : nullptr;
+        cudaEvent_t e2 = n > 0 ? prof_mark(map, s) : nullptr;
+        TSDF_CU(launch_pool_contrib(a, d, map->p.reduce, map->kpt, pdl, s));
+        cudaEvent_t e3 = n > 0 ? prof_mark(map, s) : nullptr;
+        cudaEvent_t e4 = prof_mark(map, s);
+        TSDF_CU(launch_pool_apply(d, map->p.reduce, map->p.w_max, map->p.flags, pdl, s));   // + counters
+        cudaEvent_t e5 = prof_mark(map, s);
+        prof_push(map, kRays, e0, e1);
+        prof_push(map, kContrib, e2, e3);
+        prof_push(map, kApply, e4, e5);
+        return TSDF_OK;
+    }
+    rc = ensure_acc(map);
+    if (rc != TSDF_OK) return rc;
     if (map->reduction == TSDF_REDUCTION_SORT) {
         rc = ensure_sort(map, n);
         if (rc != TSDF_OK) return rc;
@@ -627,18 +693,25 @@ int tsdf_stats(tsdf_map* map, tsdf_scan_stats* out, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     long long last[3] = {0, 0, 0};   // last_valid, last_hits, last_touched are contiguous
     static_assert(offsetof(MapCounters, last_touched) == offsetof(MapCounters, last_valid) + 16, "layout");
+    long long status = 0;
+    static_assert(offsetof(MapCounters, last_status) == offsetof(MapCounters, last_valid) + 24, "layout");
+    static_assert(kStatusCapacity == TSDF_ERR_CAPACITY, "status code");
     if (map->host_last) {
         // the last apply CTA of each scan also wrote them to mapped host memory
         TSDF_CU(cudaStreamSynchronize(s));
         std::memcpy(last, (const void*)map->host_last, sizeof(last));
+        status = ((volatile long long*)map->host_last)[3];
     } else {
-        TSDF_CU(cudaMemcpyAsync(last, &map->dev.ctr->last_valid, sizeof(last), cudaMemcpyDeviceToHost, s));
+        long long buf[4] = {0, 0, 0, 0};
+        TSDF_CU(cudaMemcpyAsync(buf, &map->dev.ctr->last_valid, sizeof(buf), cudaMemcpyDeviceToHost, s));
         TSDF_CU(cudaStreamSynchronize(s));
+        std::memcpy(last, buf, sizeof(last));
+        status = buf[3];
     }
     out->valid_rays = last[0];
     out->hits = last[1];
     out->touched = last[2];
-    return TSDF_OK;
+    return status != 0 ? (int)status : TSDF_OK;
 }
 
 int tsdf_profile_enable(tsdf_map* map, int32_t enable) {
@@ -688,8 +761,13 @@ int tsdf_set_option(tsdf_map* map, int32_t option, int64_t value) {
             if (value != 0 && value != 1) return TSDF_ERR_INVALID;
             map->pdl = value != 0;
             return TSDF_OK;
+        case TSDF_OPT_POOL_BRICKS:
+            if (value != 0 && (value < 64 || value > (int64_t)map->bricks)) return TSDF_ERR_INVALID;
+            map->pool_req = (size_t)value;
+            return TSDF_OK;
         case TSDF_OPT_REDUCTION:
-            if (value != TSDF_REDUCTION_ATOMIC && value != TSDF_REDUCTION_SORT) return TSDF_ERR_INVALID;
+            if (value != TSDF_REDUCTION_ATOMIC && value != TSDF_REDUCTION_SORT && value != TSDF_REDUCTION_POOL)
+                return TSDF_ERR_INVALID;
             map->reduction = (int)value;
             return TSDF_OK;
         case TSDF_OPT_HOST_ZERO_COPY:
@@ -931,6 +1009,24 @@ int tsdf_extract_surface(tsdf_map* map, int32_t min_weight, float* out_dev, int6
     return TSDF_OK;
 }
 
+int tsdf_map_device_bytes(const tsdf_map* map, int64_t* out) {
+    if (!map || !out) return TSDF_ERR_INVALID;
+    const size_t flag_bytes = (map->bricks + 3) / 4 * 4;
+    size_t b = map->voxels * sizeof(uint32_t) + flag_bytes + map->bricks * sizeof(uint32_t) + sizeof(MapCounters);
+    if (map->dev.acc) b += map->voxels * sizeof(unsigned long long);
+    b += map->ray_cap * 2 * sizeof(float4);
+    if (map->dev.brick_slot) b += 3 * map->bricks * sizeof(uint32_t);
+    b += map->ray_slot_cap * sizeof(uint32_t);
+    b += (size_t)map->dev.pair_cap * (sizeof(uint2) + sizeof(uint32_t));
+    if (map->dev.pool_table)
+        b += map->bricks * sizeof(uint32_t) +
+             (size_t)map->dev.pool_cap * (sizeof(uint32_t) + kBrickVoxels * sizeof(unsigned long long));
+    b += map->store_segments.size() * (size_t)kSegChunks * kChunkBytes;
+    b += map->stage_cap * sizeof(float4) + map->items_dev_cap * sizeof(ShiftItem);
+    *out = (int64_t)b;
+    return TSDF_OK;
+}
+
 int tsdf_get_origin(const tsdf_map* map, int64_t out[3]) {
     if (!map || !out) return TSDF_ERR_INVALID;
     for (int a = 0; a < 3; ++a) out[a] = map->origin[a];
@@ -953,6 +1049,7 @@ const char* tsdf_error_string(int code) {
         case TSDF_ERR_ADMISSION: return "device-memory budget exceeded";
         case TSDF_ERR_BUSY: return "resource busy";
         case TSDF_ERR_IO: return "file error or not a map file";
+        case TSDF_ERR_CAPACITY: return "scan dropped: the accumulator pool is full";
         default: return "unknown error";
     }
 }
@@ -968,6 +1065,8 @@ int prepare_batch_item(::tsdf_map* map, const float* points_dev, int64_t n, cons
     if (rc != TSDF_OK) return rc;
     if (((uintptr_t)points_dev & 15u) != 0) return TSDF_ERR_INVALID;
     DeviceScope ds(map->device);
+    rc = ensure_acc(map);   // batches use the accumulator reductions
+    if (rc != TSDF_OK) return rc;
     rc = ensure_rays(map, n);
     if (rc != TSDF_OK) return rc;
     fill_scan_args(map, points_dev, n, pose, out->a);
@@ -986,6 +1085,8 @@ const long long* map_last_counters(const ::tsdf_map* map) { return &map->dev.ctr
 int map_reserve_points(::tsdf_map* map, int64_t n) {
     if (!map || n < 0 || n > TSDF_MAX_POINTS) return TSDF_ERR_INVALID;
     DeviceScope ds(map->device);
+    int rc = ensure_acc(map);
+    if (rc != TSDF_OK) return rc;
     return ensure_rays(map, n);
 }
 

@@ -163,6 +163,36 @@ __global__ void __launch_bounds__(256, TSDF_CONTRIB_MIN_CTAS) emit_kernel(const 
     }
 }
 
+// Pool reduction: the contribution march accumulating into claimed pool
+// bricks (same work items as contrib_kernel).
+template <int MODE, int KPT>
+__global__ void __launch_bounds__(256) pool_contrib_kernel(const ScanArgs a, const MapDev m) {
+    __shared__ unsigned long long red[8];
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+    pdl_trigger();
+    pdl_wait();
+    unsigned nlive = 0;
+    if (lane == 0) nlive = __ldcg(&m.ctr->live_count);
+    nlive = __shfl_sync(kFull, nlive, 0);
+    const unsigned ngrp = (unsigned)(2 * a.K + KPT) / KPT;
+    const unsigned nitems = (nlive + 31u) / 32u * ngrp;
+    unsigned hits = 0;
+    unsigned last_brick = kNoVoxel;
+    uint32_t last_slot = kPoolEmpty;
+    for (unsigned item = gwarp; item < nitems; item += nwarps) {   // warp-uniform
+        float4 A, B;
+        load_rays(m, nlive, (item / ngrp) * 32u + lane, A, B);
+        contrib_item<MODE, false, KPT, false, true>(a, m, item % ngrp, A, B, hits, last_brick, kNoSlot, nullptr,
+                                                    &last_slot);
+    }
+    if (MODE == 1) {
+        const unsigned long long total = cta_sum<8>((unsigned long long)hits, red);
+        if (threadIdx.x == 0 && total) atomicAdd(&m.ctr->part[blockIdx.x % kParts].hits, total);
+    }
+}
+
 __global__ void __launch_bounds__(256) sort_count_kernel(const MapDev m) {
     pdl_trigger();
     pdl_wait();   // pairs come from emit, brick slots from compact
@@ -299,6 +329,63 @@ __global__ void __launch_bounds__(kApplyWarps * 32) sort_apply_kernel(const MapD
 }
 
 
+// Pool reduction: one warp per claimed slot applies Eq. 1 / Eq. 2 to its
+// brick (unless the pool overflowed: then the scan is dropped and the slots
+// are only cleared), resets the slot and the brick's table entry; the last CTA
+// publishes the counters and the scan's status.
+template <int MODE>
+__global__ void __launch_bounds__(kApplyWarps * 32) pool_apply_kernel(const MapDev m, const int32_t w_max,
+                                                                       const int32_t flags) {
+    __shared__ unsigned long long red_u[kApplyWarps], red_h[kApplyWarps];
+    __shared__ unsigned s_last;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned w = threadIdx.x >> 5;
+    const unsigned gwarp = blockIdx.x * kApplyWarps + w;
+    const unsigned nwarps = gridDim.x * kApplyWarps;
+    pdl_trigger();
+    pdl_wait();
+    unsigned ns = 0, ovf = 0;
+    if (lane == 0) {
+        ns = __ldcg(&m.ctr->pool_count);
+        ovf = __ldcg(&m.ctr->pool_overflow);
+    }
+    ns = __shfl_sync(kFull, ns, 0);
+    ovf = __shfl_sync(kFull, ovf, 0);
+    if (ns > m.pool_cap) ns = m.pool_cap;
+    unsigned long long touched = 0, hits = 0;
+    for (unsigned i = gwarp; i < ns; i += nwarps) {
+        const unsigned brick = __ldcg(m.pool_brick + i);
+        unsigned long long* accp = m.pool_acc + ((size_t)i << 9);
+        if (!ovf) {
+            apply_brick_at<MODE>(m, w_max, flags, brick, accp, touched, hits);
+        } else {
+            ulonglong2* ap = reinterpret_cast<ulonglong2*>(accp);
+#pragma unroll
+            for (int v = 0; v < 8; ++v) ap[32 * v + lane] = make_ulonglong2(0ull, 0ull);
+        }
+        if (lane == 0) m.pool_table[brick] = kPoolEmpty;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        touched += __shfl_xor_sync(kFull, touched, o);
+        hits += __shfl_xor_sync(kFull, hits, o);
+    }
+    if (lane == 0) {
+        red_u[w] = touched;
+        red_h[w] = hits;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long bu = 0, bh = 0;
+        for (int k = 0; k < kApplyWarps; ++k) {
+            bu += red_u[k];
+            bh += red_h[k];
+        }
+        if (bu) atomicAdd(&m.ctr->part[blockIdx.x % kParts].touched, bu);
+        if (MODE == 0 && bh) atomicAdd(&m.ctr->part[blockIdx.x % kParts].hits, bh);
+    }
+    finish_if_last(m, &s_last);
+}
+
 // Launch with programmatic stream serialisation when `pdl` is set.
 template <typename... KArgs, typename... Args>
 cudaError_t launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, bool pdl, Args&&... args) {
@@ -398,6 +485,30 @@ cudaError_t launch_emit(const ScanArgs& a, const MapDev& m, int32_t reduce, int 
         case 4: return launch_emit_k<1, 4>(a, m, pdl, s);
         default: return launch_emit_k<1, 1>(a, m, pdl, s);
     }
+}
+
+cudaError_t launch_pool_contrib(const ScanArgs& a, const MapDev& m, int32_t reduce, int kpt, bool pdl,
+                                cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    auto pick = [&](auto* k) { return launch(k, resident_grid(k, 256, TSDF_CONTRIB_CTAS_PER_SM), dim3(256), s, pdl, a, m); };
+    if (reduce == 0) {
+        switch (kpt) {
+            case 2: return pick(pool_contrib_kernel<0, 2>);
+            case 4: return pick(pool_contrib_kernel<0, 4>);
+            default: return pick(pool_contrib_kernel<0, 1>);
+        }
+    }
+    switch (kpt) {
+        case 2: return pick(pool_contrib_kernel<1, 2>);
+        case 4: return pick(pool_contrib_kernel<1, 4>);
+        default: return pick(pool_contrib_kernel<1, 1>);
+    }
+}
+
+cudaError_t launch_pool_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t flags, bool pdl,
+                              cudaStream_t s) {
+    auto* k = reduce == 0 ? pool_apply_kernel<0> : pool_apply_kernel<1>;
+    return launch(k, resident_grid(k, kApplyWarps * 32), dim3(kApplyWarps * 32), s, pdl, m, w_max, flags);
 }
 
 cudaError_t launch_sort_count(const MapDev& m, bool pdl, cudaStream_t s) {

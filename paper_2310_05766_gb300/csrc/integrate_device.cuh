@@ -193,11 +193,64 @@ __device__ __forceinline__ void load_rays(const MapDev& m, unsigned nlive, unsig
 // reduced: (voxel word, code) inside the window, kNoVoxel outside. Samples
 // whose slot is at or beyond the capacity (or whose ray has none) take the
 // accumulator reduction instead and set `ovf`.
-template <int MODE, bool MERGE, int KPT, bool SORT = false>
+// Pool reduction: slot of `brick` in the map's pool, claimed on first touch.
+// Lanes of the active set that need the same brick share one claim (match).
+// The claimer moves the brick's table entry from empty to a "claiming" mark
+// with a CAS, takes the next slot from the counter and publishes it; other
+// warps that meet the mark wait for the slot (a bounded wait: the claimer
+// depends on nothing, and a wait that runs out drops the scan like a full
+// pool). So every slot holds a distinct brick. Returns kPoolEmpty when the
+// pool is full (the scan is then dropped and reported).
+constexpr uint32_t kPoolClaiming = 0xFFFFFFFEu;
+constexpr long long kPoolSpinLimit = 1LL << 20;
+
+__device__ __forceinline__ uint32_t pool_slot(const MapDev& m, unsigned brick) {
+    uint32_t s = __ldcg(m.pool_table + brick);
+    if (s < kPoolClaiming) return s;
+    const unsigned act = __activemask();
+    const unsigned peers = __match_any_sync(act, brick);
+    const unsigned leader = (unsigned)(__ffs(peers) - 1);
+    if ((threadIdx.x & 31u) == leader) {
+        long long spins = 0;
+        for (;;) {
+            if (__ldcg(&m.ctr->pool_overflow) != 0u) {
+                s = kPoolEmpty;
+                break;
+            }
+            s = __ldcg(m.pool_table + brick);
+            if (s < kPoolClaiming) break;
+            if (s == kPoolEmpty) {
+                if (atomicCAS(m.pool_table + brick, kPoolEmpty, kPoolClaiming) != kPoolEmpty) continue;
+                const uint32_t ns = atomicAdd(&m.ctr->pool_count, 1u);
+                if (ns < m.pool_cap) {
+                    m.pool_brick[ns] = brick;
+                    atomicExch(m.pool_table + brick, ns);
+                    s = ns;
+                } else {
+                    atomicExch(&m.ctr->pool_overflow, 1u);
+                    atomicExch(m.pool_table + brick, kPoolEmpty);
+                    s = kPoolEmpty;
+                }
+                break;
+            }
+            if (++spins > kPoolSpinLimit) {   // another warp is claiming it
+                atomicExch(&m.ctr->pool_overflow, 1u);
+                s = kPoolEmpty;
+                break;
+            }
+            __nanosleep(32);
+        }
+    }
+    return __shfl_sync(peers, s, leader);
+}
+
+template <int MODE, bool MERGE, int KPT, bool SORT = false, bool POOL = false>
 __device__ __forceinline__ void contrib_item(const ScanArgs& a, const MapDev& m, unsigned grp, const float4 A,
                                              const float4 B, unsigned& hits, unsigned& last_brick,
-                                             uint32_t sslot = kNoSlot, bool* ovf = nullptr) {
+                                             uint32_t sslot = kNoSlot, bool* ovf = nullptr,
+                                             uint32_t* last_slot = nullptr) {
     static_assert(!(SORT && MERGE), "the sort reduction emits every sample");
+    static_assert(!(POOL && (SORT || MERGE)), "the pool reduction is a variant of the plain atomic one");
     const unsigned lane = threadIdx.x & 31u;
     const float tx = a.t[0], ty = a.t[1], tz = a.t[2];
     const float r = A.w;                // dead lanes carry r = -1
@@ -249,7 +302,21 @@ __device__ __forceinline__ void contrib_item(const ScanArgs& a, const MapDev& m,
             int q = small_int(fm(d, a.qs));
             q = max(-kQMax, min(kQMax, q));
             bool leader = act;
-            if (SORT) {
+            if (POOL) {
+                // the lane's last brick and its slot are cached: the table is
+                // read only when the lane moves to another brick
+                if (act && brick != last_brick) {
+                    *last_slot = pool_slot(m, brick);
+                    last_brick = brick;
+                }
+                if (act && *last_slot != kPoolEmpty) {
+                    unsigned long long* pa = m.pool_acc + (((size_t)*last_slot) << 9) + (word & 511u);
+                    if (MODE == 0) atomicAdd(pa, (1ull << 40) + (unsigned long long)(long long)q);
+                    else atomicMax(pa, 65536ull - (((unsigned)abs(q) << 1) | (q < 0 ? 1u : 0u)));
+                }
+                if (MODE == 1) hits += act ? 1u : 0u;
+                continue;   // no brick flags: the claimed slots list the touched bricks
+            } else if (SORT) {
                 const bool mine = lv && j >= -J && j <= J;
                 const uint32_t slot = sslot + sidx + (uint32_t)(j + J);   // no wrap: sslot <= cap, sidx < 2^21
                 if (mine && sslot != kNoSlot && slot < m.pair_cap) {
@@ -452,18 +519,19 @@ __device__ __forceinline__ void apply_staged(const MapDev& m, int32_t w_max, int
     for (int v = 0; v < 4; ++v) gpw[32 * v + lane] = sg4[32 * v + lane];
 }
 
-// ---- apply, register form: one warp updates listed brick number i. Lane l
-// holds voxels 2(32 v + l) and +1 (v = 0..7) as eight 8-byte grid pairs and
-// eight 16-byte accumulator pairs, all loaded at once; every touched voxel is
-// decoded in place (16 independent updates per lane), and only changed pairs
-// are written back and reset.
+// ---- apply, register form: one warp updates grid brick `brick` from the 512
+// accumulators at `accp` (a brick of the dense accumulator or a pool slot).
+// Lane l holds voxels 2(32 v + l) and +1 (v = 0..7) as eight 8-byte grid pairs
+// and eight 16-byte accumulator pairs, all loaded at once; every touched voxel
+// is decoded in place (16 independent updates per lane), and only changed
+// pairs are written back and reset.
 template <int MODE>
-__device__ __forceinline__ void apply_brick_reg(const MapDev& m, int32_t w_max, int32_t flags, unsigned i,
-                                                unsigned long long& touched, unsigned long long& hits) {
+__device__ __forceinline__ void apply_brick_at(const MapDev& m, int32_t w_max, int32_t flags, unsigned brick,
+                                               unsigned long long* accp, unsigned long long& touched,
+                                               unsigned long long& hits) {
     const unsigned lane = threadIdx.x & 31u;
-    const unsigned brick = m.brick_list[i];
     uint2* gp = reinterpret_cast<uint2*>(m.grid + ((size_t)brick << 9));
-    ulonglong2* ap = reinterpret_cast<ulonglong2*>(m.acc + ((size_t)brick << 9));
+    ulonglong2* ap = reinterpret_cast<ulonglong2*>(accp);
     ulonglong2 acc[8];
     uint2 g[8];
 #pragma unroll
@@ -492,6 +560,13 @@ __device__ __forceinline__ void apply_brick_reg(const MapDev& m, int32_t w_max, 
     }
     touched += cnt;
     hits += h;
+}
+
+template <int MODE>
+__device__ __forceinline__ void apply_brick_reg(const MapDev& m, int32_t w_max, int32_t flags, unsigned i,
+                                                unsigned long long& touched, unsigned long long& hits) {
+    const unsigned brick = m.brick_list[i];
+    apply_brick_at<MODE>(m, w_max, flags, brick, m.acc + ((size_t)brick << 9), touched, hits);
 }
 
 // ---- apply: one warp updates listed brick number i of the map. Shared
@@ -716,19 +791,26 @@ __device__ __forceinline__ void finish_warp(const MapDev& m) {
         u += __shfl_xor_sync(kFull, u, o);
     }
     if (lane == 0) {
+        // a pool-reduction scan that found the pool full was dropped
+        const long long st = __ldcg(&c->pool_overflow) != 0u ? kStatusCapacity : 0;
+        if (st != 0) h = u = 0ull;
         c->last_valid = (long long)v;
         c->last_hits = (long long)h;
         c->last_touched = (long long)u;
+        c->last_status = st;
         if (m.host_last) {   // also into host memory: reading them needs no copy
             m.host_last[0] = (long long)v;
             m.host_last[1] = (long long)h;
             m.host_last[2] = (long long)u;
+            m.host_last[3] = st;
         }
         c->live_count = 0u;
         c->brick_count = 0u;
         c->slot_count = 0ull;
         c->overflow = 0u;
         c->apply_done = 0u;
+        c->pool_count = 0u;
+        c->pool_overflow = 0u;
     }
 }
 

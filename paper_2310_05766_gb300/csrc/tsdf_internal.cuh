@@ -31,13 +31,19 @@ struct MapCounters {
     long long last_valid;           // counters of the last completed scan
     long long last_hits;
     long long last_touched;
+    long long last_status;          // 0, or TSDF_ERR_CAPACITY when the scan was dropped (pool full)
     unsigned int live_count;        // rays of the scan in flight that can reach the window (compacted)
     unsigned int brick_count;       // length of the touched-brick list of the scan in flight
     unsigned long long slot_count;  // sort reduction: pair slots reserved by the scan in flight
     unsigned int overflow;          // sort reduction: 1 if some contribution went to the accumulators
     unsigned int apply_done;        // CTAs of the apply kernel that have finished (the last one publishes)
     unsigned long long surface_count;   // points found by the last surface extraction
+    unsigned int pool_count;        // pool reduction: slots claimed by the scan in flight (may exceed the capacity)
+    unsigned int pool_overflow;     // pool reduction: 1 if a brick found the pool full (the scan is dropped)
 };
+
+constexpr uint32_t kPoolEmpty = 0xFFFFFFFFu;      // pool table entry of a brick without a slot
+constexpr long long kStatusCapacity = -8;        // TSDF_ERR_CAPACITY
 
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;        // ray without pair slots (all its samples overflow)
 constexpr uint32_t kRaySlotLimit = 1u << 20;      // rays with more samples than this overflow
@@ -54,7 +60,7 @@ struct MapDev {
     float4* ray_a;                  // per live ray (compacted): (dir.x, dir.y, dir.z, r)
     float4* ray_b;                  // per live ray (compacted): (int.x, int.y, int.z, fill ? 1 : 0)
     MapCounters* ctr;
-    long long* host_last;           // mapped pinned host copy of last_valid / last_hits / last_touched, or null
+    long long* host_last;           // mapped pinned host copy of last_valid / hits / touched / status, or null
     // sort reduction (null / 0 when the map has no sort buffers)
     uint32_t* brick_slot;           // per brick: its position in the brick list (touched bricks only)
     uint32_t* seg_count;            // per list position: pair count, then the scatter cursor; zero between scans
@@ -63,6 +69,11 @@ struct MapDev {
     uint2* pairs;                   // emitted (voxel word, code) per sample; word kNoVoxel = outside the window
     uint32_t* sorted;               // (offset in brick << 16) | (code & 0xFFFF), grouped by brick
     uint32_t pair_cap;              // capacity of `pairs` and `sorted`
+    // pool reduction (null / 0 when the map has no pool)
+    uint32_t* pool_table;           // per brick: its slot in the pool, kPoolEmpty between scans
+    uint32_t* pool_brick;           // per slot: the brick that claimed it
+    unsigned long long* pool_acc;   // per slot: 512 packed accumulators, all zero between scans
+    uint32_t pool_cap;              // slots
 };
 
 // Everything the kernels need about one scan, passed by value.
@@ -139,6 +150,12 @@ cudaError_t launch_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t
 // Sort reduction: emit pairs, count per brick, prefix, scatter, reduce + apply.
 cudaError_t launch_emit(const ScanArgs& a, const MapDev& m, int32_t reduce, int kpt, bool pdl, cudaStream_t s);
 cudaError_t launch_sort_count(const MapDev& m, bool pdl, cudaStream_t s);
+// Pool reduction: the contribution march into claimed pool bricks, and the
+// apply over the claimed slots (which also publishes the counters).
+cudaError_t launch_pool_contrib(const ScanArgs& a, const MapDev& m, int32_t reduce, int kpt, bool pdl,
+                                cudaStream_t s);
+cudaError_t launch_pool_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t flags, bool pdl,
+                              cudaStream_t s);
 cudaError_t launch_sort_scan(const MapDev& m, bool pdl, cudaStream_t s);
 cudaError_t launch_sort_scatter(const MapDev& m, bool pdl, cudaStream_t s);
 cudaError_t launch_sort_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t flags, bool pdl,

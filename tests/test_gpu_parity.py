@@ -228,7 +228,7 @@ def test_sort_reduction_edge_cases():
     m = b.TsdfMap(p)
     try:
         for i, st in enumerate(steps[2:]):
-            b.tsdf_set_option(m.handle, b.TSDF_OPT_REDUCTION, i % 2)
+            b.tsdf_set_option(m.handle, b.TSDF_OPT_REDUCTION, i % 3)
             m.integrate(torch.from_numpy(st[1]).cuda(), st[2])
         vg, wg = m.read()
     finally:
@@ -242,12 +242,107 @@ def test_sort_options_rejected():
     w = synth.workload_room()
     m = b.TsdfMap(w.params)
     try:
-        for opt, val in [(b.TSDF_OPT_REDUCTION, 2), (b.TSDF_OPT_REDUCTION, -1), (b.TSDF_OPT_SORT_CAPACITY, 5),
-                         (b.TSDF_OPT_SORT_CAPACITY, (1 << 28) + 1)]:
+        for opt, val in [(b.TSDF_OPT_REDUCTION, 3), (b.TSDF_OPT_REDUCTION, -1), (b.TSDF_OPT_SORT_CAPACITY, 5),
+                         (b.TSDF_OPT_SORT_CAPACITY, (1 << 28) + 1), (b.TSDF_OPT_POOL_BRICKS, 63),
+                         (b.TSDF_OPT_POOL_BRICKS, 1 << 30)]:
             with pytest.raises(b.TsdfError):
                 b.tsdf_set_option(m.handle, opt, val)
     finally:
         m.close()
+
+
+# ---------------------------------------------------------------- pool reduction (sparse accumulator)
+
+def _pool_opts(b, kpt=4, bricks=0):
+    return {b.TSDF_OPT_REDUCTION: b.TSDF_REDUCTION_POOL, b.TSDF_OPT_STEPS_PER_THREAD: kpt,
+            b.TSDF_OPT_POOL_BRICKS: bricks}
+
+
+@pytest.mark.parametrize("reduce", [0, 1])
+@pytest.mark.parametrize("kpt", [4, 1])
+def test_pool_reduction_exact(reduce, kpt):
+    """Per-scan accumulators in pooled bricks claimed on first touch: the
+    same maps and counters as the oracle (room twice, outdoor prefix with a
+    shift, a random case with shifts)."""
+    from paper_2310_05766_gb300 import binding as b
+    opts = _pool_opts(b, kpt)
+    w = synth.workload_room(reduce=reduce)
+    both(w.params, workload_steps(w) + [("scan", w.scans[0], w.poses[0])], options=opts, label=f"room pool {kpt}")
+    w2 = synth.workload_outdoor(n_scans=12, reduce=reduce)
+    both(w2.params, workload_steps(w2)[:5], options=opts, label=f"outdoor pool {kpt}")
+    p, steps = _rand_case(9)
+    both(dict(p, reduce=reduce), steps, options=opts, label=f"random pool {kpt}")
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_small_pool_exact(seed):
+    from paper_2310_05766_gb300 import binding as b
+    p, steps = _rand_case(seed)
+    nb = (p["dims"][0] // 8) * (p["dims"][1] // 8) * (p["dims"][2] // 8)
+    # a pool of exactly the window's bricks, or the default (also all of them for these small windows)
+    both(dict(p, flags=seed % 4), steps, options=_pool_opts(b, [4, 2, 1][seed % 3], nb if seed % 2 and nb >= 64 else 0),
+         label=f"random pool seed {seed}")
+
+
+def test_pool_full_drops_scan_and_recovers():
+    """A pool smaller than the scan's touched bricks: the scan is dropped
+    whole (TSDF_ERR_CAPACITY, map unchanged); with a large enough pool the
+    same map then integrates it exactly."""
+    from paper_2310_05766_gb300 import binding as b
+    w = synth.workload_room()
+    m = b.TsdfMap(w.params)
+    try:
+        pts = torch.from_numpy(w.scans[0]).cuda()
+        m.integrate(pts, w.poses[0])                 # atomic reduction first
+        v0, w0 = m.read()
+        b.tsdf_set_option(m.handle, b.TSDF_OPT_REDUCTION, b.TSDF_REDUCTION_POOL)
+        b.tsdf_set_option(m.handle, b.TSDF_OPT_POOL_BRICKS, 64)
+        m.integrate(pts, w.poses[0])
+        with pytest.raises(b.TsdfError) as ei:
+            m.stats()
+        assert ei.value.code == b.TSDF_ERR_CAPACITY
+        v1, w1 = m.read()
+        assert np.array_equal(v0, v1) and np.array_equal(w0, w1)
+        b.tsdf_set_option(m.handle, b.TSDF_OPT_POOL_BRICKS, 0)
+        m.integrate(pts, w.poses[0])
+        st = m.stats()
+        v2, w2 = m.read()
+    finally:
+        m.close()
+    vo, wo, so, _ = run_oracle(w.params, [("scan", w.scans[0], w.poses[0])] * 2)
+    assert np.array_equal(v2, vo) and np.array_equal(w2, wo) and st == so[1]
+
+
+def test_pool_map_holds_no_dense_accumulator():
+    """A map used only with the pool reduction never allocates the 8 B/voxel
+    accumulator; switching to the atomic reduction allocates it, and all
+    three reductions interleave on one map with exact results."""
+    from paper_2310_05766_gb300 import binding as b
+    w = synth.workload_outdoor(n_scans=4)
+    p = w.params
+    voxels = p["dims"][0] * p["dims"][1] * p["dims"][2]
+    m = b.TsdfMap(p)
+    try:
+        b.tsdf_set_option(m.handle, b.TSDF_OPT_REDUCTION, b.TSDF_REDUCTION_POOL)
+        steps = workload_steps(w)
+        for i, st in enumerate(steps):
+            if st[0] == "shift":
+                m.shift(st[1])
+                continue
+            if i == 2:
+                pool_bytes = b.tsdf_map_device_bytes(m.handle)
+                assert pool_bytes < voxels * 4 + voxels * 8 // 2, pool_bytes
+                b.tsdf_set_option(m.handle, b.TSDF_OPT_REDUCTION, b.TSDF_REDUCTION_ATOMIC)
+            if i == 3:
+                b.tsdf_set_option(m.handle, b.TSDF_OPT_REDUCTION, b.TSDF_REDUCTION_SORT)
+            m.integrate(torch.from_numpy(st[1]).cuda(), st[2])
+            m.stats()
+        assert b.tsdf_map_device_bytes(m.handle) >= voxels * 12
+        v, wt = m.read()
+    finally:
+        m.close()
+    vo, wo, _, _ = run_oracle(p, steps)
+    assert np.array_equal(v, vo) and np.array_equal(wt, wo)
 
 
 # ---------------------------------------------------------------- alternative readings (map flags)
