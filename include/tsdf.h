@@ -48,6 +48,7 @@ extern "C" {
 #define TSDF_ERR_ADMISSION  -5  /* a session would exceed the device-memory budget */
 #define TSDF_ERR_BUSY       -6  /* the resource is in use (e.g. an outstanding request) */
 #define TSDF_ERR_IO         -7  /* a file could not be opened, read or written, or is not a map file */
+#define TSDF_ERR_DEGENERATE -9  /* registration: too few usable points or no curvature along some direction */
 #define TSDF_ERR_CAPACITY   -8  /* the last scan needed more accumulator bricks than the pool holds; it was
                                    dropped whole (the map is unchanged) */
 
@@ -276,6 +277,37 @@ int tsdf_map_load(const char* path, tsdf_map** out, void* stream);
  * Synchronises `stream`. Errors: INVALID, CUDA. */
 int tsdf_extract_surface(tsdf_map* map, int32_t min_weight, float* out_dev, int64_t capacity, int64_t* count,
                          void* stream);
+
+/* Scan-to-map registration (Gauss-Newton on the map): minimises
+ * sum_i d(T p_i)^2, d the trilinear interpolation of the stored distances
+ * (code * tau / 32767, metres) of the 8 voxels around a point, using the
+ * points whose 8 voxels lie in the window with weights >= min_weight and
+ * whose |d| < tau. Pose update q' = Exp(w) q + v (world frame); residual
+ * Jacobian J = [q x grad d, grad d].
+ *
+ * tsdf_register_system: the normal equations at `pose` (host, row-major
+ * 3x4): out_host[0..20] = H = sum J J^T (upper triangle, row by row),
+ * [21..26] = g = sum J d, [27] = sum d^2, [28] = points used (binary64; the
+ * point position math is binary32 in a fixed order, the rest binary64).
+ * points_dev: n device float4 (16-byte aligned). Synchronises `stream`.
+ *
+ * tsdf_register: up to `iterations` steps from pose_inout (updated in
+ * place after each successful step; solve by Cholesky, stops when the step
+ * norm falls below 1e-7). result may be NULL. Returns TSDF_ERR_DEGENERATE
+ * (pose_inout keeping the last good pose) when a step finds fewer than 6
+ * points or a singular system. Errors: INVALID, DEGENERATE, CUDA. */
+typedef struct tsdf_register_result {
+    int64_t used_points;  /* points in the last evaluated system */
+    double  rms;          /* sqrt(sum d^2 / points) of the last evaluated system, metres */
+    double  step;         /* norm of the last step (w in rad, v in m) */
+    int32_t iterations;   /* steps taken */
+    int32_t reserved;
+} tsdf_register_result;
+
+int tsdf_register_system(tsdf_map* map, const float* points_dev, int64_t n, const float pose[12],
+                         int32_t min_weight, double* out_host, void* stream);
+int tsdf_register(tsdf_map* map, const float* points_dev, int64_t n, float pose_inout[12], int32_t iterations,
+                  int32_t min_weight, tsdf_register_result* result, void* stream);
 
 /* ---- measurement ------------------------------------------------------------
  * Sustained rate (operations per second) of fire-and-forget 64-bit integer

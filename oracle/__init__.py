@@ -99,6 +99,8 @@ def lib():
         L.orc_stats.argtypes = [vp, P(i64)]
         L.orc_store_chunks.restype = i64
         L.orc_store_chunks.argtypes = [vp]
+        L.orc_register_system.restype = None
+        L.orc_register_system.argtypes = [vp, f32p, i64, f32p, ctypes.c_int32, P(ctypes.c_double)]
         L.orc_surface.restype = i64
         L.orc_surface.argtypes = [vp, ctypes.c_int32, f32p, i64]
         L.orc_global_chunks.restype = i64
@@ -168,6 +170,33 @@ def hits(p: dict, points: np.ndarray, pose: np.ndarray, cap: int | None = None, 
     if with_k:
         return g[:m], q[:m], r[:m], k[:m]
     return g[:m], q[:m], r[:m]
+
+
+def pose_update(pose: np.ndarray, system: np.ndarray) -> tuple:
+    """One Gauss-Newton step of scan-to-map registration: solve H xi = -g
+    (Cholesky, float64) for xi = (w, v) and apply q' = Exp(w) q + v to the
+    pose: R' = Exp(w) R, t' = Exp(w) t + v (Rodrigues). Returns (float32 pose
+    12, xi)."""
+    H = np.zeros((6, 6))
+    k = 0
+    for r in range(6):
+        for c in range(r, 6):
+            H[r, c] = H[c, r] = system[k]
+            k += 1
+    g = system[21:27]
+    L = np.linalg.cholesky(H)
+    xi = -np.linalg.solve(L.T, np.linalg.solve(L, g))
+    w, v = xi[:3], xi[3:]
+    th = float(np.linalg.norm(w))
+    K = np.array([[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]])
+    if th < 1e-12:
+        E = np.eye(3) + K
+    else:
+        E = np.eye(3) + np.sin(th) / th * K + (1 - np.cos(th)) / th ** 2 * (K @ K)
+    P = np.asarray(pose, np.float64).reshape(3, 4)
+    R = E @ P[:, :3]
+    t = E @ P[:, 3] + v
+    return np.concatenate([R, t[:, None]], axis=1).astype(np.float32).reshape(12), xi
 
 
 class OracleMap:
@@ -254,6 +283,16 @@ class OracleMap:
         out = np.zeros((max(n, 1), 4), np.float32)
         lib().orc_surface(self.h, min_weight, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n)
         return out[:n]
+
+    def register_system(self, points: np.ndarray, pose: np.ndarray, min_weight: int = 1) -> np.ndarray:
+        """Normal equations of scan-to-map registration at `pose`: float64[29] =
+        H (21 upper-triangle entries, row by row), g (6), cost, point count."""
+        pts_a, pts_p = _f32(points.reshape(-1, 4))
+        pose_a, pose_p = _f32(pose)
+        out = np.zeros(29, np.float64)
+        lib().orc_register_system(self.h, pts_p, pts_a.shape[0], pose_p, min_weight,
+                                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return out
 
     def global_chunks(self):
         """Non-empty 8^3 chunks of the global map (window + store):

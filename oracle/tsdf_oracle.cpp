@@ -636,6 +636,85 @@ int64_t orc_surface(void* h, int32_t min_w, float* out, int64_t cap) {
     return n;
 }
 
+// Scan-to-map registration system (a consumer of the map): for every point,
+// q = R p + t (binary32, the ray set-up's order), u = q / vs - 0.5 (binary32:
+// fm then fs), i0 = floor(u), f = u - i0. If the 8 voxels i0 + {0,1}^3 lie in
+// the window with weights >= min_w and the trilinear interpolation d of their
+// distances (code * tau / 32767, binary64) has |d| < tau, the point adds its
+// residual r = d and Jacobian J = [q x grad d, grad d] (binary64; the pose
+// update q' = q + w x q + v) to H = sum J J^T (21 upper-triangle entries, row
+// by row), g = sum J r (6), cost = sum r^2 and the point count: out[0..28].
+void orc_register_system(void* h, const float* pts, int64_t n, const float pose[12], int32_t min_w, double* out) {
+    OracleMap* m = (OracleMap*)h;
+    for (int i = 0; i < 29; ++i) out[i] = 0.0;
+    const float vs = m->p.voxel_size;
+    const float inv = m->dv.inv_vs;
+    const double scale = (double)m->p.tau / 32767.0;
+    const double tau = (double)m->p.tau;
+    for (int64_t i = 0; i < n; ++i) {
+        const float x = pts[4 * i], y = pts[4 * i + 1], z = pts[4 * i + 2];
+        if (!std::isfinite(x) || !std::isfinite(y) || !std::isfinite(z)) continue;
+        float q[3];
+        for (int a = 0; a < 3; ++a)
+            q[a] = ((pose[4 * a] * x + pose[4 * a + 1] * y) + pose[4 * a + 2] * z) + pose[4 * a + 3];
+        int64_t i0[3];
+        double f[3];
+        for (int a = 0; a < 3; ++a) {
+            const float u = q[a] * inv - 0.5f;
+            const float fl = std::floor(u);
+            i0[a] = (int64_t)fl;
+            f[a] = (double)(u - fl);
+        }
+        double c[2][2][2];
+        bool ok = true;
+        for (int dz = 0; dz < 2 && ok; ++dz)
+        for (int dy = 0; dy < 2 && ok; ++dy)
+        for (int dx = 0; dx < 2 && ok; ++dx) {
+            const int64_t g[3] = {i0[0] + dx, i0[1] + dy, i0[2] + dz};
+            if (!m->inside(g)) { ok = false; break; }
+            const Cell cell = m->win[m->lin(g)];
+            if (cell.w < min_w) { ok = false; break; }
+            c[dz][dy][dx] = (double)cell.v * scale;
+        }
+        if (!ok) continue;
+        const double fx = f[0], fy = f[1], fz = f[2];
+        // interpolation along x, then y, then z
+        double cx[2][2];
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy) cx[dz][dy] = c[dz][dy][0] * (1 - fx) + c[dz][dy][1] * fx;
+        const double cy0 = cx[0][0] * (1 - fy) + cx[0][1] * fy, cy1 = cx[1][0] * (1 - fy) + cx[1][1] * fy;
+        const double d = cy0 * (1 - fz) + cy1 * fz;
+        if (!(std::fabs(d) < tau)) continue;
+        // gradient with respect to u, then q
+        double gu[3] = {0, 0, 0};
+        for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy) {
+            const double wyz = (dy ? fy : 1 - fy) * (dz ? fz : 1 - fz);
+            gu[0] += wyz * (c[dz][dy][1] - c[dz][dy][0]);
+        }
+        for (int dz = 0; dz < 2; ++dz)
+        for (int dx = 0; dx < 2; ++dx) {
+            const double wxz = (dx ? fx : 1 - fx) * (dz ? fz : 1 - fz);
+            gu[1] += wxz * (c[dz][1][dx] - c[dz][0][dx]);
+        }
+        for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+            const double wxy = (dx ? fx : 1 - fx) * (dy ? fy : 1 - fy);
+            gu[2] += wxy * (c[1][dy][dx] - c[0][dy][dx]);
+        }
+        const double gr[3] = {gu[0] / (double)vs, gu[1] / (double)vs, gu[2] / (double)vs};
+        const double qd[3] = {(double)q[0], (double)q[1], (double)q[2]};
+        const double J[6] = {qd[1] * gr[2] - qd[2] * gr[1], qd[2] * gr[0] - qd[0] * gr[2], qd[0] * gr[1] - qd[1] * gr[0],
+                             gr[0], gr[1], gr[2]};
+        int k = 0;
+        for (int r = 0; r < 6; ++r)
+            for (int cc = r; cc < 6; ++cc) out[k++] += J[r] * J[cc];
+        for (int r = 0; r < 6; ++r) out[21 + r] += J[r] * d;
+        out[27] += d * d;
+        out[28] += 1.0;
+    }
+}
+
 // The global map as non-empty 8^3 chunks: every window chunk with a non-zero
 // cell, then every stored chunk outside the window (a stored copy of a chunk
 // that is back in the window is stale). Writes up to `cap` chunks: key (the

@@ -23,6 +23,7 @@ TSDF_ERR_ADMISSION = -5
 TSDF_ERR_BUSY = -6
 TSDF_ERR_IO = -7
 TSDF_ERR_CAPACITY = -8
+TSDF_ERR_DEGENERATE = -9
 TSDF_REDUCE_WSUM = 0
 TSDF_REDUCE_MIN_ABS = 1
 TSDF_FLAG_STEP_VALUE = 1
@@ -64,6 +65,11 @@ class tsdf_params(ctypes.Structure):
 
 class tsdf_scan_stats(ctypes.Structure):
     _fields_ = [("valid_rays", ctypes.c_int64), ("hits", ctypes.c_int64), ("touched", ctypes.c_int64)]
+
+
+class tsdf_register_result(ctypes.Structure):
+    _fields_ = [("used_points", ctypes.c_int64), ("rms", ctypes.c_double), ("step", ctypes.c_double),
+                ("iterations", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class tsdf_kernel_time(ctypes.Structure):
@@ -123,6 +129,8 @@ def lib():
     L.tsdf_probe_reduction_rate.argtypes = [ctypes.c_int32, P(ctypes.c_double), vp]
     L.tsdf_map_save.argtypes = [vp, ctypes.c_char_p, vp]
     L.tsdf_map_device_bytes.argtypes = [vp, P(i64)]
+    L.tsdf_register_system.argtypes = [vp, vp, i64, f32p, ctypes.c_int32, P(ctypes.c_double), vp]
+    L.tsdf_register.argtypes = [vp, vp, i64, f32p, ctypes.c_int32, ctypes.c_int32, P(tsdf_register_result), vp]
     L.tsdf_extract_surface.argtypes = [vp, ctypes.c_int32, vp, i64, P(i64), vp]
     L.tsdf_map_load.argtypes = [ctypes.c_char_p, P(vp), vp]
     L.tsdf_batch_create.argtypes = [ctypes.c_int32, P(vp)]
@@ -147,7 +155,7 @@ def lib():
     for name in ("tsdf_map_create", "tsdf_map_destroy", "tsdf_integrate", "tsdf_integrate_host", "tsdf_shift",
                  "tsdf_read", "tsdf_write", "tsdf_stats", "tsdf_get_origin", "tsdf_grid_device_ptr",
                  "tsdf_last_cuda_error", "tsdf_profile_enable", "tsdf_profile_read", "tsdf_set_option",
-                 "tsdf_integrate_static", "tsdf_probe_reduction_rate", "tsdf_map_save", "tsdf_map_load", "tsdf_extract_surface", "tsdf_map_device_bytes", "tsdf_batch_create", "tsdf_batch_destroy", "tsdf_batch_set_option",
+                 "tsdf_integrate_static", "tsdf_probe_reduction_rate", "tsdf_map_save", "tsdf_map_load", "tsdf_extract_surface", "tsdf_map_device_bytes", "tsdf_register_system", "tsdf_register", "tsdf_batch_create", "tsdf_batch_destroy", "tsdf_batch_set_option",
                  "tsdf_batch_get_config", "tsdf_batch_integrate", "tsdf_integrate_batch", "tsdf_batch_sync",
                  "tsdf_server_create", "tsdf_server_destroy", "tsdf_server_open_session", "tsdf_server_close_session",
                  "tsdf_server_submit", "tsdf_server_wait", "tsdf_server_session_map", "tsdf_server_get_stats"):
@@ -435,6 +443,26 @@ def tsdf_extract_surface(handle: int, min_weight: int = 1, out=None, stream=None
                                       _stream_ptr(stream)), "tsdf_extract_surface")
     n = int(cnt.value)
     return out[:min(n, out.shape[0])], n
+
+
+def tsdf_register_system(handle: int, points_dev, pose, min_weight: int = 1, stream=None) -> np.ndarray:
+    """Normal equations of scan-to-map registration at `pose`: float64[29]."""
+    out = np.zeros(29, np.float64)
+    pa, pp = _pose_arg(pose)
+    _check(lib().tsdf_register_system(handle, points_dev.data_ptr(), points_dev.shape[0], pp, min_weight,
+                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream_ptr(stream)),
+           "tsdf_register_system")
+    return out
+
+
+def tsdf_register(handle: int, points_dev, pose, iterations: int = 10, min_weight: int = 1, stream=None):
+    """Gauss-Newton scan-to-map registration from `pose`; returns (float32 pose[12], result dict)."""
+    pose_a = (ctypes.c_float * 12)(*[float(x) for x in np.asarray(pose, np.float32).reshape(12)])
+    res = tsdf_register_result()
+    _check(lib().tsdf_register(handle, points_dev.data_ptr(), points_dev.shape[0], pose_a, iterations, min_weight,
+                               ctypes.byref(res), _stream_ptr(stream)), "tsdf_register")
+    return np.array(pose_a[:], np.float32), dict(used_points=res.used_points, rms=res.rms, step=res.step,
+                                                  iterations=res.iterations)
 
 
 def tsdf_map_device_bytes(handle: int) -> int:

@@ -113,6 +113,7 @@ struct tsdf_map {
     int reduction = TSDF_REDUCTION_ATOMIC;   // per-scan reduction: accumulator atomics or sort
     bool zero_copy = true;          // tsdf_integrate_host reads device-mapped pinned points in place
     long long* host_last = nullptr; // mapped pinned copy of the published counters (host address)
+    double* reg_dev = nullptr;      // registration: the 29 sums of the normal equations
     size_t pair_cap_req = 0;        // sort reduction: requested pair capacity, 0 = from the scan size
     size_t pool_req = 0;            // pool reduction: requested slots, 0 = default
     size_t ray_slot_cap = 0;        // entries of dev.ray_slot
@@ -211,6 +212,7 @@ void free_map(tsdf_map* m) {
     cudaFree(m->dev.ray_b);
     cudaFree(m->dev.ctr);
     if (m->host_last) cudaFreeHost(m->host_last);
+    cudaFree(m->reg_dev);
     cudaFree(m->dev.pool_table);
     cudaFree(m->dev.pool_brick);
     cudaFree(m->dev.pool_acc);
@@ -991,6 +993,55 @@ int tsdf_map_load(const char* path, tsdf_map** out, void* stream) {
     return TSDF_OK;
 }
 
+int tsdf_register_system(tsdf_map* map, const float* points_dev, int64_t n, const float pose[12],
+                         int32_t min_weight, double* out_host, void* stream) {
+    if (!map || !pose || !out_host || n < 0 || n > TSDF_MAX_POINTS || min_weight < 1 || min_weight > 32767)
+        return TSDF_ERR_INVALID;
+    if (n > 0 && (!points_dev || ((uintptr_t)points_dev & 15u) != 0)) return TSDF_ERR_INVALID;
+    for (int i = 0; i < 12; ++i)
+        if (!std::isfinite(pose[i])) return TSDF_ERR_INVALID;
+    DeviceScope ds(map->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!map->reg_dev) TSDF_CU(cudaMalloc(&map->reg_dev, 29 * sizeof(double)));
+    const long long o[3] = {map->origin[0], map->origin[1], map->origin[2]};
+    TSDF_CU(launch_register(points_dev, (int)n, pose, map->dev.grid, map->geom, o, map->p.voxel_size, map->inv_vs,
+                            map->p.tau, min_weight, map->reg_dev, s));
+    TSDF_CU(cudaMemcpyAsync(out_host, map->reg_dev, 29 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TSDF_CU(cudaStreamSynchronize(s));
+    return TSDF_OK;
+}
+
+int tsdf_register(tsdf_map* map, const float* points_dev, int64_t n, float pose_inout[12], int32_t iterations,
+                  int32_t min_weight, tsdf_register_result* result, void* stream) {
+    if (!pose_inout || iterations < 1 || iterations > 1000) return TSDF_ERR_INVALID;
+    float pose[12];
+    std::memcpy(pose, pose_inout, sizeof(pose));
+    double sys[29];
+    tsdf_register_result res{};
+    int it = 0;
+    for (; it < iterations; ++it) {
+        int rc = tsdf_register_system(map, points_dev, n, pose, min_weight, sys, stream);
+        if (rc != TSDF_OK) return rc;
+        res.used_points = (int64_t)sys[28];
+        res.rms = sys[28] > 0 ? std::sqrt(sys[27] / sys[28]) : 0.0;
+        double step = 0.0;
+        if (sys[28] < 6 || !register_step(sys, pose, &step)) {
+            res.iterations = it;
+            if (result) *result = res;
+            return TSDF_ERR_DEGENERATE;   // too few points or no curvature in some direction: pose unchanged
+        }
+        res.step = step;
+        std::memcpy(pose_inout, pose, sizeof(pose));
+        if (step < 1e-7) {
+            ++it;
+            break;
+        }
+    }
+    res.iterations = it;
+    if (result) *result = res;
+    return TSDF_OK;
+}
+
 int tsdf_extract_surface(tsdf_map* map, int32_t min_weight, float* out_dev, int64_t capacity, int64_t* count,
                          void* stream) {
     if (!map || !count || min_weight < 1 || min_weight > 32767 || capacity < 0) return TSDF_ERR_INVALID;
@@ -1050,6 +1101,7 @@ const char* tsdf_error_string(int code) {
         case TSDF_ERR_BUSY: return "resource busy";
         case TSDF_ERR_IO: return "file error or not a map file";
         case TSDF_ERR_CAPACITY: return "scan dropped: the accumulator pool is full";
+        case TSDF_ERR_DEGENERATE: return "registration is degenerate (too few observed points)";
         default: return "unknown error";
     }
 }
