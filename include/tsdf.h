@@ -278,6 +278,24 @@ int tsdf_map_load(const char* path, tsdf_map** out, void* stream);
 int tsdf_extract_surface(tsdf_map* map, int32_t min_weight, float* out_dev, int64_t capacity, int64_t* count,
                          void* stream);
 
+/* Triangle mesh of the window's zero level set by marching tetrahedra. Dual
+ * cubes have their corners at the centres of voxels a + {0,1}^3 (all 8 in the
+ * window with weights >= min_weight); each is split into 6 tetrahedra around
+ * its 000-111 diagonal, one per axis order (i, j, k) in lexicographic order:
+ * 000, e_i, e_i + e_j, 111. A tetrahedron whose corners differ in sign
+ * (v < 0) gives one triangle (one corner against three) or two (two against
+ * two: negatives a < b, positives c < d in tetrahedron order: (a,c),(a,d),(b,d)
+ * and (a,c),(b,d),(b,c)). A vertex on the edge from the negative corner P to
+ * the positive corner Q: t = v_P / (v_P - v_Q), coordinate ((float)g_P + 0.5
+ * + t (g_Q - g_P)) * voxel_size (binary32), so a shared edge gives the same
+ * vertex in every tetrahedron and the mesh is closed where the surface is.
+ * Triangles face the positive side. out_dev: device floats, 9 per triangle
+ * (3 vertices x y z, world metres); `capacity` triangles; the order is
+ * unspecified; *count gets the number found. Synchronises `stream`.
+ * Errors: INVALID, CUDA. */
+int tsdf_extract_mesh(tsdf_map* map, int32_t min_weight, float* out_dev, int64_t capacity, int64_t* count,
+                      void* stream);
+
 /* Scan-to-map registration (Gauss-Newton on the map): minimises
  * sum_i d(T p_i)^2, d the trilinear interpolation of the stored distances
  * (code * tau / 32767, metres) of the 8 voxels around a point, using the

@@ -101,6 +101,8 @@ def lib():
         L.orc_store_chunks.argtypes = [vp]
         L.orc_register_system.restype = None
         L.orc_register_system.argtypes = [vp, f32p, i64, f32p, ctypes.c_int32, P(ctypes.c_double)]
+        L.orc_mesh.restype = i64
+        L.orc_mesh.argtypes = [vp, ctypes.c_int32, f32p, i64]
         L.orc_surface.restype = i64
         L.orc_surface.argtypes = [vp, ctypes.c_int32, f32p, i64]
         L.orc_global_chunks.restype = i64
@@ -293,6 +295,13 @@ class OracleMap:
         lib().orc_register_system(self.h, pts_p, pts_a.shape[0], pose_p, min_weight,
                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         return out
+
+    def mesh(self, min_weight: int = 1) -> np.ndarray:
+        """Marching-tetrahedra triangles of the window's zero level set: float32 (n, 3, 3)."""
+        n = int(lib().orc_mesh(self.h, min_weight, None, 0))
+        out = np.zeros((max(n, 1), 3, 3), np.float32)
+        lib().orc_mesh(self.h, min_weight, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n)
+        return out[:n]
 
     def global_chunks(self):
         """Non-empty 8^3 chunks of the global map (window + store):

@@ -636,6 +636,117 @@ int64_t orc_surface(void* h, int32_t min_w, float* out, int64_t cap) {
     return n;
 }
 
+// Triangle mesh of the zero level set by marching tetrahedra (a consumer of
+// the map). Cubes of the dual grid: corners at the centres of voxels
+// a + {0,1}^3, all 8 inside the window with weights >= min_w. Each cube is
+// split into 6 tetrahedra sharing its diagonal 000-111, one per axis order
+// (i, j, k): 000, e_i, e_i + e_j, 111 (orders in lexicographic order of
+// (i, j, k)). In a tetrahedron with corner signs n = (v < 0): one corner
+// against three gives a triangle on the three edges leaving it; two against
+// two a quad on the four mixed edges (two triangles: (a,c),(a,d),(b,d) and
+// (a,c),(b,d),(b,c) for negatives a < b and positives c < d in tetrahedron
+// order). A vertex on edge P-Q, P the negative end (so a shared edge gives
+// the same vertex in every tetrahedron): t = v_P / (v_P - v_Q), coordinate
+// ((float)g_P + 0.5 + t * (g_Q - g_P)) * vs per axis (binary32). Each
+// triangle is oriented so that its normal (binary64 cross product of its
+// binary32 vertices) points towards the tetrahedron's positive corners.
+// Writes up to cap triangles as 9 floats; returns the number found.
+namespace {
+const int kTetAxes[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+}
+
+int64_t orc_mesh(void* h, int32_t min_w, float* out, int64_t cap) {
+    OracleMap* m = (OracleMap*)h;
+    const float vs = m->p.voxel_size;
+    int64_t n = 0;
+    auto vertex = [&](const int64_t gp[3], int vp, const int64_t gq[3], int vq, float* o) {
+        const float t = (float)vp / (float)(vp - vq);
+        for (int a = 0; a < 3; ++a) o[a] = (((float)gp[a] + 0.5f) + t * (float)(gq[a] - gp[a])) * vs;
+    };
+    for (int64_t z = 0; z + 1 < m->Z(); ++z)
+    for (int64_t y = 0; y + 1 < m->Y(); ++y)
+    for (int64_t x = 0; x + 1 < m->X(); ++x) {
+        const int64_t base[3] = {m->origin[0] + x, m->origin[1] + y, m->origin[2] + z};
+        int val[2][2][2];
+        bool ok = true;
+        for (int dz = 0; dz < 2 && ok; ++dz)
+        for (int dy = 0; dy < 2 && ok; ++dy)
+        for (int dx = 0; dx < 2 && ok; ++dx) {
+            const int64_t g[3] = {base[0] + dx, base[1] + dy, base[2] + dz};
+            const Cell c = m->win[m->lin(g)];
+            if (c.w < min_w) ok = false;
+            val[dz][dy][dx] = c.v;
+        }
+        if (!ok) continue;
+        for (int tt = 0; tt < 6; ++tt) {
+            int off[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {1, 1, 1}};
+            off[1][kTetAxes[tt][0]] = 1;
+            off[2][kTetAxes[tt][0]] = 1;
+            off[2][kTetAxes[tt][1]] = 1;
+            int64_t g[4][3];
+            int v[4];
+            int neg = 0;
+            for (int k = 0; k < 4; ++k) {
+                for (int a = 0; a < 3; ++a) g[k][a] = base[a] + off[k][a];
+                v[k] = val[off[k][2]][off[k][1]][off[k][0]];
+                neg += v[k] < 0 ? 1 : 0;
+            }
+            if (neg == 0 || neg == 4) continue;
+            float tri[2][3][3];
+            int nt = 0;
+            if (neg == 1 || neg == 3) {
+                int lone = 0;
+                for (int k = 0; k < 4; ++k)
+                    if ((v[k] < 0) == (neg == 1)) lone = k;
+                int e = 0;   // every edge is interpolated from its negative end
+                for (int k = 0; k < 4; ++k) {
+                    if (k == lone) continue;
+                    if (neg == 1) vertex(g[lone], v[lone], g[k], v[k], tri[0][e++]);
+                    else vertex(g[k], v[k], g[lone], v[lone], tri[0][e++]);
+                }
+                nt = 1;
+            } else {
+                int ng[2], ps[2], a = 0, b = 0;
+                for (int k = 0; k < 4; ++k) {
+                    if (v[k] < 0) ng[a++] = k;
+                    else ps[b++] = k;
+                }
+                float ac[3], ad[3], bd[3], bc[3];
+                vertex(g[ng[0]], v[ng[0]], g[ps[0]], v[ps[0]], ac);
+                vertex(g[ng[0]], v[ng[0]], g[ps[1]], v[ps[1]], ad);
+                vertex(g[ng[1]], v[ng[1]], g[ps[1]], v[ps[1]], bd);
+                vertex(g[ng[1]], v[ng[1]], g[ps[0]], v[ps[0]], bc);
+                for (int a2 = 0; a2 < 3; ++a2) {
+                    tri[0][0][a2] = ac[a2]; tri[0][1][a2] = ad[a2]; tri[0][2][a2] = bd[a2];
+                    tri[1][0][a2] = ac[a2]; tri[1][1][a2] = bd[a2]; tri[1][2][a2] = bc[a2];
+                }
+                nt = 2;
+            }
+            // direction towards the positive corners: their mean minus the negatives' mean
+            double dir[3] = {0, 0, 0};
+            for (int k = 0; k < 4; ++k)
+                for (int a2 = 0; a2 < 3; ++a2)
+                    dir[a2] += (v[k] < 0 ? -1.0 / neg : 1.0 / (4 - neg)) * (double)off[k][a2];
+            for (int r = 0; r < nt; ++r) {
+                const double e1[3] = {(double)tri[r][1][0] - tri[r][0][0], (double)tri[r][1][1] - tri[r][0][1],
+                                      (double)tri[r][1][2] - tri[r][0][2]};
+                const double e2[3] = {(double)tri[r][2][0] - tri[r][0][0], (double)tri[r][2][1] - tri[r][0][1],
+                                      (double)tri[r][2][2] - tri[r][0][2]};
+                const double nx = e1[1] * e2[2] - e1[2] * e2[1], ny = e1[2] * e2[0] - e1[0] * e2[2],
+                             nz = e1[0] * e2[1] - e1[1] * e2[0];
+                const bool flip = nx * dir[0] + ny * dir[1] + nz * dir[2] < 0.0;
+                if (n < cap) {
+                    const int order[3] = {0, flip ? 2 : 1, flip ? 1 : 2};
+                    for (int c = 0; c < 3; ++c)
+                        for (int a2 = 0; a2 < 3; ++a2) out[9 * n + 3 * c + a2] = tri[r][order[c]][a2];
+                }
+                ++n;
+            }
+        }
+    }
+    return n;
+}
+
 // Scan-to-map registration system (a consumer of the map): for every point,
 // q = R p + t (binary32, the ray set-up's order), u = q / vs - 0.5 (binary32:
 // fm then fs), i0 = floor(u), f = u - i0. If the 8 voxels i0 + {0,1}^3 lie in

@@ -129,6 +129,7 @@ def lib():
     L.tsdf_probe_reduction_rate.argtypes = [ctypes.c_int32, P(ctypes.c_double), vp]
     L.tsdf_map_save.argtypes = [vp, ctypes.c_char_p, vp]
     L.tsdf_map_device_bytes.argtypes = [vp, P(i64)]
+    L.tsdf_extract_mesh.argtypes = [vp, ctypes.c_int32, vp, i64, P(i64), vp]
     L.tsdf_register_system.argtypes = [vp, vp, i64, f32p, ctypes.c_int32, P(ctypes.c_double), vp]
     L.tsdf_register.argtypes = [vp, vp, i64, f32p, ctypes.c_int32, ctypes.c_int32, P(tsdf_register_result), vp]
     L.tsdf_extract_surface.argtypes = [vp, ctypes.c_int32, vp, i64, P(i64), vp]
@@ -155,7 +156,7 @@ def lib():
     for name in ("tsdf_map_create", "tsdf_map_destroy", "tsdf_integrate", "tsdf_integrate_host", "tsdf_shift",
                  "tsdf_read", "tsdf_write", "tsdf_stats", "tsdf_get_origin", "tsdf_grid_device_ptr",
                  "tsdf_last_cuda_error", "tsdf_profile_enable", "tsdf_profile_read", "tsdf_set_option",
-                 "tsdf_integrate_static", "tsdf_probe_reduction_rate", "tsdf_map_save", "tsdf_map_load", "tsdf_extract_surface", "tsdf_map_device_bytes", "tsdf_register_system", "tsdf_register", "tsdf_batch_create", "tsdf_batch_destroy", "tsdf_batch_set_option",
+                 "tsdf_integrate_static", "tsdf_probe_reduction_rate", "tsdf_map_save", "tsdf_map_load", "tsdf_extract_surface", "tsdf_map_device_bytes", "tsdf_register_system", "tsdf_register", "tsdf_extract_mesh", "tsdf_batch_create", "tsdf_batch_destroy", "tsdf_batch_set_option",
                  "tsdf_batch_get_config", "tsdf_batch_integrate", "tsdf_integrate_batch", "tsdf_batch_sync",
                  "tsdf_server_create", "tsdf_server_destroy", "tsdf_server_open_session", "tsdf_server_close_session",
                  "tsdf_server_submit", "tsdf_server_wait", "tsdf_server_session_map", "tsdf_server_get_stats"):
@@ -445,6 +446,22 @@ def tsdf_extract_surface(handle: int, min_weight: int = 1, out=None, stream=None
     return out[:min(n, out.shape[0])], n
 
 
+def tsdf_extract_mesh(handle: int, min_weight: int = 1, out=None, stream=None):
+    """Marching-tetrahedra triangles of the window. out: CUDA float32 (cap, 3, 3)
+    tensor or None (sized with a counting call first). Returns (triangles view, count)."""
+    import torch
+    cnt = ctypes.c_int64()
+    if out is None:
+        _check(lib().tsdf_extract_mesh(handle, min_weight, None, 0, ctypes.byref(cnt), _stream_ptr(stream)),
+               "tsdf_extract_mesh")
+        out = torch.empty((max(int(cnt.value), 1), 3, 3), dtype=torch.float32, device="cuda")
+    assert out.dtype == torch.float32 and out.is_contiguous() and tuple(out.shape[1:]) == (3, 3)
+    _check(lib().tsdf_extract_mesh(handle, min_weight, out.data_ptr(), out.shape[0], ctypes.byref(cnt),
+                                   _stream_ptr(stream)), "tsdf_extract_mesh")
+    n = int(cnt.value)
+    return out[:min(n, out.shape[0])], n
+
+
 def tsdf_register_system(handle: int, points_dev, pose, min_weight: int = 1, stream=None) -> np.ndarray:
     """Normal equations of scan-to-map registration at `pose`: float64[29]."""
     out = np.zeros(29, np.float64)
@@ -565,6 +582,10 @@ class TsdfMap:
     def surface(self, min_weight: int = 1, stream=None):
         """Zero-crossing points (x, y, z, axis) as a CUDA float32 tensor."""
         return tsdf_extract_surface(self.handle, min_weight, None, stream)[0]
+
+    def mesh(self, min_weight: int = 1, stream=None):
+        """Marching-tetrahedra triangles (n, 3, 3) as a CUDA float32 tensor."""
+        return tsdf_extract_mesh(self.handle, min_weight, None, stream)[0]
 
     def save(self, path: str, stream=None):
         tsdf_map_save(self.handle, path, stream)

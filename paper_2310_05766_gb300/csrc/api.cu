@@ -993,6 +993,24 @@ int tsdf_map_load(const char* path, tsdf_map** out, void* stream) {
     return TSDF_OK;
 }
 
+int tsdf_extract_mesh(tsdf_map* map, int32_t min_weight, float* out_dev, int64_t capacity, int64_t* count,
+                      void* stream) {
+    if (!map || !count || min_weight < 1 || min_weight > 32767 || capacity < 0) return TSDF_ERR_INVALID;
+    if (capacity > 0 && (!out_dev || ((uintptr_t)out_dev & 3u) != 0)) return TSDF_ERR_INVALID;
+    DeviceScope ds(map->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long* cnt = &map->dev.ctr->surface_count;
+    TSDF_CU(cudaMemsetAsync(cnt, 0, sizeof(*cnt), s));
+    const long long o[3] = {map->origin[0], map->origin[1], map->origin[2]};
+    TSDF_CU(launch_mesh(map->dev.grid, map->geom, o, min_weight, map->p.voxel_size, out_dev,
+                        (unsigned long long)capacity, cnt, s));
+    unsigned long long n = 0;
+    TSDF_CU(cudaMemcpyAsync(&n, cnt, sizeof(n), cudaMemcpyDeviceToHost, s));
+    TSDF_CU(cudaStreamSynchronize(s));
+    *count = (int64_t)n;
+    return TSDF_OK;
+}
+
 int tsdf_register_system(tsdf_map* map, const float* points_dev, int64_t n, const float pose[12],
                          int32_t min_weight, double* out_host, void* stream) {
     if (!map || !pose || !out_host || n < 0 || n > TSDF_MAX_POINTS || min_weight < 1 || min_weight > 32767)

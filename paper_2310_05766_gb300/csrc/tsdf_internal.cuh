@@ -166,6 +166,8 @@ cudaError_t launch_register(const float* pts_dev, int n, const float pose[12], c
                             const WindowGeom& geo, const long long origin[3], float vs, float inv_vs, float tau,
                             int min_w, double* out_dev, cudaStream_t s);
 bool register_step(const double sys[29], float pose[12], double* step_norm);
+cudaError_t launch_mesh(const uint32_t* grid, const WindowGeom& geo, const long long origin[3], int min_w, float vs,
+                        float* out, unsigned long long cap, unsigned long long* count, cudaStream_t s);
 cudaError_t launch_surface(const uint32_t* grid, const WindowGeom& geo, const long long origin[3], int min_w, float vs,
                            float4* out, unsigned long long cap, unsigned long long* count, cudaStream_t s);
 cudaError_t launch_read_box(const uint32_t* grid, const long long lo[3], const uint32_t box[3],

@@ -77,3 +77,41 @@ def test_surface_capacity_and_arguments():
                 b.tsdf_extract_surface(m.handle, opt, small)
     finally:
         m.close()
+
+
+def _canon_tris(t):
+    """Triangles as sorted rows, each rotated so its smallest vertex comes first
+    (keeps the orientation)."""
+    t = np.asarray(t, np.float32).reshape(-1, 3, 3)
+    out = []
+    for tri in t:
+        k = min(range(3), key=lambda i: tuple(tri[i]))
+        r = np.roll(tri, -k, axis=0)
+        out.append(r.reshape(9))
+    out = np.array(out, np.float32).reshape(-1, 9)
+    return out[np.lexsort(out.T[::-1])]
+
+
+@pytest.mark.parametrize("min_weight", [1, 3])
+def test_mesh_room_exact(min_weight):
+    w = synth.workload_room()
+    m, om = _build(w.params, workload_steps(w) + [("scan", w.scans[0], w.poses[0])])
+    try:
+        got = m.mesh(min_weight).cpu().numpy()
+        ref = om.mesh(min_weight)
+        assert len(ref) > (5000 if min_weight == 1 else 1000)
+        assert np.array_equal(_canon_tris(got), _canon_tris(ref))
+    finally:
+        m.close()
+
+
+def test_mesh_outdoor_after_shift_exact():
+    w = synth.workload_outdoor(n_scans=12)
+    m, om = _build(w.params, workload_steps(w))
+    try:
+        got = m.mesh().cpu().numpy()
+        ref = om.mesh()
+        assert len(ref) > 100000
+        assert np.array_equal(_canon_tris(got), _canon_tris(ref))
+    finally:
+        m.close()
