@@ -191,6 +191,9 @@ int tsdf_stats(tsdf_map* map, tsdf_scan_stats* out, void* stream);
                                    accumulator is never allocated for a map used only this way. A scan that
                                    needs more bricks than the pool holds is dropped whole and tsdf_stats
                                    returns TSDF_ERR_CAPACITY. Same results as the other reductions. */
+#define TSDF_REDUCTION_AUTO   3  /* the atomic and the sort reduction are each run once untimed and then
+                                   timed (CUDA events) on the next calls; once every trial has finished
+                                   the faster one is used from then on (tsdf_get_reduction tells which) */
 #define TSDF_OPT_POOL_BRICKS  7  /* pool reduction: slots of the pool (64 .. bricks of the window); 0 (default):
                                    an eighth of the window's bricks, at least 16384 */
 
@@ -198,6 +201,11 @@ int tsdf_stats(tsdf_map* map, tsdf_scan_stats* out, void* stream);
  * that have been used, ray buffers, global store) in bytes. Host-side.
  * Errors: INVALID. */
 int tsdf_map_device_bytes(const tsdf_map* map, int64_t* out);
+
+/* The reduction in use: the option's value, or for TSDF_REDUCTION_AUTO the
+ * one chosen (TSDF_REDUCTION_AUTO while the trials still run). Host-side
+ * (looks at finished trial events without waiting). Errors: INVALID. */
+int tsdf_get_reduction(tsdf_map* map, int32_t* reduction);
 
 /* Set a tuning option of a map; takes effect for later calls. Host-side
  * state only (the sort buffers are allocated by the next integrate call).

@@ -38,6 +38,7 @@ TSDF_OPT_HOST_ZERO_COPY = 6
 TSDF_REDUCTION_ATOMIC = 0
 TSDF_REDUCTION_SORT = 1
 TSDF_REDUCTION_POOL = 2
+TSDF_REDUCTION_AUTO = 3
 TSDF_OPT_POOL_BRICKS = 7
 TSDF_BATCH_OPT_GRAPH = 1
 TSDF_BATCH_OPT_AUTOTUNE = 2
@@ -129,6 +130,7 @@ def lib():
     L.tsdf_probe_reduction_rate.argtypes = [ctypes.c_int32, P(ctypes.c_double), vp]
     L.tsdf_map_save.argtypes = [vp, ctypes.c_char_p, vp]
     L.tsdf_map_device_bytes.argtypes = [vp, P(i64)]
+    L.tsdf_get_reduction.argtypes = [vp, P(ctypes.c_int32)]
     L.tsdf_extract_mesh.argtypes = [vp, ctypes.c_int32, vp, i64, P(i64), vp]
     L.tsdf_register_system.argtypes = [vp, vp, i64, f32p, ctypes.c_int32, P(ctypes.c_double), vp]
     L.tsdf_register.argtypes = [vp, vp, i64, f32p, ctypes.c_int32, ctypes.c_int32, P(tsdf_register_result), vp]
@@ -156,7 +158,7 @@ def lib():
     for name in ("tsdf_map_create", "tsdf_map_destroy", "tsdf_integrate", "tsdf_integrate_host", "tsdf_shift",
                  "tsdf_read", "tsdf_write", "tsdf_stats", "tsdf_get_origin", "tsdf_grid_device_ptr",
                  "tsdf_last_cuda_error", "tsdf_profile_enable", "tsdf_profile_read", "tsdf_set_option",
-                 "tsdf_integrate_static", "tsdf_probe_reduction_rate", "tsdf_map_save", "tsdf_map_load", "tsdf_extract_surface", "tsdf_map_device_bytes", "tsdf_register_system", "tsdf_register", "tsdf_extract_mesh", "tsdf_batch_create", "tsdf_batch_destroy", "tsdf_batch_set_option",
+                 "tsdf_integrate_static", "tsdf_probe_reduction_rate", "tsdf_map_save", "tsdf_map_load", "tsdf_extract_surface", "tsdf_map_device_bytes", "tsdf_register_system", "tsdf_register", "tsdf_extract_mesh", "tsdf_get_reduction", "tsdf_batch_create", "tsdf_batch_destroy", "tsdf_batch_set_option",
                  "tsdf_batch_get_config", "tsdf_batch_integrate", "tsdf_integrate_batch", "tsdf_batch_sync",
                  "tsdf_server_create", "tsdf_server_destroy", "tsdf_server_open_session", "tsdf_server_close_session",
                  "tsdf_server_submit", "tsdf_server_wait", "tsdf_server_session_map", "tsdf_server_get_stats"):
@@ -444,6 +446,12 @@ def tsdf_extract_surface(handle: int, min_weight: int = 1, out=None, stream=None
                                       _stream_ptr(stream)), "tsdf_extract_surface")
     n = int(cnt.value)
     return out[:min(n, out.shape[0])], n
+
+
+def tsdf_get_reduction(handle: int) -> int:
+    out = ctypes.c_int32()
+    _check(lib().tsdf_get_reduction(handle, ctypes.byref(out)), "tsdf_get_reduction")
+    return int(out.value)
 
 
 def tsdf_extract_mesh(handle: int, min_weight: int = 1, out=None, stream=None):

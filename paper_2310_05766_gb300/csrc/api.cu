@@ -116,6 +116,21 @@ struct tsdf_map {
     double* reg_dev = nullptr;      // registration: the 29 sums of the normal equations
     size_t pair_cap_req = 0;        // sort reduction: requested pair capacity, 0 = from the scan size
     size_t pool_req = 0;            // pool reduction: requested slots, 0 = default
+    // TSDF_REDUCTION_AUTO: the atomic and the sort reduction are timed on the
+    // first calls (one untimed call each, then kAutoTrials timed) and the
+    // faster one is kept
+    static constexpr int kAutoCandidates = 2;
+    static constexpr int kAutoTrials = 3;
+    static constexpr int kAutoReduction[kAutoCandidates] = {TSDF_REDUCTION_ATOMIC, TSDF_REDUCTION_SORT};
+    struct AutoTrial {
+        int candidate;
+        cudaEvent_t start, stop;
+    };
+    std::vector<AutoTrial> auto_trials;
+    int auto_started[kAutoCandidates] = {};
+    int auto_timed[kAutoCandidates] = {};
+    float auto_best[kAutoCandidates] = {};
+    int auto_choice = -1;           // decided reduction, -1 while tuning
     size_t ray_slot_cap = 0;        // entries of dev.ray_slot
     // optional per-kernel event timing
     bool prof = false;
@@ -204,6 +219,10 @@ void free_map(tsdf_map* m) {
         cudaEventDestroy(p.stop);
     }
     for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
+    for (auto& t : m->auto_trials) {
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
     cudaFree(m->dev.grid);
     cudaFree(m->dev.acc);
     cudaFree(m->dev.brick_flag);
@@ -458,14 +477,14 @@ static void fill_scan_args(const tsdf_map* map, const float* points_dev, int64_t
     a.flags = map->p.flags;
 }
 
-static int integrate_dev(tsdf_map* map, const float* points_dev, int64_t n, const float pose[12],
-                         cudaStream_t s) {
+static int integrate_with(tsdf_map* map, const float* points_dev, int64_t n, const float pose[12], cudaStream_t s,
+                          int reduction) {
     int rc = ensure_rays(map, n);
     if (rc != TSDF_OK) return rc;
     ScanArgs a;
     fill_scan_args(map, points_dev, n, pose, a);
     const bool pdl = map->pdl;
-    if (map->reduction == TSDF_REDUCTION_POOL) {
+    if (reduction == TSDF_REDUCTION_POOL) {
         rc = ensure_pool(map);
         if (rc != TSDF_OK) return rc;
         const MapDev& d = map->dev;
@@ -485,7 +504,7 @@ static int integrate_dev(tsdf_map* map, const float* points_dev, int64_t n, cons
     }
     rc = ensure_acc(map);
     if (rc != TSDF_OK) return rc;
-    if (map->reduction == TSDF_REDUCTION_SORT) {
+    if (reduction == TSDF_REDUCTION_SORT) {
         rc = ensure_sort(map, n);
         if (rc != TSDF_OK) return rc;
         const MapDev& d = map->dev;
@@ -524,6 +543,60 @@ static int integrate_dev(tsdf_map* map, const float* points_dev, int64_t n, cons
     prof_push(map, kContrib, e2, e3);
     prof_push(map, kApply, e4, e5);
     return TSDF_OK;
+}
+
+// TSDF_REDUCTION_AUTO: collect finished trials without waiting and decide
+// once every candidate has enough of them (the fastest by its best time).
+static void auto_harvest(tsdf_map* map) {
+    std::vector<tsdf_map::AutoTrial> keep;
+    for (auto& t : map->auto_trials) {
+        if (cudaEventQuery(t.stop) != cudaSuccess) {
+            keep.push_back(t);
+            continue;
+        }
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.start, t.stop) == cudaSuccess) {
+            if (map->auto_timed[t.candidate] == 0 || ms < map->auto_best[t.candidate]) map->auto_best[t.candidate] = ms;
+            map->auto_timed[t.candidate]++;
+        }
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
+    map->auto_trials.swap(keep);
+    cudaGetLastError();
+    bool all = true;
+    for (int c = 0; c < tsdf_map::kAutoCandidates; ++c) all = all && map->auto_timed[c] >= tsdf_map::kAutoTrials;
+    if (all && map->auto_choice < 0) {
+        int best = 0;
+        for (int c = 1; c < tsdf_map::kAutoCandidates; ++c)
+            if (map->auto_best[c] < map->auto_best[best]) best = c;
+        map->auto_choice = tsdf_map::kAutoReduction[best];
+    }
+}
+
+static int integrate_dev(tsdf_map* map, const float* points_dev, int64_t n, const float pose[12],
+                         cudaStream_t s) {
+    if (map->reduction != TSDF_REDUCTION_AUTO) return integrate_with(map, points_dev, n, pose, s, map->reduction);
+    auto_harvest(map);
+    if (map->auto_choice >= 0) return integrate_with(map, points_dev, n, pose, s, map->auto_choice);
+    // still tuning: one untimed first call per candidate (buffer set-up), then timed calls
+    int cand = -1;
+    for (int c = 0; c < tsdf_map::kAutoCandidates && cand < 0; ++c)
+        if (map->auto_started[c] < tsdf_map::kAutoTrials + 1) cand = c;
+    if (cand < 0) return integrate_with(map, points_dev, n, pose, s, tsdf_map::kAutoReduction[0]);
+    const int red = tsdf_map::kAutoReduction[cand];
+    if (map->auto_started[cand]++ == 0) return integrate_with(map, points_dev, n, pose, s, red);
+    tsdf_map::AutoTrial t{cand, nullptr, nullptr};
+    if (cudaEventCreate(&t.start) != cudaSuccess || cudaEventCreate(&t.stop) != cudaSuccess) {
+        if (t.start) cudaEventDestroy(t.start);
+        cudaGetLastError();
+        return integrate_with(map, points_dev, n, pose, s, red);
+    }
+    cudaEventRecord(t.start, s);
+    const int rc = integrate_with(map, points_dev, n, pose, s, red);
+    cudaEventRecord(t.stop, s);
+    map->auto_trials.push_back(t);
+    return rc;
 }
 
 static int check_scan_args(tsdf_map* map, const float* pts, int64_t n, const float pose[12]) {
@@ -768,7 +841,8 @@ int tsdf_set_option(tsdf_map* map, int32_t option, int64_t value) {
             map->pool_req = (size_t)value;
             return TSDF_OK;
         case TSDF_OPT_REDUCTION:
-            if (value != TSDF_REDUCTION_ATOMIC && value != TSDF_REDUCTION_SORT && value != TSDF_REDUCTION_POOL)
+            if (value != TSDF_REDUCTION_ATOMIC && value != TSDF_REDUCTION_SORT && value != TSDF_REDUCTION_POOL &&
+                value != TSDF_REDUCTION_AUTO)
                 return TSDF_ERR_INVALID;
             map->reduction = (int)value;
             return TSDF_OK;
@@ -1093,6 +1167,18 @@ int tsdf_map_device_bytes(const tsdf_map* map, int64_t* out) {
     b += map->store_segments.size() * (size_t)kSegChunks * kChunkBytes;
     b += map->stage_cap * sizeof(float4) + map->items_dev_cap * sizeof(ShiftItem);
     *out = (int64_t)b;
+    return TSDF_OK;
+}
+
+int tsdf_get_reduction(tsdf_map* map, int32_t* reduction) {
+    if (!map || !reduction) return TSDF_ERR_INVALID;
+    if (map->reduction == TSDF_REDUCTION_AUTO) {
+        DeviceScope ds(map->device);
+        auto_harvest(map);
+        *reduction = map->auto_choice >= 0 ? map->auto_choice : TSDF_REDUCTION_AUTO;
+    } else {
+        *reduction = map->reduction;
+    }
     return TSDF_OK;
 }
 

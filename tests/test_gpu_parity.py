@@ -251,6 +251,33 @@ def test_sort_options_rejected():
         m.close()
 
 
+def test_auto_reduction_decides_and_stays_exact():
+    """TSDF_REDUCTION_AUTO runs both reductions on the first calls (each
+    once untimed, then timed), keeps the faster one, and every scan on the way
+    is exact."""
+    from paper_2310_05766_gb300 import binding as b
+    w = synth.workload_outdoor(n_scans=12)
+    steps = workload_steps(w) + [("scan", w.scans[i], w.poses[i]) for i in range(11, 3, -1)]
+    m = b.TsdfMap(w.params)
+    try:
+        b.tsdf_set_option(m.handle, b.TSDF_OPT_REDUCTION, b.TSDF_REDUCTION_AUTO)
+        assert b.tsdf_get_reduction(m.handle) == b.TSDF_REDUCTION_AUTO
+        stats = []
+        for st in steps:
+            if st[0] == "shift":
+                m.shift(st[1])
+                continue
+            m.integrate(torch.from_numpy(st[1]).cuda(), st[2])
+            stats.append(m.stats())
+        chosen = b.tsdf_get_reduction(m.handle)
+        v, wt = m.read()
+    finally:
+        m.close()
+    assert chosen in (b.TSDF_REDUCTION_ATOMIC, b.TSDF_REDUCTION_SORT)
+    vo, wo, so, _ = run_oracle(w.params, steps)
+    assert np.array_equal(v, vo) and np.array_equal(wt, wo) and stats == so
+
+
 # ---------------------------------------------------------------- pool reduction (sparse accumulator)
 
 def _pool_opts(b, kpt=4, bricks=0):
