@@ -522,69 +522,126 @@ def run_serving_bench(args):
         az = [1024, 2048][int(rng.integers(1, 0, 2)[0])]
         w = synth.workload_outdoor(n_scans=2, seed=sp["seed"], beams=beams, azimuths=az, dims=sp["dims"],
                                    voxel_size=sp["voxel_size"], tau=sp["tau"])
+        if args.serve_pinned:   # points in pinned host memory: the server reads them in place
+            w.scans = [torch.from_numpy(x).pin_memory() for x in w.scans]
         scans.append(w)
     srv = b.tsdf_server_create(hbm_budget_bytes=120 * 10**9, max_points=128 * 2048, max_batch=32, streams=2,
                                max_outstanding=1024)
     sids = [b.tsdf_server_open_session(srv, w.params) for w in scans]
-    times, who = synth.poisson_arrivals(500.0, duration, 32, seed=101)
-    tickets = []
-    lock = threading.Lock()
+    rate = args.serve_rate
+    if rate > 0:
+        times, who = synth.poisson_arrivals(rate, duration, 32, seed=101)
+    else:
+        # saturation: every request is due at once (submitted as fast as the
+        # server's back-pressure allows); sessions drawn like the arrivals
+        _, who = synth.poisson_arrivals(20000.0, duration, 32, seed=101)
+        times = np.zeros(len(who))
+    # everything a request needs is laid out before the run (pointers, sizes,
+    # sessions, poses; result buffers), so that each burst of submissions or
+    # waits is a single library call
+    import ctypes
+    nreq = len(who)
+    ptr = np.array([(scans[who[i]].scans[i % 2].data_ptr() if args.serve_pinned else
+                     scans[who[i]].scans[i % 2].ctypes.data) for i in range(nreq)], np.uint64)
+    nn = np.array([scans[who[i]].scans[i % 2].shape[0] for i in range(nreq)], np.int64)
+    ses = np.array([sids[who[i]] for i in range(nreq)], np.int32)
+    pz = np.ascontiguousarray(np.stack([np.asarray(scans[who[i]].poses[i % 2], np.float32).reshape(12)
+                                        for i in range(nreq)]), np.float32)
+    tk = np.zeros(nreq, np.uint64)
+    res = (b.tsdf_request_result * nreq)()
+    L = b.lib()
+    P = ctypes.POINTER
+    submitted = [0]
     done_flag = [False]
 
     def submitter():
         t0 = time.perf_counter()
-        for k, (ta, si) in enumerate(zip(times, who)):
-            while True:
-                dt = ta - (time.perf_counter() - t0)
-                if dt <= 0:
-                    break
-                time.sleep(min(dt, 0.0005))
-            w = scans[si]
-            j = k % 2
-            t = b.tsdf_server_submit(srv, sids[si], w.scans[j], w.poses[j])
-            with lock:
-                tickets.append((ta, t))
+        k = 0
+        done = ctypes.c_int32()
+        while k < nreq:
+            now = time.perf_counter() - t0
+            if times[k] > now:
+                time.sleep(min(times[k] - now, 0.0005))
+                continue
+            e = int(np.searchsorted(times, now, side="right"))
+            e = max(k + 1, min(e, k + 256))
+            rc = L.tsdf_server_submit_many(
+                srv, e - k, ses[k:].ctypes.data_as(P(ctypes.c_int32)), ptr[k:].ctypes.data_as(P(ctypes.c_void_p)),
+                nn[k:].ctypes.data_as(P(ctypes.c_int64)), pz[k:].ctypes.data_as(P(ctypes.c_float)),
+                tk[k:].ctypes.data_as(P(ctypes.c_uint64)), ctypes.byref(done))
+            if rc not in (b.TSDF_OK, b.TSDF_ERR_BUSY):
+                raise b.TsdfError(rc, "tsdf_server_submit_many")
+            k += done.value
+            submitted[0] = k
+            if rc == b.TSDF_ERR_BUSY:
+                time.sleep(0.0002)   # back-pressure: results must be taken first
         done_flag[0] = True
-
-    results = []
 
     def collector():
         i = 0
-        while True:
-            with lock:
-                have = i < len(tickets)
-                item = tickets[i] if have else None
-            if not have:
-                if done_flag[0]:
-                    with lock:
-                        if i >= len(tickets):
-                            break
-                    continue
+        while i < nreq:
+            avail = submitted[0]
+            if avail <= i:
                 time.sleep(0.0002)
                 continue
-            r = b.tsdf_server_wait(srv, item[1])
-            results.append((item[0], r))
-            i += 1
+            cnt = min(avail - i, 256)
+            rc = L.tsdf_server_wait_many(srv, cnt, tk[i:].ctypes.data_as(P(ctypes.c_uint64)),
+                                         ctypes.cast(ctypes.addressof(res) + i * ctypes.sizeof(b.tsdf_request_result),
+                                                     P(b.tsdf_request_result)), -1)
+            if rc != b.TSDF_OK:
+                raise b.TsdfError(rc, "tsdf_server_wait_many")
+            i += cnt
 
-    th_s = threading.Thread(target=submitter)
-    th_c = threading.Thread(target=collector)
-    th_s.start()
-    th_c.start()
-    th_s.join()
-    th_c.join()
+    if rate > 0:
+        th_s = threading.Thread(target=submitter)
+        th_c = threading.Thread(target=collector)
+        th_s.start()
+        th_c.start()
+        th_s.join()
+        th_c.join()
+    else:
+        # saturation, closed loop: fill the server's window of outstanding
+        # requests with one call, wait for all of them with one call, repeat
+        done = ctypes.c_int32()
+        k = 0
+        while k < nreq:
+            cnt = min(1024, nreq - k)
+            rc = L.tsdf_server_submit_many(
+                srv, cnt, ses[k:].ctypes.data_as(P(ctypes.c_int32)), ptr[k:].ctypes.data_as(P(ctypes.c_void_p)),
+                nn[k:].ctypes.data_as(P(ctypes.c_int64)), pz[k:].ctypes.data_as(P(ctypes.c_float)),
+                tk[k:].ctypes.data_as(P(ctypes.c_uint64)), ctypes.byref(done))
+            if rc not in (b.TSDF_OK, b.TSDF_ERR_BUSY) or done.value == 0:
+                raise b.TsdfError(rc, "tsdf_server_submit_many")
+            rc = L.tsdf_server_wait_many(srv, done.value, tk[k:].ctypes.data_as(P(ctypes.c_uint64)),
+                                         ctypes.cast(ctypes.addressof(res) + k * ctypes.sizeof(b.tsdf_request_result),
+                                                     P(b.tsdf_request_result)), -1)
+            if rc != b.TSDF_OK:
+                raise b.TsdfError(rc, "tsdf_server_wait_many")
+            k += done.value
     st = b.tsdf_server_get_stats(srv)
     b.tsdf_server_destroy(srv)
-    keep = [r for ta, r in results if ta >= 2.0]
+    results = [(float(times[i]), b._result_dict(res[i])) for i in range(nreq)]
+    # steady state: arrivals after the first 2 s (at most a fifth of the run;
+    # saturation: all but the first 10 % of the requests)
+    if rate > 0:
+        skip = min(2.0, 0.2 * duration)
+        keep = [r for ta, r in results if ta >= skip]
+    else:
+        keep = [r for _, r in results[len(results) // 10:]]
     lat = np.array([r["t_done_us"] - r["t_submit_us"] for r in keep])
     hits = sum(r["stats"]["hits"] for r in keep)
     span = (max(r["t_done_us"] for r in keep) - min(r["t_submit_us"] for r in keep)) / 1e6
-    return dict(metric="served scan latency (p50 / p99) and throughput, 32 sessions, Poisson 500 scans/s",
+    load = ("Poisson %g scans/s" % rate if rate > 0 else
+            "saturating closed loop (bursts of 1024 requests submitted at once, then waited for)")
+    return dict(metric="served scan latency (p50 / p99) and throughput, 32 sessions, " + load,
                 value=len(keep) / span, unit="scans/s", n_gpus=1, steps=len(keep), warmup=0,
                 ms_per_step=float(np.mean(lat)) / 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f32 geometry, int64 accumulation, int16 map", data="synthetic",
                 config=dict(workload="32 sessions, grids 256^3 / 512x512x128, voxel 0.05-0.1 m, tau 0.2-0.6 m, "
-                                     "Poisson 500 scans/s, scans {16,32,64,128} x {1024,2048}, %g s, first 2 s "
-                                     "discarded, HBM budget 120 GB, 2 streams, batches up to 32" % duration),
+                                     "%s, scans {16,32,64,128} x {1024,2048}, %g s of arrivals, warm-up discarded, "
+                                     "HBM budget 120 GB, 2 streams, batches up to 32, scans %s" %
+                                     (load, duration, "pinned (read in place)" if args.serve_pinned else
+                                      "pageable (copied at submission)")),
                 latency_ms=dict(p50=float(np.percentile(lat, 50)) / 1e3, p99=float(np.percentile(lat, 99)) / 1e3,
                                 mean=float(np.mean(lat)) / 1e3, max=float(np.max(lat)) / 1e3),
                 voxel_updates_per_s=hits / span, mean_batch=st["mean_batch"], batches=st["batches"],
@@ -608,6 +665,10 @@ def main():
     ap.add_argument("--workload", default="outdoor", choices=["outdoor", "corridor", "batch", "serving"],
                     help="outdoor: the headline sequence; batch / serving: the 64-map batch and 32-session serving runs")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-rate", type=float, default=500.0,
+                    help="serving: aggregate Poisson arrival rate, scans/s (0: saturating closed loop)")
+    ap.add_argument("--serve-pinned", type=int, default=1,
+                    help="serving: scans in pinned host memory read in place (1) or pageable, copied (0)")
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=120.0, help="seconds of oracle time for --impl reference")
     args = ap.parse_args()

@@ -464,17 +464,33 @@ int tsdf_server_open_session(tsdf_server* server, const tsdf_params* params, int
 int tsdf_server_close_session(tsdf_server* server, int32_t session);
 
 /* Queue a scan for a session: n <= max_points host float4 points (copied
- * before the call returns), a host pose, and optionally a new window origin
+ * before the call returns; points in pinned host memory mapped into the device
+ * and 16-byte aligned are instead read in place by the batch and must stay
+ * unchanged until tsdf_server_wait has returned for the ticket), a host
+ * pose, and optionally a new window origin
  * (multiples of 8; the window is shifted before the scan is integrated).
  * Returns a ticket for tsdf_server_wait. Errors: BUSY (max_outstanding
  * requests not yet waited for), INVALID, or a previous worker error. */
 int tsdf_server_submit(tsdf_server* server, int32_t session, const float* points_host, int64_t n,
                        const float pose[12], const int64_t* new_origin, uint64_t* ticket);
 
+/* Submit `count` scans at once (no window shifts), in order, as
+ * tsdf_server_submit with sessions[k], points_host[k], n[k], poses + 12 k,
+ * writing tickets[k]. Stops at the first error, which it returns; *submitted
+ * says how many were queued. */
+int tsdf_server_submit_many(tsdf_server* server, int32_t count, const int32_t* sessions,
+                            const float* const* points_host, const int64_t* n, const float* poses,
+                            uint64_t* tickets, int32_t* submitted);
+
 /* Wait up to timeout_us (negative: forever) for a request and take its
  * result (each ticket can be waited for once). Returns the request's status,
  * or TIMEOUT (the request is still pending), or INVALID (unknown ticket). */
 int tsdf_server_wait(tsdf_server* server, uint64_t ticket, tsdf_request_result* out, int64_t timeout_us);
+
+/* tsdf_server_wait for tickets[0..count) in order (each with timeout_us),
+ * results into out[0..count). Stops at the first error, which it returns. */
+int tsdf_server_wait_many(tsdf_server* server, int32_t count, const uint64_t* tickets, tsdf_request_result* out,
+                          int64_t timeout_us);
 
 /* The session's map, for tsdf_read and tsdf_stats once all of its requests
  * have been waited for. Errors: INVALID. */

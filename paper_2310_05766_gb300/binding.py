@@ -148,6 +148,9 @@ def lib():
     L.tsdf_server_open_session.argtypes = [vp, P(tsdf_params), P(ctypes.c_int32)]
     L.tsdf_server_close_session.argtypes = [vp, ctypes.c_int32]
     L.tsdf_server_submit.argtypes = [vp, ctypes.c_int32, vp, i64, f32p, P(i64), P(ctypes.c_uint64)]
+    L.tsdf_server_submit_many.argtypes = [vp, ctypes.c_int32, P(ctypes.c_int32), P(vp), P(i64), f32p,
+                                          P(ctypes.c_uint64), P(ctypes.c_int32)]
+    L.tsdf_server_wait_many.argtypes = [vp, ctypes.c_int32, P(ctypes.c_uint64), P(tsdf_request_result), i64]
     L.tsdf_server_wait.argtypes = [vp, ctypes.c_uint64, P(tsdf_request_result), i64]
     L.tsdf_server_session_map.argtypes = [vp, ctypes.c_int32, P(vp)]
     L.tsdf_server_get_stats.argtypes = [vp, P(tsdf_server_stats)]
@@ -161,7 +164,7 @@ def lib():
                  "tsdf_integrate_static", "tsdf_probe_reduction_rate", "tsdf_map_save", "tsdf_map_load", "tsdf_extract_surface", "tsdf_map_device_bytes", "tsdf_register_system", "tsdf_register", "tsdf_extract_mesh", "tsdf_get_reduction", "tsdf_batch_create", "tsdf_batch_destroy", "tsdf_batch_set_option",
                  "tsdf_batch_get_config", "tsdf_batch_integrate", "tsdf_integrate_batch", "tsdf_batch_sync",
                  "tsdf_server_create", "tsdf_server_destroy", "tsdf_server_open_session", "tsdf_server_close_session",
-                 "tsdf_server_submit", "tsdf_server_wait", "tsdf_server_session_map", "tsdf_server_get_stats"):
+                 "tsdf_server_submit", "tsdf_server_submit_many", "tsdf_server_wait", "tsdf_server_wait_many", "tsdf_server_session_map", "tsdf_server_get_stats"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -383,14 +386,51 @@ def tsdf_server_close_session(server: int, session: int) -> None:
 
 
 def tsdf_server_submit(server: int, session: int, points_host, pose, new_origin=None) -> int:
-    """points_host: float32 (n, 4) host array (copied before returning). Returns a ticket."""
-    pts = np.ascontiguousarray(points_host, dtype=np.float32).reshape(-1, 4)
+    """points_host: float32 (n, 4) host numpy array (copied before returning) or
+    pinned CPU tensor (read in place: keep it unchanged until the ticket is
+    waited for). Returns a ticket."""
+    if isinstance(points_host, np.ndarray):
+        pts = np.ascontiguousarray(points_host, dtype=np.float32).reshape(-1, 4)
+        ptr, n = pts.ctypes.data, pts.shape[0]
+    else:
+        ptr, n = points_host.data_ptr(), points_host.shape[0]
     pa, pp = _pose_arg(pose)
     org = _i64_3(new_origin) if new_origin is not None else None
     t = ctypes.c_uint64()
-    _check(lib().tsdf_server_submit(server, int(session), pts.ctypes.data, pts.shape[0], pp, org, ctypes.byref(t)),
-           "tsdf_server_submit")
+    _check(lib().tsdf_server_submit(server, int(session), ptr, n, pp, org, ctypes.byref(t)), "tsdf_server_submit")
     return t.value
+
+
+def tsdf_server_submit_many(server: int, sessions, points_host, poses):
+    """Submit several scans in one call (pinned tensors read in place, numpy
+    arrays copied). Returns the tickets of the scans queued: all of them, or a
+    prefix when the server pushed back (TSDF_ERR_BUSY); other errors raise."""
+    k = len(sessions)
+    keep = []
+    ptrs = (ctypes.c_void_p * k)()
+    ns = (ctypes.c_int64 * k)()
+    for i, p in enumerate(points_host):
+        if isinstance(p, np.ndarray):
+            p = np.ascontiguousarray(p, dtype=np.float32).reshape(-1, 4)
+            keep.append(p)
+            ptrs[i], ns[i] = p.ctypes.data, p.shape[0]
+        else:
+            ptrs[i], ns[i] = p.data_ptr(), p.shape[0]
+    ses = (ctypes.c_int32 * k)(*[int(x) for x in sessions])
+    pz = np.ascontiguousarray(np.asarray(poses, np.float32).reshape(k, 12))
+    tk = (ctypes.c_uint64 * k)()
+    done = ctypes.c_int32()
+    rc = lib().tsdf_server_submit_many(server, k, ses, ptrs, ns, pz.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                       tk, ctypes.byref(done))
+    if rc not in (TSDF_OK, TSDF_ERR_BUSY):
+        raise TsdfError(rc, "tsdf_server_submit_many")
+    return list(tk)[:done.value]
+
+
+def _result_dict(r) -> dict:
+    return dict(ticket=r.ticket, session=r.session, status=r.status, batch_size=r.batch_size,
+                stats=dict(valid_rays=r.stats.valid_rays, hits=r.stats.hits, touched=r.stats.touched),
+                t_submit_us=r.t_submit_us, t_start_us=r.t_start_us, t_done_us=r.t_done_us)
 
 
 def tsdf_server_wait(server: int, ticket: int, timeout_us: int = -1) -> dict:
@@ -398,9 +438,16 @@ def tsdf_server_wait(server: int, ticket: int, timeout_us: int = -1) -> dict:
     rc = lib().tsdf_server_wait(server, ctypes.c_uint64(ticket), ctypes.byref(r), int(timeout_us))
     if rc != TSDF_OK:
         raise TsdfError(rc, "tsdf_server_wait")
-    return dict(ticket=r.ticket, session=r.session, status=r.status, batch_size=r.batch_size,
-                stats=dict(valid_rays=r.stats.valid_rays, hits=r.stats.hits, touched=r.stats.touched),
-                t_submit_us=r.t_submit_us, t_start_us=r.t_start_us, t_done_us=r.t_done_us)
+    return _result_dict(r)
+
+
+def tsdf_server_wait_many(server: int, tickets, timeout_us: int = -1) -> list:
+    """Wait for several tickets in order (one call); returns their result dicts."""
+    k = len(tickets)
+    tk = (ctypes.c_uint64 * k)(*[int(t) for t in tickets])
+    res = (tsdf_request_result * k)()
+    _check(lib().tsdf_server_wait_many(server, k, tk, res, int(timeout_us)), "tsdf_server_wait_many")
+    return [_result_dict(r) for r in res]
 
 
 def tsdf_server_session_map(server: int, session: int) -> int:

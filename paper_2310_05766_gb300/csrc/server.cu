@@ -4,7 +4,8 @@
 // Every session owns a map that stays resident in device memory; sessions are
 // admitted against a device-memory budget. Requests (a host point cloud, a
 // pose and optionally a new window origin) are copied into pinned slabs at
-// submission and queued per session. A worker thread forms batches from the
+// submission, or, when the points already lie in device-mapped pinned memory,
+// read in place by the batch; requests are queued per session. A worker thread forms batches from the
 // requests that have arrived: at most one request per session per batch and
 // at most one batch per session in flight, so each map sees its scans in
 // submission order. Each batch goes to a free stream slot: host-to-device
@@ -47,6 +48,7 @@ struct Request {
     int64_t origin[3] = {0, 0, 0};
     float4* host = nullptr;   // pinned slab
     int slab = -1;
+    const float4* mapped = nullptr;   // the caller's pinned buffer, read in place (no slab copy)
     tsdf_request_result res{};
     bool done = false;
 };
@@ -67,6 +69,7 @@ struct Slot {
     cudaEvent_t done = nullptr;
     std::vector<Request*> reqs;
     bool busy = false;
+    bool launching = false;             // being filled by the worker outside the lock
 };
 
 size_t session_bytes(const tsdf_params& p, int64_t max_points) {
@@ -104,8 +107,10 @@ void release_request(tsdf_server* s, Request* r) {
     delete r;
 }
 
-// Launch a batch on slot `k`; called with the lock held.
-int launch_batch(tsdf_server* s, int k, std::vector<Request*>& reqs) {
+// Launch a batch on slot `k`. Called WITHOUT the lock: the requests and the
+// slot belong to the worker until it records the launch (`maps` were taken
+// under the lock; sessions in flight cannot be closed).
+int launch_batch(tsdf_server* s, int k, std::vector<Request*>& reqs, const std::vector<tsdf_map*>& smaps) {
     Slot& sl = s->slots[k];
     const int count = (int)reqs.size();
     std::vector<tsdf_map*> maps(count);
@@ -116,16 +121,20 @@ int launch_batch(tsdf_server* s, int k, std::vector<Request*>& reqs) {
     const double t0 = now_us();
     for (int i = 0; i < count; ++i) {
         Request* r = reqs[i];
-        Session& ss = s->sessions[r->session];
-        maps[i] = ss.map;
+        maps[i] = smaps[i];
         float4* dst = sl.dev_pts + (size_t)i * s->cfg.max_points;
-        if (r->n > 0 && e == cudaSuccess)
-            e = cudaMemcpyAsync(dst, r->host, (size_t)r->n * sizeof(float4), cudaMemcpyHostToDevice, sl.stream);
-        pts[i] = reinterpret_cast<const float*>(dst);
+        if (r->mapped) {
+            pts[i] = reinterpret_cast<const float*>(r->mapped);   // read in place over the host link
+        } else {
+            if (r->n > 0 && e == cudaSuccess)
+                e = cudaMemcpyAsync(dst, r->host, (size_t)r->n * sizeof(float4), cudaMemcpyHostToDevice,
+                                    sl.stream);
+            pts[i] = reinterpret_cast<const float*>(dst);
+        }
         ns[i] = r->n;
         std::memcpy(&poses[12 * (size_t)i], r->pose, sizeof(r->pose));
         if (r->shift && e == cudaSuccess) {
-            int rc = tsdf_shift(ss.map, r->origin, sl.stream);
+            int rc = tsdf_shift(maps[i], r->origin, sl.stream);
             if (rc != TSDF_OK) return rc;
         }
         r->res.t_start_us = t0;
@@ -138,10 +147,6 @@ int launch_batch(tsdf_server* s, int k, std::vector<Request*>& reqs) {
                             cudaMemcpyDeviceToHost, sl.stream);
     if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
     if (e != cudaSuccess) return TSDF_ERR_CUDA;
-    sl.reqs = reqs;
-    sl.busy = true;
-    s->batches++;
-    s->batched_requests += count;
     return TSDF_OK;
 }
 
@@ -152,7 +157,7 @@ void worker_loop(tsdf_server* s) {
         bool progress = false;
         // 1. completions
         for (Slot& sl : s->slots) {
-            if (!sl.busy || cudaEventQuery(sl.done) != cudaSuccess) continue;
+            if (!sl.busy || sl.launching || cudaEventQuery(sl.done) != cudaSuccess) continue;
             const double t = now_us();
             for (size_t i = 0; i < sl.reqs.size(); ++i) {
                 Request* r = sl.reqs[i];
@@ -182,13 +187,28 @@ void worker_loop(tsdf_server* s) {
                 if ((int)reqs.size() >= s->cfg.max_batch) break;
             }
             if (reqs.empty()) break;
-            // oldest first is implicit in the per-session queues; mark and launch
+            // oldest first is implicit in the per-session queues; mark, then
+            // launch outside the lock so that submissions are not held up
+            std::vector<tsdf_map*> maps;
             for (Request* r : reqs) {
-                s->sessions[r->session].queue.pop_front();
-                s->sessions[r->session].in_flight = true;
+                Session& ss = s->sessions[r->session];
+                ss.queue.pop_front();
+                ss.in_flight = true;
+                maps.push_back(ss.map);
             }
-            int rc = launch_batch(s, (int)k, reqs);
-            if (rc != TSDF_OK) {
+            Slot& sl = s->slots[k];
+            sl.busy = true;
+            sl.launching = true;
+            lk.unlock();
+            int rc = launch_batch(s, (int)k, reqs, maps);
+            lk.lock();
+            sl.launching = false;
+            if (rc == TSDF_OK) {
+                sl.reqs = reqs;
+                s->batches++;
+                s->batched_requests += (int64_t)reqs.size();
+            } else {
+                sl.busy = false;
                 for (Request* r : reqs) {
                     r->res.status = rc;
                     r->res.t_done_us = now_us();
@@ -359,7 +379,19 @@ int tsdf_server_submit(tsdf_server* s, int32_t session, const float* points_host
     r->res.session = session;
     r->res.t_submit_us = now_us();
     lk.unlock();
-    if (n > 0) std::memcpy(r->host, points_host, (size_t)n * sizeof(float4));   // slab is ours alone
+    if (n > 0) {
+        // pinned host memory mapped into the device is read in place by the
+        // batch (the caller keeps it unchanged until the request completes);
+        // anything else is copied into the request's slab
+        cudaPointerAttributes at{};
+        if (((uintptr_t)points_host & 15u) == 0 && cudaPointerGetAttributes(&at, points_host) == cudaSuccess &&
+            at.type == cudaMemoryTypeHost && at.devicePointer != nullptr && ((uintptr_t)at.devicePointer & 15u) == 0) {
+            r->mapped = static_cast<const float4*>(at.devicePointer);
+        } else {
+            cudaGetLastError();
+            std::memcpy(r->host, points_host, (size_t)n * sizeof(float4));   // slab is ours alone
+        }
+    }
     lk.lock();
     it = s->sessions.find(session);
     if (it == s->sessions.end()) {
@@ -372,6 +404,20 @@ int tsdf_server_submit(tsdf_server* s, int32_t session, const float* points_host
     *ticket = r->ticket;
     lk.unlock();
     s->cv_work.notify_one();
+    return TSDF_OK;
+}
+
+int tsdf_server_submit_many(tsdf_server* s, int32_t count, const int32_t* sessions, const float* const* points_host,
+                            const int64_t* n, const float* poses, uint64_t* tickets, int32_t* submitted) {
+    if (!s || count < 0 || !submitted || (count > 0 && (!sessions || !points_host || !n || !poses || !tickets)))
+        return TSDF_ERR_INVALID;
+    *submitted = 0;
+    for (int32_t k = 0; k < count; ++k) {
+        const int rc = tsdf_server_submit(s, sessions[k], points_host[k], n[k], poses + 12 * (size_t)k, nullptr,
+                                          tickets + k);
+        if (rc != TSDF_OK) return rc;
+        *submitted = k + 1;
+    }
     return TSDF_OK;
 }
 
@@ -392,6 +438,16 @@ int tsdf_server_wait(tsdf_server* s, uint64_t ticket, tsdf_request_result* out, 
     s->requests.erase(it);
     release_request(s, r);
     return out->status;
+}
+
+int tsdf_server_wait_many(tsdf_server* s, int32_t count, const uint64_t* tickets, tsdf_request_result* out,
+                          int64_t timeout_us) {
+    if (!s || count < 0 || (count > 0 && (!tickets || !out))) return TSDF_ERR_INVALID;
+    for (int32_t i = 0; i < count; ++i) {
+        const int rc = tsdf_server_wait(s, tickets[i], out + i, timeout_us);
+        if (rc != TSDF_OK) return rc;
+    }
+    return TSDF_OK;
 }
 
 int tsdf_server_session_map(tsdf_server* s, int32_t session, tsdf_map** out) {

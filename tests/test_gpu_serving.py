@@ -43,9 +43,13 @@ def _alone(b, w):
     return v, wt, stats
 
 
-def test_mixed_equals_alone():
+@pytest.mark.parametrize("pinned", [False, True])
+def test_mixed_equals_alone(pinned):
+    """Each session's map is the same in the mix as alone; with pinned
+    submissions the server reads the points in place instead of copying."""
     from paper_2310_05766_gb300 import binding as b
     ws = _sessions(6, seed=1)
+    held = {}   # pinned submissions must stay alive until their tickets are waited for
     srv = b.tsdf_server_create(hbm_budget_bytes=8 << 30, max_points=1 << 16, max_batch=4, streams=2,
                                max_outstanding=64)
     try:
@@ -59,7 +63,11 @@ def test_mixed_equals_alone():
             org = tuple(w.origins[k])
             shift = org if org != cur[i] else None
             cur[i] = org
-            tickets[i].append(b.tsdf_server_submit(srv, sids[i], w.scans[k], w.poses[k], new_origin=shift))
+            pts = w.scans[k]
+            if pinned:
+                pts = torch.from_numpy(np.ascontiguousarray(pts, np.float32)).pin_memory()
+                held[(i, k)] = pts
+            tickets[i].append(b.tsdf_server_submit(srv, sids[i], pts, w.poses[k], new_origin=shift))
         results = {i: [b.tsdf_server_wait(srv, t) for t in tickets[i]] for i in tickets}
         st = b.tsdf_server_get_stats(srv)
         assert st["completed"] == 4 * len(ws)
