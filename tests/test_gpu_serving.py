@@ -133,3 +133,39 @@ def test_admission_by_budget_and_back_pressure():
             b.tsdf_server_wait(srv, t1)   # each ticket is waited for once
     finally:
         b.tsdf_server_destroy(srv)
+
+
+def test_submit_many_and_wait_many():
+    """Bursts through tsdf_server_submit_many / tsdf_server_wait_many (pinned
+    points read in place): every session ends as its scans run alone, and a
+    burst larger than the outstanding window is queued up to the window."""
+    from paper_2310_05766_gb300 import binding as b
+    ws = _sessions(4, seed=9)
+    srv = b.tsdf_server_create(hbm_budget_bytes=8 << 30, max_points=1 << 16, max_batch=4, streams=2,
+                               max_outstanding=6)
+    try:
+        sids = [b.tsdf_server_open_session(srv, w.params) for w in ws]
+        # scans without window shifts: the first two of each session if they share the origin
+        plan = [(i, k) for k in range(2) for i in range(len(ws)) if tuple(ws[i].origins[k]) == tuple(ws[i].params["origin"])]
+        pts = [torch.from_numpy(np.ascontiguousarray(ws[i].scans[k], np.float32)).pin_memory() for i, k in plan]
+        tickets = b.tsdf_server_submit_many(srv, [sids[i] for i, _ in plan], pts, [ws[i].poses[k] for i, k in plan])
+        assert len(tickets) == min(6, len(plan))          # the window holds 6 outstanding requests
+        res = b.tsdf_server_wait_many(srv, tickets)
+        rest = b.tsdf_server_submit_many(srv, [sids[i] for i, _ in plan[len(tickets):]], pts[len(tickets):],
+                                         [ws[i].poses[k] for i, k in plan[len(tickets):]])
+        res += b.tsdf_server_wait_many(srv, rest)
+        assert len(res) == len(plan) and all(r["status"] == 0 for r in res)
+        for i, w in enumerate(ws):
+            ks = [k for j, k in plan if j == i]
+            m = b.TsdfMap(w.params)
+            for k in ks:
+                m.integrate(torch.from_numpy(w.scans[k]).cuda(), w.poses[k])
+            va, wa = m.read()
+            m.close()
+            mh = b.tsdf_server_session_map(srv, sids[i])
+            o = b.tsdf_get_origin(mh)
+            d = w.params["dims"]
+            vm, wm = b.tsdf_read(mh, o, tuple(o[a] + d[a] for a in range(3)))
+            assert np.array_equal(vm, va) and np.array_equal(wm, wa)
+    finally:
+        b.tsdf_server_destroy(srv)
