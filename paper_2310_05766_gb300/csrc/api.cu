@@ -49,13 +49,64 @@ struct ChunkKey {
     long long x, y, z;
     bool operator==(const ChunkKey& o) const { return x == o.x && y == o.y && z == o.z; }
 };
-struct ChunkKeyHash {
-    size_t operator()(const ChunkKey& k) const {
+
+// Index of the global store: chunk key -> store slot, an open-addressing hash
+// table over the full keys (linear probing, grown by doubling at half load).
+class ChunkIndex {
+public:
+    // slot of `k`, or -1
+    long long find(const ChunkKey& k) const {
+        if (keys_.empty()) return -1;
+        for (size_t i = hash(k) & mask_;; i = (i + 1) & mask_) {
+            if (used_[i] && keys_[i] == k) return vals_[i];
+            if (!used_[i]) return -1;
+        }
+    }
+    void insert(const ChunkKey& k, uint32_t v) {
+        if (2 * (count_ + 1) > keys_.size()) grow();
+        put(k, v);
+        ++count_;
+    }
+    size_t size() const { return count_; }
+    template <typename F>
+    void for_each(F&& f) const {
+        for (size_t i = 0; i < keys_.size(); ++i)
+            if (used_[i]) f(keys_[i], vals_[i]);
+    }
+
+private:
+    static size_t hash(const ChunkKey& k) {
         unsigned long long h = (unsigned long long)k.x * 0x9E3779B97F4A7C15ull;
         h ^= (unsigned long long)k.y * 0xC2B2AE3D27D4EB4Full + (h << 6) + (h >> 2);
         h ^= (unsigned long long)k.z * 0x165667B19E3779F9ull + (h << 6) + (h >> 2);
-        return (size_t)h;
+        return (size_t)(h ^ (h >> 29));
     }
+    void put(const ChunkKey& k, uint32_t v) {
+        size_t i = hash(k) & mask_;
+        while (used_[i]) i = (i + 1) & mask_;
+        keys_[i] = k;
+        vals_[i] = v;
+        used_[i] = 1;
+    }
+    void grow() {
+        std::vector<ChunkKey> ok;
+        std::vector<uint32_t> ov;
+        std::vector<unsigned char> ou;
+        ok.swap(keys_);
+        ov.swap(vals_);
+        ou.swap(used_);
+        const size_t n = ok.empty() ? 4096 : 2 * ok.size();
+        keys_.assign(n, ChunkKey{0, 0, 0});
+        vals_.assign(n, 0u);
+        used_.assign(n, 0);
+        mask_ = n - 1;
+        for (size_t i = 0; i < ok.size(); ++i)
+            if (ou[i]) put(ok[i], ov[i]);
+    }
+    std::vector<ChunkKey> keys_;
+    std::vector<uint32_t> vals_;
+    std::vector<unsigned char> used_;
+    size_t mask_ = 0, count_ = 0;
 };
 
 constexpr uint32_t kChunkBytes = 8 * 8 * 8 * 4;
@@ -94,7 +145,7 @@ struct tsdf_map {
     size_t ray_cap = 0;
     MapDev dev{};
     // device-resident global store of 8^3 chunks
-    std::unordered_map<ChunkKey, uint32_t, ChunkKeyHash> store_index;
+    ChunkIndex store_index;
     std::vector<char*> store_segments;
     uint32_t store_count = 0;
     ShiftItem* items_dev = nullptr;
@@ -259,9 +310,9 @@ bool box_inside(const tsdf_map* m, const int64_t lo[3], const int64_t hi[3], uin
 
 // Store address of a chunk, allocating a new store slot when `create`.
 int store_lookup(tsdf_map* m, const ChunkKey& k, bool create, unsigned long long* out) {
-    auto it = m->store_index.find(k);
-    if (it != m->store_index.end()) {
-        uint32_t idx = it->second;
+    const long long found = m->store_index.find(k);
+    if (found >= 0) {
+        uint32_t idx = (uint32_t)found;
         *out = (unsigned long long)(m->store_segments[idx / kSegChunks] + (size_t)(idx % kSegChunks) * kChunkBytes);
         return TSDF_OK;
     }
@@ -277,7 +328,7 @@ int store_lookup(tsdf_map* m, const ChunkKey& k, bool create, unsigned long long
         m->store_segments.push_back(seg);
     }
     m->store_count++;
-    m->store_index.emplace(k, idx);
+    m->store_index.insert(k, idx);
     *out = (unsigned long long)(m->store_segments[idx / kSegChunks] + (size_t)(idx % kSegChunks) * kChunkBytes);
     return TSDF_OK;
 }
@@ -666,24 +717,16 @@ int tsdf_shift(tsdf_map* map, const int64_t new_origin[3], void* stream) {
             chg[a][sl] = oldc[a][sl] != newc[a][sl];
         }
     }
-    std::vector<ShiftItem> items;
-    for (long long sz = 0; sz < C[2]; ++sz) {
-        for (long long sy = 0; sy < C[1]; ++sy) {
-            const bool row_changes = chg[2][sz] || chg[1][sy];
-            for (long long sx = 0; sx < C[0]; ++sx) {
-                if (!row_changes && !chg[0][sx]) continue;
-                ShiftItem it{};
-                it.brick = (uint32_t)((sz * C[1] + sy) * C[0] + sx);
-                int rc = store_lookup(map, ChunkKey{oldc[0][sx], oldc[1][sy], oldc[2][sz]}, true, &it.out_ptr);
-                if (rc != TSDF_OK) return rc;
-                rc = store_lookup(map, ChunkKey{newc[0][sx], newc[1][sy], newc[2][sz]}, false, &it.in_ptr);
-                if (rc != TSDF_OK) return rc;
-                items.push_back(it);
-            }
-        }
-    }
-    const size_t cnt = items.size();
+    // ring slots whose chunk changes: every slot of a changed x, y or z layer
+    std::vector<long long> chx;
+    for (long long sx = 0; sx < C[0]; ++sx)
+        if (chg[0][sx]) chx.push_back(sx);
+    size_t cnt = 0;
+    for (long long sz = 0; sz < C[2]; ++sz)
+        for (long long sy = 0; sy < C[1]; ++sy)
+            cnt += (chg[2][sz] || chg[1][sy]) ? (size_t)C[0] : chx.size();
     if (cnt > 0) {
+        // the pinned item buffer may still be read by the previous shift's copy
         if (map->items_event_pending) {
             TSDF_CU(cudaEventSynchronize(map->items_event));
             map->items_event_pending = false;
@@ -702,7 +745,26 @@ int tsdf_shift(tsdf_map* map, const int64_t new_origin[3], void* stream) {
             TSDF_CU(cudaMalloc(&map->items_dev, cnt * sizeof(ShiftItem)));
             map->items_dev_cap = cnt;
         }
-        std::memcpy(map->items_host, items.data(), cnt * sizeof(ShiftItem));
+        size_t k = 0;
+        auto add = [&](long long sx, long long sy, long long sz) -> int {
+            ShiftItem& it = map->items_host[k++];
+            it = ShiftItem{};
+            it.brick = (uint32_t)((sz * C[1] + sy) * C[0] + sx);
+            int rc = store_lookup(map, ChunkKey{oldc[0][sx], oldc[1][sy], oldc[2][sz]}, true, &it.out_ptr);
+            if (rc != TSDF_OK) return rc;
+            return store_lookup(map, ChunkKey{newc[0][sx], newc[1][sy], newc[2][sz]}, false, &it.in_ptr);
+        };
+        for (long long sz = 0; sz < C[2]; ++sz) {
+            for (long long sy = 0; sy < C[1]; ++sy) {
+                int rc = TSDF_OK;
+                if (chg[2][sz] || chg[1][sy]) {
+                    for (long long sx = 0; sx < C[0] && rc == TSDF_OK; ++sx) rc = add(sx, sy, sz);
+                } else {
+                    for (size_t q = 0; q < chx.size() && rc == TSDF_OK; ++q) rc = add(chx[q], sy, sz);
+                }
+                if (rc != TSDF_OK) return rc;
+            }
+        }
         TSDF_CU(cudaMemcpyAsync(map->items_dev, map->items_host, cnt * sizeof(ShiftItem), cudaMemcpyHostToDevice, s));
         TSDF_CU(cudaEventRecord(map->items_event, s));
         map->items_event_pending = true;
@@ -954,16 +1016,15 @@ int tsdf_map_save(tsdf_map* map, const char* path, void* stream) {
     // 2. stored chunks outside the window (a stored copy of a chunk that is
     //    back in the window is stale), segment by segment
     std::vector<std::vector<std::pair<uint32_t, ChunkKey>>> by_seg(map->store_segments.size());
-    for (const auto& kv : map->store_index) {
-        const ChunkKey& k = kv.first;
+    map->store_index.for_each([&](const ChunkKey& k, uint32_t slot) {
         const long long kc[3] = {k.x, k.y, k.z};
         bool inside = true;
         for (int a = 0; a < 3; ++a) {
             const long long co = floordiv8(map->origin[a]);
             inside = inside && kc[a] >= co && kc[a] < co + C[a];
         }
-        if (!inside) by_seg[kv.second / kSegChunks].push_back({kv.second % kSegChunks, k});
-    }
+        if (!inside) by_seg[slot / kSegChunks].push_back({slot % kSegChunks, k});
+    });
     for (size_t sg = 0; sg < by_seg.size(); ++sg) {
         if (by_seg[sg].empty()) continue;
         TSDF_CU(cudaMemcpyAsync(stage.p, map->store_segments[sg], (size_t)kSegChunks * kChunkBytes,
