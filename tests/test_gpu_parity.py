@@ -242,7 +242,7 @@ def test_sort_options_rejected():
     w = synth.workload_room()
     m = b.TsdfMap(w.params)
     try:
-        for opt, val in [(b.TSDF_OPT_REDUCTION, 3), (b.TSDF_OPT_REDUCTION, -1), (b.TSDF_OPT_SORT_CAPACITY, 5),
+        for opt, val in [(b.TSDF_OPT_REDUCTION, 4), (b.TSDF_OPT_REDUCTION, -1), (b.TSDF_OPT_SORT_CAPACITY, 5),
                          (b.TSDF_OPT_SORT_CAPACITY, (1 << 28) + 1), (b.TSDF_OPT_POOL_BRICKS, 63),
                          (b.TSDF_OPT_POOL_BRICKS, 1 << 30)]:
             with pytest.raises(b.TsdfError):
