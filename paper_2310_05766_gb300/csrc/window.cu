@@ -13,19 +13,28 @@
 namespace tsdf {
 namespace {
 
-// One CTA of 128 threads per brick: each thread moves 16 contiguous bytes of
-// the 2048-byte brick. The store keeps a brick in the same [z][y][x] order.
+// One warp per brick (4 per CTA): each lane moves 4 x 16 bytes of the
+// 2048-byte brick, issuing all of its loads (the leaving brick and the
+// entering one) before any store, so that each lane has 128 bytes in flight.
+// The store keeps a brick in the same [z][y][x] order.
 __global__ void __launch_bounds__(128) shift_kernel(uint32_t* __restrict__ grid, const ShiftItem* __restrict__ items,
                                                      int count) {
-    const int t = threadIdx.x;
-    for (int it = blockIdx.x; it < count; it += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    for (int it = blockIdx.x * 4 + (threadIdx.x >> 5); it < count; it += gridDim.x * 4) {
         const ShiftItem s = items[it];
-        uint4* gp = reinterpret_cast<uint4*>(grid + ((size_t)s.brick << 9)) + t;
-        const uint4 old = *gp;
-        if (s.out_ptr) reinterpret_cast<uint4*>(s.out_ptr)[t] = old;
-        uint4 nv = make_uint4(0u, 0u, 0u, 0u);
-        if (s.in_ptr) nv = reinterpret_cast<const uint4*>(s.in_ptr)[t];
-        *gp = nv;
+        uint4* gp = reinterpret_cast<uint4*>(grid + ((size_t)s.brick << 9));
+        uint4 old[4], nv[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) old[v] = gp[32 * v + lane];
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            nv[v] = s.in_ptr ? reinterpret_cast<const uint4*>(s.in_ptr)[32 * v + lane] : make_uint4(0u, 0u, 0u, 0u);
+        if (s.out_ptr) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) reinterpret_cast<uint4*>(s.out_ptr)[32 * v + lane] = old[v];
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) gp[32 * v + lane] = nv[v];
     }
 }
 
@@ -84,7 +93,8 @@ cudaError_t launch_copy_chunks(const ChunkCopy* items, int count, cudaStream_t s
 
 cudaError_t launch_shift(uint32_t* grid, const ShiftItem* items, int count, cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
-    const int blocks = count < 65536 ? count : 65536;
+    const int need = (count + 3) / 4;
+    const int blocks = need < 65536 ? need : 65536;
     shift_kernel<<<blocks, 128, 0, s>>>(grid, items, count);
     return cudaGetLastError();
 }
