@@ -191,9 +191,11 @@ int tsdf_stats(tsdf_map* map, tsdf_scan_stats* out, void* stream);
                                    accumulator is never allocated for a map used only this way. A scan that
                                    needs more bricks than the pool holds is dropped whole and tsdf_stats
                                    returns TSDF_ERR_CAPACITY. Same results as the other reductions. */
-#define TSDF_REDUCTION_AUTO   3  /* the atomic and the sort reduction are each run once untimed and then
+#define TSDF_REDUCTION_AUTO   3  /* the atomic, sort and pool reductions are each run once untimed and then
                                    timed (CUDA events) on the next calls; once every trial has finished
-                                   the faster one is used from then on (tsdf_get_reduction tells which) */
+                                   the fastest is used from then on (tsdf_get_reduction tells which). A pool
+                                   trial that overflows is dropped like any pool scan: do not use AUTO with a
+                                   pool too small for the scans */
 #define TSDF_OPT_POOL_BRICKS  7  /* pool reduction: slots of the pool (64 .. bricks of the window); 0 (default):
                                    an eighth of the window's bricks, at least 16384 */
 

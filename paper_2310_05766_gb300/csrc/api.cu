@@ -167,12 +167,13 @@ struct tsdf_map {
     double* reg_dev = nullptr;      // registration: the 29 sums of the normal equations
     size_t pair_cap_req = 0;        // sort reduction: requested pair capacity, 0 = from the scan size
     size_t pool_req = 0;            // pool reduction: requested slots, 0 = default
-    // TSDF_REDUCTION_AUTO: the atomic and the sort reduction are timed on the
-    // first calls (one untimed call each, then kAutoTrials timed) and the
-    // faster one is kept
-    static constexpr int kAutoCandidates = 2;
+    // TSDF_REDUCTION_AUTO: the atomic, sort and pool reductions are timed on
+    // the first calls (one untimed call each, then kAutoTrials timed) and the
+    // fastest is kept
+    static constexpr int kAutoCandidates = 3;
     static constexpr int kAutoTrials = 3;
-    static constexpr int kAutoReduction[kAutoCandidates] = {TSDF_REDUCTION_ATOMIC, TSDF_REDUCTION_SORT};
+    static constexpr int kAutoReduction[kAutoCandidates] = {TSDF_REDUCTION_ATOMIC, TSDF_REDUCTION_SORT,
+                                                            TSDF_REDUCTION_POOL};
     struct AutoTrial {
         int candidate;
         cudaEvent_t start, stop;
