@@ -396,7 +396,8 @@ int tsdf_batch_integrate(tsdf_batch* batch, tsdf_map* const* maps, const float* 
                          const float* poses, int32_t count, void* stream);
 
 /* Convenience form of tsdf_batch_integrate with a batch object per host thread
- * and device, created on first use (up to 1024 maps per call). */
+ * and device, created on first use and destroyed when the thread exits (up to
+ * 1024 maps per call). */
 int tsdf_integrate_batch(tsdf_map* const* maps, const float* const* points_dev, const int64_t* n, const float* poses,
                          int32_t count, void* stream);
 
@@ -489,8 +490,11 @@ int tsdf_server_submit_many(tsdf_server* server, int32_t count, const int32_t* s
  * or TIMEOUT (the request is still pending), or INVALID (unknown ticket). */
 int tsdf_server_wait(tsdf_server* server, uint64_t ticket, tsdf_request_result* out, int64_t timeout_us);
 
-/* tsdf_server_wait for tickets[0..count) in order (each with timeout_us),
- * results into out[0..count). Stops at the first error, which it returns. */
+/* tsdf_server_wait for every ticket of tickets[0..count) in order (each with
+ * timeout_us), results into out[0..count); out[i].status is the request's
+ * status, or TIMEOUT / INVALID for a ticket that was not taken (a timed-out
+ * ticket stays pending and can be waited for again). Returns TSDF_OK, or the
+ * first non-OK status met. */
 int tsdf_server_wait_many(tsdf_server* server, int32_t count, const uint64_t* tickets, tsdf_request_result* out,
                           int64_t timeout_us);
 

@@ -442,11 +442,14 @@ def tsdf_server_wait(server: int, ticket: int, timeout_us: int = -1) -> dict:
 
 
 def tsdf_server_wait_many(server: int, tickets, timeout_us: int = -1) -> list:
-    """Wait for several tickets in order (one call); returns their result dicts."""
+    """Wait for several tickets in order (one call); returns one result dict per
+    ticket. A dict's "status" is the request's status, or TSDF_ERR_TIMEOUT /
+    TSDF_ERR_INVALID for a ticket that was not taken (a timed-out one stays
+    pending)."""
     k = len(tickets)
     tk = (ctypes.c_uint64 * k)(*[int(t) for t in tickets])
     res = (tsdf_request_result * k)()
-    _check(lib().tsdf_server_wait_many(server, k, tk, res, int(timeout_us)), "tsdf_server_wait_many")
+    lib().tsdf_server_wait_many(server, k, tk, res, int(timeout_us))
     return [_result_dict(r) for r in res]
 
 

@@ -646,15 +646,23 @@ int tsdf_batch_integrate(tsdf_batch* b, tsdf_map* const* maps, const float* cons
 
 int tsdf_integrate_batch(tsdf_map* const* maps, const float* const* points_dev, const int64_t* n, const float* poses,
                          int32_t count, void* stream) {
-    // one batch object per host thread and device, created on first use
-    static thread_local tsdf_batch* per_device[64] = {};
+    // one batch object per host thread and device, created on first use and
+    // destroyed when the thread exits
+    struct PerThread {
+        tsdf_batch* b[64] = {};
+        ~PerThread() {
+            for (tsdf_batch* x : b) tsdf_batch_destroy(x);
+        }
+    };
+    static thread_local PerThread per_thread;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TSDF_ERR_CUDA;
-    if (!per_device[dev]) {
-        int rc = tsdf_batch_create(kBatchMax, &per_device[dev]);
+    tsdf_batch*& b = per_thread.b[dev];
+    if (!b) {
+        int rc = tsdf_batch_create(kBatchMax, &b);
         if (rc != TSDF_OK) return rc;
     }
-    return tsdf_batch_integrate(per_device[dev], maps, points_dev, n, poses, count, stream);
+    return tsdf_batch_integrate(b, maps, points_dev, n, poses, count, stream);
 }
 
 int tsdf_batch_sync(tsdf_batch* b, void* stream) {

@@ -443,11 +443,18 @@ int tsdf_server_wait(tsdf_server* s, uint64_t ticket, tsdf_request_result* out, 
 int tsdf_server_wait_many(tsdf_server* s, int32_t count, const uint64_t* tickets, tsdf_request_result* out,
                           int64_t timeout_us) {
     if (!s || count < 0 || (count > 0 && (!tickets || !out))) return TSDF_ERR_INVALID;
+    int first = TSDF_OK;
     for (int32_t i = 0; i < count; ++i) {
         const int rc = tsdf_server_wait(s, tickets[i], out + i, timeout_us);
-        if (rc != TSDF_OK) return rc;
+        if (rc == TSDF_ERR_TIMEOUT || rc == TSDF_ERR_INVALID) {
+            // not taken: mark the slot so the caller can tell it from a result
+            out[i] = tsdf_request_result{};
+            out[i].ticket = tickets[i];
+            out[i].status = rc;
+        }
+        if (first == TSDF_OK) first = rc;
     }
-    return TSDF_OK;
+    return first;
 }
 
 int tsdf_server_session_map(tsdf_server* s, int32_t session, tsdf_map** out) {

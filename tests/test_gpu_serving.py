@@ -150,7 +150,11 @@ def test_submit_many_and_wait_many():
         pts = [torch.from_numpy(np.ascontiguousarray(ws[i].scans[k], np.float32)).pin_memory() for i, k in plan]
         tickets = b.tsdf_server_submit_many(srv, [sids[i] for i, _ in plan], pts, [ws[i].poses[k] for i, k in plan])
         assert len(tickets) == min(6, len(plan))          # the window holds 6 outstanding requests
-        res = b.tsdf_server_wait_many(srv, tickets)
+        # an unknown ticket in the list is marked, the others are still taken
+        res = b.tsdf_server_wait_many(srv, [tickets[0], 1 << 60] + tickets[1:])
+        assert res[1]["status"] == b.TSDF_ERR_INVALID and res[1]["ticket"] == 1 << 60
+        del res[1]
+        assert [r["ticket"] for r in res] == tickets
         rest = b.tsdf_server_submit_many(srv, [sids[i] for i, _ in plan[len(tickets):]], pts[len(tickets):],
                                          [ws[i].poses[k] for i, k in plan[len(tickets):]])
         res += b.tsdf_server_wait_many(srv, rest)
