@@ -101,10 +101,13 @@ __global__ void __launch_bounds__(256) rays_kernel(const ScanArgs a, const MapDe
 template <int MODE, bool MERGE, int KPT>
 __global__ void __launch_bounds__(256, TSDF_CONTRIB_MIN_CTAS) contrib_kernel(const ScanArgs a, const MapDev m) {
     __shared__ unsigned long long red[8];
+    __shared__ uint32_t btab[kBrickCache];
     const unsigned lane = threadIdx.x & 31u;
     const unsigned gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
     pdl_trigger();
+    brick_cache_init(btab);
+    __syncthreads();
     pdl_wait();   // ray list and live count come from the rays kernel
     // A coherent load after the wait (a read-only __ldg could be hoisted above
     // it and see a count from before the rays kernel finished), one per warp.
@@ -121,7 +124,7 @@ __global__ void __launch_bounds__(256, TSDF_CONTRIB_MIN_CTAS) contrib_kernel(con
         float4 An, Bn;
         const unsigned next = item + nwarps;
         load_rays(m, next < nitems ? nlive : 0u, (next / ngrp) * 32u + lane, An, Bn);   // prefetch
-        contrib_item<MODE, MERGE, KPT>(a, m, item % ngrp, A, B, hits, last_brick);
+        contrib_item<MODE, MERGE, KPT>(a, m, item % ngrp, A, B, hits, last_brick, kNoSlot, nullptr, nullptr, btab);
         A = An;
         B = Bn;
     }
@@ -136,10 +139,13 @@ __global__ void __launch_bounds__(256, TSDF_CONTRIB_MIN_CTAS) contrib_kernel(con
 template <int MODE, int KPT>
 __global__ void __launch_bounds__(256, TSDF_CONTRIB_MIN_CTAS) emit_kernel(const ScanArgs a, const MapDev m) {
     __shared__ unsigned long long red[8];
+    __shared__ uint32_t btab[kBrickCache];
     const unsigned lane = threadIdx.x & 31u;
     const unsigned gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
     pdl_trigger();
+    brick_cache_init(btab);
+    __syncthreads();
     pdl_wait();
     unsigned nlive = 0;
     if (lane == 0) nlive = __ldcg(&m.ctr->live_count);
@@ -154,7 +160,7 @@ __global__ void __launch_bounds__(256, TSDF_CONTRIB_MIN_CTAS) emit_kernel(const 
         float4 A, B;
         load_rays(m, nlive, ray, A, B);
         const uint32_t sslot = ray < nlive ? m.ray_slot[ray] : kNoSlot;
-        contrib_item<MODE, false, KPT, true>(a, m, item % ngrp, A, B, hits, last_brick, sslot, &ovf);
+        contrib_item<MODE, false, KPT, true>(a, m, item % ngrp, A, B, hits, last_brick, sslot, &ovf, nullptr, btab);
     }
     if (ovf) m.ctr->overflow = 1u;
     if (MODE == 1) {

@@ -11,6 +11,16 @@ namespace dev {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr unsigned kNoVoxel = 0xFFFFFFFFu;
 
+// Per-CTA cache of marked bricks (direct mapped, multiplicative hash).
+constexpr int kBrickCacheLog2 = 11;
+constexpr int kBrickCache = 1 << kBrickCacheLog2;
+
+// Empty the CTA's brick cache (every thread calls it; a __syncthreads
+// must follow before the first use).
+__device__ __forceinline__ void brick_cache_init(uint32_t* btab) {
+    for (int i = threadIdx.x; i < kBrickCache; i += blockDim.x) btab[i] = kNoVoxel;
+}
+
 #ifndef TSDF_MARK_SHFL
 #define TSDF_MARK_SHFL 0
 #endif
@@ -248,7 +258,7 @@ template <int MODE, bool MERGE, int KPT, bool SORT = false, bool POOL = false>
 __device__ __forceinline__ void contrib_item(const ScanArgs& a, const MapDev& m, unsigned grp, const float4 A,
                                              const float4 B, unsigned& hits, unsigned& last_brick,
                                              uint32_t sslot = kNoSlot, bool* ovf = nullptr,
-                                             uint32_t* last_slot = nullptr) {
+                                             uint32_t* last_slot = nullptr, uint32_t* btab = nullptr) {
     static_assert(!(SORT && MERGE), "the sort reduction emits every sample");
     static_assert(!(POOL && (SORT || MERGE)), "the pool reduction is a variant of the plain atomic one");
     const unsigned lane = threadIdx.x & 31u;
@@ -352,7 +362,11 @@ __device__ __forceinline__ void contrib_item(const ScanArgs& a, const MapDev& m,
             if (MODE == 1 && !SORT) hits += act ? 1u : 0u;
             // mark the brick unless this lane marked it last (same-address
             // byte stores of a warp merge into one transaction); optionally
-            // also skip when the lane below marks the same brick now
+            // also skip when the lane below marks the same brick now. With
+            // `btab` (the CTA's shared-memory cache of bricks it has marked)
+            // the global store is issued only on a cache miss: many lanes and
+            // warps of a CTA touch the same few bricks, and same-address
+            // stores from every SM are what makes the marking costly.
 #if TSDF_MARK_SHFL
             const unsigned below = __shfl_up_sync(kFull, leader ? brick : kNoVoxel, 1);
             if (leader && brick != last_brick && (lane == 0 || below != brick)) {
@@ -360,7 +374,15 @@ __device__ __forceinline__ void contrib_item(const ScanArgs& a, const MapDev& m,
             if (leader && brick != last_brick) {
 #endif
                 last_brick = brick;
-                m.brick_flag[brick] = 1;
+                if (btab) {
+                    const unsigned h = (brick * 2654435761u) >> (32 - kBrickCacheLog2);
+                    if (btab[h] != brick) {
+                        btab[h] = brick;
+                        m.brick_flag[brick] = 1;
+                    }
+                } else {
+                    m.brick_flag[brick] = 1;
+                }
             }
         }
         if (SORT && lv) sidx += 2u * (uint32_t)J + 1u;
