@@ -50,6 +50,8 @@ constexpr int kBatchMax = 1024;               // maps per batch
 constexpr int kBatchThreads = 256;
 constexpr int kBatchWarps = kBatchThreads / 32;
 constexpr size_t kApplySmemPerWarp = kBrickVoxels * (4 + 8 + 2);   // grid, accumulator, offsets
+constexpr int kWarpBrickCacheLog2 = 10;                              // per-warp brick cache in phase 2
+static_assert((4u << kWarpBrickCacheLog2) <= kApplySmemPerWarp, "brick cache fits the staging area");
 
 struct BatchHeader {
     int32_t count;
@@ -184,6 +186,9 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem
         int cur = -1;
         unsigned hits = 0;
         bool ovf = false;
+        // each warp's brick cache lives in its apply staging area (unused
+        // until phase 4) and is emptied whenever the warp moves to another map
+        const BrickCache bc{reinterpret_cast<uint32_t*>(dyn + w * kApplySmemPerWarp), 32u - kWarpBrickCacheLog2};
         for (uint32_t g = gwarp; g < s_prefix[count]; g += nwarps) {   // warp-uniform
             const int i = find_segment(s_prefix, count, g);
             if (i != cur) {
@@ -194,6 +199,8 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem
                 ovf = false;
                 last_brick = kNoVoxel;
                 cur = i;
+                for (int e = (int)lane; e < (1 << kWarpBrickCacheLog2); e += 32) bc.tab[e] = kNoVoxel;
+                __syncwarp();
             }
             const BatchItem& it = items[i];
             const unsigned ngrp = (unsigned)(2 * it.a.K + KPT) / KPT;
@@ -205,11 +212,16 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem
             if (SORT) {
                 const uint32_t sslot = ray < nl ? it.m.ray_slot[ray] : kNoSlot;
                 if (it.reduce == 0)
-                    contrib_item<0, false, KPT, true>(it.a, it.m, local % ngrp, A, B, hits, last_brick, sslot, &ovf);
-                else contrib_item<1, false, KPT, true>(it.a, it.m, local % ngrp, A, B, hits, last_brick, sslot, &ovf);
+                    contrib_item<0, false, KPT, true>(it.a, it.m, local % ngrp, A, B, hits, last_brick, sslot, &ovf,
+                                                      nullptr, bc);
+                else contrib_item<1, false, KPT, true>(it.a, it.m, local % ngrp, A, B, hits, last_brick, sslot, &ovf,
+                                                       nullptr, bc);
             } else {
-                if (it.reduce == 0) contrib_item<0, MERGE, KPT>(it.a, it.m, local % ngrp, A, B, hits, last_brick);
-                else contrib_item<1, MERGE, KPT>(it.a, it.m, local % ngrp, A, B, hits, last_brick);
+                if (it.reduce == 0)
+                    contrib_item<0, MERGE, KPT>(it.a, it.m, local % ngrp, A, B, hits, last_brick, kNoSlot, nullptr,
+                                                nullptr, bc);
+                else contrib_item<1, MERGE, KPT>(it.a, it.m, local % ngrp, A, B, hits, last_brick, kNoSlot, nullptr,
+                                                 nullptr, bc);
             }
         }
         if (cur >= 0 && items[cur].reduce == 1) warp_add(hits, &items[cur].m.ctr->part[gwarp % kParts].hits);

@@ -73,6 +73,10 @@
 #ifndef TSDF_APPLY_CTAS_PER_SM
 #define TSDF_APPLY_CTAS_PER_SM 0
 #endif
+// Threads per CTA of the contribution kernel.
+#ifndef TSDF_CONTRIB_THREADS
+#define TSDF_CONTRIB_THREADS 256
+#endif
 // Minimum resident CTAs per SM requested for the apply kernel.
 #ifndef TSDF_APPLY_MIN_CTAS
 #define TSDF_APPLY_MIN_CTAS 1
@@ -98,9 +102,12 @@ __global__ void __launch_bounds__(256) rays_kernel(const ScanArgs a, const MapDe
 // steps). The grid is persistent (it fills the GPU once); each warp walks the
 // items with a grid stride and loads the next item's rays while it processes
 // the current one.
+constexpr int kContribThreads = TSDF_CONTRIB_THREADS;
+
 template <int MODE, bool MERGE, int KPT>
-__global__ void __launch_bounds__(256, TSDF_CONTRIB_MIN_CTAS) contrib_kernel(const ScanArgs a, const MapDev m) {
-    __shared__ unsigned long long red[8];
+__global__ void __launch_bounds__(kContribThreads, TSDF_CONTRIB_MIN_CTAS) contrib_kernel(const ScanArgs a,
+                                                                                        const MapDev m) {
+    __shared__ unsigned long long red[kContribThreads / 32];
     __shared__ uint32_t btab[kBrickCache];
     const unsigned lane = threadIdx.x & 31u;
     const unsigned gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -124,13 +131,14 @@ __global__ void __launch_bounds__(256, TSDF_CONTRIB_MIN_CTAS) contrib_kernel(con
         float4 An, Bn;
         const unsigned next = item + nwarps;
         load_rays(m, next < nitems ? nlive : 0u, (next / ngrp) * 32u + lane, An, Bn);   // prefetch
-        contrib_item<MODE, MERGE, KPT>(a, m, item % ngrp, A, B, hits, last_brick, kNoSlot, nullptr, nullptr, btab);
+        contrib_item<MODE, MERGE, KPT>(a, m, item % ngrp, A, B, hits, last_brick, kNoSlot, nullptr, nullptr,
+                                       BrickCache{btab, 32u - kBrickCacheLog2});
         A = An;
         B = Bn;
     }
     if (MODE == 1) {
         // MIN_ABS keeps no contribution count per voxel: count them here
-        const unsigned long long total = cta_sum<8>((unsigned long long)hits, red);
+        const unsigned long long total = cta_sum<kContribThreads / 32>((unsigned long long)hits, red);
         if (threadIdx.x == 0 && total) atomicAdd(&m.ctr->part[blockIdx.x % kParts].hits, total);
     }
 }
@@ -160,7 +168,8 @@ __global__ void __launch_bounds__(256, TSDF_CONTRIB_MIN_CTAS) emit_kernel(const 
         float4 A, B;
         load_rays(m, nlive, ray, A, B);
         const uint32_t sslot = ray < nlive ? m.ray_slot[ray] : kNoSlot;
-        contrib_item<MODE, false, KPT, true>(a, m, item % ngrp, A, B, hits, last_brick, sslot, &ovf, nullptr, btab);
+        contrib_item<MODE, false, KPT, true>(a, m, item % ngrp, A, B, hits, last_brick, sslot, &ovf, nullptr,
+                                             BrickCache{btab, 32u - kBrickCacheLog2});
     }
     if (ovf) m.ctr->overflow = 1u;
     if (MODE == 1) {
@@ -450,7 +459,8 @@ dim3 resident_grid(void (*kernel)(KArgs...), int threads, int per_sm = 0) {
 template <int MODE, bool MERGE, int KPT>
 cudaError_t launch_contrib_kk(const ScanArgs& a, const MapDev& m, bool pdl, cudaStream_t s) {
     auto* k = contrib_kernel<MODE, MERGE, KPT>;
-    return launch(k, resident_grid(k, 256, TSDF_CONTRIB_CTAS_PER_SM), dim3(256), s, pdl, a, m);
+    return launch(k, resident_grid(k, kContribThreads, TSDF_CONTRIB_CTAS_PER_SM), dim3(kContribThreads), s, pdl, a,
+                  m);
 }
 
 template <int MODE, bool MERGE>

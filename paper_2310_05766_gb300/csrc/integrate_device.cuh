@@ -11,7 +11,15 @@ namespace dev {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr unsigned kNoVoxel = 0xFFFFFFFFu;
 
-// Per-CTA cache of marked bricks (direct mapped, multiplicative hash).
+// Shared-memory cache of bricks already marked in the scan's brick flags
+// (direct mapped on a multiplicative hash of the brick index). A null table
+// sends every mark to global memory.
+struct BrickCache {
+    uint32_t* tab = nullptr;
+    unsigned shift = 32;          // 32 - log2(entries)
+};
+
+// The per-map contribution kernels keep one cache per CTA.
 constexpr int kBrickCacheLog2 = 11;
 constexpr int kBrickCache = 1 << kBrickCacheLog2;
 
@@ -258,7 +266,7 @@ template <int MODE, bool MERGE, int KPT, bool SORT = false, bool POOL = false>
 __device__ __forceinline__ void contrib_item(const ScanArgs& a, const MapDev& m, unsigned grp, const float4 A,
                                              const float4 B, unsigned& hits, unsigned& last_brick,
                                              uint32_t sslot = kNoSlot, bool* ovf = nullptr,
-                                             uint32_t* last_slot = nullptr, uint32_t* btab = nullptr) {
+                                             uint32_t* last_slot = nullptr, BrickCache bc = BrickCache{}) {
     static_assert(!(SORT && MERGE), "the sort reduction emits every sample");
     static_assert(!(POOL && (SORT || MERGE)), "the pool reduction is a variant of the plain atomic one");
     const unsigned lane = threadIdx.x & 31u;
@@ -362,11 +370,12 @@ __device__ __forceinline__ void contrib_item(const ScanArgs& a, const MapDev& m,
             if (MODE == 1 && !SORT) hits += act ? 1u : 0u;
             // mark the brick unless this lane marked it last (same-address
             // byte stores of a warp merge into one transaction); optionally
-            // also skip when the lane below marks the same brick now. With
-            // `btab` (the CTA's shared-memory cache of bricks it has marked)
-            // the global store is issued only on a cache miss: many lanes and
-            // warps of a CTA touch the same few bricks, and same-address
-            // stores from every SM are what makes the marking costly.
+            // also skip when the lane below marks the same brick now. With a
+            // brick cache the global store is issued only on a cache miss:
+            // many lanes and warps touch the same few bricks, and same-address
+            // stores from every SM are what makes the marking costly. (Any
+            // thread that puts a brick into the cache also stores its flag,
+            // so a hit never hides an unmarked brick.)
 #if TSDF_MARK_SHFL
             const unsigned below = __shfl_up_sync(kFull, leader ? brick : kNoVoxel, 1);
             if (leader && brick != last_brick && (lane == 0 || below != brick)) {
@@ -374,10 +383,10 @@ __device__ __forceinline__ void contrib_item(const ScanArgs& a, const MapDev& m,
             if (leader && brick != last_brick) {
 #endif
                 last_brick = brick;
-                if (btab) {
-                    const unsigned h = (brick * 2654435761u) >> (32 - kBrickCacheLog2);
-                    if (btab[h] != brick) {
-                        btab[h] = brick;
+                if (bc.tab) {
+                    const unsigned h = (brick * 2654435761u) >> bc.shift;
+                    if (bc.tab[h] != brick) {
+                        bc.tab[h] = brick;
                         m.brick_flag[brick] = 1;
                     }
                 } else {
