@@ -242,25 +242,42 @@ __global__ void __launch_bounds__(256) compact_kernel(const MapDev m, const uint
     compact_words(m, blockIdx.x * blockDim.x + threadIdx.x, nwords);
 }
 
-constexpr int kApplyWarps = 4;
+constexpr int kApplyWarps = 4;   // CTA size of the staged (sort and pool) apply kernels
+// CTA size of the register apply kernel.
+#ifndef TSDF_APPLY_WARPS
+#define TSDF_APPLY_WARPS 4
+#endif
+#if TSDF_APPLY_REG
+constexpr int kRegApplyWarps = TSDF_APPLY_WARPS;
+#else
+constexpr int kRegApplyWarps = kApplyWarps;
+#endif
+// Voxel pairs per lane in one apply task: 8 = a warp per brick, 4 = a warp
+// per half brick, 2 = per quarter brick (more, shorter tasks in flight: the
+// apply is latency-bound).
+#ifndef TSDF_APPLY_PAIRS
+#define TSDF_APPLY_PAIRS 2
+#endif
+constexpr int kApplyPairs = TSDF_APPLY_PAIRS;
 
 // The last CTA to finish also publishes the scan's counters (finish_if_last).
 template <int MODE>
-__global__ void __launch_bounds__(kApplyWarps * 32, TSDF_APPLY_MIN_CTAS) apply_kernel(const MapDev m, const int32_t w_max,
-                                                                  const int32_t flags) {
+__global__ void __launch_bounds__(kRegApplyWarps * 32, TSDF_APPLY_MIN_CTAS) apply_kernel(const MapDev m,
+                                                                                         const int32_t w_max,
+                                                                                         const int32_t flags) {
 #if !TSDF_APPLY_REG
     // per warp: the brick's grid words and accumulators, and the offsets of
     // its touched voxels (compacted)
-    __shared__ uint32_t s_grid[kApplyWarps][kBrickVoxels];
-    __shared__ unsigned long long s_acc[kApplyWarps][kBrickVoxels];
-    __shared__ uint16_t s_off[kApplyWarps][kBrickVoxels];
+    __shared__ uint32_t s_grid[kRegApplyWarps][kBrickVoxels];
+    __shared__ unsigned long long s_acc[kRegApplyWarps][kBrickVoxels];
+    __shared__ uint16_t s_off[kRegApplyWarps][kBrickVoxels];
 #endif
-    __shared__ unsigned long long red_u[kApplyWarps], red_h[kApplyWarps];
+    __shared__ unsigned long long red_u[kRegApplyWarps], red_h[kRegApplyWarps];
     __shared__ unsigned s_last;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned w = threadIdx.x >> 5;
-    const unsigned gwarp = blockIdx.x * kApplyWarps + w;
-    const unsigned nwarps = gridDim.x * kApplyWarps;
+    const unsigned gwarp = blockIdx.x * kRegApplyWarps + w;
+    const unsigned nwarps = gridDim.x * kRegApplyWarps;
     pdl_trigger();
     pdl_wait();   // list and accumulators come from the earlier kernels
     // coherent load after the wait (see contrib_kernel), one per warp
@@ -268,13 +285,13 @@ __global__ void __launch_bounds__(kApplyWarps * 32, TSDF_APPLY_MIN_CTAS) apply_k
     if (lane == 0) nb = __ldcg(&m.ctr->brick_count);
     nb = __shfl_sync(kFull, nb, 0);
     unsigned long long touched = 0, hits = 0;
-    for (unsigned i = gwarp; i < nb; i += nwarps) {
 #if TSDF_APPLY_REG
-        apply_brick_reg<MODE>(m, w_max, flags, i, touched, hits);
+    for (unsigned t = gwarp; t < nb * (8u / kApplyPairs); t += nwarps)
+        apply_part_reg<MODE, kApplyPairs>(m, w_max, flags, t, touched, hits);
 #else
+    for (unsigned i = gwarp; i < nb; i += nwarps)
         apply_brick<MODE>(m, w_max, flags, i, s_grid[w], s_acc[w], s_off[w], touched, hits);
 #endif
-    }
     for (int o = 16; o > 0; o >>= 1) {
         touched += __shfl_xor_sync(kFull, touched, o);
         hits += __shfl_xor_sync(kFull, hits, o);
@@ -286,7 +303,7 @@ __global__ void __launch_bounds__(kApplyWarps * 32, TSDF_APPLY_MIN_CTAS) apply_k
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long bu = 0, bh = 0;
-        for (int k = 0; k < kApplyWarps; ++k) {
+        for (int k = 0; k < kRegApplyWarps; ++k) {
             bu += red_u[k];
             bh += red_h[k];
         }
@@ -561,8 +578,8 @@ cudaError_t launch_compact(const MapDev& m, uint32_t bricks, bool pdl, cudaStrea
 
 cudaError_t launch_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t flags, bool pdl, cudaStream_t s) {
     auto* k = reduce == 0 ? apply_kernel<0> : apply_kernel<1>;
-    return launch(k, resident_grid(k, kApplyWarps * 32, TSDF_APPLY_CTAS_PER_SM), dim3(kApplyWarps * 32), s, pdl, m,
-                  w_max, flags);
+    return launch(k, resident_grid(k, kRegApplyWarps * 32, TSDF_APPLY_CTAS_PER_SM), dim3(kRegApplyWarps * 32), s,
+                  pdl, m, w_max, flags);
 }
 
 }  // namespace tsdf

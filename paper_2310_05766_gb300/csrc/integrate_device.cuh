@@ -556,23 +556,26 @@ __device__ __forceinline__ void apply_staged(const MapDev& m, int32_t w_max, int
 // and eight 16-byte accumulator pairs, all loaded at once; every touched voxel
 // is decoded in place (16 independent updates per lane), and only changed
 // pairs are written back and reset.
-template <int MODE>
+// NV voxel pairs per lane, starting at pair row v0: NV = 8 is the whole
+// brick, NV = 4 (v0 = 0 or 4) one half, NV = 2 a quarter.
+template <int MODE, int NV = 8>
 __device__ __forceinline__ void apply_brick_at(const MapDev& m, int32_t w_max, int32_t flags, unsigned brick,
                                                unsigned long long* accp, unsigned long long& touched,
-                                               unsigned long long& hits) {
+                                               unsigned long long& hits, unsigned v0 = 0) {
+    static_assert(NV == 8 || NV == 4 || NV == 2, "whole, half or quarter bricks");
     const unsigned lane = threadIdx.x & 31u;
-    uint2* gp = reinterpret_cast<uint2*>(m.grid + ((size_t)brick << 9));
-    ulonglong2* ap = reinterpret_cast<ulonglong2*>(accp);
-    ulonglong2 acc[8];
-    uint2 g[8];
+    uint2* gp = reinterpret_cast<uint2*>(m.grid + ((size_t)brick << 9)) + 32 * v0;
+    ulonglong2* ap = reinterpret_cast<ulonglong2*>(accp) + 32 * v0;
+    ulonglong2 acc[NV];
+    uint2 g[NV];
 #pragma unroll
-    for (int v = 0; v < 8; ++v) acc[v] = ap[32 * v + lane];
+    for (int v = 0; v < NV; ++v) acc[v] = ap[32 * v + lane];
 #pragma unroll
-    for (int v = 0; v < 8; ++v) g[v] = gp[32 * v + lane];
+    for (int v = 0; v < NV; ++v) g[v] = gp[32 * v + lane];
     unsigned cnt = 0;
     unsigned long long h = 0;
 #pragma unroll
-    for (int v = 0; v < 8; ++v) {
+    for (int v = 0; v < NV; ++v) {
         if (acc[v].x != 0ull) {
             h += decode_apply<MODE>(acc[v].x, g[v].x, w_max, flags);
             ++cnt;
@@ -583,7 +586,7 @@ __device__ __forceinline__ void apply_brick_at(const MapDev& m, int32_t w_max, i
         }
     }
 #pragma unroll
-    for (int v = 0; v < 8; ++v) {
+    for (int v = 0; v < NV; ++v) {
         if ((acc[v].x | acc[v].y) != 0ull) {
             gp[32 * v + lane] = g[v];
             ap[32 * v + lane] = make_ulonglong2(0ull, 0ull);
@@ -598,6 +601,15 @@ __device__ __forceinline__ void apply_brick_reg(const MapDev& m, int32_t w_max, 
                                                 unsigned long long& touched, unsigned long long& hits) {
     const unsigned brick = m.brick_list[i];
     apply_brick_at<MODE>(m, w_max, flags, brick, m.acc + ((size_t)brick << 9), touched, hits);
+}
+
+// Part t % P of listed brick t / P (P = 8 / NV parts per brick).
+template <int MODE, int NV>
+__device__ __forceinline__ void apply_part_reg(const MapDev& m, int32_t w_max, int32_t flags, unsigned t,
+                                               unsigned long long& touched, unsigned long long& hits) {
+    constexpr unsigned P = 8 / NV;
+    const unsigned brick = m.brick_list[t / P];
+    apply_brick_at<MODE, NV>(m, w_max, flags, brick, m.acc + ((size_t)brick << 9), touched, hits, (t % P) * NV);
 }
 
 // ---- apply: one warp updates listed brick number i of the map. Shared
