@@ -453,11 +453,13 @@ static int ensure_rays(tsdf_map* map, int64_t n) {
     cudaFree(map->dev.ray_b);
     map->dev.ray_a = map->dev.ray_b = nullptr;
     map->ray_cap = 0;
+    map->dev.ray_cap = 0;
     size_t cap = 1024;
     while (cap < (size_t)n) cap *= 2;
     TSDF_CU(cudaMalloc(&map->dev.ray_a, cap * sizeof(float4)));
     TSDF_CU(cudaMalloc(&map->dev.ray_b, cap * sizeof(float4)));
     map->ray_cap = cap;
+    map->dev.ray_cap = (uint32_t)cap;
     return TSDF_OK;
 }
 
@@ -541,7 +543,7 @@ static int integrate_with(tsdf_map* map, const float* points_dev, int64_t n, con
         if (rc != TSDF_OK) return rc;
         const MapDev& d = map->dev;
         cudaEvent_t e0 = n > 0 ? prof_mark(map, s) : nullptr;
-        TSDF_CU(launch_rays(a, d, false, pdl, s));
+        TSDF_CU(launch_rays(a, d, false, false, pdl, s));
         cudaEvent_t e1 = n > 0 ? prof_mark(map, s) : nullptr;
         cudaEvent_t e2 = n > 0 ? prof_mark(map, s) : nullptr;
         TSDF_CU(launch_pool_contrib(a, d, map->p.reduce, map->kpt, pdl, s));
@@ -561,7 +563,7 @@ static int integrate_with(tsdf_map* map, const float* points_dev, int64_t n, con
         if (rc != TSDF_OK) return rc;
         const MapDev& d = map->dev;
         cudaEvent_t e0 = n > 0 ? prof_mark(map, s) : nullptr;
-        TSDF_CU(launch_rays(a, d, true, pdl, s));
+        TSDF_CU(launch_rays(a, d, true, false, pdl, s));
         cudaEvent_t e1 = n > 0 ? prof_mark(map, s) : nullptr;
         cudaEvent_t e2 = n > 0 ? prof_mark(map, s) : nullptr;
         TSDF_CU(launch_emit(a, d, map->p.reduce, map->kpt, pdl, s));
@@ -582,7 +584,7 @@ static int integrate_with(tsdf_map* map, const float* points_dev, int64_t n, con
         return TSDF_OK;
     }
     cudaEvent_t e0 = n > 0 ? prof_mark(map, s) : nullptr;
-    TSDF_CU(launch_rays(a, map->dev, false, pdl, s));
+    TSDF_CU(launch_rays(a, map->dev, false, true, pdl, s));
     cudaEvent_t e1 = n > 0 ? prof_mark(map, s) : nullptr;
     cudaEvent_t e2 = n > 0 ? prof_mark(map, s) : nullptr;
     TSDF_CU(launch_contrib(a, map->dev, map->p.reduce, map->merge, map->kpt, pdl, s));

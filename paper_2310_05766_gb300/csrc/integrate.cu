@@ -73,6 +73,11 @@
 #ifndef TSDF_APPLY_CTAS_PER_SM
 #define TSDF_APPLY_CTAS_PER_SM 0
 #endif
+// 1: the plain path splits its ray list into heavy and light rays (see
+// rays_task); 0: one list in arrival order.
+#ifndef TSDF_RAYS_SPLIT
+#define TSDF_RAYS_SPLIT 1
+#endif
 // Threads per CTA of the contribution kernel.
 #ifndef TSDF_CONTRIB_THREADS
 #define TSDF_CONTRIB_THREADS 256
@@ -92,10 +97,10 @@ namespace {
 
 using namespace dev;
 
-template <bool SORT>
+template <bool SORT, bool SPLIT>
 __global__ void __launch_bounds__(256) rays_kernel(const ScanArgs a, const MapDev m) {
     __shared__ RaysSmem sm;
-    rays_task<true, SORT>(a, m, (int)(blockIdx.x * blockDim.x), blockIdx.x, &sm);
+    rays_task<true, SORT, SPLIT>(a, m, (int)(blockIdx.x * blockDim.x), blockIdx.x, &sm);
 }
 
 // Contribution work items: (block of 32 consecutive live rays, group of KPT
@@ -118,21 +123,44 @@ __global__ void __launch_bounds__(kContribThreads, TSDF_CONTRIB_MIN_CTAS) contri
     pdl_wait();   // ray list and live count come from the rays kernel
     // A coherent load after the wait (a read-only __ldg could be hoisted above
     // it and see a count from before the rays kernel finished), one per warp.
-    unsigned nlive = 0;
-    if (lane == 0) nlive = __ldcg(&m.ctr->live_count);
-    nlive = __shfl_sync(kFull, nlive, 0);
+    // The ray list may be split (heavy rays from the front, light ones from
+    // the end): the blocks of the front come first, so the costly items are
+    // taken in the first round and the CTAs that start late get light ones.
+    unsigned nf = 0, nb = 0;
+    if (lane == 0) {
+        nf = __ldcg(&m.ctr->live_count);
+        nb = __ldcg(&m.ctr->live_back);
+    }
+    nf = __shfl_sync(kFull, nf, 0);
+    nb = __shfl_sync(kFull, nb, 0);
+    const unsigned bf = (nf + 31u) / 32u, bb = (nb + 31u) / 32u;
     const unsigned ngrp = (unsigned)(2 * a.K + KPT) / KPT;   // ceil((2K+1) / KPT)
-    const unsigned nitems = (nlive + 31u) / 32u * ngrp;
+    const unsigned nitems = (bf + bb) * ngrp;
+    // first ray of block `blk` and the end of its part of the list
+    auto block_ray = [&](unsigned blk, unsigned& end) {
+        if (blk < bf) {
+            end = nf;
+            return blk * 32u;
+        }
+        end = m.ray_cap;
+        return m.ray_cap - nb + (blk - bf) * 32u;
+    };
     unsigned hits = 0;
     unsigned last_brick = kNoVoxel;
+    const BrickCache bc{btab, 32u - kBrickCacheLog2};
     float4 A, B;
-    load_rays(m, gwarp < nitems ? nlive : 0u, (gwarp / ngrp) * 32u + lane, A, B);
+    {
+        unsigned end;
+        const unsigned r0 = block_ray(gwarp / ngrp, end);
+        load_rays(m, gwarp < nitems ? end : 0u, r0 + lane, A, B);
+    }
     for (unsigned item = gwarp; item < nitems; item += nwarps) {   // warp-uniform
         float4 An, Bn;
         const unsigned next = item + nwarps;
-        load_rays(m, next < nitems ? nlive : 0u, (next / ngrp) * 32u + lane, An, Bn);   // prefetch
-        contrib_item<MODE, MERGE, KPT>(a, m, item % ngrp, A, B, hits, last_brick, kNoSlot, nullptr, nullptr,
-                                       BrickCache{btab, 32u - kBrickCacheLog2});
+        unsigned end;
+        const unsigned r0 = block_ray(next / ngrp, end);
+        load_rays(m, next < nitems ? end : 0u, r0 + lane, An, Bn);   // prefetch
+        contrib_item<MODE, MERGE, KPT>(a, m, item % ngrp, A, B, hits, last_brick, kNoSlot, nullptr, nullptr, bc);
         A = An;
         B = Bn;
     }
@@ -497,11 +525,12 @@ cudaError_t launch_emit_k(const ScanArgs& a, const MapDev& m, bool pdl, cudaStre
 
 }  // namespace
 
-cudaError_t launch_rays(const ScanArgs& a, const MapDev& m, bool sort, bool pdl, cudaStream_t s) {
+cudaError_t launch_rays(const ScanArgs& a, const MapDev& m, bool sort, bool split, bool pdl, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
     const dim3 grid((unsigned)((a.n + 255) / 256));
-    return sort ? launch(rays_kernel<true>, grid, dim3(256), s, pdl, a, m)
-                : launch(rays_kernel<false>, grid, dim3(256), s, pdl, a, m);
+    if (sort) return launch(rays_kernel<true, false>, grid, dim3(256), s, pdl, a, m);
+    return split && TSDF_RAYS_SPLIT ? launch(rays_kernel<false, true>, grid, dim3(256), s, pdl, a, m)
+                 : launch(rays_kernel<false, false>, grid, dim3(256), s, pdl, a, m);
 }
 
 cudaError_t launch_emit(const ScanArgs& a, const MapDev& m, int32_t reduce, int kpt, bool pdl, cudaStream_t s) {

@@ -88,19 +88,26 @@ __device__ __forceinline__ uint32_t ray_slots(const ScanArgs& a, float r, bool f
 }
 
 struct RaysSmem {
-    unsigned wl[8], wv[8], ws[8];   // per warp: live rays, valid rays, pair slots
+    unsigned wl[8], wv[8], ws[8];   // per warp: live (split: heavy) rays, valid rays, pair slots
+    unsigned wb[8];                 // per warp, split list: light rays
     unsigned base;                  // the CTA's first ray-list entry
+    unsigned bbase;                 // split list: the CTA's first light-ray entry, counted from the end
     unsigned long long sbase;       // the CTA's first pair slot (sort reduction)
 };
 
 // ---- rays: the CTA's 256 threads set up points [base, base + 256) of a scan
 // and append the live ones to the map's ray list. With SORT each live ray also
-// reserves its pair slots (one 64-bit atomic per CTA). With PDL the wait for
-// the preceding grid comes before the first access to the map's counters and
-// ray list.
-template <bool PDL, bool SORT>
+// reserves its pair slots (one 64-bit atomic per CTA). With SPLIT the rays
+// whose fill reaches at least one voxel each side at the hit (delta_z r >= vs,
+// the costly ones) go to the front of the list and the others to its end
+// (entry ray_cap - 1 - j for the j-th), so that the contribution kernel can
+// take the costly work first; with both ends counted, they never meet. With
+// PDL the wait for the preceding grid comes before the first access to the
+// map's counters and ray list.
+template <bool PDL, bool SORT, bool SPLIT = false>
 __device__ __forceinline__ void rays_task(const ScanArgs& a, const MapDev& m, int base, unsigned part,
                                           RaysSmem* sm) {
+    static_assert(!(SORT && SPLIT), "the sort reduction keeps one list");
     const int i = base + (int)threadIdx.x;
     const unsigned lane = threadIdx.x & 31u;
     float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -156,33 +163,46 @@ __device__ __forceinline__ void rays_task(const ScanArgs& a, const MapDev& m, in
             if (lane >= (unsigned)o) sincl += y;
         }
     }
-    // CTA-level compaction of the live rays: one list atomic per CTA
+    // CTA-level compaction of the live rays: one list atomic per CTA (per end)
     const unsigned warp = threadIdx.x >> 5;
-    const unsigned lmask = __ballot_sync(kFull, live);
+    const bool heavy = !SPLIT || (live && rb.w != 0.f && fm(fm(a.dz, ra.w), a.inv_vs) >= 1.f);
+    const unsigned lmask = __ballot_sync(kFull, live && heavy);
+    const unsigned bmask = SPLIT ? __ballot_sync(kFull, live && !heavy) : 0u;
     const unsigned vmask = __ballot_sync(kFull, valid);
     if (lane == 0) {
         sm->wl[warp] = __popc(lmask);
         sm->wv[warp] = __popc(vmask);
+        if (SPLIT) sm->wb[warp] = __popc(bmask);
     }
     if (SORT && lane == 31) sm->ws[warp] = sincl;
     __syncthreads();
     if (PDL) pdl_wait();   // the previous scan's finish kernel resets live_count and the counters
     if (threadIdx.x == 0) {
-        unsigned tl = 0, tv = 0;
+        unsigned tl = 0, tv = 0, tb = 0;
         unsigned long long ts = 0;
         for (int w = 0; w < 8; ++w) {
             tl += sm->wl[w];
             tv += sm->wv[w];
             if (SORT) ts += sm->ws[w];
+            if (SPLIT) tb += sm->wb[w];
         }
         sm->base = tl ? atomicAdd(&m.ctr->live_count, tl) : 0u;
+        if (SPLIT) sm->bbase = tb ? atomicAdd(&m.ctr->live_back, tb) : 0u;
         if (tv) atomicAdd(&m.ctr->part[part % kParts].valid, (unsigned long long)tv);
         if (SORT) sm->sbase = ts ? atomicAdd(&m.ctr->slot_count, ts) : 0ull;
     }
     __syncthreads();
     if (live) {
-        unsigned off = sm->base + __popc(lmask & ((1u << lane) - 1u));
-        for (unsigned w = 0; w < warp; ++w) off += sm->wl[w];
+        const unsigned below = (1u << lane) - 1u;
+        unsigned off;
+        if (heavy) {
+            off = sm->base + __popc(lmask & below);
+            for (unsigned w = 0; w < warp; ++w) off += sm->wl[w];
+        } else {
+            unsigned j = sm->bbase + __popc(bmask & below);
+            for (unsigned w = 0; w < warp; ++w) j += sm->wb[w];
+            off = m.ray_cap - 1u - j;
+        }
         m.ray_a[off] = ra;
         m.ray_b[off] = rb;
         if (SORT) {
@@ -195,11 +215,12 @@ __device__ __forceinline__ void rays_task(const ScanArgs& a, const MapDev& m, in
     }
 }
 
-// ---- contrib: rays of one 32-ray block (one per lane, dead lanes r = -1)
-__device__ __forceinline__ void load_rays(const MapDev& m, unsigned nlive, unsigned ray, float4& A, float4& B) {
+// ---- contrib: rays of one 32-ray block (one per lane, dead lanes r = -1);
+// `ray` is live when below `end`
+__device__ __forceinline__ void load_rays(const MapDev& m, unsigned end, unsigned ray, float4& A, float4& B) {
     A = make_float4(0.f, 0.f, 0.f, -1.f);
     B = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (ray < nlive) {
+    if (ray < end) {
         A = m.ray_a[ray];
         B = m.ray_b[ray];
     }
@@ -854,6 +875,7 @@ __device__ __forceinline__ void finish_warp(const MapDev& m) {
         c->apply_done = 0u;
         c->pool_count = 0u;
         c->pool_overflow = 0u;
+        c->live_back = 0u;
     }
 }
 

@@ -120,6 +120,7 @@ extern "C" int tsdf_integrate_static(uint32_t* grid_dev, const tsdf_params* para
     md.brick_list = reinterpret_cast<uint32_t*>(base + kOffList);
     md.ray_a = reinterpret_cast<float4*>(base + kOffRayA);
     md.ray_b = reinterpret_cast<float4*>(base + kOffRayB);
+    md.ray_cap = (uint32_t)kMaxPoints;
 
     // The array keeps the previous call's contents: clear everything that
     // must start at zero (counters, brick flags, this window's accumulators).
@@ -158,7 +159,7 @@ extern "C" int tsdf_integrate_static(uint32_t* grid_dev, const tsdf_params* para
     a.lcxy = a.lcx + ilog2((uint32_t)params->dims[1] / 8u);
     a.flags = params->flags;
 
-    if (e == cudaSuccess) e = launch_rays(a, md, false, true, s);
+    if (e == cudaSuccess) e = launch_rays(a, md, false, true, true, s);
     if (e == cudaSuccess) e = launch_contrib(a, md, params->reduce, false, 4, true, s);
     if (e == cudaSuccess) e = launch_compact(md, (uint32_t)bricks, true, s);
     if (e == cudaSuccess) e = launch_apply(md, params->reduce, params->w_max, params->flags, true, s);

@@ -40,6 +40,8 @@ struct MapCounters {
     unsigned long long surface_count;   // points found by the last surface extraction
     unsigned int pool_count;        // pool reduction: slots claimed by the scan in flight (may exceed the capacity)
     unsigned int pool_overflow;     // pool reduction: 1 if a brick found the pool full (the scan is dropped)
+    unsigned int live_back;         // split ray list: light rays of the scan in flight, stored from the list's end
+    unsigned int pad_;
 };
 
 constexpr uint32_t kPoolEmpty = 0xFFFFFFFFu;      // pool table entry of a brick without a slot
@@ -59,6 +61,7 @@ struct MapDev {
     uint32_t* brick_list;           // touched bricks of the scan in flight, built by the compaction kernel
     float4* ray_a;                  // per live ray (compacted): (dir.x, dir.y, dir.z, r)
     float4* ray_b;                  // per live ray (compacted): (int.x, int.y, int.z, fill ? 1 : 0)
+    uint32_t ray_cap;               // entries of ray_a / ray_b (the split list fills them from both ends)
     MapCounters* ctr;
     long long* host_last;           // mapped pinned host copy of last_valid / hits / touched / status, or null
     // sort reduction (null / 0 when the map has no sort buffers)
@@ -142,7 +145,10 @@ int map_reserve_points(::tsdf_map* map, int64_t n);
 int map_reserve_sort(::tsdf_map* map, int64_t n);
 
 // Launchers (return the cudaError_t of the launch).
-cudaError_t launch_rays(const ScanArgs& a, const MapDev& m, bool sort, bool pdl, cudaStream_t s);
+// sort: reserve pair slots per ray (sort reduction); split: heavy rays (fill
+// of at least one voxel each side) from the list's front, the others from
+// its end (the plain contribution kernel takes heavy work first).
+cudaError_t launch_rays(const ScanArgs& a, const MapDev& m, bool sort, bool split, bool pdl, cudaStream_t s);
 cudaError_t launch_contrib(const ScanArgs& a, const MapDev& m, int32_t reduce, bool merge, int kpt, bool pdl,
                            cudaStream_t s);
 cudaError_t launch_compact(const MapDev& m, uint32_t bricks, bool pdl, cudaStream_t s);

@@ -446,6 +446,22 @@ def test_fill_disabled_and_tiny_window():
     both(p, [("scan", pts, synth.pose12(synth.rot_zyx(0.3, 0.2, 0.1), np.array([0.0, 0.4, 0.0])))], label="tiny")
 
 
+@pytest.mark.parametrize("rlo, rhi", [(0.5, 2.0), (0.5, 1.2), (1.3, 2.0)])
+def test_heavy_and_light_rays(rlo, rhi):
+    """The plain path orders its ray list by fill size (rays with delta_z r >=
+    voxel size first): mixed, light-only and heavy-only scans, with both parts
+    of the list ending inside a 32-ray block."""
+    p = _edge_params(delta_z=0.08)   # heavy from r = 1.25 m
+    rng = np.random.default_rng(11)
+    for n in (1, 37, 1001):
+        pts = np.zeros((n, 4), np.float32)
+        d = rng.normal(size=(n, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        pts[:, :3] = d * rng.uniform(rlo, rhi, (n, 1))
+        pose = synth.pose12(synth.rot_zyx(0.4, 0.1, -0.2), np.array([0.05, -0.1, 0.02]))
+        both(p, [("scan", pts, pose), ("scan", pts[::-1].copy(), pose)], label=f"split n={n} r=[{rlo},{rhi}]")
+
+
 def test_weight_cap_reached():
     p = _edge_params(w_max=3)
     pose = synth.pose12(np.eye(3), np.zeros(3))
