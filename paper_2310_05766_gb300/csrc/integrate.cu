@@ -97,10 +97,16 @@ namespace {
 
 using namespace dev;
 
+// Threads per CTA of the ray set-up kernel (one list atomic per CTA and list end).
+#ifndef TSDF_RAYS_THREADS
+#define TSDF_RAYS_THREADS 256
+#endif
+constexpr int kRaysThreads = TSDF_RAYS_THREADS;
+
 template <bool SORT, bool SPLIT>
-__global__ void __launch_bounds__(256) rays_kernel(const ScanArgs a, const MapDev m) {
-    __shared__ RaysSmem sm;
-    rays_task<true, SORT, SPLIT>(a, m, (int)(blockIdx.x * blockDim.x), blockIdx.x, &sm);
+__global__ void __launch_bounds__(kRaysThreads) rays_kernel(const ScanArgs a, const MapDev m) {
+    __shared__ RaysSmemT<kRaysThreads / 32> sm;
+    rays_task<true, SORT, SPLIT, kRaysThreads / 32>(a, m, (int)(blockIdx.x * blockDim.x), blockIdx.x, &sm);
 }
 
 // Contribution work items: (block of 32 consecutive live rays, group of KPT
@@ -527,10 +533,10 @@ cudaError_t launch_emit_k(const ScanArgs& a, const MapDev& m, bool pdl, cudaStre
 
 cudaError_t launch_rays(const ScanArgs& a, const MapDev& m, bool sort, bool split, bool pdl, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
-    const dim3 grid((unsigned)((a.n + 255) / 256));
-    if (sort) return launch(rays_kernel<true, false>, grid, dim3(256), s, pdl, a, m);
-    return split && TSDF_RAYS_SPLIT ? launch(rays_kernel<false, true>, grid, dim3(256), s, pdl, a, m)
-                 : launch(rays_kernel<false, false>, grid, dim3(256), s, pdl, a, m);
+    const dim3 grid((unsigned)((a.n + kRaysThreads - 1) / kRaysThreads)), block(kRaysThreads);
+    if (sort) return launch(rays_kernel<true, false>, grid, block, s, pdl, a, m);
+    return split && TSDF_RAYS_SPLIT ? launch(rays_kernel<false, true>, grid, block, s, pdl, a, m)
+                                    : launch(rays_kernel<false, false>, grid, block, s, pdl, a, m);
 }
 
 cudaError_t launch_emit(const ScanArgs& a, const MapDev& m, int32_t reduce, int kpt, bool pdl, cudaStream_t s) {

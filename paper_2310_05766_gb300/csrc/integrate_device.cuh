@@ -87,16 +87,19 @@ __device__ __forceinline__ uint32_t ray_slots(const ScanArgs& a, float r, bool f
     return n;
 }
 
-struct RaysSmem {
-    unsigned wl[8], wv[8], ws[8];   // per warp: live (split: heavy) rays, valid rays, pair slots
-    unsigned wb[8];                 // per warp, split list: light rays
+template <int NW>
+struct RaysSmemT {
+    // per warp: live (split: heavy) rays, valid rays, pair slots, light rays
+    // (split list); thread 0 turns them into exclusive prefixes over the warps
+    unsigned wl[NW], wv[NW], ws[NW], wb[NW];
     unsigned base;                  // the CTA's first ray-list entry
     unsigned bbase;                 // split list: the CTA's first light-ray entry, counted from the end
     unsigned long long sbase;       // the CTA's first pair slot (sort reduction)
 };
+using RaysSmem = RaysSmemT<8>;
 
-// ---- rays: the CTA's 256 threads set up points [base, base + 256) of a scan
-// and append the live ones to the map's ray list. With SORT each live ray also
+// ---- rays: the CTA's 32 NW threads set up points [base, base + 32 NW) of a
+// scan and append the live ones to the map's ray list. With SORT each live ray also
 // reserves its pair slots (one 64-bit atomic per CTA). With SPLIT the rays
 // whose fill reaches at least one voxel each side at the hit (delta_z r >= vs,
 // the costly ones) go to the front of the list and the others to its end
@@ -104,9 +107,9 @@ struct RaysSmem {
 // take the costly work first; with both ends counted, they never meet. With
 // PDL the wait for the preceding grid comes before the first access to the
 // map's counters and ray list.
-template <bool PDL, bool SORT, bool SPLIT = false>
+template <bool PDL, bool SORT, bool SPLIT = false, int NW = 8>
 __device__ __forceinline__ void rays_task(const ScanArgs& a, const MapDev& m, int base, unsigned part,
-                                          RaysSmem* sm) {
+                                          RaysSmemT<NW>* sm) {
     static_assert(!(SORT && SPLIT), "the sort reduction keeps one list");
     const int i = base + (int)threadIdx.x;
     const unsigned lane = threadIdx.x & 31u;
@@ -178,13 +181,22 @@ __device__ __forceinline__ void rays_task(const ScanArgs& a, const MapDev& m, in
     __syncthreads();
     if (PDL) pdl_wait();   // the previous scan's finish kernel resets live_count and the counters
     if (threadIdx.x == 0) {
-        unsigned tl = 0, tv = 0, tb = 0;
+        unsigned tl = 0, tv = 0, tb = 0, ts32 = 0;
         unsigned long long ts = 0;
-        for (int w = 0; w < 8; ++w) {
-            tl += sm->wl[w];
+        for (int w = 0; w < NW; ++w) {
+            const unsigned l = sm->wl[w], b = SPLIT ? sm->wb[w] : 0u, q = SORT ? sm->ws[w] : 0u;
+            sm->wl[w] = tl;
+            tl += l;
             tv += sm->wv[w];
-            if (SORT) ts += sm->ws[w];
-            if (SPLIT) tb += sm->wb[w];
+            if (SPLIT) {
+                sm->wb[w] = tb;
+                tb += b;
+            }
+            if (SORT) {
+                sm->ws[w] = ts32;
+                ts32 += q;
+                ts += q;
+            }
         }
         sm->base = tl ? atomicAdd(&m.ctr->live_count, tl) : 0u;
         if (SPLIT) sm->bbase = tb ? atomicAdd(&m.ctr->live_back, tb) : 0u;
@@ -196,18 +208,14 @@ __device__ __forceinline__ void rays_task(const ScanArgs& a, const MapDev& m, in
         const unsigned below = (1u << lane) - 1u;
         unsigned off;
         if (heavy) {
-            off = sm->base + __popc(lmask & below);
-            for (unsigned w = 0; w < warp; ++w) off += sm->wl[w];
+            off = sm->base + sm->wl[warp] + __popc(lmask & below);
         } else {
-            unsigned j = sm->bbase + __popc(bmask & below);
-            for (unsigned w = 0; w < warp; ++w) j += sm->wb[w];
-            off = m.ray_cap - 1u - j;
+            off = m.ray_cap - 1u - (sm->bbase + sm->wb[warp] + __popc(bmask & below));
         }
         m.ray_a[off] = ra;
         m.ray_b[off] = rb;
         if (SORT) {
-            unsigned long long first = sm->sbase + (sincl - (nslot == kNoSlot ? 0u : nslot));
-            for (unsigned w = 0; w < warp; ++w) first += sm->ws[w];
+            const unsigned long long first = sm->sbase + sm->ws[warp] + (sincl - (nslot == kNoSlot ? 0u : nslot));
             // slots at or beyond the capacity overflow, sample by sample
             m.ray_slot[off] = nslot == kNoSlot ? kNoSlot
                                                 : (uint32_t)(first < m.pair_cap ? first : (unsigned long long)m.pair_cap);
