@@ -40,8 +40,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "TSDF voxel updates/s (OS1-128-shaped scan)"
 # DRAM bytes (read + write) per launch from the committed ncu capture of these
-# kernels on this workload (profiles/contrib_apply_outdoor_128x1024.md). Reset
-# an entry to None whenever its kernel changes.
+# kernels on the outdoor workload, the default one
+# (profiles/contrib_apply_outdoor_128x1024.md); other workloads report none.
+# Reset an entry to None whenever its kernel changes.
 NCU_DRAM_BYTES = {"contrib": 13.25e6 + 0.5e3, "apply": 27.55e6 + 1.5e3, "rays": None}
 UNIT = "voxel_updates/s"
 N_SEQ = 100
@@ -367,7 +368,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                      (1e3 * float(sum(prof_step_ms)) / K),
         roofline=dict(kernel=kname, bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
                       peak_source=f"{peak_kind} hbm_gbs",
-                      traffic=NCU_DRAM_BYTES.get(kname) if args.reduction == "atomic" else None,
+                      traffic=(NCU_DRAM_BYTES.get(kname) if args.reduction == "atomic" and args.workload == "outdoor"
+                               else None),
                       alg_bytes_def=("16 B per point read + 8 B per touched voxel of the per-scan volume"
                                      if kname in ("contrib", "emit") else
                                      "16 B per touched voxel (volume read + grid RMW)"),
