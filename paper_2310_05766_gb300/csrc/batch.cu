@@ -40,6 +40,13 @@
 #ifndef TSDF_BATCH_APPLY_REG
 #define TSDF_BATCH_APPLY_REG 1
 #endif
+// Voxel pairs per lane in one register-apply task of the atomic configurations
+// (8: a warp per brick, 4: per half brick, 2: per quarter brick). Whole bricks
+// measured fastest here (quarter bricks: 1.85 against 1.67 ms for 64 maps;
+// every task pays a search for its map).
+#ifndef TSDF_BATCH_APPLY_PAIRS
+#define TSDF_BATCH_APPLY_PAIRS 8
+#endif
 
 namespace tsdf {
 namespace {
@@ -259,7 +266,9 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem
     }
 
     // ---- phase 4: Eq. 1 / Eq. 2 on the touched bricks, one warp per brick
-    block_prefix(count, [&](int i) { return __ldcg(&items[i].m.ctr->brick_count); }, s_prefix);
+    // tasks per map: its listed bricks, or (register apply) kParts8 parts of each
+    constexpr unsigned kParts8 = (!SORT && TSDF_BATCH_APPLY_REG) ? 8u / TSDF_BATCH_APPLY_PAIRS : 1u;
+    block_prefix(count, [&](int i) { return __ldcg(&items[i].m.ctr->brick_count) * kParts8; }, s_prefix);
     {
         uint32_t* s_grid = reinterpret_cast<uint32_t*>(dyn + w * kApplySmemPerWarp);
         unsigned long long* s_acc = reinterpret_cast<unsigned long long*>(dyn + w * kApplySmemPerWarp + 2048);
@@ -285,8 +294,9 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem
                 else sort_apply_brick<1>(it.m, it.w_max, it.flags, local, ovf, s_grid, s_acc, s_off, touched, hits);
             } else {
 #if TSDF_BATCH_APPLY_REG
-                if (it.reduce == 0) apply_brick_reg<0>(it.m, it.w_max, it.flags, local, touched, hits);
-                else apply_brick_reg<1>(it.m, it.w_max, it.flags, local, touched, hits);
+                if (it.reduce == 0)
+                    apply_part_reg<0, TSDF_BATCH_APPLY_PAIRS>(it.m, it.w_max, it.flags, local, touched, hits);
+                else apply_part_reg<1, TSDF_BATCH_APPLY_PAIRS>(it.m, it.w_max, it.flags, local, touched, hits);
 #else
                 if (it.reduce == 0) apply_brick<0>(it.m, it.w_max, it.flags, local, s_grid, s_acc, s_off, touched, hits);
                 else apply_brick<1>(it.m, it.w_max, it.flags, local, s_grid, s_acc, s_off, touched, hits);
