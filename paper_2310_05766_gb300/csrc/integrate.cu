@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kContribThreads, TSDF_CONTRIB_MIN_CTAS) contri
     // it and see a count from before the rays kernel finished), one per warp.
     // The ray list may be split (heavy rays from the front, light ones from
     // the end): the blocks of the front come first, so the costly items are
-    // taken in the first round and the CTAs that start late get light ones.
+    // taken by the first wave of CTAs and the CTAs that start late get light ones.
     unsigned nf = 0, nb = 0;
     if (lane == 0) {
         nf = __ldcg(&m.ctr->live_count);
