@@ -265,10 +265,10 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem
         if (!grid_barrier(sync, arrivals, spin)) return;
     }
 
-    // ---- phase 4: Eq. 1 / Eq. 2 on the touched bricks, one warp per brick
-    // tasks per map: its listed bricks, or (register apply) kParts8 parts of each
-    constexpr unsigned kParts8 = (!SORT && TSDF_BATCH_APPLY_REG) ? 8u / TSDF_BATCH_APPLY_PAIRS : 1u;
-    block_prefix(count, [&](int i) { return __ldcg(&items[i].m.ctr->brick_count) * kParts8; }, s_prefix);
+    // ---- phase 4: Eq. 1 / Eq. 2 on the touched bricks, one warp task per brick
+    // (register apply: per part of a brick, kTaskParts parts each)
+    constexpr unsigned kTaskParts = (!SORT && TSDF_BATCH_APPLY_REG) ? 8u / TSDF_BATCH_APPLY_PAIRS : 1u;
+    block_prefix(count, [&](int i) { return __ldcg(&items[i].m.ctr->brick_count) * kTaskParts; }, s_prefix);
     {
         uint32_t* s_grid = reinterpret_cast<uint32_t*>(dyn + w * kApplySmemPerWarp);
         unsigned long long* s_acc = reinterpret_cast<unsigned long long*>(dyn + w * kApplySmemPerWarp + 2048);

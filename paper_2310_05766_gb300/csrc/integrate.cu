@@ -7,7 +7,9 @@
 //   march (+-tau around the hit, widened by the fill height of Eq. 4 and a
 //   safety margin) stays outside the window box is dropped, since none of its
 //   samples could land in the window. Order is kept within a CTA, so
-//   neighbouring rays stay neighbours.
+//   neighbouring rays stay neighbours. On the plain path the list is split:
+//   rays whose fill reaches a voxel each side (delta_z r >= vs) are appended
+//   from its front, the others from its end.
 // contrib (K-B): persistent; a warp takes work items (32 consecutive live
 //   rays, a group of KPT steps k of k = -K..K), one ray per lane. For each of its steps the
 //   thread walks the fill samples j = -J..J (Eq. 3 / Eq. 4) in warp lock-step.
@@ -21,19 +23,21 @@
 //   voxel in the same iteration are first combined with match.any +
 //   redux.sync so that one lane per distinct voxel issues the reduction. The
 //   issuing lane marks the voxel's brick in a byte-per-brick flag array with
-//   a plain store (idempotent, nothing to wait for). Integer accumulation
-//   makes the result independent of the order of the atomics.
+//   a plain store (idempotent, nothing to wait for), filtered by a per-CTA
+//   shared-memory cache of the bricks the CTA has marked. The items of the
+//   list's front (the costly rays) come first. Integer accumulation makes the
+//   result independent of the order of the atomics.
 // compact: turns the brick flags into a list of touched bricks (4 flags per
 //   thread, one list atomic per warp) and clears the flags.
-// apply (K-C): one warp per listed brick (grid-stride over the list). The
-//   warp copies the brick's grid words and accumulators into shared memory with
-//   coalesced 16-byte loads and compacts its
-//   touched voxels (non-zero accumulators) into a dense list with a warp scan,
-//   then applies Eq. 1 in exact integers with one rounding (half away from
-//   zero) and Eq. 2 with the weight cap one touched voxel per lane, writes the
-//   brick back with 16-byte stores and resets the accumulators. Touched voxels
-//   are counted, and in WSUM mode the contributions too (the sum of the decoded
-//   weights).
+// apply (K-C): warp tasks over the listed bricks (grid-stride), by default a
+//   quarter brick per task: each lane loads its voxel pairs' accumulators and
+//   grid words into registers with coalesced loads, applies Eq. 1 in exact
+//   integers with one rounding (half away from zero) and Eq. 2 with the weight
+//   cap to every touched voxel (non-zero accumulator), writes changed pairs
+//   back and resets their accumulators. (TSDF_APPLY_REG 0 selects the older
+//   form: a warp per brick staged in shared memory, touched voxels compacted
+//   with a warp scan.) Touched voxels are counted, and in WSUM mode the
+//   contributions too (the sum of the decoded weights).
 // finish: the last apply CTA to retire sums the per-scan counters into the
 //   published ones and clears the per-scan state (one warp).
 //
