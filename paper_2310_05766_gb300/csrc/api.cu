@@ -11,6 +11,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "chunk_index.h"
 #include "tsdf_internal.cuh"
 #include "../../include/tsdf.h"
 
@@ -43,116 +44,6 @@ struct DeviceScope {
     ~DeviceScope() {
         if (changed) cudaSetDevice(prev);
     }
-};
-
-struct ChunkKey {
-    long long x, y, z;
-    bool operator==(const ChunkKey& o) const { return x == o.x && y == o.y && z == o.z; }
-};
-
-// Index of the global store: chunk key -> store slot, in two levels. Chunks
-// are grouped into 8 x 8 x 8 super-chunks; an open-addressing hash table
-// (linear probing, grown by doubling at half load) maps a super-chunk key to
-// a block of 512 slots. A shift enumerates runs of neighbouring chunks,
-// looking up each leaving and each entering one, so the last two blocks found
-// are kept and most lookups are one array access instead of a cache miss in a
-// large table.
-class ChunkIndex {
-public:
-    // slot of `k`, or -1
-    long long find(const ChunkKey& k) {
-        const uint32_t* b = block(super(k), false);
-        if (!b) return -1;
-        const uint32_t v = b[local(k)];
-        return v == kNone ? -1 : (long long)v;
-    }
-    void insert(const ChunkKey& k, uint32_t v) {
-        uint32_t* b = block(super(k), true);
-        uint32_t& e = b[local(k)];
-        if (e == kNone) ++count_;
-        e = v;
-    }
-    size_t size() const { return count_; }
-    template <typename F>
-    void for_each(F&& f) const {
-        for (size_t i = 0; i < keys_.size(); ++i) {
-            if (!used_[i]) continue;
-            const uint32_t* b = &slots_[(size_t)vals_[i] * 512];
-            for (int j = 0; j < 512; ++j)
-                if (b[j] != kNone)
-                    f(ChunkKey{keys_[i].x * 8 + (j & 7), keys_[i].y * 8 + ((j >> 3) & 7), keys_[i].z * 8 + (j >> 6)},
-                      b[j]);
-        }
-    }
-
-private:
-    static constexpr uint32_t kNone = 0xFFFFFFFFu;
-    // floor division by 8 and the remainder (arithmetic shift on the signed keys)
-    static ChunkKey super(const ChunkKey& k) { return ChunkKey{k.x >> 3, k.y >> 3, k.z >> 3}; }
-    static int local(const ChunkKey& k) { return (int)(((k.z & 7) << 6) | ((k.y & 7) << 3) | (k.x & 7)); }
-    // the 512 slots of super-chunk `s`, created (all empty) when `create`, else null if absent
-    uint32_t* block(const ChunkKey& s, bool create) {
-        for (int c = 0; c < 2; ++c)
-            if (last_[c] >= 0 && last_key_[c] == s) return &slots_[(size_t)last_[c] * 512];
-        long long bi = -1;
-        if (!keys_.empty()) {
-            for (size_t i = hash(s) & mask_;; i = (i + 1) & mask_) {
-                if (!used_[i]) break;
-                if (keys_[i] == s) {
-                    bi = vals_[i];
-                    break;
-                }
-            }
-        }
-        if (bi < 0) {
-            if (!create) return nullptr;
-            bi = (long long)(slots_.size() / 512);
-            slots_.resize(slots_.size() + 512, kNone);
-            if (2 * (nblocks_ + 1) > keys_.size()) grow();
-            put(s, (uint32_t)bi);
-            ++nblocks_;
-        }
-        last_[1] = last_[0];
-        last_key_[1] = last_key_[0];
-        last_[0] = bi;
-        last_key_[0] = s;
-        return &slots_[(size_t)bi * 512];
-    }
-    static size_t hash(const ChunkKey& k) {
-        unsigned long long h = (unsigned long long)k.x * 0x9E3779B97F4A7C15ull;
-        h ^= (unsigned long long)k.y * 0xC2B2AE3D27D4EB4Full + (h << 6) + (h >> 2);
-        h ^= (unsigned long long)k.z * 0x165667B19E3779F9ull + (h << 6) + (h >> 2);
-        return (size_t)(h ^ (h >> 29));
-    }
-    void put(const ChunkKey& k, uint32_t v) {
-        size_t i = hash(k) & mask_;
-        while (used_[i]) i = (i + 1) & mask_;
-        keys_[i] = k;
-        vals_[i] = v;
-        used_[i] = 1;
-    }
-    void grow() {
-        std::vector<ChunkKey> ok;
-        std::vector<uint32_t> ov;
-        std::vector<unsigned char> ou;
-        ok.swap(keys_);
-        ov.swap(vals_);
-        ou.swap(used_);
-        const size_t n = ok.empty() ? 4096 : 2 * ok.size();
-        keys_.assign(n, ChunkKey{0, 0, 0});
-        vals_.assign(n, 0u);
-        used_.assign(n, 0);
-        mask_ = n - 1;
-        for (size_t i = 0; i < ok.size(); ++i)
-            if (ou[i]) put(ok[i], ov[i]);
-    }
-    std::vector<ChunkKey> keys_;          // super-chunk keys
-    std::vector<uint32_t> vals_;          // their block numbers
-    std::vector<unsigned char> used_;
-    std::vector<uint32_t> slots_;         // 512 slots per block
-    size_t mask_ = 0, count_ = 0, nblocks_ = 0;
-    long long last_[2] = {-1, -1};        // the last two blocks found, and their keys
-    ChunkKey last_key_[2] = {};
 };
 
 constexpr uint32_t kChunkBytes = 8 * 8 * 8 * 4;
