@@ -3,6 +3,7 @@
 // launch sequence of each call. No float arithmetic of the method runs here
 // beyond the per-map constants 1/voxel, QMAX/tau and K, derived once in
 // binary64 and rounded to binary32.
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -83,7 +84,8 @@ struct tsdf_map {
     MapDev dev{};
     // device-resident global store of 8^3 chunks
     ChunkIndex store_index;
-    std::vector<char*> store_segments;
+    std::vector<char*> store_segments;   // 8 MiB each, carved from store_allocs
+    std::vector<char*> store_allocs;     // the device allocations behind them
     uint32_t store_count = 0;
     ShiftItem* items_dev = nullptr;
     size_t items_dev_cap = 0;
@@ -230,7 +232,7 @@ void free_map(tsdf_map* m) {
     cudaFree(m->dev.ray_slot);
     cudaFree(m->dev.pairs);
     cudaFree(m->dev.sorted);
-    for (char* s : m->store_segments) cudaFree(s);
+    for (char* s : m->store_allocs) cudaFree(s);
     cudaFree(m->items_dev);
     if (m->items_host) cudaFreeHost(m->items_host);
     if (m->items_event) cudaEventDestroy(m->items_event);
@@ -260,10 +262,20 @@ int store_lookup(tsdf_map* m, const ChunkKey& k, bool create, unsigned long long
     }
     uint32_t idx = m->store_count;
     if (idx / kSegChunks >= m->store_segments.size()) {
-        char* seg = nullptr;
-        cudaError_t e = cudaMalloc(&seg, (size_t)kSegChunks * kChunkBytes);
+        // segments come in growing batches (1, 2, 4, ... 32 per allocation), so
+        // a map moving into new ground does not pay an allocation at every shift
+        const size_t seg_bytes = (size_t)kSegChunks * kChunkBytes;
+        size_t n = (size_t)1 << std::min<size_t>(5, m->store_allocs.size());
+        char* base = nullptr;
+        cudaError_t e = cudaMalloc(&base, n * seg_bytes);
+        if (e != cudaSuccess && n > 1) {   // short of memory: one segment at a time
+            cudaGetLastError();
+            n = 1;
+            e = cudaMalloc(&base, seg_bytes);
+        }
         if (e != cudaSuccess) return cuda_fail(e);
-        m->store_segments.push_back(seg);
+        m->store_allocs.push_back(base);
+        for (size_t i = 0; i < n; ++i) m->store_segments.push_back(base + i * seg_bytes);
     }
     m->store_count++;
     m->store_index.insert(k, idx);

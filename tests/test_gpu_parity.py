@@ -523,6 +523,32 @@ def test_outdoor_sequence_prefix_exact():
     assert min(s["hits"] for s in g[2]) > 1_000_000
 
 
+def test_store_over_several_allocations():
+    """A 64^3 window moved by its own size 26 times (512 chunks stored per
+    shift, over 13 k in all: store segments from three growing allocations)
+    with a scan at every position, then walked back, reading every stored
+    chunk again; compared with the oracle throughout."""
+    p = synth.params_dict((64, 64, 64), 0.1, 0.3, 64, 0.05, 0.3, 3.0, 0, (0, 0, 0))
+    rng = np.random.default_rng(21)
+    pts = np.zeros((3000, 4), np.float32)
+    d = rng.normal(size=(3000, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    pts[:, :3] = d * rng.uniform(0.5, 2.8, (3000, 1))
+    steps = []
+    checks = []   # walk-back positions whose chunks sit in the third, second and first allocation
+    xs = list(range(0, 27)) + list(range(25, -1, -1))
+    for k, xi in enumerate(xs):
+        origin = (64 * xi, 0, 0)
+        if k > 0:
+            steps.append(("shift", origin))
+        t = np.array([(origin[0] + 32) * 0.1, 3.2, 3.2])
+        steps.append(("scan", pts, synth.pose12(synth.rot_zyx(0.1 * k, 0.0, 0.0), t)))
+        if k > 26 and xi in (24, 20, 0):
+            checks.append((xi, len(steps)))
+    for xi, n in checks:
+        both(p, steps[:n], label=f"store over several allocations, back at x = {64 * xi}")
+
+
 def test_corridor_prefix_exact():
     """High-resolution corridor at full size (1024 x 1024 x 256 at 0.02 m): two
     scans, a 24-voxel shift along x, one more scan."""
