@@ -95,3 +95,22 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(b, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         b.lib()
+
+
+def test_binding_constants_match_the_header():
+    """Every integer #define of include/tsdf.h that the Python binding also
+    defines has the same value there, and the binding defines all error codes,
+    options and mode constants."""
+    from paper_2310_05766_gb300 import binding as b
+    text = open(os.path.join(ROOT, "include", "tsdf.h")).read()
+    consts = {}
+    for m in re.finditer(r"^#define\s+(TSDF_\w+)\s+(\(?-?\d+(?:LL)?(?:\s*<<\s*\d+)?\)?)", text, flags=re.M):
+        expr = m.group(2).replace("LL", "")
+        consts[m.group(1)] = int(eval(expr, {"__builtins__": {}}))
+    assert len(consts) > 30
+    required = [n for n in consts if n.startswith(("TSDF_ERR_", "TSDF_OPT_", "TSDF_REDUCE_", "TSDF_REDUCTION_",
+                                                  "TSDF_FLAG_", "TSDF_BATCH_OPT_"))] + ["TSDF_OK"]
+    missing = [n for n in required if not hasattr(b, n)]
+    assert not missing, missing
+    wrong = [(n, v, getattr(b, n)) for n, v in consts.items() if hasattr(b, n) and getattr(b, n) != v]
+    assert not wrong, wrong
