@@ -116,8 +116,9 @@ def lib():
     f32p = P(ctypes.c_float)
     L.tsdf_map_create.argtypes = [P(tsdf_params), P(vp)]
     L.tsdf_map_destroy.argtypes = [vp]
-    L.tsdf_integrate.argtypes = [vp, vp, i64, f32p, vp]
-    L.tsdf_integrate_host.argtypes = [vp, vp, i64, f32p, vp]
+    # the pose by address (the per-scan calls skip building a ctypes pointer)
+    L.tsdf_integrate.argtypes = [vp, vp, i64, vp, vp]
+    L.tsdf_integrate_host.argtypes = [vp, vp, i64, vp, vp]
     L.tsdf_shift.argtypes = [vp, P(i64), vp]
     L.tsdf_read.argtypes = [vp, P(i64), P(i64), vp, vp, vp]
     L.tsdf_write.argtypes = [vp, P(i64), P(i64), vp, vp, vp]
@@ -205,6 +206,15 @@ def _pose_arg(pose):
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
 
 
+def _pose_addr(pose):
+    """The pose as float32[12] (the array itself when it already is one, else a
+    copy) and its address; the caller keeps the array alive over the call."""
+    if not (isinstance(pose, np.ndarray) and pose.dtype == np.float32 and pose.size == 12
+            and pose.flags.c_contiguous):
+        pose = np.ascontiguousarray(np.asarray(pose, dtype=np.float32).reshape(12))
+    return pose, pose.ctypes.data
+
+
 def _i64_3(v):
     a = (ctypes.c_int64 * 3)(*[int(x) for x in v])
     return a
@@ -234,7 +244,7 @@ def tsdf_map_destroy(handle: int) -> None:
 def tsdf_integrate(handle: int, points_dev, n: int, pose, stream=None) -> None:
     """points_dev: a CUDA float32 tensor of shape (n, 4) (or a raw device pointer)."""
     ptr = points_dev if isinstance(points_dev, int) else points_dev.data_ptr()
-    pa, pp = _pose_arg(pose)
+    pa, pp = _pose_addr(pose)
     _check(lib().tsdf_integrate(handle, ptr, int(n), pp, _stream_ptr(stream)), "tsdf_integrate")
 
 
@@ -247,7 +257,7 @@ def tsdf_integrate_host(handle: int, points_host, n: int, pose, stream=None) -> 
         ptr = points_host.ctypes.data
     else:
         ptr = points_host.data_ptr()
-    pa, pp = _pose_arg(pose)
+    pa, pp = _pose_addr(pose)
     _check(lib().tsdf_integrate_host(handle, ptr, int(n), pp, _stream_ptr(stream)), "tsdf_integrate_host")
 
 
