@@ -138,8 +138,9 @@ int tsdf_integrate_host(tsdf_map* map, const float* points_host, int64_t n, cons
  * addressing: no data moves). Chunks of 8^3 voxels that leave the window are
  * written to the map's device-resident global store; chunks that enter are
  * read back from the store, or set to (0, 0) if never stored. Asynchronous
- * on `stream`; may allocate store memory synchronously. Errors: INVALID, OOM,
- * CUDA. */
+ * on `stream`; may allocate store memory synchronously (8 MiB segments, in
+ * batches that grow from one to 32 segments as the store grows). Errors:
+ * INVALID, OOM, CUDA. */
 int tsdf_shift(tsdf_map* map, const int64_t new_origin[3], void* stream);
 
 /* Copy the global voxel box [lo, hi) (must lie inside the current window) to
