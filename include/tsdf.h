@@ -95,11 +95,14 @@ typedef struct tsdf_map tsdf_map;   /* opaque; owns all of its device memory */
 
 /* Create a map on the current CUDA device. The window starts at
  * params->origin with every voxel (0, 0). Allocates the voxel grid (4 bytes
- * per voxel: int16 value, int16 weight), the per-scan accumulator (8 bytes
- * per voxel, kept all-zero between calls) and a touched-brick flag array and list
- * (bricks of 8^3 voxels). Per-ray buffers (32 bytes per point) are allocated
- * by the first integrate call that needs them. Synchronous. On success *out receives the handle, which the caller
- * releases with tsdf_map_destroy. Errors: INVALID, OOM, CUDA. */
+ * per voxel: int16 value, int16 weight) and a touched-brick flag array and
+ * list (bricks of 8^3 voxels). The per-scan accumulator (8 bytes per voxel,
+ * kept all-zero between calls) is allocated by the first integrate call that
+ * uses the atomic or sort reduction (the pool reduction keeps a smaller one of
+ * its own), and the per-ray buffers (32 bytes per point) by the first
+ * integrate call that needs them. Synchronous. On success *out receives the
+ * handle, which the caller releases with tsdf_map_destroy. Errors: INVALID,
+ * OOM, CUDA. */
 int tsdf_map_create(const tsdf_params* params, tsdf_map** out);
 
 /* Release a map and all of its device memory. Waits for the map's work to
