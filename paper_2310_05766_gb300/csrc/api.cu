@@ -478,6 +478,7 @@ static void fill_scan_args(const tsdf_map* map, const float* points_dev, int64_t
     a.lcx = map->geom.lcx;
     a.lcxy = map->geom.lcxy;
     a.flags = map->p.flags;
+    fill_lean_args(a);
 }
 
 static int integrate_with(tsdf_map* map, const float* points_dev, int64_t n, const float pose[12], cudaStream_t s,

@@ -32,6 +32,11 @@ __device__ __forceinline__ void brick_cache_init(uint32_t* btab) {
 #ifndef TSDF_MARK_SHFL
 #define TSDF_MARK_SHFL 0
 #endif
+// 1: the plain atomic contribution march runs lean_march (fewer instructions
+// per sample, same results); 0: the general march
+#ifndef TSDF_LEAN_MARCH
+#define TSDF_LEAN_MARCH 1
+#endif
 
 __device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
@@ -291,6 +296,139 @@ __device__ __forceinline__ uint32_t pool_slot(const MapDev& m, unsigned brick) {
     return __shfl_sync(peers, s, leader);
 }
 
+// ---- lean march of the plain atomic reduction (no sort, pool or merge).
+//
+// The same samples, voxels and codes as the general march below, with fewer
+// instructions per sample:
+//  * window test and ring index from one float add per axis: for the
+//    integer-valued float f = floor(q / vs), RN(f + (1.5 * 2^23 - o)) is
+//    exact whenever f - o lies in [-2^22, 2^22), and its bit pattern minus
+//    that of 1.5 * 2^23 is then f - o; outside that range the difference is
+//    at least 2^22 as an unsigned number. So `rel < dims` (unsigned) is
+//    exactly the window test o <= f < o + dims, and (rel + o mod dims) mod
+//    dims the ring index, for any finite f;
+//  * x and y in packed binary32 pairs (each lane of a pair is an IEEE
+//    round-to-nearest operation, as the scalar ones);
+//  * fill samples +j and -j share the offset B * (j vs): the oracle's
+//    b + B * (-(j vs)) is exactly b - B * (j vs), and the j = 0 sample is b
+//    itself (b + B * 0 rounds to b, up to the sign of a zero, which changes
+//    neither the floor, the window test nor the voxel centre);
+//  * no clamp of the code: |d| <= tau gives |d * qs| <= 32767.002, whose
+//    rounding never leaves [-32767, 32767].
+constexpr uint32_t kMagicBits = 0x4B400000u;   // bit pattern of 1.5 * 2^23
+
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+
+// Packed (x, y) binary32 add and multiply, each component round-to-nearest.
+// TSDF_LEAN_PACKED selects where packed pairs are used: bit 0 for the sample
+// position (b, q, q / vs, the window add), bit 1 for the voxel centre and the
+// projection; 0 = scalar operations throughout.
+#ifndef TSDF_LEAN_PACKED
+#define TSDF_LEAN_PACKED 0
+#endif
+template <bool PACKED>
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    if (PACKED) return __fadd2_rn(a, b);
+    return make_float2(fa(a.x, b.x), fa(a.y, b.y));
+}
+template <bool PACKED>
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    if (PACKED) return __fmul2_rn(a, b);
+    return make_float2(fm(a.x, b.x), fm(a.y, b.y));
+}
+constexpr bool kPackPos = (TSDF_LEAN_PACKED & 1) != 0;
+constexpr bool kPackCtr = (TSDF_LEAN_PACKED & 2) != 0;
+
+// One sample at q = (qxy, qz) of a ray (direction A, range r): voxel, code,
+// reduction and brick mark. `mine` = the lane's ray has this sample.
+template <int MODE, bool SV>
+__device__ __forceinline__ void lean_sample(const ScanArgs& a, const MapDev& m, float2 qxy,
+                                            float qz, const float4& A, float dstep, bool mine, unsigned& hits,
+                                            unsigned& last_brick, const BrickCache& bc) {
+    const float2 yxy = mul2<kPackPos>(qxy, a.l_inv);
+    const float yz = fm(qz, a.inv_vs);
+    const float fx = floorf(yxy.x), fy = floorf(yxy.y), fz = floorf(yz);
+    const float2 uxy = add2<kPackPos>(f2(fx, fy), a.l_m);
+    const float uz = fa(fz, a.l_mz);
+    const uint32_t bx = __float_as_uint(uxy.x), by = __float_as_uint(uxy.y), bz = __float_as_uint(uz);
+    const bool act = mine && (bx - kMagicBits < a.l_dim[0]) && (by - kMagicBits < a.l_dim[1]) &&
+                     (bz - kMagicBits < a.l_dim[2]);
+    // ring coordinates and the bricked word index:
+    // word = sx + 8 sy + 64 sz + 504 (sx >> 3) + cy (sy >> 3) + cz (sz >> 3)
+    const uint32_t sx = (bx + a.l_omb[0]) & a.dmask[0];
+    const uint32_t sy = (by + a.l_omb[1]) & a.dmask[1];
+    const uint32_t sz = (bz + a.l_omb[2]) & a.dmask[2];
+    const uint32_t word = sx + (sy << 3) + (sz << 6) + (sx >> 3) * 504u + (sy >> 3) * a.l_cy + (sz >> 3) * a.l_cz;
+    float d;
+    if (SV) {
+        d = dstep;
+    } else {
+        // projective distance of the voxel centre (f + 0.5) vs
+        const float2 cxy = mul2<kPackCtr>(add2<kPackCtr>(f2(fx, fy), f2(0.5f, 0.5f)), a.l_vs);
+        const float cz = fm(fa(fz, 0.5f), a.vs);
+        const float2 exy = mul2<kPackCtr>(add2<kPackCtr>(cxy, a.l_nt), f2(A.x, A.y));
+        const float ez = fm(fa(cz, a.l_ntz), A.z);
+        d = fs(A.w, fa(fa(exy.x, exy.y), ez));
+    }
+    d = fminf(fmaxf(d, -a.tau), a.tau);
+    const int q = small_int(fm(d, a.qs));
+    if (act) {
+        if (MODE == 0) {
+            atomicAdd(m.acc + word, (1ull << 40) + (unsigned long long)(long long)q);
+        } else {
+            const unsigned key = ((unsigned)abs(q) << 1) | (q < 0 ? 1u : 0u);
+            atomicMax(m.acc + word, 65536ull - key);
+            ++hits;
+        }
+        // mark the brick unless this lane marked it last; with a brick cache
+        // the global flag store only on a cache miss (see contrib_item)
+        const unsigned brick = word >> 9;
+        if (brick != last_brick) {
+            last_brick = brick;
+            if (bc.tab) {
+                const unsigned h = (brick * 2654435761u) >> bc.shift;
+                if (bc.tab[h] != brick) {
+                    bc.tab[h] = brick;
+                    m.brick_flag[brick] = 1;
+                }
+            } else {
+                m.brick_flag[brick] = 1;
+            }
+        }
+    }
+}
+
+// The steps k0 .. k0 + KPT - 1 (at most K) of the warp's 32 rays.
+template <int MODE, int KPT, bool SV>
+__device__ __forceinline__ void lean_march(const ScanArgs& a, const MapDev& m, int k0, const float4& A,
+                                           const float4& B, unsigned& hits, unsigned& last_brick,
+                                           const BrickCache& bc) {
+    const float r = A.w;                // dead lanes carry r = -1
+    const bool rfill = B.w != 0.f;
+#pragma unroll 1
+    for (int kk = 0; kk < KPT; ++kk) {
+        const int k = k0 + kk;
+        if (k > a.K) break;   // uniform
+        float l;
+        const int J = step_fill(a, r, rfill, k, l);   // -1: no sample
+        const int Jw = __reduce_max_sync(kFull, J);
+        if (Jw < 0) continue;   // uniform
+        const float2 bxy = add2<kPackPos>(a.l_t, mul2<kPackPos>(f2(A.x, A.y), f2(l, l)));
+        const float bz = fa(a.t[2], fm(A.z, l));
+        const float dstep = fs(r, l);
+        lean_sample<MODE, SV>(a, m, bxy, bz, A, dstep, J >= 0, hits, last_brick, bc);
+        for (int j = 1; j <= Jw; ++j) {   // warp-uniform bounds
+            const float jd = fm((float)j, a.vs);
+            const float2 oxy = mul2<kPackPos>(f2(B.x, B.y), f2(jd, jd));
+            const float oz = fm(B.z, jd);
+            const bool mine = j <= J;
+            lean_sample<MODE, SV>(a, m, add2<kPackPos>(bxy, oxy), fa(bz, oz), A, dstep, mine, hits, last_brick, bc);
+            lean_sample<MODE, SV>(a, m, add2<kPackPos>(bxy, f2(-oxy.x, -oxy.y)), fs(bz, oz), A, dstep, mine, hits,
+                                  last_brick, bc);
+        }
+    }
+}
+
 template <int MODE, bool MERGE, int KPT, bool SORT = false, bool POOL = false>
 __device__ __forceinline__ void contrib_item(const ScanArgs& a, const MapDev& m, unsigned grp, const float4 A,
                                              const float4 B, unsigned& hits, unsigned& last_brick,
@@ -298,6 +436,14 @@ __device__ __forceinline__ void contrib_item(const ScanArgs& a, const MapDev& m,
                                              uint32_t* last_slot = nullptr, BrickCache bc = BrickCache{}) {
     static_assert(!(SORT && MERGE), "the sort reduction emits every sample");
     static_assert(!(POOL && (SORT || MERGE)), "the pool reduction is a variant of the plain atomic one");
+#if TSDF_LEAN_MARCH
+    if constexpr (!SORT && !POOL && !MERGE) {
+        const int k0l = (int)grp * KPT - a.K;
+        if (a.flags & kFlagStepValue) lean_march<MODE, KPT, true>(a, m, k0l, A, B, hits, last_brick, bc);
+        else lean_march<MODE, KPT, false>(a, m, k0l, A, B, hits, last_brick, bc);
+        return;
+    }
+#endif
     const unsigned lane = threadIdx.x & 31u;
     const float tx = a.t[0], ty = a.t[1], tz = a.t[2];
     const float r = A.w;                // dead lanes carry r = -1

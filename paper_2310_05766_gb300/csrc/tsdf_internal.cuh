@@ -96,7 +96,37 @@ struct ScanArgs {
     uint32_t dmask[3];              // dims - 1 per axis
     uint32_t omod[3];               // origin mod dims per axis (ring offset of the window origin)
     int32_t flags;                  // TSDF_FLAG_* bits
+    // Derived constants of the lean contribution march, in pairs for the
+    // packed (x, y) arithmetic (set by fill_lean_args).
+    float2 l_t;                     // (t.x, t.y)
+    float2 l_nt;                    // (-t.x, -t.y)
+    float2 l_inv;                   // (1 / vs, 1 / vs)
+    float2 l_vs;                    // (vs, vs)
+    float2 l_m;                     // 1.5 * 2^23 - origin, x and y (exact: origins are multiples of 8)
+    float l_mz;                     // the same for z
+    float l_ntz;                    // -t.z
+    uint32_t l_dim[3];              // window size per axis
+    uint32_t l_omb[3];              // (origin mod dims) - 0x4B400000 per axis, modulo 2^32
+    uint32_t l_cy, l_cz;            // 2^(lcx + 9) - 64 and 2^(lcxy + 9) - 512 (brick strides in the word index)
 };
+
+// Fill the lean-march constants of `a` from its other fields (host side,
+// after t, vs, inv_vs, fo, dmask, omod, lcx and lcxy are set).
+inline void fill_lean_args(ScanArgs& a) {
+    a.l_t = make_float2(a.t[0], a.t[1]);
+    a.l_nt = make_float2(-a.t[0], -a.t[1]);
+    a.l_inv = make_float2(a.inv_vs, a.inv_vs);
+    a.l_vs = make_float2(a.vs, a.vs);
+    a.l_m = make_float2(12582912.0f - a.fo[0], 12582912.0f - a.fo[1]);
+    a.l_mz = 12582912.0f - a.fo[2];
+    a.l_ntz = -a.t[2];
+    for (int i = 0; i < 3; ++i) {
+        a.l_dim[i] = a.dmask[i] + 1u;
+        a.l_omb[i] = a.omod[i] - 0x4B400000u;
+    }
+    a.l_cy = (1u << (a.lcx + 9u)) - 64u;
+    a.l_cz = (1u << (a.lcxy + 9u)) - 512u;
+}
 
 // One brick slot that changes owner during a shift.
 struct ShiftItem {
