@@ -64,11 +64,17 @@ extern "C" {
                                      weight 1: value (gv*gw*W + S) / ((gw + 1) * W), weight min(w_max, gw + 1);
                                      default: weight W (its contribution count) */
 
-/* Largest number of points accepted by one integrate call. With weight 1 per
- * contribution, a voxel receives at most 4 contributions per ray, so the
- * per-scan weight sum of a voxel stays below 2^24 and its distance sum below
- * 2^39: both fit the packed 64-bit accumulator exactly. */
-#define TSDF_MAX_POINTS      (1LL << 22)
+/* Largest number of points accepted by one integrate call. A ray's samples
+ * lie on a square lattice of spacing voxel_size (march steps along the ray,
+ * fill samples along the interpolation direction); among any five points of
+ * such a lattice two are at least two spacings apart, more than a voxel's
+ * diagonal, so at most four samples of one ray fall in one voxel (four do
+ * occur). With weight 1 per contribution a voxel's per-scan count is then at
+ * most 4 * (2^22 - 1) < 2^24 and its distance sum below 2^39: both fit the
+ * packed 64-bit accumulator exactly. (The bound assumes binary32 rounding
+ * moves a sample by far less than a voxel, which holds while ranges and
+ * coordinates stay below about 2^17 voxels.) */
+#define TSDF_MAX_POINTS      ((1LL << 22) - 1)
 
 /* Map parameters. */
 typedef struct tsdf_params {
@@ -538,11 +544,15 @@ int tsdf_server_get_stats(tsdf_server* server, tsdf_server_stats* out);
  *                synchronises `stream`. If NULL the call is asynchronous.
  * Set-up: the first call on each device looks up the device address of the
  * scratch array (cudaGetSymbolAddress) with that device current, so make that
- * first call before any stream capture.
- * All calls share the one scratch array, and each call clears the parts that
- * must start at zero: calls that overlap on the GPU (different streams, or
- * different host threads, on one device) race and give undefined results;
- * serialise them.
+ * first call before any stream capture. The address is kept for the process:
+ * after cudaDeviceReset (which unloads the library's device code) this entry
+ * point must not be called again in that process.
+ * The array keeps the last call's contents: each call clears the counters;
+ * accumulators and brick flags are left all zero by every call that completes
+ * and are cleared in full by the call that follows a failed one.
+ * All calls share the one scratch array: calls that overlap on the GPU
+ * (different streams, or different host threads, on one device) race and give
+ * undefined results; serialise them.
  * Errors: INVALID (null or misaligned pointers, bad parameters, window larger
  * than TSDF_STATIC_MAX_VOXELS voxels, n < 0 or n > TSDF_STATIC_MAX_POINTS),
  * CUDA. */

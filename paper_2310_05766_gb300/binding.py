@@ -28,7 +28,7 @@ TSDF_REDUCE_WSUM = 0
 TSDF_REDUCE_MIN_ABS = 1
 TSDF_FLAG_STEP_VALUE = 1
 TSDF_FLAG_SCAN_WEIGHT = 2
-TSDF_MAX_POINTS = 1 << 22
+TSDF_MAX_POINTS = (1 << 22) - 1
 TSDF_OPT_WARP_MERGE = 1
 TSDF_OPT_STEPS_PER_THREAD = 2
 TSDF_OPT_PDL = 3
@@ -307,9 +307,31 @@ def tsdf_integrate_static(grid_dev, params, points_dev, n: int, pose, stream=Non
     points_dev: CUDA float32 (n, 4) tensor (or device pointer). Returns the
     scan's counters (and synchronises the stream) when want_stats, else None.
     """
+    prm = params if isinstance(params, tsdf_params) else make_params(params)
+    # The caller owns the grid here, so nothing on the C side knows its size:
+    # tensors are checked before their addresses are passed on (a raw pointer
+    # is the caller's responsibility).
+    if not isinstance(grid_dev, int):
+        voxels = int(prm.dims[0]) * int(prm.dims[1]) * int(prm.dims[2])
+        if (not grid_dev.is_cuda or not grid_dev.is_contiguous() or grid_dev.element_size() != 4
+                or grid_dev.is_floating_point() or grid_dev.numel() != voxels):
+            raise TsdfError(TSDF_ERR_INVALID, "tsdf_integrate_static: grid must be a contiguous 32-bit integer CUDA "
+                                              f"tensor of {voxels} words")
+    if not isinstance(points_dev, int):
+        import torch
+        if (not points_dev.is_cuda or not points_dev.is_contiguous() or points_dev.dtype != torch.float32
+                or points_dev.dim() != 2 or points_dev.shape[1] != 4 or int(n) > points_dev.shape[0]):
+            raise TsdfError(TSDF_ERR_INVALID, "tsdf_integrate_static: points must be a contiguous float32 (>= n, 4) "
+                                              "CUDA tensor")
+        if not isinstance(grid_dev, int) and points_dev.device != grid_dev.device:
+            raise TsdfError(TSDF_ERR_INVALID, "tsdf_integrate_static: grid and points on different devices")
+    for t in (grid_dev, points_dev):
+        if not isinstance(t, int):
+            import torch
+            if t.device.index != torch.cuda.current_device():
+                raise TsdfError(TSDF_ERR_INVALID, "tsdf_integrate_static: tensors must be on the current device")
     gptr = grid_dev if isinstance(grid_dev, int) else grid_dev.data_ptr()
     pptr = points_dev if isinstance(points_dev, int) else points_dev.data_ptr()
-    prm = params if isinstance(params, tsdf_params) else make_params(params)
     pa, pp = _pose_arg(pose)
     st = tsdf_scan_stats()
     _check(lib().tsdf_integrate_static(gptr, ctypes.byref(prm), pptr, int(n), pp,

@@ -11,7 +11,8 @@
 // the library keeps until the process exits.
 //
 // The kernels are the library's integration kernels (rays, contrib, compact,
-// apply, finish); only the origin of their scratch memory differs.
+// and apply, whose last CTA publishes the counters); only the origin of their
+// scratch memory differs.
 #include <cmath>
 #include <cstddef>
 #include <cstdint>
@@ -46,8 +47,14 @@ static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char* g_scratch_ptr[kMaxDevices] = {};
+// Per device: a call failed after its contribution kernel may have written
+// accumulators or brick flags, so the next call clears them. (A call that
+// completes leaves both all zero: the compaction clears the flags it lists
+// and the apply resets every accumulator it reads; a freshly loaded module's
+// array is zero.)
+bool g_dirty[kMaxDevices] = {};
 
-int scratch_for_current_device(unsigned char** out) {
+int scratch_for_current_device(unsigned char** out, int* dev_out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TSDF_ERR_CUDA;
@@ -61,6 +68,7 @@ int scratch_for_current_device(unsigned char** out) {
         g_scratch_ptr[dev] = p;
     }
     *out = g_scratch_ptr[dev];
+    *dev_out = dev;
     return TSDF_OK;
 }
 
@@ -106,7 +114,8 @@ extern "C" int tsdf_integrate_static(uint32_t* grid_dev, const tsdf_params* para
     for (int i = 0; i < 12; ++i)
         if (!std::isfinite(pose[i])) return TSDF_ERR_INVALID;
     unsigned char* base = nullptr;
-    rc = scratch_for_current_device(&base);
+    int dev = 0;
+    rc = scratch_for_current_device(&base, &dev);
     if (rc != TSDF_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t voxels = (size_t)params->dims[0] * params->dims[1] * params->dims[2];
@@ -122,11 +131,23 @@ extern "C" int tsdf_integrate_static(uint32_t* grid_dev, const tsdf_params* para
     md.ray_b = reinterpret_cast<float4*>(base + kOffRayB);
     md.ray_cap = (uint32_t)kMaxPoints;
 
-    // The array keeps the previous call's contents: clear everything that
-    // must start at zero (counters, brick flags, this window's accumulators).
+    // The array keeps the previous call's contents: the counters are cleared
+    // on every call; the brick flags and accumulators (zero after any call
+    // that completed) only after a failed call, and then over the whole array.
     cudaError_t e = cudaMemsetAsync(md.ctr, 0, sizeof(MapCounters), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(md.brick_flag, 0, (bricks + 3) / 4 * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(md.acc, 0, voxels * sizeof(unsigned long long), s);
+    bool dirty = false;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        dirty = g_dirty[dev];
+    }
+    if (dirty) {
+        if (e == cudaSuccess) e = cudaMemsetAsync(md.brick_flag, 0, round_up(kMaxBricks), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(md.acc, 0, kMaxVoxels * sizeof(unsigned long long), s);
+        if (e == cudaSuccess) {
+            std::lock_guard<std::mutex> lk(g_mu);
+            g_dirty[dev] = false;
+        }
+    }
 
     ScanArgs a{};
     a.pts = reinterpret_cast<const float4*>(points_dev);
@@ -158,9 +179,14 @@ extern "C" int tsdf_integrate_static(uint32_t* grid_dev, const tsdf_params* para
     a.lcx = ilog2((uint32_t)params->dims[0] / 8u);
     a.lcxy = a.lcx + ilog2((uint32_t)params->dims[1] / 8u);
     a.flags = params->flags;
+    fill_lean_args(a);
 
     if (e == cudaSuccess) e = launch_rays(a, md, false, true, true, s);
-    if (e == cudaSuccess) e = launch_contrib(a, md, params->reduce, false, 4, true, s);
+    bool launched_contrib = false;
+    if (e == cudaSuccess) {
+        e = launch_contrib(a, md, params->reduce, false, 4, true, s);
+        launched_contrib = true;
+    }
     if (e == cudaSuccess) e = launch_compact(md, (uint32_t)bricks, true, s);
     if (e == cudaSuccess) e = launch_apply(md, params->reduce, params->w_max, params->flags, true, s);
     if (e == cudaSuccess && stats_host) {
@@ -172,6 +198,10 @@ extern "C" int tsdf_integrate_static(uint32_t* grid_dev, const tsdf_params* para
             stats_host->hits = last[1];
             stats_host->touched = last[2];
         }
+    }
+    if (e != cudaSuccess && launched_contrib) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_dirty[dev] = true;
     }
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? TSDF_ERR_OOM : TSDF_ERR_CUDA;
     return TSDF_OK;

@@ -104,10 +104,11 @@ def test_binding_constants_match_the_header():
     from paper_2310_05766_gb300 import binding as b
     text = open(os.path.join(ROOT, "include", "tsdf.h")).read()
     consts = {}
-    for m in re.finditer(r"^#define\s+(TSDF_\w+)\s+(\(?-?\d+(?:LL)?(?:\s*<<\s*\d+)?\)?)", text, flags=re.M):
+    for m in re.finditer(r"^#define\s+(TSDF_\w+)\s+([-+()<\d\sL]+?)\s*(?:/\*.*)?$", text, flags=re.M):
         expr = m.group(2).replace("LL", "")
         consts[m.group(1)] = int(eval(expr, {"__builtins__": {}}))
     assert len(consts) > 30
+    assert consts["TSDF_MAX_POINTS"] == (1 << 22) - 1
     required = [n for n in consts if n.startswith(("TSDF_ERR_", "TSDF_OPT_", "TSDF_REDUCE_", "TSDF_REDUCTION_",
                                                   "TSDF_FLAG_", "TSDF_BATCH_OPT_"))] + ["TSDF_OK"]
     missing = [n for n in required if not hasattr(b, n)]

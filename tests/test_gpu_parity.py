@@ -633,3 +633,33 @@ def test_write_read_roundtrip():
             m.write(v, bad)
     finally:
         m.close()
+
+
+def test_packed_count_at_the_documented_maximum():
+    """One voxel at the largest per-scan count the packed accumulator must hold.
+
+    A ray whose march lattice puts four of its nine samples (tau = voxel size,
+    fill J = 1) into voxel (5, 0, 12) -- the most one ray can, by the lattice
+    argument of TSDF_MAX_POINTS -- repeated TSDF_MAX_POINTS times: the voxel's
+    count is 4 (2^22 - 1) = 2^24 - 4, just inside the 24-bit count field of
+    the packed word. The grid and counters must equal the oracle's (int64
+    maps, no packing)."""
+    import oracle
+    from paper_2310_05766_gb300 import binding as b
+    pt = np.array([[1.5753395557403564, 0.6343674659729004, 0.46042734384536743, 0.0]], np.float32)
+    pose = np.array([-0.025146624073386192, 0.975757896900177, 0.2174031287431717, 0.0,
+                     -0.1916240155696869, -0.21814407408237457, 0.9569187164306641, 0.0,
+                     0.9811462163925171, -0.01759638637304306, 0.19246424734592438, 0.0], np.float32)
+    p = synth.params_dict((8, 8, 8), 0.125, 0.125, 32767, 0.08914640378552456, 0.0, 100.0, 0, (0, 0, 8))
+    g, q, ray = oracle.hits(p, pt, pose)
+    voxels, counts = np.unique(g, axis=0, return_counts=True)
+    assert len(g) == 9 and counts.max() == 4 and tuple(voxels[counts.argmax()]) == (5, 0, 12)
+    assert b.TSDF_MAX_POINTS * 4 == (1 << 24) - 4
+    n = b.TSDF_MAX_POINTS
+    pts = np.repeat(pt, n, axis=0)
+    steps = [("scan", pts, pose)]
+    gpu = run_gpu(p, steps, torch)
+    orc = run_oracle(p, steps)
+    assert_same(gpu, orc, "maximum count")
+    assert orc[2][0]["hits"] == 6 * n          # three of the nine samples fall outside the window (y = -1)
+    assert orc[1][12 - 8, 0, 5] == 32767       # weight capped by Eq. 2; the count itself was 2^24 - 4
