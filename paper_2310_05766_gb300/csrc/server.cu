@@ -312,18 +312,28 @@ int tsdf_server_open_session(tsdf_server* s, const tsdf_params* params, int32_t*
         if ((long long)(s->used_bytes + bytes) > s->cfg.hbm_budget_bytes) return TSDF_ERR_ADMISSION;
         s->used_bytes += bytes;   // reserve before the (slow) allocation
     }
+    // the session's map lives on the server's device, whichever device is
+    // current on the calling thread (restored before returning)
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(s->device) != cudaSuccess) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->used_bytes -= bytes;
+        return TSDF_ERR_CUDA;
+    }
     tsdf_map* m = nullptr;
     int rc = tsdf_map_create(params, &m);
-    std::lock_guard<std::mutex> lk(s->mu);
-    if (rc != TSDF_OK) {
-        s->used_bytes -= bytes;
-        return rc;
-    }
     // size the per-ray buffers for the largest scan now, so that no request
     // reallocates them (which would synchronise the device) while batches run
-    rc = map_reserve_points(m, s->cfg.max_points);
+    if (rc == TSDF_OK) {
+        rc = map_reserve_points(m, s->cfg.max_points);
+        if (rc != TSDF_OK) {
+            tsdf_map_destroy(m);
+            m = nullptr;
+        }
+    }
+    cudaSetDevice(prev);
+    std::lock_guard<std::mutex> lk(s->mu);
     if (rc != TSDF_OK) {
-        tsdf_map_destroy(m);
         s->used_bytes -= bytes;
         return rc;
     }
