@@ -43,6 +43,23 @@ def _alone(b, w):
     return v, wt, stats
 
 
+def _oracle_session(w):
+    """The oracle's map and per-scan counters after a session's scans (and
+    shifts) in order."""
+    om = oracle.OracleMap(w.params)
+    cur = tuple(w.params["origin"])
+    stats = []
+    for pts, pose, org in zip(w.scans, w.poses, w.origins):
+        if tuple(org) != cur:
+            om.shift(org)
+            cur = tuple(org)
+        om.integrate(pts, pose)
+        stats.append(om.stats())
+    v, wt = om.read()
+    om.close()
+    return v, wt, stats
+
+
 @pytest.mark.parametrize("pinned", [False, True])
 def test_mixed_equals_alone(pinned):
     """Each session's map is the same in the mix as alone; with pinned
@@ -81,21 +98,15 @@ def test_mixed_equals_alone(pinned):
             va, wa, sa = _alone(b, w)
             assert np.array_equal(vm, va) and np.array_equal(wm, wa), f"session {i}"
             assert [r["stats"] for r in results[i]] == sa
-        # one session also against the oracle
-        w = ws[0]
-        om = oracle.OracleMap(w.params)
-        cur0 = tuple(w.params["origin"])
-        for pts, pose, org in zip(w.scans, w.poses, w.origins):
-            if tuple(org) != cur0:
-                om.shift(org)
-                cur0 = tuple(org)
-            om.integrate(pts, pose)
-        vo, wo = om.read()
-        mh = b.tsdf_server_session_map(srv, sids[0])
-        o = b.tsdf_get_origin(mh)
-        d = w.params["dims"]
-        vm, wm = b.tsdf_read(mh, o, tuple(o[a] + d[a] for a in range(3)))
-        assert np.array_equal(vm, vo) and np.array_equal(wm, wo)
+        # every session also against the oracle
+        for i, w in enumerate(ws):
+            vo, wo, so = _oracle_session(w)
+            mh = b.tsdf_server_session_map(srv, sids[i])
+            o = b.tsdf_get_origin(mh)
+            d = w.params["dims"]
+            vm, wm = b.tsdf_read(mh, o, tuple(o[a] + d[a] for a in range(3)))
+            assert np.array_equal(vm, vo) and np.array_equal(wm, wo), f"session {i} vs oracle"
+            assert [r["stats"] for r in results[i]] == so
         assert st["mean_batch"] >= 1.0
     finally:
         b.tsdf_server_destroy(srv)
@@ -171,5 +182,45 @@ def test_submit_many_and_wait_many():
             d = w.params["dims"]
             vm, wm = b.tsdf_read(mh, o, tuple(o[a] + d[a] for a in range(3)))
             assert np.array_equal(vm, va) and np.array_equal(wm, wa)
+    finally:
+        b.tsdf_server_destroy(srv)
+
+
+def test_serving_config_shapes_equal_oracle():
+    """The serving workload's shapes: 32 sessions (grids 256^3 / 512x512x128,
+    voxel 0.05-0.1 m, tau 0.2-0.6 m), two scans each of {16,32,64,128} x
+    {1024,2048} points, submitted interleaved over all sessions (batches of up
+    to 32 on two streams). Every session's map and counters equal the oracle's."""
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2310_05766_gb300 import binding as b
+    sess = synth.serving_sessions(32, seed=100)
+    rng = synth.SplitMix64(777)
+    ws = []
+    for sp in sess:
+        beams = [16, 32, 64, 128][int(rng.integers(1, 0, 4)[0])]
+        az = [1024, 2048][int(rng.integers(1, 0, 2)[0])]
+        ws.append(synth.workload_outdoor(n_scans=2, seed=sp["seed"], beams=beams, azimuths=az, dims=sp["dims"],
+                                         voxel_size=sp["voxel_size"], tau=sp["tau"]))
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        ref = list(ex.map(_oracle_session, ws))
+    srv = b.tsdf_server_create(hbm_budget_bytes=120 * 10**9, max_points=128 * 2048, max_batch=32, streams=2,
+                               max_outstanding=1024)
+    try:
+        sids = [b.tsdf_server_open_session(srv, w.params) for w in ws]
+        order = [(i, k) for k in range(2) for i in np.random.default_rng(5).permutation(len(ws))]
+        tickets = {i: [] for i in range(len(ws))}
+        for i, k in order:
+            tickets[i].append(b.tsdf_server_submit(srv, sids[i], ws[i].scans[k], ws[i].poses[k]))
+        for i, w in enumerate(ws):
+            res = [b.tsdf_server_wait(srv, t) for t in tickets[i]]
+            assert all(r["status"] == 0 for r in res)
+            mh = b.tsdf_server_session_map(srv, sids[i])
+            o = b.tsdf_get_origin(mh)
+            d = w.params["dims"]
+            vm, wm = b.tsdf_read(mh, o, tuple(o[a] + d[a] for a in range(3)))
+            vo, wo, so = ref[i]
+            assert np.array_equal(vm, vo) and np.array_equal(wm, wo), f"session {i}"
+            assert [r["stats"] for r in res] == so, f"session {i}"
+        assert b.tsdf_server_get_stats(srv)["mean_batch"] > 1.0
     finally:
         b.tsdf_server_destroy(srv)
