@@ -39,11 +39,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "TSDF voxel updates/s (OS1-128-shaped scan)"
-# DRAM bytes (read + write) per launch from the committed ncu capture of these
+# DRAM bytes (read + write) per launch from the committed ncu captures of these
 # kernels on the outdoor workload, the default one
-# (profiles/contrib_apply_outdoor_128x1024.md); other workloads report none.
-# Reset an entry to None whenever its kernel changes.
-NCU_DRAM_BYTES = {"contrib": 13.25e6 + 0.5e3, "apply": 27.55e6 + 1.5e3, "rays": None}
+# (profiles/contrib_outdoor_128x1024.md, profiles/contrib_apply_outdoor_128x1024.md);
+# other workloads report none. Reset an entry to None whenever its kernel changes.
+NCU_DRAM_BYTES = {"contrib": 13.20e6 + 0.5e3, "apply": 27.55e6 + 1.5e3, "rays": None}
 UNIT = "voxel_updates/s"
 N_SEQ = 100
 
@@ -305,34 +305,53 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     K = len(timed)
     # roofline of the dominant kernel
     peak, peak_kind = peaks()
+    n_pts = scans_dev[0].shape[0]
     # (the sort group -- compaction, count, prefix, scatter -- only reorders
     # contributions and has no algorithmic bytes of its own)
     kern = max(((k, v) for k, v in prof.items() if k in ("contrib", "emit", "apply")), key=lambda kv: kv[1][1])
     kname, (klaunch, kms) = kern
-    n_pts = scans_dev[0].shape[0]
-    if kname in ("contrib", "emit"):
-        # points in (16 B each) + the per-scan volume written once (8 B per touched voxel)
-        alg_bytes = (16.0 * n_pts * K + 8.0 * touched_timed) / klaunch
-    elif kname == "apply":
-        # per touched voxel: volume read (8 B) + grid read-modify-write (4 + 4 B)
-        alg_bytes = 16.0 * touched_timed / klaunch
-    else:
-        alg_bytes = float("nan")
-    k_avg_s = kms / klaunch / 1e3
-    achieved = alg_bytes / k_avg_s / 1e9
-    # contribution kernel against the measured L2 reduction rate (one 64-bit
-    # reduction per in-window sample in the atomic reduction)
+
+    def hbm_fig(name):
+        """HBM figure of one kernel with the algorithmic bytes it owns: the
+        march reads the scan's points (16 B each), the apply read-modify-writes
+        the grid (4 + 4 B per touched voxel)."""
+        if name not in prof:
+            return None
+        nl, ms = prof[name]
+        alg = (16.0 * n_pts * K if name in ("contrib", "emit", "rays") else 8.0 * touched_timed) / nl
+        ach = alg / (ms / nl / 1e3) / 1e9
+        return dict(kernel=name, achieved=ach, peak=peak, unit="GB/s", frac=ach / peak,
+                    peak_source=f"{peak_kind} hbm_gbs",
+                    alg_bytes_def=("16 B per point of the scan" if name in ("contrib", "emit", "rays")
+                                   else "8 B per touched voxel (grid read-modify-write)"),
+                    alg_bytes_per_launch=alg, avg_launch_us=1e3 * ms / nl,
+                    traffic=(NCU_DRAM_BYTES.get(name) if args.reduction == "atomic" and args.workload == "outdoor"
+                             else None))
+    # the binding roofline of the contribution kernel: its 64-bit L2
+    # reductions (one per in-window contribution) against the rate the
+    # reduction probe measures in this run
     l2red = None
     if "contrib" in prof:
         rate_coal = b.tsdf_probe_reduction_rate(0, stream)
         rate_scat = b.tsdf_probe_reduction_rate(1, stream)
         c_launch, c_ms = prof["contrib"]
         red_rate = hits_timed / (c_ms / 1e3) if c_launch == K else float("nan")
-        l2red = dict(kernel="contrib", achieved=red_rate, unit="reductions/s",
+        l2red = dict(kernel="contrib", bound="l2_reduction", achieved=red_rate, peak=rate_scat,
+                     unit="reductions/s", frac=red_rate / rate_scat,
                      peak_coalesced=rate_coal, peak_scattered=rate_scat,
                      frac_coalesced=red_rate / rate_coal, frac_scattered=red_rate / rate_scat,
+                     avg_launch_us=1e3 * c_ms / c_launch,
                      peak_source="tsdf_probe_reduction_rate, measured in this run (64-bit red.add into a 64 MiB "
-                                 "L2-resident buffer, GPU-filling grid)")
+                                 "L2-resident buffer, GPU-filling grid; scattered: every lane its own hashed word)",
+                     traffic=(NCU_DRAM_BYTES.get("contrib") if args.reduction == "atomic" and args.workload == "outdoor"
+                              else None))
+    if l2red is not None:
+        roof = dict(l2red)
+        roof["hbm"] = hbm_fig("contrib")
+        roof["apply_hbm"] = hbm_fig("apply")
+    else:
+        roof = hbm_fig(kname)
+        roof["bound"] = "hbm"
     kernels = {k: dict(launches=v[0], total_ms=round(v[1], 4), avg_us=round(1e3 * v[1] / v[0], 3),
                        share=round(v[1] / sum(x[1] for x in prof.values()), 4)) for k, v in prof.items()}
 
@@ -366,14 +385,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         kernels_note="per-kernel times from a second pass over the same timed steps with library events around "
                      "each kernel (that pass: %.1f us/scan; events serialise the kernels of a step)" %
                      (1e3 * float(sum(prof_step_ms)) / K),
-        roofline=dict(kernel=kname, bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
-                      peak_source=f"{peak_kind} hbm_gbs",
-                      traffic=(NCU_DRAM_BYTES.get(kname) if args.reduction == "atomic" and args.workload == "outdoor"
-                               else None),
-                      alg_bytes_def=("16 B per point read + 8 B per touched voxel of the per-scan volume"
-                                     if kname in ("contrib", "emit") else
-                                     "16 B per touched voxel (volume read + grid RMW)"),
-                      alg_bytes_per_launch=alg_bytes, avg_launch_us=k_avg_s * 1e6, l2_reductions=l2red),
+        roofline=roof,
         e2e=dict(value=e2e_hits_all / t_e2e_max, unit=UNIT, h2d_bytes_per_step=int(16 * n_pts),
                  d2h_bytes_per_step=24, steps=n_e2e,
                  zero_copy=args.zero_copy != 0,
@@ -389,6 +401,76 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         cpu_baseline=cpu,
         cpu_baseline_parallel=cpu_par,
     )
+    return out
+
+
+# ---------------------------------------------------------------- the other configured workloads
+
+def run_room_bench(steps: int = 200):
+    """Box room, one 16 x 360 scan into a 256 x 256 x 64 window at 0.05 m: the
+    same scan integrated `steps` times, L2 flushed before each, per-step events
+    (a latency-bound workload: reported in microseconds per scan)."""
+    import torch
+    from paper_2310_05766_gb300 import binding as b, synth
+    w = synth.workload_room()
+    pts = torch.from_numpy(w.scans[0]).cuda()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    m = b.TsdfMap(w.params)
+    try:
+        b.tsdf_integrate(m.handle, pts, pts.shape[0], w.poses[0], stream)
+        hits = m.stats()["hits"]
+        for _ in range(10):
+            b.tsdf_integrate(m.handle, pts, pts.shape[0], w.poses[0], stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            b.tsdf_integrate(m.handle, pts, pts.shape[0], w.poses[0], stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        us = np.array([1e3 * e0.elapsed_time(e1) for e0, e1 in ev])
+    finally:
+        m.close()
+    return dict(workload="box room: 16 x 360 beams (5760 points), 256x256x64 window at 0.05 m, tau 0.2 m, "
+                         "the same scan integrated every step",
+                steps=steps, us_per_scan=dict(mean=float(us.mean()), p50=float(np.percentile(us, 50)),
+                                              p99=float(np.percentile(us, 99))),
+                scans_per_s=1e6 / float(us.mean()), voxel_updates_per_s=hits / (float(us.mean()) / 1e6),
+                hits_per_scan=hits, note="latency-bound (a few microseconds of work per scan); not judged by roofline")
+
+
+def run_configs(args):
+    """The configured workloads besides the headline one, each short, as
+    sub-records of the default line: box room (us per scan), the 64-map batch
+    against 64 plain calls, the high-resolution corridor and a 32-session
+    serving run at Poisson 500 scans/s (p50 / p99 latency)."""
+    import copy
+    out = {}
+    out["room"] = run_room_bench(200)
+    a = copy.copy(args)
+    a.workload, a.steps, a.warmup, a.no_cpu_baseline = "corridor", 100, 5, True
+    c = run_gpu(a, 0, 1, 0)
+    out["corridor"] = dict(workload=c["config"]["workload"], steps=c["steps"], value=c["value"], unit=c["unit"],
+                           us_per_scan=c["us_per_scan"], scans_per_s=c["scans_per_s"],
+                           hits_per_scan=c["hits_per_scan"], contrib_avg_us=c["kernels"]["contrib"]["avg_us"],
+                           l2_reductions_frac_scattered=c["roofline"].get("frac_scattered"),
+                           e2e=c["e2e"]["value"], map_device_bytes=c["config"]["map_device_bytes"])
+    a = copy.copy(args)
+    a.steps, a.warmup = 20, 16
+    bt = run_batch_bench(a)
+    out["batch"] = dict(workload=bt["config"]["workload"], steps=bt["steps"], ms_per_batch=bt["ms_per_step"],
+                        value=bt["value"], unit=bt["unit"], scans_per_s=bt["scans_per_s"],
+                        plain_ms_per_64_scans=bt["plain_per_scan_launches"]["ms_per_step"],
+                        speedup_vs_plain=bt["batch_speedup_vs_plain"], tuned_config=bt["config"]["tuned_config"])
+    a = copy.copy(args)
+    a.serve_seconds, a.serve_rate, a.serve_pinned = 6.0, 500.0, 1
+    sv = run_serving_bench(a)
+    out["serving"] = dict(workload=sv["config"]["workload"], requests=sv["steps"], scans_per_s=sv["value"],
+                          p50_ms=sv["latency_ms"]["p50"], p99_ms=sv["latency_ms"]["p99"],
+                          mean_ms=sv["latency_ms"]["mean"], voxel_updates_per_s=sv["voxel_updates_per_s"],
+                          mean_batch=sv["mean_batch"], sessions=sv["sessions"])
     return out
 
 
@@ -650,6 +732,19 @@ def run_serving_bench(args):
                 sessions=st["sessions"], used_bytes=st["used_bytes"])
 
 
+def spawn_ranks(n: int, argv) -> int:
+    """Re-run this script as n ranks on one node (torch.distributed.run, one
+    process per GPU, rendezvous on 127.0.0.1); returns the launcher's exit
+    code. Each rank then reads RANK / LOCAL_RANK / WORLD_SIZE."""
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__), *argv]
+    return subprocess.call(cmd)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -671,11 +766,16 @@ def main():
                     help="serving: aggregate Poisson arrival rate, scans/s (0: saturating closed loop)")
     ap.add_argument("--serve-pinned", type=int, default=1,
                     help="serving: scans in pinned host memory read in place (1) or pageable, copied (0)")
+    ap.add_argument("--no-extra-configs", action="store_true",
+                    help="headline workload only (skip the room, batch, corridor and serving sub-records)")
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=120.0, help="seconds of oracle time for --impl reference")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one process per GPU: run this same command under torch.distributed.run
+        sys.exit(spawn_ranks(args.gpus, sys.argv[1:]))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -695,6 +795,8 @@ def main():
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
+        elif args.workload == "outdoor" and not args.no_extra_configs and out is not None:
+            out["configs"] = run_configs(args)
     if out is not None and rank == 0:
         print(json.dumps(out), flush=True)
 
