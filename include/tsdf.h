@@ -145,12 +145,39 @@ int tsdf_integrate_host(tsdf_map* map, const float* points_host, int64_t n, cons
 /* Move the window to new_origin (global voxel coordinates, multiples of 8,
  * |new_origin| <= 2^23). Voxels inside both windows keep their values (ring
  * addressing: no data moves). Chunks of 8^3 voxels that leave the window are
- * written to the map's device-resident global store; chunks that enter are
- * read back from the store, or set to (0, 0) if never stored. Asynchronous
- * on `stream`; may allocate store memory synchronously (8 MiB segments, in
- * batches that grow from one to 32 segments as the store grows). Errors:
- * INVALID, OOM, CUDA. */
+ * written to the map's global store if any of their voxels is non-zero (the
+ * others are dropped); chunks that enter are read back from the store (and
+ * leave it, freeing their slot), or set to (0, 0) if not stored. (Introduction
+ * of the paper: the local map is shifted, map parts leaving it are written out
+ * and previously mapped parts are read back.)
+ * The store has two tiers of 2 KiB slots: device memory, up to
+ * TSDF_OPT_STORE_DEVICE_CHUNKS slots, and pinned host memory mapped into the
+ * device, which the shift kernel reads and writes in place. When the device
+ * tier is full, its chunks stored longest ago move to the host tier first
+ * (and, with TSDF_OPT_STORE_SPILL_AGE, any chunk stored that many shifts ago).
+ * Asynchronous on `stream`, except that it waits for the previous shift's
+ * kernel (whose per-chunk "held data" flags it needs), and that growing a tier
+ * allocates synchronously (8 MiB segments; see tsdf_map_reserve_store to
+ * allocate the device tier up front). Errors: INVALID, OOM, CUDA. */
 int tsdf_shift(tsdf_map* map, const int64_t new_origin[3], void* stream);
+
+/* Allocate the device tier of the map's global store now: `device_chunks`
+ * slots (2 KiB each, rounded up to whole 8 MiB segments), which also become
+ * its limit (TSDF_OPT_STORE_DEVICE_CHUNKS), so that later shifts allocate no
+ * device memory (chunks beyond it go to the host tier). device_chunks >= 1.
+ * Synchronous. Errors: INVALID, OOM, CUDA. */
+int tsdf_map_reserve_store(tsdf_map* map, int64_t device_chunks);
+
+/* Global-store counters of a map (waits for the last shift's kernel). */
+typedef struct tsdf_store_stats {
+    int64_t device_chunks;      /* chunks held in device memory */
+    int64_t device_capacity;    /* device-tier slots allocated */
+    int64_t host_chunks;        /* chunks held in pinned host memory */
+    int64_t host_capacity;      /* host-tier slots allocated */
+    int64_t spilled;            /* chunks moved from device to host memory so far */
+    int64_t dropped;            /* leaving chunks found empty (all voxels zero) and not stored, so far */
+} tsdf_store_stats;
+int tsdf_get_store_stats(tsdf_map* map, tsdf_store_stats* out);
 
 /* Copy the global voxel box [lo, hi) (must lie inside the current window) to
  * the host in [z][y][x] order: value_host and weight_host each receive
@@ -208,6 +235,12 @@ int tsdf_stats(tsdf_map* map, tsdf_scan_stats* out, void* stream);
                                    pool too small for the scans */
 #define TSDF_OPT_POOL_BRICKS  7  /* pool reduction: slots of the pool (64 .. bricks of the window); 0 (default):
                                    an eighth of the window's bricks, at least 16384 */
+#define TSDF_OPT_STORE_DEVICE_CHUNKS 8  /* global store: most slots of its device tier (2 KiB each); 0 (default):
+                                          as many as the window has bricks. Chunks beyond it go to pinned host
+                                          memory. Lowering it frees nothing already allocated. */
+#define TSDF_OPT_STORE_SPILL_AGE 9  /* global store: a chunk stored this many shifts ago moves from device to
+                                      host memory at the next shift; 0 (default): only when the device tier is
+                                      full */
 
 /* Device memory held by the map (grid, per-scan buffers of the reductions
  * that have been used, ray buffers, global store) in bytes. Host-side.
@@ -371,11 +404,16 @@ typedef struct tsdf_batch tsdf_batch;   /* opaque; owns pinned and device descri
 #define TSDF_BATCH_OPT_AUTOTUNE   2  /* 1 (default): time every tuning configuration on the first calls and keep the fastest */
 #define TSDF_BATCH_OPT_CONFIG     3  /* fix the tuning configuration; turns autotuning off. 0..5: atomic reduction,
                                         {no merge, merge} x {4, 2, 1} steps per item; 6, 7: sort reduction
-                                        (TSDF_REDUCTION_SORT) with 4, 2 steps per item */
+                                        (TSDF_REDUCTION_SORT) with 4, 2 steps per item (all with CTAs of 256
+                                        threads, as many per SM as fit, whole-brick apply tasks); 8..11: atomic
+                                        reduction, no merge, 4 steps per item, with CTAs of 128 threads, of 512
+                                        threads, of 256 threads but 2 per SM, or quarter-brick apply tasks */
 #define TSDF_BATCH_OPT_SPIN_LIMIT 4  /* polls before a grid-barrier wait gives up (default 2^24, about a second) */
 #define TSDF_BATCH_OPT_TEST_MISSING_ARRIVALS 5  /* test hook: the barrier waits for this many CTAs that do not exist (default 0) */
 #define TSDF_BATCH_OPT_GRID_FRACTION 6  /* percent (1..100, default 100) of the device's co-resident CTAs the launch uses,
                                            so that launches on several streams can be resident together */
+#define TSDF_BATCH_OPT_TUNE_SORT  7  /* 1 (default): the autotuner also times the sort configurations, whose first use
+                                        allocates each map's sort buffers; 0: only the atomic ones (no allocation) */
 
 /* Create a batch object for up to max_count (1..1024) maps per call, on the
  * current device. Synchronous. Errors: INVALID, OOM, CUDA. */
@@ -388,10 +426,13 @@ int tsdf_batch_destroy(tsdf_batch* batch);
 int tsdf_batch_set_option(tsdf_batch* batch, int32_t option, int64_t value);
 
 /* The tuning configuration in use: index, warp merge (0/1), steps per work
- * item, reduction (TSDF_REDUCTION_*), and whether autotuning has finished
- * (any pointer may be NULL). */
+ * item, reduction (TSDF_REDUCTION_*), whether autotuning has finished, and the
+ * launch shape: threads per CTA, CTAs launched, and voxel pairs per lane of
+ * an apply task (8: a warp per brick, 2: a quarter brick). Any pointer may be
+ * NULL. */
 int tsdf_batch_get_config(const tsdf_batch* batch, int32_t* config, int32_t* merge, int32_t* steps_per_item,
-                          int32_t* reduction, int32_t* tuned);
+                          int32_t* reduction, int32_t* tuned, int32_t* threads_per_cta, int32_t* ctas,
+                          int32_t* apply_voxel_pairs);
 
 /* Integrate scan i (points_dev[i]: n[i] device float4 points, 16-byte
  * aligned; poses + 12*i: host row-major 3x4 pose) into maps[i], for i <
@@ -427,12 +468,16 @@ int tsdf_batch_sync(tsdf_batch* batch, void* stream);
 typedef struct tsdf_server tsdf_server;   /* opaque; owns its sessions' maps, streams and pinned slabs */
 
 typedef struct tsdf_server_config {
-    int64_t hbm_budget_bytes;   /* device memory the sessions may take (grid, accumulator, ray buffers) */
+    int64_t hbm_budget_bytes;   /* device memory the sessions may take (grid, accumulator, ray buffers, the device
+                                   tier of each session's global store) */
     int64_t max_points;         /* largest scan accepted, 1..TSDF_MAX_POINTS */
     int32_t max_batch;          /* most sessions in one batch, 1..1024 */
     int32_t streams;            /* batches that may be in flight together, 1..8 */
     int32_t max_outstanding;    /* submitted requests not yet waited for (pinned slabs of max_points points) */
-    int32_t reserved;           /* must be 0 */
+    int32_t store_chunks;       /* device-tier slots of each session's global store, allocated when the session
+                                   opens and charged to the budget (2 KiB each); 0: an eighth of the window's
+                                   bricks. Shifts never allocate device memory; chunks beyond it go to pinned
+                                   host memory. */
 } tsdf_server_config;
 
 typedef struct tsdf_request_result {

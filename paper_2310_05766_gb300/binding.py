@@ -40,12 +40,15 @@ TSDF_REDUCTION_SORT = 1
 TSDF_REDUCTION_POOL = 2
 TSDF_REDUCTION_AUTO = 3
 TSDF_OPT_POOL_BRICKS = 7
+TSDF_OPT_STORE_DEVICE_CHUNKS = 8
+TSDF_OPT_STORE_SPILL_AGE = 9
 TSDF_BATCH_OPT_GRAPH = 1
 TSDF_BATCH_OPT_AUTOTUNE = 2
 TSDF_BATCH_OPT_CONFIG = 3
 TSDF_BATCH_OPT_SPIN_LIMIT = 4
 TSDF_BATCH_OPT_TEST_MISSING_ARRIVALS = 5
 TSDF_BATCH_OPT_GRID_FRACTION = 6
+TSDF_BATCH_OPT_TUNE_SORT = 7
 TSDF_STATIC_MAX_VOXELS = 1 << 21
 TSDF_STATIC_MAX_POINTS = 1 << 17
 
@@ -79,7 +82,7 @@ class tsdf_kernel_time(ctypes.Structure):
 
 class tsdf_server_config(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_points", ctypes.c_int64), ("max_batch", ctypes.c_int32),
-                ("streams", ctypes.c_int32), ("max_outstanding", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("streams", ctypes.c_int32), ("max_outstanding", ctypes.c_int32), ("store_chunks", ctypes.c_int32)]
 
 
 class tsdf_request_result(ctypes.Structure):
@@ -131,6 +134,8 @@ def lib():
     L.tsdf_probe_reduction_rate.argtypes = [ctypes.c_int32, P(ctypes.c_double), vp]
     L.tsdf_map_save.argtypes = [vp, ctypes.c_char_p, vp]
     L.tsdf_map_device_bytes.argtypes = [vp, P(i64)]
+    L.tsdf_map_reserve_store.argtypes = [vp, i64]
+    L.tsdf_get_store_stats.argtypes = [vp, vp]
     L.tsdf_get_reduction.argtypes = [vp, P(ctypes.c_int32)]
     L.tsdf_extract_mesh.argtypes = [vp, ctypes.c_int32, vp, i64, P(i64), vp]
     L.tsdf_register_system.argtypes = [vp, vp, i64, f32p, ctypes.c_int32, P(ctypes.c_double), vp]
@@ -140,7 +145,7 @@ def lib():
     L.tsdf_batch_create.argtypes = [ctypes.c_int32, P(vp)]
     L.tsdf_batch_destroy.argtypes = [vp]
     L.tsdf_batch_set_option.argtypes = [vp, ctypes.c_int32, ctypes.c_int64]
-    L.tsdf_batch_get_config.argtypes = [vp] + [P(ctypes.c_int32)] * 5
+    L.tsdf_batch_get_config.argtypes = [vp] + [P(ctypes.c_int32)] * 8
     L.tsdf_batch_integrate.argtypes = [vp, P(vp), P(vp), P(i64), f32p, ctypes.c_int32, vp]
     L.tsdf_integrate_batch.argtypes = [P(vp), P(vp), P(i64), f32p, ctypes.c_int32, vp]
     L.tsdf_batch_sync.argtypes = [vp, vp]
@@ -366,10 +371,12 @@ def tsdf_batch_set_option(batch: int, option: int, value: int) -> None:
 
 
 def tsdf_batch_get_config(batch: int) -> dict:
-    c, m, k, r, t = (ctypes.c_int32() for _ in range(5))
+    c, m, k, r, t, th, ct, ap = (ctypes.c_int32() for _ in range(8))
     _check(lib().tsdf_batch_get_config(batch, ctypes.byref(c), ctypes.byref(m), ctypes.byref(k), ctypes.byref(r),
-                                       ctypes.byref(t)), "tsdf_batch_get_config")
-    return dict(config=c.value, merge=m.value, steps_per_item=k.value, reduction=r.value, tuned=bool(t.value))
+                                       ctypes.byref(t), ctypes.byref(th), ctypes.byref(ct), ctypes.byref(ap)),
+           "tsdf_batch_get_config")
+    return dict(config=c.value, merge=m.value, steps_per_item=k.value, reduction=r.value, tuned=bool(t.value),
+                threads_per_cta=th.value, ctas=ct.value, apply_voxel_pairs=ap.value)
 
 
 def tsdf_batch_integrate(batch: int, maps, points, poses, stream=None) -> None:
@@ -394,9 +401,9 @@ def tsdf_batch_sync(batch: int, stream=None) -> int:
 
 
 def tsdf_server_create(hbm_budget_bytes: int, max_points: int = 1 << 18, max_batch: int = 32, streams: int = 2,
-                       max_outstanding: int = 64) -> int:
+                       max_outstanding: int = 64, store_chunks: int = 0) -> int:
     cfg = tsdf_server_config(int(hbm_budget_bytes), int(max_points), int(max_batch), int(streams),
-                             int(max_outstanding), 0)
+                             int(max_outstanding), int(store_chunks))
     h = ctypes.c_void_p()
     _check(lib().tsdf_server_create(ctypes.byref(cfg), ctypes.byref(h)), "tsdf_server_create")
     return h.value
@@ -576,6 +583,22 @@ def tsdf_map_device_bytes(handle: int) -> int:
     out = ctypes.c_int64()
     _check(lib().tsdf_map_device_bytes(handle, ctypes.byref(out)), "tsdf_map_device_bytes")
     return int(out.value)
+
+
+class tsdf_store_stats(ctypes.Structure):
+    _fields_ = [("device_chunks", ctypes.c_int64), ("device_capacity", ctypes.c_int64),
+                ("host_chunks", ctypes.c_int64), ("host_capacity", ctypes.c_int64),
+                ("spilled", ctypes.c_int64), ("dropped", ctypes.c_int64)]
+
+
+def tsdf_map_reserve_store(handle: int, device_chunks: int) -> None:
+    _check(lib().tsdf_map_reserve_store(handle, int(device_chunks)), "tsdf_map_reserve_store")
+
+
+def tsdf_get_store_stats(handle: int) -> dict:
+    st = tsdf_store_stats()
+    _check(lib().tsdf_get_store_stats(handle, ctypes.byref(st)), "tsdf_get_store_stats")
+    return {k: int(getattr(st, k)) for k, _ in tsdf_store_stats._fields_}
 
 
 def tsdf_map_save(handle: int, path: str, stream=None) -> None:

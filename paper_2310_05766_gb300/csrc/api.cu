@@ -1,6 +1,6 @@
 // Host side of the C ABI declared in include/tsdf.h: argument validation,
-// device memory ownership, the device-resident global chunk store and the
-// launch sequence of each call. No float arithmetic of the method runs here
+// device memory ownership, the two-tier global chunk store (device memory,
+// then pinned host memory) and the launch sequence of each call. No float arithmetic of the method runs here
 // beyond the per-map constants 1/voxel, QMAX/tau and K, derived once in
 // binary64 and rounded to binary32.
 #include <algorithm>
@@ -12,7 +12,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "chunk_index.h"
+#include "chunk_store.h"
 #include "tsdf_internal.cuh"
 #include "../../include/tsdf.h"
 
@@ -82,11 +82,28 @@ struct tsdf_map {
     size_t bricks = 0;
     size_t ray_cap = 0;
     MapDev dev{};
-    // device-resident global store of 8^3 chunks
-    ChunkIndex store_index;
-    std::vector<char*> store_segments;   // 8 MiB each, carved from store_allocs
-    std::vector<char*> store_allocs;     // the device allocations behind them
-    uint32_t store_count = 0;
+    // global store of the 8^3 chunks outside the window that hold data: slots
+    // in device memory (tier 0) and in pinned, device-mapped host memory
+    // (tier 1), 4096 slots (8 MiB) per segment
+    ChunkStore store;
+    std::vector<char*> store_seg[2];     // device-visible address of each segment
+    std::vector<char*> store_allocs[2];  // the allocations behind them (host tier: host pointers)
+    std::vector<char*> store_seg_host;   // host tier: host address of each segment
+    size_t store_dev_cap = 0;            // most device-tier slots (TSDF_OPT_STORE_DEVICE_CHUNKS; 0 = the window's bricks)
+    uint32_t spill_age = 0;              // shifts after which a stored chunk moves to host memory (0: only when short)
+    uint64_t shift_serial = 0;           // shifts done so far
+    uint64_t chunks_spilled = 0;         // chunks moved from the device tier to the host tier
+    uint64_t chunks_dropped = 0;         // leaving chunks found empty (not stored)
+    uint8_t* flags_dev = nullptr;        // per shift item: the leaving brick held data (written by the shift kernel)
+    uint8_t* flags_host = nullptr;       // pinned copy of the last shift's flags
+    size_t flags_cap = 0;
+    size_t flags_count = 0;              // candidates of the last shift, awaiting their flags
+    cudaEvent_t flags_event = nullptr;
+    ChunkCopy* spill_dev = nullptr;      // copies device slot -> host slot of one shift
+    ChunkCopy* spill_host = nullptr;
+    size_t spill_cap = 0;
+    cudaEvent_t spill_event = nullptr;   // the copy list of the last spill has been read
+    bool spill_pending = false;
     ShiftItem* items_dev = nullptr;
     size_t items_dev_cap = 0;
     ShiftItem* items_host = nullptr;
@@ -232,7 +249,14 @@ void free_map(tsdf_map* m) {
     cudaFree(m->dev.ray_slot);
     cudaFree(m->dev.pairs);
     cudaFree(m->dev.sorted);
-    for (char* s : m->store_allocs) cudaFree(s);
+    for (char* a : m->store_allocs[0]) cudaFree(a);
+    for (char* a : m->store_allocs[1]) cudaFreeHost(a);
+    cudaFree(m->flags_dev);
+    if (m->flags_host) cudaFreeHost(m->flags_host);
+    if (m->flags_event) cudaEventDestroy(m->flags_event);
+    cudaFree(m->spill_dev);
+    if (m->spill_host) cudaFreeHost(m->spill_host);
+    if (m->spill_event) cudaEventDestroy(m->spill_event);
     cudaFree(m->items_dev);
     if (m->items_host) cudaFreeHost(m->items_host);
     if (m->items_event) cudaEventDestroy(m->items_event);
@@ -248,39 +272,180 @@ bool box_inside(const tsdf_map* m, const int64_t lo[3], const int64_t hi[3], uin
     return true;
 }
 
-// Store address of a chunk, allocating a new store slot when `create`.
-int store_lookup(tsdf_map* m, const ChunkKey& k, bool create, unsigned long long* out) {
-    const long long found = m->store_index.find(k);
-    if (found >= 0) {
-        uint32_t idx = (uint32_t)found;
-        *out = (unsigned long long)(m->store_segments[idx / kSegChunks] + (size_t)(idx % kSegChunks) * kChunkBytes);
-        return TSDF_OK;
-    }
-    if (!create) {
-        *out = 0ull;
-        return TSDF_OK;
-    }
-    uint32_t idx = m->store_count;
-    if (idx / kSegChunks >= m->store_segments.size()) {
-        // segments come in growing batches (1, 2, 4, ... 32 per allocation), so
-        // a map moving into new ground does not pay an allocation at every shift
-        const size_t seg_bytes = (size_t)kSegChunks * kChunkBytes;
-        size_t n = (size_t)1 << std::min<size_t>(5, m->store_allocs.size());
-        char* base = nullptr;
-        cudaError_t e = cudaMalloc(&base, n * seg_bytes);
-        if (e != cudaSuccess && n > 1) {   // short of memory: one segment at a time
+// Most device-tier slots of the map's store.
+size_t store_dev_limit(const tsdf_map* m) { return m->store_dev_cap ? m->store_dev_cap : m->bricks; }
+
+// Device-visible address of a store location.
+unsigned long long store_addr(const tsdf_map* m, uint32_t loc) {
+    const int t = ChunkStore::is_host(loc) ? 1 : 0;
+    const uint32_t slot = ChunkStore::slot_of(loc);
+    return (unsigned long long)(m->store_seg[t][slot / kSegChunks] + (size_t)(slot % kSegChunks) * kChunkBytes);
+}
+
+// Adds `segs` segments to a tier: device memory, or pinned host memory mapped
+// into the device's address space. Returns false when the allocation fails.
+bool store_grow(tsdf_map* m, int tier, size_t segs) {
+    const size_t bytes = segs * (size_t)kSegChunks * kChunkBytes;
+    char* base = nullptr;
+    char* dev = nullptr;
+    if (tier == 0) {
+        if (cudaMalloc(&base, bytes) != cudaSuccess) {
             cudaGetLastError();
-            n = 1;
-            e = cudaMalloc(&base, seg_bytes);
+            return false;
         }
-        if (e != cudaSuccess) return cuda_fail(e);
-        m->store_allocs.push_back(base);
-        for (size_t i = 0; i < n; ++i) m->store_segments.push_back(base + i * seg_bytes);
+        dev = base;
+    } else {
+        if (cudaHostAlloc(&base, bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        void* dp = nullptr;
+        if (cudaHostGetDevicePointer(&dp, base, 0) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFreeHost(base);
+            return false;
+        }
+        dev = static_cast<char*>(dp);
     }
-    m->store_count++;
-    m->store_index.insert(k, idx);
-    *out = (unsigned long long)(m->store_segments[idx / kSegChunks] + (size_t)(idx % kSegChunks) * kChunkBytes);
+    const uint32_t first = (uint32_t)(m->store_seg[tier].size() * kSegChunks);
+    m->store_allocs[tier].push_back(base);
+    for (size_t i = 0; i < segs; ++i) {
+        m->store_seg[tier].push_back(dev + i * (size_t)kSegChunks * kChunkBytes);
+        if (tier == 1) m->store_seg_host.push_back(base + i * (size_t)kSegChunks * kChunkBytes);
+    }
+    m->store.add_slots(tier, first, (uint32_t)(segs * kSegChunks));
+    return true;
+}
+
+
+// Takes the previous shift's flags (waiting for them if needed): candidates
+// whose brick held no data are dropped and their slots freed.
+int store_resolve(tsdf_map* m) {
+    if (!m->store.pending()) return TSDF_OK;
+    TSDF_CU(cudaEventSynchronize(m->flags_event));
+    size_t empty = 0;
+    for (size_t i = 0; i < m->flags_count; ++i) empty += m->flags_host[i] ? 0 : 1;
+    m->chunks_dropped += empty;
+    m->store.resolve(m->flags_host);
+    m->flags_count = 0;
     return TSDF_OK;
+}
+
+// Bookkeeping buffers of a shift moving `cnt` bricks: the item list (pinned
+// and device), the per-item flags (device and pinned) and the list of
+// device -> host chunk copies (as many as the device tier has slots).
+int ensure_shift_buffers(tsdf_map* m, size_t cnt) {
+    if (m->items_event_pending && cnt > m->items_host_cap) {
+        TSDF_CU(cudaEventSynchronize(m->items_event));
+        m->items_event_pending = false;
+    }
+    if (cnt > m->items_host_cap) {
+        if (m->items_host) cudaFreeHost(m->items_host);
+        m->items_host = nullptr;
+        m->items_host_cap = 0;
+        TSDF_CU(cudaMallocHost(&m->items_host, cnt * sizeof(ShiftItem)));
+        m->items_host_cap = cnt;
+    }
+    if (cnt > m->items_dev_cap || cnt > m->flags_cap) {
+        int rc = store_resolve(m);   // the flags still to be read live in these buffers
+        if (rc != TSDF_OK) return rc;
+        cudaFree(m->items_dev);   // waits for the device
+        cudaFree(m->flags_dev);
+        if (m->flags_host) cudaFreeHost(m->flags_host);
+        m->items_dev = nullptr;
+        m->flags_dev = nullptr;
+        m->flags_host = nullptr;
+        m->items_dev_cap = 0;
+        m->flags_cap = 0;
+        TSDF_CU(cudaMalloc(&m->items_dev, cnt * sizeof(ShiftItem)));
+        m->items_dev_cap = cnt;
+        TSDF_CU(cudaMalloc(&m->flags_dev, cnt));
+        TSDF_CU(cudaMallocHost(&m->flags_host, cnt));
+        m->flags_cap = cnt;
+    }
+    // (the copy list exists once chunks can move: the device tier is at its
+    // limit, or chunks move by age)
+    const size_t limit = store_dev_limit(m);
+    const size_t moves = (m->store.capacity(0) >= limit || m->spill_age > 0) ? std::max(limit, m->store.capacity(0)) : 0;
+    if (moves > m->spill_cap) {
+        if (m->spill_pending) TSDF_CU(cudaEventSynchronize(m->spill_event));   // the old list has been read
+        m->spill_pending = false;
+        cudaFree(m->spill_dev);   // waits for the device
+        if (m->spill_host) cudaFreeHost(m->spill_host);
+        m->spill_dev = nullptr;
+        m->spill_host = nullptr;
+        m->spill_cap = 0;
+        TSDF_CU(cudaMalloc(&m->spill_dev, moves * sizeof(ChunkCopy)));
+        TSDF_CU(cudaMallocHost(&m->spill_host, moves * sizeof(ChunkCopy)));
+        m->spill_cap = moves;
+    }
+    return TSDF_OK;
+}
+
+// Makes room for `need` leaving chunks before a shift: the device tier grows
+// up to its limit, then its oldest chunks move to the host tier (as do chunks
+// stored more than spill_age shifts ago), and the host tier takes whatever
+// the device tier cannot. The moves are copies on `s`, issued before the
+// shift kernel, so the device slots they free can be reused by this shift.
+int store_make_room(tsdf_map* m, size_t need, cudaStream_t s) {
+    const size_t limit = store_dev_limit(m);
+    while (m->store.free_count(0) < need && m->store.capacity(0) < limit) {
+        const size_t room = (limit - m->store.capacity(0) + kSegChunks - 1) / kSegChunks;
+        size_t segs = (size_t)1 << std::min<size_t>(5, m->store_allocs[0].size());   // 1, 2, 4 ... 32 at a time
+        segs = std::min(segs, room);
+        if (!store_grow(m, 0, segs) && !(segs > 1 && store_grow(m, 0, 1))) break;   // short of memory: spill
+    }
+    int rc = ensure_shift_buffers(m, 0);   // the copy list, once chunks can move
+    if (rc != TSDF_OK) return rc;
+    std::vector<ChunkCopy> moves;
+    auto host_slot = [&]() -> bool {
+        return m->store.free_count(1) > 0 || store_grow(m, 1, 1);
+    };
+    // (a move is recorded in the index as it is planned, so every planned move
+    // is launched below, also when the host tier cannot grow further)
+    rc = TSDF_OK;
+    // chunks stored too long ago
+    if (m->spill_age > 0) {
+        ChunkKey k;
+        uint32_t loc;
+        uint64_t stamp;
+        while (m->store.oldest_device(&k, &loc, &stamp) && stamp + m->spill_age <= m->shift_serial) {
+            if (!host_slot()) {
+                rc = TSDF_ERR_OOM;
+                break;
+            }
+            uint32_t from = 0, to = 0;
+            if (!m->store.spill_oldest(&from, &to)) break;
+            moves.push_back(ChunkCopy{store_addr(m, to), store_addr(m, from)});
+        }
+    }
+    // room on the device tier for this shift's chunks
+    while (rc == TSDF_OK && m->store.free_count(0) < need) {
+        if (!host_slot()) {
+            rc = TSDF_ERR_OOM;
+            break;
+        }
+        uint32_t from = 0, to = 0;
+        if (!m->store.spill_oldest(&from, &to)) break;
+        moves.push_back(ChunkCopy{store_addr(m, to), store_addr(m, from)});
+    }
+    // whatever the device tier cannot take goes to the host tier
+    const size_t dev_free = m->store.free_count(0);
+    while (rc == TSDF_OK && dev_free + m->store.free_count(1) < need) {
+        if (!store_grow(m, 1, (need - dev_free - m->store.free_count(1) + kSegChunks - 1) / kSegChunks))
+            rc = TSDF_ERR_OOM;
+    }
+    if (!moves.empty()) {
+        if (moves.size() > m->spill_cap) return TSDF_ERR_OOM;   // not reached: moves <= device-tier chunks
+        if (m->spill_pending) TSDF_CU(cudaEventSynchronize(m->spill_event));   // the last copy list is read
+        std::memcpy(m->spill_host, moves.data(), moves.size() * sizeof(ChunkCopy));
+        TSDF_CU(cudaMemcpyAsync(m->spill_dev, m->spill_host, moves.size() * sizeof(ChunkCopy), cudaMemcpyHostToDevice, s));
+        TSDF_CU(cudaEventRecord(m->spill_event, s));
+        m->spill_pending = true;
+        TSDF_CU(launch_copy_chunks(m->spill_dev, (int)moves.size(), s));
+        m->chunks_spilled += moves.size();
+    }
+    return rc;
 }
 
 }  // namespace
@@ -334,6 +499,8 @@ int tsdf_map_create(const tsdf_params* params, tsdf_map** out) {
         cudaGetLastError();   // clear a failed mapping request
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->items_event, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->flags_event, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->spill_event, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         free_map(m);
@@ -684,46 +851,53 @@ int tsdf_shift(tsdf_map* map, const int64_t new_origin[3], void* stream) {
             TSDF_CU(cudaEventSynchronize(map->items_event));
             map->items_event_pending = false;
         }
-        if (cnt > map->items_host_cap) {
-            if (map->items_host) cudaFreeHost(map->items_host);
-            map->items_host = nullptr;
-            map->items_host_cap = 0;
-            TSDF_CU(cudaMallocHost(&map->items_host, cnt * sizeof(ShiftItem)));
-            map->items_host_cap = cnt;
-        }
-        if (cnt > map->items_dev_cap) {
-            cudaFree(map->items_dev);   // waits for the device
-            map->items_dev = nullptr;
-            map->items_dev_cap = 0;
-            TSDF_CU(cudaMalloc(&map->items_dev, cnt * sizeof(ShiftItem)));
-            map->items_dev_cap = cnt;
-        }
+        int rc = store_resolve(map);   // the previous shift's empty chunks are dropped
+        if (rc == TSDF_OK) rc = ensure_shift_buffers(map, cnt);
+        if (rc == TSDF_OK) rc = store_make_room(map, cnt, s);
+        if (rc != TSDF_OK) return rc;
+        // every leaving chunk gets a slot (device tier first); the kernel writes
+        // only those that hold data. Then the entering chunks are looked up and
+        // leave the store: their slots are freed after all leaving chunks have
+        // theirs, so no slot is both read and written by this shift.
+        const uint64_t stamp = ++map->shift_serial;
         size_t k = 0;
-        auto add = [&](long long sx, long long sy, long long sz) -> int {
+        auto add_out = [&](long long sx, long long sy, long long sz) -> int {
             ShiftItem& it = map->items_host[k++];
             it = ShiftItem{};
             it.brick = (uint32_t)((sz * C[1] + sy) * C[0] + sx);
-            int rc = store_lookup(map, ChunkKey{oldc[0][sx], oldc[1][sy], oldc[2][sz]}, true, &it.out_ptr);
-            if (rc != TSDF_OK) return rc;
-            return store_lookup(map, ChunkKey{newc[0][sx], newc[1][sy], newc[2][sz]}, false, &it.in_ptr);
+            const long long loc = map->store.place(ChunkKey{oldc[0][sx], oldc[1][sy], oldc[2][sz]}, stamp);
+            if (loc < 0) return TSDF_ERR_OOM;
+            it.out_ptr = store_addr(map, (uint32_t)loc);
+            return TSDF_OK;
         };
         for (long long sz = 0; sz < C[2]; ++sz) {
             for (long long sy = 0; sy < C[1]; ++sy) {
-                int rc = TSDF_OK;
+                int r2 = TSDF_OK;
                 if (chg[2][sz] || chg[1][sy]) {
-                    for (long long sx = 0; sx < C[0] && rc == TSDF_OK; ++sx) rc = add(sx, sy, sz);
+                    for (long long sx = 0; sx < C[0] && r2 == TSDF_OK; ++sx) r2 = add_out(sx, sy, sz);
                 } else {
-                    for (size_t q = 0; q < chx.size() && rc == TSDF_OK; ++q) rc = add(chx[q], sy, sz);
+                    for (size_t q = 0; q < chx.size() && r2 == TSDF_OK; ++q) r2 = add_out(chx[q], sy, sz);
                 }
-                if (rc != TSDF_OK) return rc;
+                if (r2 != TSDF_OK) return r2;
             }
         }
+        for (size_t i = 0; i < cnt; ++i) {
+            ShiftItem& it = map->items_host[i];
+            const long long b = it.brick;
+            const long long sx = b % C[0], sy = (b / C[0]) % C[1], sz = b / (C[0] * C[1]);
+            const long long loc = map->store.take(ChunkKey{newc[0][sx], newc[1][sy], newc[2][sz]});
+            it.in_ptr = loc >= 0 ? store_addr(map, (uint32_t)loc) : 0ull;
+        }
+        map->store.end_shift();
+        map->flags_count = cnt;
         TSDF_CU(cudaMemcpyAsync(map->items_dev, map->items_host, cnt * sizeof(ShiftItem), cudaMemcpyHostToDevice, s));
         TSDF_CU(cudaEventRecord(map->items_event, s));
         map->items_event_pending = true;
         cudaEvent_t e0 = prof_mark(map, s);
-        TSDF_CU(launch_shift(map->dev.grid, map->items_dev, (int)cnt, s));
+        TSDF_CU(launch_shift(map->dev.grid, map->items_dev, (int)cnt, map->flags_dev, s));
         prof_push(map, kShift, e0, prof_mark(map, s));
+        TSDF_CU(cudaMemcpyAsync(map->flags_host, map->flags_dev, cnt, cudaMemcpyDeviceToHost, s));
+        TSDF_CU(cudaEventRecord(map->flags_event, s));
     }
     for (int a = 0; a < 3; ++a) map->origin[a] = new_origin[a];
     return TSDF_OK;
@@ -869,8 +1043,43 @@ int tsdf_set_option(tsdf_map* map, int32_t option, int64_t value) {
             if (value != 0 && (value < 1024 || value > (int64_t)kPairCapMax)) return TSDF_ERR_INVALID;
             map->pair_cap_req = (size_t)value;
             return TSDF_OK;
+        case TSDF_OPT_STORE_DEVICE_CHUNKS:
+            if (value < 0 || value > (1LL << 30)) return TSDF_ERR_INVALID;
+            map->store_dev_cap = (size_t)value;
+            return TSDF_OK;
+        case TSDF_OPT_STORE_SPILL_AGE:
+            if (value < 0 || value > (1LL << 30)) return TSDF_ERR_INVALID;
+            map->spill_age = (uint32_t)value;
+            return TSDF_OK;
         default: return TSDF_ERR_INVALID;
     }
+}
+
+int tsdf_map_reserve_store(tsdf_map* map, int64_t device_chunks) {
+    if (!map || device_chunks < 1 || device_chunks > (1LL << 30)) return TSDF_ERR_INVALID;
+    DeviceScope ds(map->device);
+    const size_t want = ((size_t)device_chunks + kSegChunks - 1) / kSegChunks * kSegChunks;
+    map->store_dev_cap = std::max(want, map->store.capacity(0));
+    while (map->store.capacity(0) < want) {
+        const size_t segs = (want - map->store.capacity(0)) / kSegChunks;
+        if (!store_grow(map, 0, segs) && !store_grow(map, 0, 1)) return TSDF_ERR_OOM;
+    }
+    // and the bookkeeping of a shift that moves every brick of the window
+    return ensure_shift_buffers(map, map->bricks);
+}
+
+int tsdf_get_store_stats(tsdf_map* map, tsdf_store_stats* out) {
+    if (!map || !out) return TSDF_ERR_INVALID;
+    DeviceScope ds(map->device);
+    int rc = store_resolve(map);
+    if (rc != TSDF_OK) return rc;
+    out->device_chunks = (int64_t)map->store.used(0);
+    out->device_capacity = (int64_t)map->store.capacity(0);
+    out->host_chunks = (int64_t)map->store.used(1);
+    out->host_capacity = (int64_t)map->store.capacity(1);
+    out->spilled = (int64_t)map->chunks_spilled;
+    out->dropped = (int64_t)map->chunks_dropped;
+    return TSDF_OK;
 }
 
 // ---- persistence ------------------------------------------------------------
@@ -966,33 +1175,38 @@ int tsdf_map_save(tsdf_map* map, const char* path, void* stream) {
             ++count;
         }
     }
-    // 2. stored chunks outside the window (a stored copy of a chunk that is
-    //    back in the window is stale), segment by segment
-    std::vector<std::vector<std::pair<uint32_t, ChunkKey>>> by_seg(map->store_segments.size());
-    map->store_index.for_each([&](const ChunkKey& k, uint32_t slot) {
-        const long long kc[3] = {k.x, k.y, k.z};
-        bool inside = true;
-        for (int a = 0; a < 3; ++a) {
-            const long long co = floordiv8(map->origin[a]);
-            inside = inside && kc[a] >= co && kc[a] < co + C[a];
-        }
-        if (!inside) by_seg[slot / kSegChunks].push_back({slot % kSegChunks, k});
+    // 2. stored chunks (all outside the window): device-tier chunks segment by
+    //    segment through the staging buffer, host-tier chunks in place
+    int rc = store_resolve(map);
+    if (rc != TSDF_OK) return rc;
+    std::vector<std::vector<std::pair<uint32_t, ChunkKey>>> by_seg(map->store_seg[0].size());
+    std::vector<std::pair<uint32_t, ChunkKey>> on_host;
+    map->store.for_each([&](const ChunkKey& k, uint32_t loc) {
+        if (ChunkStore::is_host(loc)) on_host.push_back({ChunkStore::slot_of(loc), k});
+        else by_seg[loc / kSegChunks].push_back({loc % kSegChunks, k});
     });
+    auto put = [&](const uint32_t* w, const ChunkKey& k) -> bool {
+        if (all_zero(w)) return true;
+        rec.chunk[0] = k.x;
+        rec.chunk[1] = k.y;
+        rec.chunk[2] = k.z;
+        std::memcpy(rec.word, w, kChunkBytes);
+        if (std::fwrite(&rec, sizeof(rec), 1, fc.f) != 1) return false;
+        ++count;
+        return true;
+    };
     for (size_t sg = 0; sg < by_seg.size(); ++sg) {
         if (by_seg[sg].empty()) continue;
-        TSDF_CU(cudaMemcpyAsync(stage.p, map->store_segments[sg], (size_t)kSegChunks * kChunkBytes,
+        TSDF_CU(cudaMemcpyAsync(stage.p, map->store_seg[0][sg], (size_t)kSegChunks * kChunkBytes,
                                 cudaMemcpyDeviceToHost, s));
         TSDF_CU(cudaStreamSynchronize(s));
-        for (const auto& e : by_seg[sg]) {
-            const uint32_t* w = sw + (size_t)e.first * kBrickVoxels;
-            if (all_zero(w)) continue;
-            rec.chunk[0] = e.second.x;
-            rec.chunk[1] = e.second.y;
-            rec.chunk[2] = e.second.z;
-            std::memcpy(rec.word, w, kChunkBytes);
-            if (std::fwrite(&rec, sizeof(rec), 1, fc.f) != 1) return TSDF_ERR_IO;
-            ++count;
-        }
+        for (const auto& e : by_seg[sg])
+            if (!put(sw + (size_t)e.first * kBrickVoxels, e.second)) return TSDF_ERR_IO;
+    }
+    for (const auto& e : on_host) {
+        const uint32_t* w = reinterpret_cast<const uint32_t*>(map->store_seg_host[e.first / kSegChunks] +
+                                                              (size_t)(e.first % kSegChunks) * kChunkBytes);
+        if (!put(w, e.second)) return TSDF_ERR_IO;
     }
     h.chunk_count = count;
     if (std::fseek(fc.f, 0, SEEK_SET) != 0 || std::fwrite(&h, sizeof(h), 1, fc.f) != 1) return TSDF_ERR_IO;
@@ -1062,8 +1276,14 @@ int tsdf_map_load(const char* path, tsdf_map** out, void* stream) {
                 const size_t brick = (size_t)((slot[2] * C[1] + slot[1]) * C[0] + slot[0]);
                 dst = (unsigned long long)(map->dev.grid + brick * kBrickVoxels);
             } else {
-                rc = store_lookup(map, ChunkKey{rec.chunk[0], rec.chunk[1], rec.chunk[2]}, true, &dst);
-                if (rc != TSDF_OK) return fail(rc);
+                if (map->store.free_count(0) == 0 && map->store.free_count(1) == 0) {
+                    const bool dev = map->store.capacity(0) < store_dev_limit(map);
+                    if (!store_grow(map, dev ? 0 : 1, 1) && !(dev && store_grow(map, 1, 1))) return fail(TSDF_ERR_OOM);
+                }
+                const long long loc = map->store.insert_stored(ChunkKey{rec.chunk[0], rec.chunk[1], rec.chunk[2]},
+                                                               map->shift_serial);
+                if (loc < 0) return fail(TSDF_ERR_OOM);
+                dst = store_addr(map, (uint32_t)loc);
             }
             items[k].dst = dst;
             items[k].src = (unsigned long long)(static_cast<char*>(stage_d) + k * kChunkBytes);
@@ -1178,8 +1398,9 @@ int tsdf_map_device_bytes(const tsdf_map* map, int64_t* out) {
     if (map->dev.pool_table)
         b += map->bricks * sizeof(uint32_t) +
              (size_t)map->dev.pool_cap * (sizeof(uint32_t) + kBrickVoxels * sizeof(unsigned long long));
-    b += map->store_segments.size() * (size_t)kSegChunks * kChunkBytes;
-    b += map->stage_cap * sizeof(float4) + map->items_dev_cap * sizeof(ShiftItem);
+    b += map->store_seg[0].size() * (size_t)kSegChunks * kChunkBytes;   // the host tier is host memory
+    b += map->stage_cap * sizeof(float4) + map->items_dev_cap * sizeof(ShiftItem) + map->flags_cap +
+         map->spill_cap * sizeof(ChunkCopy);
     *out = (int64_t)b;
     return TSDF_OK;
 }

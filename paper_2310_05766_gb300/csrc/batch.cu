@@ -21,8 +21,8 @@
 // other.
 //
 // Tuning (per-scan reduction by accumulator atomics or by sort, warp merge,
-// steps per work item) changes speed only: results are bit-identical for every
-// setting. The sort configurations add three phases (count, prefix, scatter:
+// steps per work item, CTA size, CTAs per SM, apply task size) changes speed
+// only: results are bit-identical for every setting. The sort configurations add three phases (count, prefix, scatter:
 // a counting sort of the emitted pairs by brick, see integrate.cu) and apply
 // each brick from its sorted segment. With autotuning on, the first calls
 // cycle through the settings, timing each with events, and the fastest is
@@ -54,8 +54,6 @@ namespace {
 using namespace dev;
 
 constexpr int kBatchMax = 1024;               // maps per batch
-constexpr int kBatchThreads = 256;
-constexpr int kBatchWarps = kBatchThreads / 32;
 constexpr size_t kApplySmemPerWarp = kBrickVoxels * (4 + 8 + 2);   // grid, accumulator, offsets
 constexpr int kWarpBrickCacheLog2 = 10;                              // per-warp brick cache in phase 2
 static_assert((4u << kWarpBrickCacheLog2) <= kApplySmemPerWarp, "brick cache fits the staging area");
@@ -160,13 +158,16 @@ __device__ __forceinline__ uint32_t written_slots(const MapDev& m) {
     return (uint32_t)(n < m.pair_cap ? n : (unsigned long long)m.pair_cap);
 }
 
-template <bool MERGE, int KPT, bool SORT>
-__global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem* __restrict__ items,
-                                                                  const BatchHeader* __restrict__ hdr,
-                                                                  BatchSync* sync) {
+// THREADS: CTA size (a ray task is THREADS points of a map); APAIRS: voxel
+// pairs per lane of a register-apply task (8: a warp per brick, 2: a quarter).
+template <bool MERGE, int KPT, bool SORT, int THREADS, int APAIRS>
+__global__ void __launch_bounds__(THREADS, 768 / THREADS) batch_kernel(const BatchItem* __restrict__ items,
+                                                                         const BatchHeader* __restrict__ hdr,
+                                                                         BatchSync* sync) {
+    constexpr int kBatchWarps = THREADS / 32;
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ uint32_t s_prefix[kBatchMax + 1];
-    __shared__ RaysSmem rsm;
+    __shared__ RaysSmemT<kBatchWarps> rsm;
     const int count = hdr->count;
     const unsigned arrivals = gridDim.x + hdr->extra_arrivals;
     const long long spin = hdr->spin_limit;
@@ -175,10 +176,11 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem
     const unsigned gwarp = blockIdx.x * kBatchWarps + w;
     const unsigned nwarps = gridDim.x * kBatchWarps;
 
-    // ---- phase 1: ray set-up and compaction, one CTA task = 256 points of a map
+    // ---- phase 1: ray set-up and compaction, one CTA task = THREADS points of a map
     for (uint32_t t = blockIdx.x; t < hdr->ray_tasks; t += gridDim.x) {
         const int i = find_segment(hdr->ray_prefix, count, t);
-        rays_task<false, SORT>(items[i].a, items[i].m, (int)((t - hdr->ray_prefix[i]) * 256u), t, &rsm);
+        rays_task<false, SORT, false, kBatchWarps>(items[i].a, items[i].m, (int)((t - hdr->ray_prefix[i]) * THREADS),
+                                                   t, &rsm);
         __syncthreads();
     }
     if (!grid_barrier(sync, arrivals, spin)) return;
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem
 
     // ---- phase 4: Eq. 1 / Eq. 2 on the touched bricks, one warp task per brick
     // (register apply: per part of a brick, kTaskParts parts each)
-    constexpr unsigned kTaskParts = (!SORT && TSDF_BATCH_APPLY_REG) ? 8u / TSDF_BATCH_APPLY_PAIRS : 1u;
+    constexpr unsigned kTaskParts = (!SORT && TSDF_BATCH_APPLY_REG) ? 8u / APAIRS : 1u;
     block_prefix(count, [&](int i) { return __ldcg(&items[i].m.ctr->brick_count) * kTaskParts; }, s_prefix);
     {
         uint32_t* s_grid = reinterpret_cast<uint32_t*>(dyn + w * kApplySmemPerWarp);
@@ -295,8 +297,8 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem
             } else {
 #if TSDF_BATCH_APPLY_REG
                 if (it.reduce == 0)
-                    apply_part_reg<0, TSDF_BATCH_APPLY_PAIRS>(it.m, it.w_max, it.flags, local, touched, hits);
-                else apply_part_reg<1, TSDF_BATCH_APPLY_PAIRS>(it.m, it.w_max, it.flags, local, touched, hits);
+                    apply_part_reg<0, APAIRS>(it.m, it.w_max, it.flags, local, touched, hits);
+                else apply_part_reg<1, APAIRS>(it.m, it.w_max, it.flags, local, touched, hits);
 #else
                 if (it.reduce == 0) apply_brick<0>(it.m, it.w_max, it.flags, local, s_grid, s_acc, s_off, touched, hits);
                 else apply_brick<1>(it.m, it.w_max, it.flags, local, s_grid, s_acc, s_off, touched, hits);
@@ -314,26 +316,46 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchItem
     for (uint32_t i = gwarp; i < (uint32_t)count; i += nwarps) finish_warp(items[i].m);
 }
 
-constexpr size_t kDynSmem = kBatchWarps * kApplySmemPerWarp;
-
 using BatchKernel = void (*)(const BatchItem*, const BatchHeader*, BatchSync*);
 
+// Tuning configurations: reduction, warp merge and steps per item, then the
+// launch shape (CTA size, CTAs per SM -- 0: as many as fit -- and the apply
+// task size). Every one gives bit-identical results.
 struct Config {
     bool merge;
     int kpt;
     bool sort;
+    int threads;
+    int ctas_per_sm;
+    int apply_pairs;
 };
-const Config kConfigs[] = {{false, 4, false}, {false, 2, false}, {false, 1, false}, {true, 4, false},
-                           {true, 2, false},  {true, 1, false},  {false, 4, true},  {false, 2, true}};
-constexpr int kNumConfigs = 8;
+constexpr int kP = TSDF_BATCH_APPLY_PAIRS;
+const Config kConfigs[] = {
+    {false, 4, false, 256, 0, kP}, {false, 2, false, 256, 0, kP}, {false, 1, false, 256, 0, kP},
+    {true, 4, false, 256, 0, kP},  {true, 2, false, 256, 0, kP},  {true, 1, false, 256, 0, kP},
+    {false, 4, true, 256, 0, kP},  {false, 2, true, 256, 0, kP},
+    // launch shapes of the plain atomic configuration
+    {false, 4, false, 128, 0, kP}, {false, 4, false, 512, 0, kP}, {false, 4, false, 256, 2, kP},
+    {false, 4, false, 256, 0, 2}};
+constexpr int kNumConfigs = 12;
+
+size_t dyn_smem(const Config& c) { return (size_t)(c.threads / 32) * kApplySmemPerWarp; }
+
+template <int T, int AP>
+BatchKernel kernel_shape(const Config& c) {
+    if (c.sort) return c.kpt == 2 ? batch_kernel<false, 2, true, T, AP> : batch_kernel<false, 4, true, T, AP>;
+    if (c.merge)
+        return c.kpt == 1 ? batch_kernel<true, 1, false, T, AP>
+                          : c.kpt == 2 ? batch_kernel<true, 2, false, T, AP> : batch_kernel<true, 4, false, T, AP>;
+    return c.kpt == 1 ? batch_kernel<false, 1, false, T, AP>
+                      : c.kpt == 2 ? batch_kernel<false, 2, false, T, AP> : batch_kernel<false, 4, false, T, AP>;
+}
 
 BatchKernel kernel_for(const Config& c) {
-    if (c.sort) return c.kpt == 2 ? batch_kernel<false, 2, true> : batch_kernel<false, 4, true>;
-    if (c.merge)
-        return c.kpt == 1 ? batch_kernel<true, 1, false> : c.kpt == 2 ? batch_kernel<true, 2, false>
-                                                                       : batch_kernel<true, 4, false>;
-    return c.kpt == 1 ? batch_kernel<false, 1, false> : c.kpt == 2 ? batch_kernel<false, 2, false>
-                                                                    : batch_kernel<false, 4, false>;
+    if (c.threads == 128) return batch_kernel<false, 4, false, 128, kP>;
+    if (c.threads == 512) return batch_kernel<false, 4, false, 512, kP>;
+    if (c.apply_pairs == 2) return batch_kernel<false, 4, false, 256, 2>;
+    return kernel_shape<256, kP>(c);
 }
 
 }  // namespace
@@ -344,8 +366,8 @@ using namespace tsdf;
 struct tsdf_batch {
     int device = 0;
     int max_count = 0;
-    int grid = 0;                          // CTAs of the cooperative launch (co-resident)
-    int grid_max = 0;                      // all co-resident CTAs of the device
+    int grid_pct = 100;                    // percentage of each configuration's co-resident CTAs launched
+    int grid_max[kNumConfigs] = {};        // co-resident CTAs of each configuration (its launch shape)
     // two alternating descriptor sets
     struct Slot {
         unsigned char* host = nullptr;     // pinned: header + items
@@ -365,6 +387,7 @@ struct tsdf_batch {
     long long spin_limit = 1LL << 24;
     // autotuning state
     int trials_per_config = 2;
+    bool tune_sort = true;                 // the autotuner also times the sort configurations
     int tuned = -1;                        // chosen config, -1 while tuning
     struct Trial {
         int config;
@@ -409,6 +432,12 @@ void free_batch(tsdf_batch* b) {
     delete b;
 }
 
+// CTAs launched for configuration `cfg`: its co-resident CTAs (limited to
+// ctas_per_sm per SM when set), scaled by the grid-fraction option.
+int grid_of(const tsdf_batch* b, int cfg) {
+    return std::max(1, (int)((long long)b->grid_max[cfg] * b->grid_pct / 100));
+}
+
 // Enqueue copy + barrier reset + cooperative kernel for descriptor slot `si`.
 cudaError_t enqueue(tsdf_batch* b, int si, int cfg, cudaStream_t s) {
     tsdf_batch::Slot& sl = b->slot[si];
@@ -416,9 +445,10 @@ cudaError_t enqueue(tsdf_batch* b, int si, int cfg, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaMemsetAsync(b->sync, 0, sizeof(BatchSync), s);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3((unsigned)b->grid);
-    lc.blockDim = dim3(kBatchThreads);
-    lc.dynamicSmemBytes = kDynSmem;
+    const Config& c = kConfigs[cfg];
+    lc.gridDim = dim3((unsigned)grid_of(b, cfg));
+    lc.blockDim = dim3((unsigned)c.threads);
+    lc.dynamicSmemBytes = dyn_smem(c);
     lc.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -448,11 +478,12 @@ void harvest_trials(tsdf_batch* b) {
     }
     b->trials.swap(keep);
     bool all = true;
-    for (int c = 0; c < kNumConfigs; ++c) all = all && b->n_timed[c] >= b->trials_per_config;
+    for (int c = 0; c < kNumConfigs; ++c)
+        all = all && (b->n_timed[c] >= b->trials_per_config || (kConfigs[c].sort && !b->tune_sort));
     if (all && b->tuned < 0) {
         int best = 0;
         for (int c = 1; c < kNumConfigs; ++c)
-            if (b->best_ms[c] < b->best_ms[best]) best = c;
+            if (!(kConfigs[c].sort && !b->tune_sort) && b->best_ms[c] < b->best_ms[best]) best = c;
         b->tuned = best;
         b->config = best;
     }
@@ -468,20 +499,20 @@ int tsdf_batch_create(int32_t max_count, tsdf_batch** out) {
     tsdf_batch* b = new tsdf_batch();
     b->max_count = max_count;
     cudaError_t e = cudaGetDevice(&b->device);
-    int sms = 0, per_sm = 0;
+    int sms = 0;
     for (int c = 0; c < kNumConfigs && e == cudaSuccess; ++c)
         e = cudaFuncSetAttribute(kernel_for(kConfigs[c]),
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDynSmem);
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem(kConfigs[c]));
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-    // the grid must be co-resident for every config: take the smallest occupancy
-    int occ = 1 << 30;
+    // each configuration's grid must be co-resident (a cooperative launch)
     for (int c = 0; c < kNumConfigs && e == cudaSuccess; ++c) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(kConfigs[c]),
-                                                          kBatchThreads, kDynSmem);
-        occ = std::min(occ, per_sm);
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(kConfigs[c]), kConfigs[c].threads,
+                                                          dyn_smem(kConfigs[c]));
+        if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+        if (kConfigs[c].ctas_per_sm > 0) per_sm = std::min(per_sm, kConfigs[c].ctas_per_sm);
+        b->grid_max[c] = sms * std::max(per_sm, 1);
     }
-    if (e == cudaSuccess && occ < 1) e = cudaErrorInvalidConfiguration;
-    b->grid = b->grid_max = sms * (occ > 0 ? occ : 1);
     b->desc_bytes = sizeof(BatchHeader) + (size_t)max_count * sizeof(BatchItem);
     for (auto& s : b->slot) {
         if (e == cudaSuccess) e = cudaMallocHost(&s.host, b->desc_bytes);
@@ -534,8 +565,7 @@ int tsdf_batch_set_option(tsdf_batch* b, int32_t option, int64_t value) {
             // captured graphs are rebuilt for the new grid
             if (value < 1 || value > 100) return TSDF_ERR_INVALID;
             {
-                const int g = std::max(1, (int)((long long)b->grid_max * value / 100));
-                if (g != b->grid) {
+                if ((int)value != b->grid_pct) {
                     for (auto& sl : b->slot) {
                         if (sl.pending) {
                             cudaEventSynchronize(sl.done);
@@ -547,9 +577,13 @@ int tsdf_batch_set_option(tsdf_batch* b, int32_t option, int64_t value) {
                                 e = nullptr;
                             }
                     }
-                    b->grid = g;
+                    b->grid_pct = (int)value;
                 }
             }
+            return TSDF_OK;
+        case TSDF_BATCH_OPT_TUNE_SORT:
+            if (value != 0 && value != 1) return TSDF_ERR_INVALID;
+            b->tune_sort = value != 0;
             return TSDF_OK;
         case TSDF_BATCH_OPT_TEST_MISSING_ARRIVALS:
             if (value < 0 || value > 1024) return TSDF_ERR_INVALID;
@@ -560,9 +594,13 @@ int tsdf_batch_set_option(tsdf_batch* b, int32_t option, int64_t value) {
 }
 
 int tsdf_batch_get_config(const tsdf_batch* b, int32_t* config, int32_t* merge, int32_t* steps_per_item,
-                          int32_t* reduction, int32_t* tuned) {
+                          int32_t* reduction, int32_t* tuned, int32_t* threads_per_cta, int32_t* ctas,
+                          int32_t* apply_voxel_pairs) {
     if (!b) return TSDF_ERR_INVALID;
     if (config) *config = b->config;
+    if (threads_per_cta) *threads_per_cta = kConfigs[b->config].threads;
+    if (ctas) *ctas = grid_of(b, b->config);
+    if (apply_voxel_pairs) *apply_voxel_pairs = kConfigs[b->config].apply_pairs;
     if (reduction) *reduction = kConfigs[b->config].sort ? TSDF_REDUCTION_SORT : TSDF_REDUCTION_ATOMIC;
     if (merge) *merge = kConfigs[b->config].merge ? 1 : 0;
     if (steps_per_item) *steps_per_item = kConfigs[b->config].kpt;
@@ -596,6 +634,7 @@ int tsdf_batch_integrate(tsdf_batch* b, tsdf_map* const* maps, const float* cons
         int pending_of[kNumConfigs] = {};
         for (auto& t : b->trials) pending_of[t.config]++;
         for (int c = 0; c < kNumConfigs; ++c) {
+            if (kConfigs[c].sort && !b->tune_sort) continue;
             if (b->n_timed[c] + pending_of[c] < b->trials_per_config) {
                 cfg = c;
                 timing = true;
@@ -615,7 +654,7 @@ int tsdf_batch_integrate(tsdf_batch* b, tsdf_map* const* maps, const float* cons
         if (rc != TSDF_OK) return rc;
         hdr->ray_prefix[i] = rt;
         hdr->word_prefix[i] = wt;
-        rt += (uint32_t)((n[i] + 255) / 256);
+        rt += (uint32_t)((n[i] + kConfigs[cfg].threads - 1) / kConfigs[cfg].threads);
         wt += ((items[i].bricks + 3u) / 4u + 31u) / 32u;
     }
     hdr->ray_prefix[count] = rt;

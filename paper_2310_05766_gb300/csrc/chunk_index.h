@@ -13,13 +13,13 @@ struct ChunkKey {
     bool operator==(const ChunkKey& o) const { return x == o.x && y == o.y && z == o.z; }
 };
 
-// Index of the global store: chunk key -> store slot, in two levels. Chunks
+// Index of the global store: chunk key -> store location, in two levels. Chunks
 // are grouped into 8 x 8 x 8 super-chunks; an open-addressing hash table
 // (linear probing, grown by doubling at half load) maps a super-chunk key to
 // a block of 512 slots. A shift enumerates runs of neighbouring chunks,
 // looking up each leaving and each entering one, so the last two blocks found
-// are kept and most lookups are one array access instead of a cache miss in a
-// large table.
+// (and the last super-chunk found absent) are kept and most lookups are one
+// array access instead of a cache miss in a large table.
 class ChunkIndex {
 public:
     // slot of `k`, or -1
@@ -34,6 +34,15 @@ public:
         uint32_t& e = b[local(k)];
         if (e == kNone) ++count_;
         e = v;
+    }
+    void erase(const ChunkKey& k) {
+        uint32_t* b = block(super(k), false);
+        if (!b) return;
+        uint32_t& e = b[local(k)];
+        if (e != kNone) {
+            e = kNone;
+            --count_;
+        }
     }
     size_t size() const { return count_; }
     template <typename F>
@@ -57,6 +66,7 @@ private:
     uint32_t* block(const ChunkKey& s, bool create) {
         for (int c = 0; c < 2; ++c)
             if (last_[c] >= 0 && last_key_[c] == s) return &slots_[(size_t)last_[c] * 512];
+        if (!create && miss_valid_ && miss_key_ == s) return nullptr;   // absent, as found last time
         long long bi = -1;
         if (!keys_.empty()) {
             for (size_t i = hash(s) & mask_;; i = (i + 1) & mask_) {
@@ -68,7 +78,12 @@ private:
             }
         }
         if (bi < 0) {
-            if (!create) return nullptr;
+            if (!create) {
+                miss_key_ = s;
+                miss_valid_ = true;
+                return nullptr;
+            }
+            if (miss_valid_ && miss_key_ == s) miss_valid_ = false;
             bi = (long long)(slots_.size() / 512);
             slots_.resize(slots_.size() + 512, kNone);
             if (2 * (nblocks_ + 1) > keys_.size()) grow();
@@ -116,6 +131,8 @@ private:
     size_t mask_ = 0, count_ = 0, nblocks_ = 0;
     long long last_[2] = {-1, -1};        // the last two blocks found, and their keys
     ChunkKey last_key_[2] = {};
+    ChunkKey miss_key_ = {};              // the last super-chunk looked up and found absent
+    bool miss_valid_ = false;
 };
 
 }  // namespace tsdf

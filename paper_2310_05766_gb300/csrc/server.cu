@@ -72,10 +72,20 @@ struct Slot {
     bool launching = false;             // being filled by the worker outside the lock
 };
 
-size_t session_bytes(const tsdf_params& p, int64_t max_points) {
+// Device-tier slots of a session's global store (rounded up to the 8 MiB
+// segments the store allocates).
+size_t session_store_chunks(const tsdf_params& p, int32_t store_chunks) {
+    const size_t bricks = (size_t)p.dims[0] * p.dims[1] * p.dims[2] / 512;
+    size_t c = store_chunks > 0 ? (size_t)store_chunks : bricks / 8;
+    if (c < 1) c = 1;
+    return (c + 4095) / 4096 * 4096;
+}
+
+size_t session_bytes(const tsdf_params& p, int64_t max_points, int32_t store_chunks) {
     const size_t voxels = (size_t)p.dims[0] * p.dims[1] * p.dims[2];
     const size_t bricks = voxels / 512;
-    return voxels * (4 + 8) + bricks * (1 + 4) + (size_t)max_points * 32 + 8192;
+    return voxels * (4 + 8) + bricks * (1 + 4) + (size_t)max_points * 32 + 8192 +
+           session_store_chunks(p, store_chunks) * 2048;
 }
 
 }  // namespace
@@ -254,7 +264,7 @@ int tsdf_server_create(const tsdf_server_config* cfg, tsdf_server** out) {
     *out = nullptr;
     if (cfg->max_batch < 1 || cfg->max_batch > 1024 || cfg->streams < 1 || cfg->streams > 8 || cfg->max_points < 1 ||
         cfg->max_points > TSDF_MAX_POINTS || cfg->max_outstanding < 1 || cfg->max_outstanding > 65536 ||
-        cfg->hbm_budget_bytes < 0)
+        cfg->hbm_budget_bytes < 0 || cfg->store_chunks < 0 || cfg->store_chunks > (1 << 30))
         return TSDF_ERR_INVALID;
     tsdf_server* s = new tsdf_server();
     s->cfg = *cfg;
@@ -274,6 +284,9 @@ int tsdf_server_create(const tsdf_server_config* cfg, tsdf_server** out) {
         // each slot's launch uses its share of the GPU so that batches on
         // different slots can be resident together
         tsdf_batch_set_option(sl.batch, TSDF_BATCH_OPT_GRID_FRACTION, 100 / cfg->streams);
+        // the sort configurations allocate each map's sort buffers: served
+        // batches allocate no device memory
+        tsdf_batch_set_option(sl.batch, TSDF_BATCH_OPT_TUNE_SORT, 0);
     }
     for (int i = 0; i < cfg->max_outstanding && e == cudaSuccess; ++i) {
         float4* p = nullptr;
@@ -306,7 +319,7 @@ int tsdf_server_destroy(tsdf_server* s) {
 
 int tsdf_server_open_session(tsdf_server* s, const tsdf_params* params, int32_t* session) {
     if (!s || !params || !session) return TSDF_ERR_INVALID;
-    const size_t bytes = session_bytes(*params, s->cfg.max_points);
+    const size_t bytes = session_bytes(*params, s->cfg.max_points, s->cfg.store_chunks);
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if ((long long)(s->used_bytes + bytes) > s->cfg.hbm_budget_bytes) return TSDF_ERR_ADMISSION;
@@ -326,6 +339,9 @@ int tsdf_server_open_session(tsdf_server* s, const tsdf_params* params, int32_t*
     // reallocates them (which would synchronise the device) while batches run
     if (rc == TSDF_OK) {
         rc = map_reserve_points(m, s->cfg.max_points);
+        // the store's device tier too: served shifts allocate no device memory
+        if (rc == TSDF_OK)
+            rc = tsdf_map_reserve_store(m, (int64_t)session_store_chunks(*params, s->cfg.store_chunks));
         if (rc != TSDF_OK) {
             tsdf_map_destroy(m);
             m = nullptr;

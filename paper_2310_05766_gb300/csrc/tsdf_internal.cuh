@@ -196,7 +196,9 @@ cudaError_t launch_sort_scan(const MapDev& m, bool pdl, cudaStream_t s);
 cudaError_t launch_sort_scatter(const MapDev& m, bool pdl, cudaStream_t s);
 cudaError_t launch_sort_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t flags, bool pdl,
                               cudaStream_t s);
-cudaError_t launch_shift(uint32_t* grid, const ShiftItem* items, int count, cudaStream_t s);
+// flags (may be null): per item, 1 if the leaving brick held a non-zero voxel
+// and was written to its out_ptr, else 0 (and out_ptr was left untouched).
+cudaError_t launch_shift(uint32_t* grid, const ShiftItem* items, int count, uint8_t* flags, cudaStream_t s);
 cudaError_t launch_copy_chunks(const ChunkCopy* items, int count, cudaStream_t s);
 cudaError_t launch_register(const float* pts_dev, int n, const float pose[12], const uint32_t* grid,
                             const WindowGeom& geo, const long long origin[3], float vs, float inv_vs, float tau,

@@ -19,3 +19,17 @@ def test_chunk_index_matches_std_map(tmp_path):
                    check=True)
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
+
+
+def test_chunk_store_slots_across_tiers(tmp_path):
+    """The store's slot bookkeeping (csrc/chunk_store.h) over 4000 random shifts
+    with a small device tier: stored exactly the chunks that hold data, read
+    back as themselves, no shared slots, oldest device chunks moved first."""
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    exe = str(tmp_path / "chunk_store_check")
+    subprocess.run([cxx, "-std=c++17", "-O2", "-I", CSRC, os.path.join(HERE, "chunk_store_check.cpp"), "-o", exe],
+                   check=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr

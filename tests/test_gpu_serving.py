@@ -115,8 +115,10 @@ def test_mixed_equals_alone(pinned):
 def test_admission_by_budget_and_back_pressure():
     from paper_2310_05766_gb300 import binding as b
     p = synth.params_dict((256, 256, 128), 0.064, 0.3, 64, 0.006, 0.5, 50.0, 0, (-128, -128, -64))
-    # one session: 2^23 voxels * 12 B = 96 MiB + ray buffers; a 300 MiB budget admits 3
-    srv = b.tsdf_server_create(hbm_budget_bytes=300 * MiB, max_points=1 << 12, max_batch=4, streams=2,
+    # one session: 2^23 voxels * 12 B = 96 MiB + ray buffers + the store's device
+    # tier (an eighth of 16384 bricks, rounded up to one 8 MiB segment): 104.2 MiB;
+    # a 330 MiB budget admits 3
+    srv = b.tsdf_server_create(hbm_budget_bytes=330 * MiB, max_points=1 << 12, max_batch=4, streams=2,
                                max_outstanding=2)
     try:
         sids = [b.tsdf_server_open_session(srv, p) for _ in range(3)]
