@@ -94,11 +94,18 @@ struct tsdf_map {
     uint64_t shift_serial = 0;           // shifts done so far
     uint64_t chunks_spilled = 0;         // chunks moved from the device tier to the host tier
     uint64_t chunks_dropped = 0;         // leaving chunks found empty (not stored)
-    uint8_t* flags_dev = nullptr;        // per shift item: the leaving brick held data (written by the shift kernel)
-    uint8_t* flags_host = nullptr;       // pinned copy of the last shift's flags
+    // per shift item: the candidate slot's address (pinned + device), the
+    // candidate the kernel claimed for the leaving brick or -1 (device +
+    // pinned copy), and the claim counter (device)
+    unsigned long long* addr_host = nullptr;
+    unsigned long long* addr_dev = nullptr;
+    int* claim_dev = nullptr;
+    int* claim_host = nullptr;
+    unsigned* claimed_dev = nullptr;
     size_t flags_cap = 0;
-    size_t flags_count = 0;              // candidates of the last shift, awaiting their flags
-    cudaEvent_t flags_event = nullptr;
+    cudaEvent_t flags_event = nullptr;   // the last shift's claims have reached claim_host
+    std::vector<ChunkKey> leave_keys;    // the shift's leaving chunks, in item order
+    std::vector<uint32_t> cand_locs;     // their candidate slots
     ChunkCopy* spill_dev = nullptr;      // copies device slot -> host slot of one shift
     ChunkCopy* spill_host = nullptr;
     size_t spill_cap = 0;
@@ -251,8 +258,11 @@ void free_map(tsdf_map* m) {
     cudaFree(m->dev.sorted);
     for (char* a : m->store_allocs[0]) cudaFree(a);
     for (char* a : m->store_allocs[1]) cudaFreeHost(a);
-    cudaFree(m->flags_dev);
-    if (m->flags_host) cudaFreeHost(m->flags_host);
+    if (m->addr_host) cudaFreeHost(m->addr_host);
+    cudaFree(m->addr_dev);
+    cudaFree(m->claim_dev);
+    if (m->claim_host) cudaFreeHost(m->claim_host);
+    cudaFree(m->claimed_dev);
     if (m->flags_event) cudaEventDestroy(m->flags_event);
     cudaFree(m->spill_dev);
     if (m->spill_host) cudaFreeHost(m->spill_host);
@@ -318,16 +328,13 @@ bool store_grow(tsdf_map* m, int tier, size_t segs) {
 }
 
 
-// Takes the previous shift's flags (waiting for them if needed): candidates
-// whose brick held no data are dropped and their slots freed.
+// Takes the previous shift's claims (waiting for them if needed): the leaving
+// chunks that held data are recorded, the other candidate slots freed.
 int store_resolve(tsdf_map* m) {
     if (!m->store.pending()) return TSDF_OK;
     TSDF_CU(cudaEventSynchronize(m->flags_event));
-    size_t empty = 0;
-    for (size_t i = 0; i < m->flags_count; ++i) empty += m->flags_host[i] ? 0 : 1;
-    m->chunks_dropped += empty;
-    m->store.resolve(m->flags_host);
-    m->flags_count = 0;
+    const size_t n = m->leave_keys.size();
+    m->chunks_dropped += n - m->store.commit(m->claim_host);
     return TSDF_OK;
 }
 
@@ -347,20 +354,29 @@ int ensure_shift_buffers(tsdf_map* m, size_t cnt) {
         m->items_host_cap = cnt;
     }
     if (cnt > m->items_dev_cap || cnt > m->flags_cap) {
-        int rc = store_resolve(m);   // the flags still to be read live in these buffers
+        int rc = store_resolve(m);   // the claims still to be read live in these buffers
         if (rc != TSDF_OK) return rc;
         cudaFree(m->items_dev);   // waits for the device
-        cudaFree(m->flags_dev);
-        if (m->flags_host) cudaFreeHost(m->flags_host);
+        cudaFree(m->addr_dev);
+        cudaFree(m->claim_dev);
+        cudaFree(m->claimed_dev);
+        if (m->addr_host) cudaFreeHost(m->addr_host);
+        if (m->claim_host) cudaFreeHost(m->claim_host);
         m->items_dev = nullptr;
-        m->flags_dev = nullptr;
-        m->flags_host = nullptr;
+        m->addr_dev = nullptr;
+        m->claim_dev = nullptr;
+        m->claimed_dev = nullptr;
+        m->addr_host = nullptr;
+        m->claim_host = nullptr;
         m->items_dev_cap = 0;
         m->flags_cap = 0;
         TSDF_CU(cudaMalloc(&m->items_dev, cnt * sizeof(ShiftItem)));
         m->items_dev_cap = cnt;
-        TSDF_CU(cudaMalloc(&m->flags_dev, cnt));
-        TSDF_CU(cudaMallocHost(&m->flags_host, cnt));
+        TSDF_CU(cudaMalloc(&m->addr_dev, cnt * sizeof(unsigned long long)));
+        TSDF_CU(cudaMalloc(&m->claim_dev, cnt * sizeof(int)));
+        TSDF_CU(cudaMalloc(&m->claimed_dev, sizeof(unsigned)));
+        TSDF_CU(cudaMallocHost(&m->addr_host, cnt * sizeof(unsigned long long)));
+        TSDF_CU(cudaMallocHost(&m->claim_host, cnt * sizeof(int)));
         m->flags_cap = cnt;
     }
     // (the copy list exists once chunks can move: the device tier is at its
@@ -855,48 +871,49 @@ int tsdf_shift(tsdf_map* map, const int64_t new_origin[3], void* stream) {
         if (rc == TSDF_OK) rc = ensure_shift_buffers(map, cnt);
         if (rc == TSDF_OK) rc = store_make_room(map, cnt, s);
         if (rc != TSDF_OK) return rc;
-        // every leaving chunk gets a slot (device tier first); the kernel writes
-        // only those that hold data. Then the entering chunks are looked up and
-        // leave the store: their slots are freed after all leaving chunks have
-        // theirs, so no slot is both read and written by this shift.
+        // every leaving chunk gets a candidate slot (device tier first); the
+        // kernel claims candidates in order for the chunks that hold data, and
+        // the next shift records those. Then the entering chunks are looked up
+        // and leave the store: their slots are freed after the candidates are
+        // taken, so no slot is both read and written by this shift.
         const uint64_t stamp = ++map->shift_serial;
-        size_t k = 0;
-        auto add_out = [&](long long sx, long long sy, long long sz) -> int {
-            ShiftItem& it = map->items_host[k++];
+        map->leave_keys.clear();
+        auto add_out = [&](long long sx, long long sy, long long sz) {
+            ShiftItem& it = map->items_host[map->leave_keys.size()];
             it = ShiftItem{};
             it.brick = (uint32_t)((sz * C[1] + sy) * C[0] + sx);
-            const long long loc = map->store.place(ChunkKey{oldc[0][sx], oldc[1][sy], oldc[2][sz]}, stamp);
-            if (loc < 0) return TSDF_ERR_OOM;
-            it.out_ptr = store_addr(map, (uint32_t)loc);
-            return TSDF_OK;
+            map->leave_keys.push_back(ChunkKey{oldc[0][sx], oldc[1][sy], oldc[2][sz]});
         };
         for (long long sz = 0; sz < C[2]; ++sz) {
             for (long long sy = 0; sy < C[1]; ++sy) {
-                int r2 = TSDF_OK;
                 if (chg[2][sz] || chg[1][sy]) {
-                    for (long long sx = 0; sx < C[0] && r2 == TSDF_OK; ++sx) r2 = add_out(sx, sy, sz);
+                    for (long long sx = 0; sx < C[0]; ++sx) add_out(sx, sy, sz);
                 } else {
-                    for (size_t q = 0; q < chx.size() && r2 == TSDF_OK; ++q) r2 = add_out(chx[q], sy, sz);
+                    for (size_t q = 0; q < chx.size(); ++q) add_out(chx[q], sy, sz);
                 }
-                if (r2 != TSDF_OK) return r2;
             }
         }
+        if (!map->store.candidates(map->leave_keys, stamp, &map->cand_locs)) return TSDF_ERR_OOM;
         for (size_t i = 0; i < cnt; ++i) {
             ShiftItem& it = map->items_host[i];
+            map->addr_host[i] = store_addr(map, map->cand_locs[i]);
             const long long b = it.brick;
             const long long sx = b % C[0], sy = (b / C[0]) % C[1], sz = b / (C[0] * C[1]);
             const long long loc = map->store.take(ChunkKey{newc[0][sx], newc[1][sy], newc[2][sz]});
             it.in_ptr = loc >= 0 ? store_addr(map, (uint32_t)loc) : 0ull;
         }
         map->store.end_shift();
-        map->flags_count = cnt;
         TSDF_CU(cudaMemcpyAsync(map->items_dev, map->items_host, cnt * sizeof(ShiftItem), cudaMemcpyHostToDevice, s));
+        TSDF_CU(cudaMemcpyAsync(map->addr_dev, map->addr_host, cnt * sizeof(unsigned long long),
+                                cudaMemcpyHostToDevice, s));
+        TSDF_CU(cudaMemsetAsync(map->claimed_dev, 0, sizeof(unsigned), s));
         TSDF_CU(cudaEventRecord(map->items_event, s));
         map->items_event_pending = true;
         cudaEvent_t e0 = prof_mark(map, s);
-        TSDF_CU(launch_shift(map->dev.grid, map->items_dev, (int)cnt, map->flags_dev, s));
+        TSDF_CU(launch_shift(map->dev.grid, map->items_dev, (int)cnt, map->addr_dev, map->claimed_dev, map->claim_dev,
+                             s));
         prof_push(map, kShift, e0, prof_mark(map, s));
-        TSDF_CU(cudaMemcpyAsync(map->flags_host, map->flags_dev, cnt, cudaMemcpyDeviceToHost, s));
+        TSDF_CU(cudaMemcpyAsync(map->claim_host, map->claim_dev, cnt * sizeof(int), cudaMemcpyDeviceToHost, s));
         TSDF_CU(cudaEventRecord(map->flags_event, s));
     }
     for (int a = 0; a < 3; ++a) map->origin[a] = new_origin[a];
@@ -1399,7 +1416,8 @@ int tsdf_map_device_bytes(const tsdf_map* map, int64_t* out) {
         b += map->bricks * sizeof(uint32_t) +
              (size_t)map->dev.pool_cap * (sizeof(uint32_t) + kBrickVoxels * sizeof(unsigned long long));
     b += map->store_seg[0].size() * (size_t)kSegChunks * kChunkBytes;   // the host tier is host memory
-    b += map->stage_cap * sizeof(float4) + map->items_dev_cap * sizeof(ShiftItem) + map->flags_cap +
+    b += map->stage_cap * sizeof(float4) + map->items_dev_cap * sizeof(ShiftItem) +
+         map->flags_cap * (sizeof(unsigned long long) + sizeof(int)) + (map->claimed_dev ? sizeof(unsigned) : 0) +
          map->spill_cap * sizeof(ChunkCopy);
     *out = (int64_t)b;
     return TSDF_OK;

@@ -16,12 +16,15 @@ struct ChunkKey {
 // Index of the global store: chunk key -> store location, in two levels. Chunks
 // are grouped into 8 x 8 x 8 super-chunks; an open-addressing hash table
 // (linear probing, grown by doubling at half load) maps a super-chunk key to
-// a block of 512 slots. A shift enumerates runs of neighbouring chunks,
-// looking up each leaving and each entering one, so the last two blocks found
-// (and the last super-chunk found absent) are kept and most lookups are one
-// array access instead of a cache miss in a large table.
+// a block of 512 slots. A shift works on a few dozen neighbouring
+// super-chunks, so the blocks found recently are kept in a small direct-mapped
+// cache (and the last super-chunk found absent is remembered): most lookups
+// are one array access instead of a probe of the table.
 class ChunkIndex {
 public:
+    ChunkIndex() {
+        for (size_t i = 0; i < kCache; ++i) cache_blk_[i] = -1;
+    }
     // slot of `k`, or -1
     long long find(const ChunkKey& k) {
         const uint32_t* b = block(super(k), false);
@@ -64,8 +67,8 @@ private:
     static int local(const ChunkKey& k) { return (int)(((k.z & 7) << 6) | ((k.y & 7) << 3) | (k.x & 7)); }
     // the 512 slots of super-chunk `s`, created (all empty) when `create`, else null if absent
     uint32_t* block(const ChunkKey& s, bool create) {
-        for (int c = 0; c < 2; ++c)
-            if (last_[c] >= 0 && last_key_[c] == s) return &slots_[(size_t)last_[c] * 512];
+        const size_t ci = cache_slot(s);
+        if (cache_blk_[ci] >= 0 && cache_key_[ci] == s) return &slots_[(size_t)cache_blk_[ci] * 512];
         if (!create && miss_valid_ && miss_key_ == s) return nullptr;   // absent, as found last time
         long long bi = -1;
         if (!keys_.empty()) {
@@ -90,11 +93,14 @@ private:
             put(s, (uint32_t)bi);
             ++nblocks_;
         }
-        last_[1] = last_[0];
-        last_key_[1] = last_key_[0];
-        last_[0] = bi;
-        last_key_[0] = s;
+        cache_blk_[ci] = bi;
+        cache_key_[ci] = s;
         return &slots_[(size_t)bi * 512];
+    }
+    // direct-mapped cache of found blocks, indexed by a cheap mix of the key
+    static size_t cache_slot(const ChunkKey& k) {
+        return (size_t)(((unsigned long long)k.x * 0x9E3779B1ull + (unsigned long long)k.y * 0x85EBCA77ull +
+                         (unsigned long long)k.z * 0xC2B2AE3Dull) >> 7) & (kCache - 1);
     }
     static size_t hash(const ChunkKey& k) {
         unsigned long long h = (unsigned long long)k.x * 0x9E3779B97F4A7C15ull;
@@ -129,8 +135,9 @@ private:
     std::vector<unsigned char> used_;
     std::vector<uint32_t> slots_;         // 512 slots per block
     size_t mask_ = 0, count_ = 0, nblocks_ = 0;
-    long long last_[2] = {-1, -1};        // the last two blocks found, and their keys
-    ChunkKey last_key_[2] = {};
+    static constexpr size_t kCache = 256;
+    long long cache_blk_[kCache] = {};    // blocks found recently (-1: none), and their keys
+    ChunkKey cache_key_[kCache] = {};
     ChunkKey miss_key_ = {};              // the last super-chunk looked up and found absent
     bool miss_valid_ = false;
 };

@@ -7,14 +7,16 @@
 // holds which chunk; the owner allocates the memory behind the slots (it adds
 // slots with add_slots), copies chunks between tiers and runs the shift.
 //
-// A shift hands every leaving chunk a slot before the shift kernel runs
-// (place), but the kernel writes only the chunks that hold data; it reports
-// per candidate whether it did, and the next call of resolve() drops the
-// empty ones and frees their slots. Entering chunks are looked up and removed
-// (take); their slots are freed by end_shift(), after the leaving chunks of the
-// same shift have their slots, so that no slot is read and written by one
-// kernel. Device-tier chunks are queued in the order they were stored, so that
-// the oldest can be moved to the host tier first (oldest_device).
+// A shift hands its kernel one candidate slot per leaving chunk (candidates:
+// device-tier slots first), and the kernel claims candidates in order for the
+// leaving chunks that hold data: the claimed ones form a prefix of the list.
+// The next call of commit() records the claimed chunks and frees the unclaimed
+// candidates, so chunks without data never enter the index. Entering chunks
+// are looked up and removed (take); their slots are freed by end_shift(),
+// after the candidates of the same shift are out of the free lists, so that no
+// slot is read and written by one kernel. Device-tier chunks are queued in the
+// order they were stored, so that the oldest can be moved to the host tier
+// first (oldest_device, spill_oldest).
 #pragma once
 
 #include <cstddef>
@@ -39,28 +41,57 @@ public:
     }
     size_t capacity(int tier) const { return cap_[tier]; }
     size_t free_count(int tier) const { return free_[tier].size(); }
+    // slots not free: stored chunks plus the candidates of a shift not yet committed
     size_t used(int tier) const { return cap_[tier] - free_[tier].size(); }
-    // chunks known to the index (stored ones, plus candidates of the last
-    // shift not yet resolved)
     size_t chunks() const { return index_.size(); }
-    bool pending() const { return !pend_.empty(); }
+    bool pending() const { return !cand_.empty(); }
 
     // location of a stored chunk, or -1
     long long find(const ChunkKey& k) { return index_.find(k); }
 
-    // The previous shift's candidates, in the order place() handed them out:
-    // flags[i] != 0 when candidate i was written (it held data); the others
-    // are dropped and their slots freed.
-    void resolve(const uint8_t* flags) {
-        for (size_t i = 0; i < pend_.size(); ++i) {
-            if (flags[i]) continue;
-            const Pending& p = pend_[i];
-            if (index_.find(p.key) == (long long)p.loc) {
-                index_.erase(p.key);
-                release(p.loc);
+    // Candidate slots for a shift whose leaving chunks are `keys` (in the
+    // kernel's item order): `locs` receives one location per key, device tier
+    // first; false when the tiers have fewer free slots (nothing is taken).
+    bool candidates(const std::vector<ChunkKey>& keys, uint64_t stamp, std::vector<uint32_t>* locs) {
+        const size_t n = keys.size();
+        if (free_[0].size() + free_[1].size() < n) return false;
+        locs->resize(n);
+        for (size_t i = 0; i < n; ++i) {
+            if (!free_[0].empty()) {
+                (*locs)[i] = free_[0].back();
+                free_[0].pop_back();
+            } else {
+                (*locs)[i] = free_[1].back() | kHostBit;
+                free_[1].pop_back();
             }
         }
-        pend_.clear();
+        cand_ = *locs;
+        keys_ = keys;
+        stamp_ = stamp;
+        return true;
+    }
+
+    // The last shift's outcome: claim[i] is the candidate index the kernel
+    // claimed for leaving chunk i, or -1 when the chunk held no data. Claimed
+    // chunks are recorded (device-tier ones queued by age), unclaimed
+    // candidates freed. Returns the number of chunks stored.
+    size_t commit(const int32_t* claim) {
+        size_t stored = 0;
+        for (size_t i = 0; i < keys_.size(); ++i) {
+            const int32_t c = claim[i];
+            if (c < 0 || (size_t)c >= cand_.size()) continue;
+            const uint32_t loc = cand_[(size_t)c];
+            index_.insert(keys_[i], loc);
+            if (!is_host(loc)) fifo_.push_back(Entry{keys_[i], loc, stamp_});
+            cand_[(size_t)c] = kClaimed;
+            ++stored;
+        }
+        for (uint32_t loc : cand_)
+            if (loc != kClaimed) release(loc);
+        cand_.clear();
+        keys_.clear();
+        if (fifo_.size() > 64 && fifo_.size() > 2 * index_.size()) compact_fifo();
+        return stored;
     }
 
     // An entering chunk: its location (or -1 when it is not stored), removed
@@ -74,31 +105,10 @@ public:
         return loc;
     }
 
-    // A leaving chunk: a slot for it, from the device tier while it has free
-    // slots, else from the host tier; -1 when neither has one (the owner adds
-    // slots first). Recorded as a candidate of this shift.
-    long long place(const ChunkKey& k, uint64_t stamp) {
-        uint32_t loc;
-        if (!free_[0].empty()) {
-            loc = free_[0].back();
-            free_[0].pop_back();
-            fifo_.push_back(Entry{k, loc, stamp});
-        } else if (!free_[1].empty()) {
-            loc = free_[1].back() | kHostBit;
-            free_[1].pop_back();
-        } else {
-            return -1;
-        }
-        index_.insert(k, loc);
-        pend_.push_back(Pending{k, loc});
-        return (long long)loc;
-    }
-
-    // After a shift's place() calls: the entering chunks' slots become free.
+    // After a shift's candidates are out: the entering chunks' slots become free.
     void end_shift() {
         for (uint32_t loc : taken_) release(loc);
         taken_.clear();
-        if (fifo_.size() > 64 && fifo_.size() > 2 * index_.size()) compact_fifo();
     }
 
     // The device-tier chunk stored longest ago (and when), without removing it;
@@ -112,7 +122,7 @@ public:
                 *stamp = e.stamp;
                 return true;
             }
-            fifo_.pop_front();   // the chunk re-entered, was dropped, or moved
+            fifo_.pop_front();   // the chunk re-entered or moved
         }
         return false;
     }
@@ -136,27 +146,34 @@ public:
         return true;
     }
 
-    // Every stored chunk (call after resolve(): unresolved candidates are listed too).
+    // Every stored chunk (after commit(): a shift's candidates are not listed).
     template <typename F>
     void for_each(F&& f) const { index_.for_each(f); }
 
-    // A chunk written directly (loading a saved map): a slot as place()
-    // gives, not a candidate (it is known to hold data).
+    // A chunk written directly (loading a saved map): a free slot, device tier
+    // first, recorded as stored; -1 when both tiers are full.
     long long insert_stored(const ChunkKey& k, uint64_t stamp) {
-        const long long loc = place(k, stamp);
-        if (loc >= 0) pend_.pop_back();
-        return loc;
+        uint32_t loc;
+        if (!free_[0].empty()) {
+            loc = free_[0].back();
+            free_[0].pop_back();
+            fifo_.push_back(Entry{k, loc, stamp});
+        } else if (!free_[1].empty()) {
+            loc = free_[1].back() | kHostBit;
+            free_[1].pop_back();
+        } else {
+            return -1;
+        }
+        index_.insert(k, loc);
+        return (long long)loc;
     }
 
 private:
+    static constexpr uint32_t kClaimed = 0xFFFFFFFFu;
     struct Entry {
         ChunkKey key;
         uint32_t loc;
         uint64_t stamp;
-    };
-    struct Pending {
-        ChunkKey key;
-        uint32_t loc;
     };
     void release(uint32_t loc) {
         if (is_host(loc)) free_[1].push_back(slot_of(loc));
@@ -171,9 +188,11 @@ private:
     ChunkIndex index_;
     std::vector<uint32_t> free_[2];
     size_t cap_[2] = {0, 0};
-    std::vector<Pending> pend_;
+    std::vector<uint32_t> cand_;     // the last shift's candidate slots (kClaimed once recorded)
+    std::vector<ChunkKey> keys_;     // the last shift's leaving chunks, in item order
+    uint64_t stamp_ = 0;
     std::vector<uint32_t> taken_;
-    std::deque<Entry> fifo_;   // device-tier chunks in the order they were stored (stale entries skipped)
+    std::deque<Entry> fifo_;         // device-tier chunks in the order they were stored (stale entries skipped)
 };
 
 }  // namespace tsdf

@@ -132,7 +132,7 @@ inline void fill_lean_args(ScanArgs& a) {
 struct ShiftItem {
     uint32_t brick;                 // ring brick index
     uint32_t pad0;
-    unsigned long long out_ptr;     // store address for the leaving brick (2048 B), 0 = discard
+    unsigned long long out_ptr;     // unused (leaving bricks go to the shift's claimed candidate slots)
     unsigned long long in_ptr;      // store address of the entering brick, 0 = zero fill
     unsigned long long pad1;
 };
@@ -196,9 +196,11 @@ cudaError_t launch_sort_scan(const MapDev& m, bool pdl, cudaStream_t s);
 cudaError_t launch_sort_scatter(const MapDev& m, bool pdl, cudaStream_t s);
 cudaError_t launch_sort_apply(const MapDev& m, int32_t reduce, int32_t w_max, int32_t flags, bool pdl,
                               cudaStream_t s);
-// flags (may be null): per item, 1 if the leaving brick held a non-zero voxel
-// and was written to its out_ptr, else 0 (and out_ptr was left untouched).
-cudaError_t launch_shift(uint32_t* grid, const ShiftItem* items, int count, uint8_t* flags, cudaStream_t s);
+// The leaving brick of each item that holds a non-zero voxel claims the next
+// candidate slot (*claimed counts them, from 0) and is copied to
+// slot_addr[claim]; claim[item] is that index or -1 (the brick held no data).
+cudaError_t launch_shift(uint32_t* grid, const ShiftItem* items, int count, const unsigned long long* slot_addr,
+                         unsigned* claimed, int* claim, cudaStream_t s);
 cudaError_t launch_copy_chunks(const ChunkCopy* items, int count, cudaStream_t s);
 cudaError_t launch_register(const float* pts_dev, int n, const float pose[12], const uint32_t* grid,
                             const WindowGeom& geo, const long long origin[3], float vs, float inv_vs, float tau,

@@ -16,12 +16,15 @@ namespace {
 // One warp per brick (4 per CTA): each lane moves 4 x 16 bytes of the
 // 2048-byte brick, issuing all of its loads (the leaving brick and the
 // entering one) before any store, so that each lane has 128 bytes in flight.
-// The leaving brick is written to its store slot only if some voxel of it is
-// non-zero, and flags[item] says whether it was (the host then keeps or drops
-// the slot). The store keeps a brick in the same [z][y][x] order; a slot may
-// lie in pinned host memory, which the kernel reads and writes in place.
+// A leaving brick with some non-zero voxel claims the next of the shift's
+// candidate store slots (one atomic per such brick) and is written there;
+// claim[item] receives the candidate's index, or -1 for a brick that held no
+// data (not written). The store keeps a brick in the same [z][y][x] order; a
+// slot may lie in pinned host memory, which the kernel reads and writes in
+// place.
 __global__ void __launch_bounds__(128) shift_kernel(uint32_t* __restrict__ grid, const ShiftItem* __restrict__ items,
-                                                     int count, uint8_t* __restrict__ flags) {
+                                                     int count, const unsigned long long* __restrict__ slot_addr,
+                                                     unsigned* __restrict__ claimed, int* __restrict__ claim) {
     const int lane = threadIdx.x & 31;
     for (int it = blockIdx.x * 4 + (threadIdx.x >> 5); it < count; it += gridDim.x * 4) {
         const ShiftItem s = items[it];
@@ -36,11 +39,15 @@ __global__ void __launch_bounds__(128) shift_kernel(uint32_t* __restrict__ grid,
 #pragma unroll
         for (int v = 0; v < 4; ++v) any |= old[v].x | old[v].y | old[v].z | old[v].w;
         const bool keep = __any_sync(0xFFFFFFFFu, any != 0u);
-        if (s.out_ptr && keep) {
+        int c = -1;
+        if (keep && claimed) {
+            if (lane == 0) c = (int)atomicAdd(claimed, 1u);
+            c = __shfl_sync(0xFFFFFFFFu, c, 0);
+            uint4* dst = reinterpret_cast<uint4*>(slot_addr[c]);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) reinterpret_cast<uint4*>(s.out_ptr)[32 * v + lane] = old[v];
+            for (int v = 0; v < 4; ++v) dst[32 * v + lane] = old[v];
         }
-        if (flags && lane == 0) flags[it] = keep ? 1 : 0;
+        if (claim && lane == 0) claim[it] = c;
 #pragma unroll
         for (int v = 0; v < 4; ++v) gp[32 * v + lane] = nv[v];
     }
@@ -99,11 +106,12 @@ cudaError_t launch_copy_chunks(const ChunkCopy* items, int count, cudaStream_t s
     return cudaGetLastError();
 }
 
-cudaError_t launch_shift(uint32_t* grid, const ShiftItem* items, int count, uint8_t* flags, cudaStream_t s) {
+cudaError_t launch_shift(uint32_t* grid, const ShiftItem* items, int count, const unsigned long long* slot_addr,
+                         unsigned* claimed, int* claim, cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     const int need = (count + 3) / 4;
     const int blocks = need < 65536 ? need : 65536;
-    shift_kernel<<<blocks, 128, 0, s>>>(grid, items, count, flags);
+    shift_kernel<<<blocks, 128, 0, s>>>(grid, items, count, slot_addr, claimed, claim);
     return cudaGetLastError();
 }
 

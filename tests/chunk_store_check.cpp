@@ -1,12 +1,14 @@
 // Host check of the global store's slot bookkeeping (csrc/chunk_store.h): a
 // window of chunks walks back and forth over a line of chunk keys, some of
 // which hold data. A fake two-tier memory records which chunk each slot
-// holds, standing in for the shift kernel (which writes a leaving chunk only
-// when it holds data) and the tier-to-tier copies. Checked after every shift:
+// holds, standing in for the shift kernel (which claims candidate slots, in a
+// random order, only for leaving chunks that hold data) and the tier-to-tier
+// copies. Checked after every shift:
 // every chunk that holds data and is outside the window is stored exactly
 // once, reads back as itself when it re-enters, no two chunks share a slot,
 // empty chunks are not kept, device-tier use never exceeds its capacity, and
 // the device chunks moved out are the ones stored longest ago. Prints "ok".
+#include <algorithm>
 #include <cstdio>
 #include <map>
 #include <random>
@@ -35,7 +37,7 @@ int main() {
     auto at = [&](uint32_t loc) -> long long& {
         return mem[ChunkStore::is_host(loc) ? 1 : 0][ChunkStore::slot_of(loc)];
     };
-    std::vector<uint8_t> flags;
+    std::vector<int32_t> claim;
     std::set<long long> seen;                    // chunks that have been inside the window
     for (long long x = 0; x < W; ++x) seen.insert(x);
     long long o = 0;
@@ -44,13 +46,13 @@ int main() {
     for (int step = 0; step < 4000; ++step) {
         const long long d = (long long)(rng() % 9) - 4;   // shift by -4 .. +4 chunks
         const long long no = o + d;
-        st.resolve(flags.data());
-        // room: move the oldest device chunks out until the shift fits
+        if (!claim.empty() || step > 0) st.commit(claim.data());
         std::vector<long long> leave, enter;
         for (long long x = o; x < o + W; ++x)
             if (x < no || x >= no + W) leave.push_back(x);
         for (long long x = no; x < no + W; ++x)
             if (x < o || x >= o + W) enter.push_back(x);
+        // room: move the oldest device chunks out until the shift fits
         uint64_t last_stamp = 0;
         while (st.free_count(0) < leave.size()) {
             ChunkKey k;
@@ -66,13 +68,10 @@ int main() {
             ++spilled;
         }
         ++serial;
-        flags.clear();
-        std::vector<std::pair<long long, long long>> out;   // (chunk, loc)
-        for (long long x : leave) {
-            const long long loc = st.place(ChunkKey{x, 0, 0}, serial);
-            if (loc < 0) { std::printf("no slot\n"); return 1; }
-            out.push_back({x, loc});
-        }
+        std::vector<ChunkKey> keys;
+        for (long long x : leave) keys.push_back(ChunkKey{x, 0, 0});
+        std::vector<uint32_t> locs;
+        if (!st.candidates(keys, serial, &locs) || locs.size() != keys.size()) { std::printf("no slots\n"); return 1; }
         for (long long x : enter) {
             const long long loc = st.take(ChunkKey{x, 0, 0});
             const bool stored = loc >= 0;
@@ -80,28 +79,33 @@ int main() {
                 std::printf("chunk %lld: stored %d, holds data %d\n", x, (int)stored, (int)has(x));
                 return 1;
             }
-            seen.insert(x);
             if (stored && at((uint32_t)loc) != x) {
                 std::printf("chunk %lld read back %lld\n", x, at((uint32_t)loc));
                 return 1;
             }
+            seen.insert(x);
         }
         st.end_shift();
-        // the kernel: leaving chunks with data are written, their flags set
-        for (auto& e : out) {
-            flags.push_back(has(e.first) ? 1 : 0);
-            if (has(e.first)) at((uint32_t)e.second) = e.first;
+        // the kernel: the leaving chunks with data claim candidates in some order
+        std::vector<size_t> order;
+        for (size_t i = 0; i < leave.size(); ++i)
+            if (has(leave[i])) order.push_back(i);
+        std::shuffle(order.begin(), order.end(), rng);
+        claim.assign(leave.size(), -1);
+        for (size_t c = 0; c < order.size(); ++c) {
+            claim[order[c]] = (int32_t)c;
+            at(locs[c]) = leave[order[c]];
         }
         o = no;
-        // invariants (with this shift's candidates resolved on a copy)
+        // invariants, with this shift committed on a copy
         ChunkStore copy = st;
-        copy.resolve(flags.data());
-        std::set<uint32_t> locs;
+        copy.commit(claim.data());
+        std::set<uint32_t> locset;
         size_t n = 0;
         bool ok = true;
         copy.for_each([&](const ChunkKey& k, uint32_t loc) {
             ++n;
-            if (!locs.insert(loc).second) ok = false;                      // shared slot
+            if (!locset.insert(loc).second) ok = false;                    // shared slot
             if (k.x >= o && k.x < o + W) ok = false;                       // inside the window
             if (!has(k.x)) ok = false;                                     // empty chunk kept
             if (at(loc) != k.x) ok = false;                                // wrong contents
