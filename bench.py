@@ -441,11 +441,62 @@ def run_room_bench(steps: int = 200):
                 hits_per_scan=hits, note="latency-bound (a few microseconds of work per scan); not judged by roofline")
 
 
+def run_drive_bench(n_pos: int = 1000):
+    """A 1 km drive of the outdoor window (512 x 512 x 128 at 0.064 m), a scan and
+    a shift every metre: the global store's device tier fills to its limit (the
+    window's brick count) and the oldest chunks move to pinned host memory.
+    Reports the shift's host time and device time (events on the stream) and
+    the map's device memory. Scans: the first 20 of the outdoor sequence, each
+    placed at the next metre (a synthetic drive, not a ray-cast of a 1 km scene)."""
+    import torch
+    from paper_2310_05766_gb300 import binding as b, synth
+    w = synth.workload_outdoor(n_scans=20)
+    pts = [torch.from_numpy(x).cuda() for x in w.scans]
+    dims, vs = w.params["dims"], w.params["voxel_size"]
+    stream = torch.cuda.current_stream()
+    m = b.TsdfMap(w.params)
+    host_us, dev_us, dev_bytes = [], [], []
+    try:
+        cur = tuple(w.params["origin"])
+        for k in range(n_pos):
+            j = k % len(pts)
+            pose = np.array(w.poses[j], np.float32).reshape(3, 4).copy()
+            pose[:, 3] = (float(k), 0.0, 0.0)
+            o = synth.window_origin(pose[:, 3].astype(np.float64), dims, vs)
+            if o != cur:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                t0 = time.perf_counter()
+                b.tsdf_shift(m.handle, o, stream)
+                host_us.append(1e6 * (time.perf_counter() - t0))
+                e1.record(stream)
+                torch.cuda.synchronize()
+                dev_us.append(1e3 * e0.elapsed_time(e1))
+                dev_bytes.append(b.tsdf_map_device_bytes(m.handle))
+                cur = o
+            b.tsdf_integrate(m.handle, pts[j], pts[j].shape[0], pose.reshape(12), stream)
+        torch.cuda.synchronize()
+        st = b.tsdf_get_store_stats(m.handle)
+    finally:
+        m.close()
+    pct = lambda v, q: float(np.percentile(v, q))
+    return dict(workload="1 km drive, window 512x512x128 at 0.064 m, a scan (128x1024) and a 1 m shift every metre; "
+                         "store device tier limited to the window's brick count, the rest in pinned host memory",
+                shifts=len(host_us), shift_host_us=dict(p50=pct(host_us, 50), p99=pct(host_us, 99), mean=float(np.mean(host_us))),
+                shift_device_us=dict(p50=pct(dev_us, 50), p99=pct(dev_us, 99), mean=float(np.mean(dev_us)),
+                                     note="from the start event to the end of the shift kernel, including its host time"),
+                map_device_bytes=dict(first=dev_bytes[0], max=max(dev_bytes), last=dev_bytes[-1]),
+                store=st)
+
+
 def run_configs(args):
     """The configured workloads besides the headline one, each short, as
     sub-records of the default line: box room (us per scan), the 64-map batch
-    against 64 plain calls, the high-resolution corridor and a 32-session
-    serving run at Poisson 500 scans/s (p50 / p99 latency)."""
+    against 64 plain calls, the high-resolution corridor, a 1 km drive through
+    the two-tier global store (shift latency) and a 32-session serving run at
+    Poisson 500 scans/s (p50 / p99 latency)."""
     import copy
     out = {}
     out["room"] = run_room_bench(200)
@@ -464,6 +515,7 @@ def run_configs(args):
                         value=bt["value"], unit=bt["unit"], scans_per_s=bt["scans_per_s"],
                         plain_ms_per_64_scans=bt["plain_per_scan_launches"]["ms_per_step"],
                         speedup_vs_plain=bt["batch_speedup_vs_plain"], tuned_config=bt["config"]["tuned_config"])
+    out["drive"] = run_drive_bench(1000)
     a = copy.copy(args)
     a.serve_seconds, a.serve_rate, a.serve_pinned = 6.0, 500.0, 1
     sv = run_serving_bench(a)

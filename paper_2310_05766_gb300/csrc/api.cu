@@ -94,14 +94,10 @@ struct tsdf_map {
     uint64_t shift_serial = 0;           // shifts done so far
     uint64_t chunks_spilled = 0;         // chunks moved from the device tier to the host tier
     uint64_t chunks_dropped = 0;         // leaving chunks found empty (not stored)
-    // per shift item: the candidate slot's address (pinned + device), the
-    // candidate the kernel claimed for the leaving brick or -1 (device +
-    // pinned copy), and the claim counter (device)
-    unsigned long long* addr_host = nullptr;
-    unsigned long long* addr_dev = nullptr;
-    int* claim_dev = nullptr;
+    // per shift item: the candidate the kernel claimed for the leaving brick,
+    // or -1 (pinned host memory written by the kernel in place)
     int* claim_host = nullptr;
-    unsigned* claimed_dev = nullptr;
+    int* claim_dev = nullptr;            // its device-visible address
     size_t flags_cap = 0;
     cudaEvent_t flags_event = nullptr;   // the last shift's claims have reached claim_host
     std::vector<ChunkKey> leave_keys;    // the shift's leaving chunks, in item order
@@ -258,11 +254,7 @@ void free_map(tsdf_map* m) {
     cudaFree(m->dev.sorted);
     for (char* a : m->store_allocs[0]) cudaFree(a);
     for (char* a : m->store_allocs[1]) cudaFreeHost(a);
-    if (m->addr_host) cudaFreeHost(m->addr_host);
-    cudaFree(m->addr_dev);
-    cudaFree(m->claim_dev);
     if (m->claim_host) cudaFreeHost(m->claim_host);
-    cudaFree(m->claimed_dev);
     if (m->flags_event) cudaEventDestroy(m->flags_event);
     cudaFree(m->spill_dev);
     if (m->spill_host) cudaFreeHost(m->spill_host);
@@ -346,37 +338,31 @@ int ensure_shift_buffers(tsdf_map* m, size_t cnt) {
         TSDF_CU(cudaEventSynchronize(m->items_event));
         m->items_event_pending = false;
     }
+    // items: entry 0 is a header whose first word is the kernel's claim
+    // counter (zero in every copy), entries 1..cnt the moved bricks
     if (cnt > m->items_host_cap) {
         if (m->items_host) cudaFreeHost(m->items_host);
         m->items_host = nullptr;
         m->items_host_cap = 0;
-        TSDF_CU(cudaMallocHost(&m->items_host, cnt * sizeof(ShiftItem)));
+        TSDF_CU(cudaMallocHost(&m->items_host, (cnt + 1) * sizeof(ShiftItem)));
         m->items_host_cap = cnt;
     }
     if (cnt > m->items_dev_cap || cnt > m->flags_cap) {
         int rc = store_resolve(m);   // the claims still to be read live in these buffers
         if (rc != TSDF_OK) return rc;
         cudaFree(m->items_dev);   // waits for the device
-        cudaFree(m->addr_dev);
-        cudaFree(m->claim_dev);
-        cudaFree(m->claimed_dev);
-        if (m->addr_host) cudaFreeHost(m->addr_host);
         if (m->claim_host) cudaFreeHost(m->claim_host);
         m->items_dev = nullptr;
-        m->addr_dev = nullptr;
-        m->claim_dev = nullptr;
-        m->claimed_dev = nullptr;
-        m->addr_host = nullptr;
         m->claim_host = nullptr;
+        m->claim_dev = nullptr;
         m->items_dev_cap = 0;
         m->flags_cap = 0;
-        TSDF_CU(cudaMalloc(&m->items_dev, cnt * sizeof(ShiftItem)));
+        TSDF_CU(cudaMalloc(&m->items_dev, (cnt + 1) * sizeof(ShiftItem)));
         m->items_dev_cap = cnt;
-        TSDF_CU(cudaMalloc(&m->addr_dev, cnt * sizeof(unsigned long long)));
-        TSDF_CU(cudaMalloc(&m->claim_dev, cnt * sizeof(int)));
-        TSDF_CU(cudaMalloc(&m->claimed_dev, sizeof(unsigned)));
-        TSDF_CU(cudaMallocHost(&m->addr_host, cnt * sizeof(unsigned long long)));
-        TSDF_CU(cudaMallocHost(&m->claim_host, cnt * sizeof(int)));
+        TSDF_CU(cudaHostAlloc(&m->claim_host, cnt * sizeof(int), cudaHostAllocMapped));
+        void* dp = nullptr;
+        TSDF_CU(cudaHostGetDevicePointer(&dp, m->claim_host, 0));
+        m->claim_dev = static_cast<int*>(dp);
         m->flags_cap = cnt;
     }
     // (the copy list exists once chunks can move: the device tier is at its
@@ -878,8 +864,10 @@ int tsdf_shift(tsdf_map* map, const int64_t new_origin[3], void* stream) {
         // taken, so no slot is both read and written by this shift.
         const uint64_t stamp = ++map->shift_serial;
         map->leave_keys.clear();
+        ShiftItem* items = map->items_host + 1;   // entry 0: the header (claim counter)
+        map->items_host[0] = ShiftItem{};
         auto add_out = [&](long long sx, long long sy, long long sz) {
-            ShiftItem& it = map->items_host[map->leave_keys.size()];
+            ShiftItem& it = items[map->leave_keys.size()];
             it = ShiftItem{};
             it.brick = (uint32_t)((sz * C[1] + sy) * C[0] + sx);
             map->leave_keys.push_back(ChunkKey{oldc[0][sx], oldc[1][sy], oldc[2][sz]});
@@ -895,26 +883,23 @@ int tsdf_shift(tsdf_map* map, const int64_t new_origin[3], void* stream) {
         }
         if (!map->store.candidates(map->leave_keys, stamp, &map->cand_locs)) return TSDF_ERR_OOM;
         for (size_t i = 0; i < cnt; ++i) {
-            ShiftItem& it = map->items_host[i];
-            map->addr_host[i] = store_addr(map, map->cand_locs[i]);
+            ShiftItem& it = items[i];
+            it.out_ptr = store_addr(map, map->cand_locs[i]);   // candidate i, claimed in order by the kernel
             const long long b = it.brick;
             const long long sx = b % C[0], sy = (b / C[0]) % C[1], sz = b / (C[0] * C[1]);
             const long long loc = map->store.take(ChunkKey{newc[0][sx], newc[1][sy], newc[2][sz]});
             it.in_ptr = loc >= 0 ? store_addr(map, (uint32_t)loc) : 0ull;
         }
         map->store.end_shift();
-        TSDF_CU(cudaMemcpyAsync(map->items_dev, map->items_host, cnt * sizeof(ShiftItem), cudaMemcpyHostToDevice, s));
-        TSDF_CU(cudaMemcpyAsync(map->addr_dev, map->addr_host, cnt * sizeof(unsigned long long),
-                                cudaMemcpyHostToDevice, s));
-        TSDF_CU(cudaMemsetAsync(map->claimed_dev, 0, sizeof(unsigned), s));
+        TSDF_CU(cudaMemcpyAsync(map->items_dev, map->items_host, (cnt + 1) * sizeof(ShiftItem), cudaMemcpyHostToDevice,
+                                s));
         TSDF_CU(cudaEventRecord(map->items_event, s));
         map->items_event_pending = true;
         cudaEvent_t e0 = prof_mark(map, s);
-        TSDF_CU(launch_shift(map->dev.grid, map->items_dev, (int)cnt, map->addr_dev, map->claimed_dev, map->claim_dev,
-                             s));
+        TSDF_CU(launch_shift(map->dev.grid, map->items_dev + 1, (int)cnt, reinterpret_cast<unsigned*>(map->items_dev),
+                             map->claim_dev, s));
         prof_push(map, kShift, e0, prof_mark(map, s));
-        TSDF_CU(cudaMemcpyAsync(map->claim_host, map->claim_dev, cnt * sizeof(int), cudaMemcpyDeviceToHost, s));
-        TSDF_CU(cudaEventRecord(map->flags_event, s));
+        TSDF_CU(cudaEventRecord(map->flags_event, s));   // the claims have reached claim_host
     }
     for (int a = 0; a < 3; ++a) map->origin[a] = new_origin[a];
     return TSDF_OK;
@@ -1416,8 +1401,7 @@ int tsdf_map_device_bytes(const tsdf_map* map, int64_t* out) {
         b += map->bricks * sizeof(uint32_t) +
              (size_t)map->dev.pool_cap * (sizeof(uint32_t) + kBrickVoxels * sizeof(unsigned long long));
     b += map->store_seg[0].size() * (size_t)kSegChunks * kChunkBytes;   // the host tier is host memory
-    b += map->stage_cap * sizeof(float4) + map->items_dev_cap * sizeof(ShiftItem) +
-         map->flags_cap * (sizeof(unsigned long long) + sizeof(int)) + (map->claimed_dev ? sizeof(unsigned) : 0) +
+    b += map->stage_cap * sizeof(float4) + (map->items_dev ? (map->items_dev_cap + 1) * sizeof(ShiftItem) : 0) +
          map->spill_cap * sizeof(ChunkCopy);
     *out = (int64_t)b;
     return TSDF_OK;

@@ -132,7 +132,7 @@ inline void fill_lean_args(ScanArgs& a) {
 struct ShiftItem {
     uint32_t brick;                 // ring brick index
     uint32_t pad0;
-    unsigned long long out_ptr;     // unused (leaving bricks go to the shift's claimed candidate slots)
+    unsigned long long out_ptr;     // address of the shift's candidate slot with this item's index
     unsigned long long in_ptr;      // store address of the entering brick, 0 = zero fill
     unsigned long long pad1;
 };
@@ -198,9 +198,10 @@ cudaError_t launch_sort_apply(const MapDev& m, int32_t reduce, int32_t w_max, in
                               cudaStream_t s);
 // The leaving brick of each item that holds a non-zero voxel claims the next
 // candidate slot (*claimed counts them, from 0) and is copied to
-// slot_addr[claim]; claim[item] is that index or -1 (the brick held no data).
-cudaError_t launch_shift(uint32_t* grid, const ShiftItem* items, int count, const unsigned long long* slot_addr,
-                         unsigned* claimed, int* claim, cudaStream_t s);
+// items[claim].out_ptr; claim[item] is that index or -1 (the brick held no
+// data). claim may point to mapped host memory.
+cudaError_t launch_shift(uint32_t* grid, const ShiftItem* items, int count, unsigned* claimed, int* claim,
+                         cudaStream_t s);
 cudaError_t launch_copy_chunks(const ChunkCopy* items, int count, cudaStream_t s);
 cudaError_t launch_register(const float* pts_dev, int n, const float pose[12], const uint32_t* grid,
                             const WindowGeom& geo, const long long origin[3], float vs, float inv_vs, float tau,

@@ -17,14 +17,13 @@ namespace {
 // 2048-byte brick, issuing all of its loads (the leaving brick and the
 // entering one) before any store, so that each lane has 128 bytes in flight.
 // A leaving brick with some non-zero voxel claims the next of the shift's
-// candidate store slots (one atomic per such brick) and is written there;
-// claim[item] receives the candidate's index, or -1 for a brick that held no
-// data (not written). The store keeps a brick in the same [z][y][x] order; a
+// candidate store slots (one atomic per such brick; candidate c's address is
+// items[c].out_ptr) and is written there; claim[item] receives the
+// candidate's index, or -1 for a brick that held no data (not written). The store keeps a brick in the same [z][y][x] order; a
 // slot may lie in pinned host memory, which the kernel reads and writes in
 // place.
 __global__ void __launch_bounds__(128) shift_kernel(uint32_t* __restrict__ grid, const ShiftItem* __restrict__ items,
-                                                     int count, const unsigned long long* __restrict__ slot_addr,
-                                                     unsigned* __restrict__ claimed, int* __restrict__ claim) {
+                                                     int count, unsigned* __restrict__ claimed, int* __restrict__ claim) {
     const int lane = threadIdx.x & 31;
     for (int it = blockIdx.x * 4 + (threadIdx.x >> 5); it < count; it += gridDim.x * 4) {
         const ShiftItem s = items[it];
@@ -43,7 +42,7 @@ __global__ void __launch_bounds__(128) shift_kernel(uint32_t* __restrict__ grid,
         if (keep && claimed) {
             if (lane == 0) c = (int)atomicAdd(claimed, 1u);
             c = __shfl_sync(0xFFFFFFFFu, c, 0);
-            uint4* dst = reinterpret_cast<uint4*>(slot_addr[c]);
+            uint4* dst = reinterpret_cast<uint4*>(items[c].out_ptr);
 #pragma unroll
             for (int v = 0; v < 4; ++v) dst[32 * v + lane] = old[v];
         }
@@ -106,12 +105,12 @@ cudaError_t launch_copy_chunks(const ChunkCopy* items, int count, cudaStream_t s
     return cudaGetLastError();
 }
 
-cudaError_t launch_shift(uint32_t* grid, const ShiftItem* items, int count, const unsigned long long* slot_addr,
-                         unsigned* claimed, int* claim, cudaStream_t s) {
+cudaError_t launch_shift(uint32_t* grid, const ShiftItem* items, int count, unsigned* claimed, int* claim,
+                         cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     const int need = (count + 3) / 4;
     const int blocks = need < 65536 ? need : 65536;
-    shift_kernel<<<blocks, 128, 0, s>>>(grid, items, count, slot_addr, claimed, claim);
+    shift_kernel<<<blocks, 128, 0, s>>>(grid, items, count, claimed, claim);
     return cudaGetLastError();
 }
 

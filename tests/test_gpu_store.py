@@ -112,7 +112,10 @@ def test_store_spills_to_host_memory_and_reads_back(age):
                 om.integrate(st[1], st[2])
             else:
                 om.shift(st[1])
-        assert ss["device_chunks"] + ss["host_chunks"] == om.store_chunks()
+        o = om.origin
+        lo = [o[a] // 8 for a in range(3)]
+        outside = [k for k in om.global_chunks() if any(not (lo[a] <= k[a] < lo[a] + 8) for a in range(3))]
+        assert ss["device_chunks"] + ss["host_chunks"] == len(outside)
         om.close()
     finally:
         m.close()
@@ -207,3 +210,57 @@ def test_serving_charges_the_store_reservation():
         b.tsdf_server_close_session(srv, s2)
     finally:
         b.tsdf_server_destroy(srv)
+
+
+def test_one_km_drive_bounded_device_memory_exact_at_every_reentry():
+    """A 1 km drive (500 m out along x and back, a scan every 4 m) with a 32 x 32
+    x 8 m window (128 x 128 x 32 at 0.25 m) over a seeded ground-and-boxes
+    scene, the store's device tier limited to one segment (4096 chunks, fewer
+    than the drive stores): device memory stays bounded, chunks spill to host
+    memory, and on the way back the window equals the oracle's at every
+    position (every re-entered chunk read back exactly)."""
+    from paper_2310_05766_gb300 import binding as b
+    vs, dims = 0.25, (128, 128, 32)
+    xs = [4.0 * i for i in range(126)] + [4.0 * i for i in range(124, -1, -1)]
+    path = np.array([[x, 0.0] for x in xs[:126]])
+    scene = synth.outdoor_scene(41, path, n_boxes=400, n_cyl=100, extent=520.0)
+    dirs = synth.beam_directions(16, 360, -15.0, 15.0)
+    rng = synth.SplitMix64(42)
+    p = synth.params_dict(dims, vs, 0.75, 64, synth.delta_z_for(30.0, 16), 0.5, 40.0, 0,
+                          synth.window_origin((0.0, 0.0, 0.0), dims, vs))
+    m = b.TsdfMap(p)
+    om = oracle.OracleMap(p)
+    try:
+        b.tsdf_set_option(m.handle, b.TSDF_OPT_STORE_DEVICE_CHUNKS, 4096)
+        sizes = []
+        checked = 0
+        for k, x in enumerate(xs):
+            R = synth.rot_zyx(0.05 * np.sin(0.1 * k))
+            t = np.array([x, 0.0, 0.0])
+            o = synth.window_origin(t, dims, vs)
+            if k:
+                m.shift(o)
+                om.shift(o)
+                sizes.append(b.tsdf_map_device_bytes(m.handle))
+            pts = synth.make_scan(scene, R, t, dirs, 0.01, rng, r_max=40.0)
+            pose = synth.pose12(R, t)
+            m.integrate(torch.from_numpy(pts).cuda(), pose)
+            om.integrate(pts, pose)
+            if k > 125:   # on the way back: every position
+                vg, wg = m.read()
+                vo, wo = om.read()
+                assert np.array_equal(vg, vo) and np.array_equal(wg, wo), f"position {k} (x = {x})"
+                checked += 1
+        st = b.tsdf_get_store_stats(m.handle)
+        assert checked == 125
+        assert st["spilled"] > 0 and st["device_capacity"] == 4096
+        assert max(sizes) == sizes[0]          # bounded: the device tier never grew past its first segment
+        # the store holds exactly the oracle's non-empty chunks outside the window
+        # (the oracle's own store also keeps copies of chunks that re-entered)
+        o = om.origin
+        lo = [o[a] // 8 for a in range(3)]
+        outside = [k for k in om.global_chunks() if any(not (lo[a] <= k[a] < lo[a] + dims[a] // 8) for a in range(3))]
+        assert len(outside) == st["device_chunks"] + st["host_chunks"]
+    finally:
+        m.close()
+        om.close()
