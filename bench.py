@@ -279,9 +279,11 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     touched_timed = int(sum(touched[i] for i in timed))
     n_shift_timed = prof.get("shift", (0, 0.0))[0]
 
-    # ---- end to end through host buffers (pinned), counters read back each step
-    n_e2e = min(len(timed), 400)
-    e2e_sched = timed[:n_e2e]
+    # ---- end to end through host buffers (pinned), counters read back each step;
+    # at least 200 steps of the ping-pong schedule (one in ten shifts the window),
+    # so that the figure does not hang on two or three shifts
+    n_e2e = max(min(len(timed), 400), 200)
+    e2e_sched = ping_pong(args.warmup + n_e2e, n_seq)[args.warmup:]
     t_e2e = 0.0
     for i in e2e_sched:
         flush.zero_()
@@ -523,6 +525,14 @@ def run_configs(args):
                           p50_ms=sv["latency_ms"]["p50"], p99_ms=sv["latency_ms"]["p99"],
                           mean_ms=sv["latency_ms"]["mean"], voxel_updates_per_s=sv["voxel_updates_per_s"],
                           mean_batch=sv["mean_batch"], sessions=sv["sessions"])
+    # the same sessions saturated (every request due at once, bursts of 1024
+    # outstanding): where continuous batching shows
+    a = copy.copy(args)
+    a.serve_seconds, a.serve_rate, a.serve_pinned = 2.0, 0.0, 1
+    ss = run_serving_bench(a)
+    out["serving_saturated"] = dict(workload=ss["config"]["workload"], requests=ss["steps"], scans_per_s=ss["value"],
+                                    p50_ms=ss["latency_ms"]["p50"], p99_ms=ss["latency_ms"]["p99"],
+                                    voxel_updates_per_s=ss["voxel_updates_per_s"], mean_batch=ss["mean_batch"])
     return out
 
 
