@@ -127,22 +127,23 @@ __global__ void __launch_bounds__(kContribThreads, TSDF_CONTRIB_MIN_CTAS) contri
     const unsigned lane = threadIdx.x & 31u;
     const unsigned gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+    __shared__ unsigned s_counts[2];
     pdl_trigger();
     brick_cache_init(btab);
-    __syncthreads();
     pdl_wait();   // ray list and live count come from the rays kernel
     // A coherent load after the wait (a read-only __ldg could be hoisted above
-    // it and see a count from before the rays kernel finished), one per warp.
-    // The ray list may be split (heavy rays from the front, light ones from
-    // the end): the blocks of the front come first, so the costly items are
-    // taken by the first wave of CTAs and the CTAs that start late get light ones.
-    unsigned nf = 0, nb = 0;
-    if (lane == 0) {
-        nf = __ldcg(&m.ctr->live_count);
-        nb = __ldcg(&m.ctr->live_back);
+    // it and see a count from before the rays kernel finished), one per CTA:
+    // every CTA of the grid reads the same line, so per-warp reads would make
+    // it a hot spot. The ray list may be split (heavy rays from the front,
+    // light ones from the end): the blocks of the front come first, so the
+    // costly items are taken by the first wave of CTAs and the CTAs that start
+    // late get light ones.
+    if (threadIdx.x == 0) {
+        s_counts[0] = __ldcg(&m.ctr->live_count);
+        s_counts[1] = __ldcg(&m.ctr->live_back);
     }
-    nf = __shfl_sync(kFull, nf, 0);
-    nb = __shfl_sync(kFull, nb, 0);
+    __syncthreads();   // (also orders the brick cache initialisation)
+    const unsigned nf = s_counts[0], nb = s_counts[1];
     const unsigned bf = (nf + 31u) / 32u, bb = (nb + 31u) / 32u;
     const unsigned ngrp = (unsigned)(2 * a.K + KPT) / KPT;   // ceil((2K+1) / KPT)
     const unsigned nitems = (bf + bb) * ngrp;
@@ -318,10 +319,11 @@ __global__ void __launch_bounds__(kRegApplyWarps * 32, TSDF_APPLY_MIN_CTAS) appl
     const unsigned nwarps = gridDim.x * kRegApplyWarps;
     pdl_trigger();
     pdl_wait();   // list and accumulators come from the earlier kernels
-    // coherent load after the wait (see contrib_kernel), one per warp
-    unsigned nb = 0;
-    if (lane == 0) nb = __ldcg(&m.ctr->brick_count);
-    nb = __shfl_sync(kFull, nb, 0);
+    // coherent load after the wait (see contrib_kernel), one per CTA
+    if (threadIdx.x == 0) s_last = __ldcg(&m.ctr->brick_count);
+    __syncthreads();
+    const unsigned nb = s_last;
+    __syncthreads();   // s_last is reused by finish_if_last
     unsigned long long touched = 0, hits = 0;
 #if TSDF_APPLY_REG
     for (unsigned t = gwarp; t < nb * (8u / kApplyPairs); t += nwarps)
