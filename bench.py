@@ -44,7 +44,7 @@ METRIC = "TSDF voxel updates/s (OS1-128-shaped scan)"
 # kernels on the outdoor workload, the default one
 # (profiles/contrib_outdoor_128x1024.md, profiles/contrib_apply_outdoor_128x1024.md);
 # other workloads report none. Reset an entry to None whenever its kernel changes.
-NCU_DRAM_BYTES = {"contrib": 13.20e6 + 0.5e3, "apply": 27.55e6 + 1.5e3, "rays": None}
+NCU_DRAM_BYTES = {"contrib": 13.209e6, "apply": 27.350e6, "rays": None}
 UNIT = "voxel_updates/s"
 N_SEQ = 100
 
