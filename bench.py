@@ -226,7 +226,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     red_opt = {"atomic": None, "sort": b.TSDF_REDUCTION_SORT, "pool": b.TSDF_REDUCTION_POOL}[args.reduction]
     for opt, val in ((b.TSDF_OPT_WARP_MERGE, args.merge), (b.TSDF_OPT_STEPS_PER_THREAD, args.kpt),
                      (b.TSDF_OPT_PDL, args.pdl), (b.TSDF_OPT_REDUCTION, red_opt),
-                     (b.TSDF_OPT_HOST_ZERO_COPY, args.zero_copy)):
+                     (b.TSDF_OPT_HOST_ZERO_COPY, args.zero_copy),
+                     (b.TSDF_OPT_LAUNCH_GRAPH, getattr(args, "graph", None))):
         if val is not None:
             b.tsdf_set_option(h, opt, val)
     cur = tuple(p["origin"])
@@ -838,6 +839,8 @@ def main():
     ap.add_argument("--merge", type=int, default=None, help="tuning: warp match-merge (0/1)")
     ap.add_argument("--kpt", type=int, default=None, help="tuning: march steps per contribution thread (1/2/4)")
     ap.add_argument("--pdl", type=int, default=None, help="tuning: programmatic dependent launch (0/1)")
+    ap.add_argument("--graph", type=int, default=None,
+                    help="tuning: one graph launch per scan (1) or four kernel launches (0, library default)")
     ap.add_argument("--zero-copy", type=int, default=None,
                     help="e2e: pinned host points read in place (1, library default) or staged (0)")
     ap.add_argument("--reduction", default="atomic", choices=["atomic", "sort", "pool"],

@@ -241,6 +241,13 @@ int tsdf_stats(tsdf_map* map, tsdf_scan_stats* out, void* stream);
 #define TSDF_OPT_STORE_SPILL_AGE 9  /* global store: a chunk stored this many shifts ago moves from device to
                                       host memory at the next shift; 0 (default): only when the device tier is
                                       full */
+#define TSDF_OPT_LAUNCH_GRAPH 10  /* 1: the atomic reduction's four kernels are captured once into a CUDA
+                                    graph (again after buffers or options change) and each scan sets the
+                                    graph's arguments and launches it once: less host time per scan, for
+                                    callers whose thread is the bottleneck; 0 (default): four launches per
+                                    scan, which let consecutive scans overlap on the device. Scans while
+                                    profiling is enabled or while the caller's stream is being captured use
+                                    four launches. */
 
 /* Device memory held by the map (grid, per-scan buffers of the reductions
  * that have been used, ray buffers, global store) in bytes. Host-side.

@@ -42,6 +42,7 @@ TSDF_REDUCTION_AUTO = 3
 TSDF_OPT_POOL_BRICKS = 7
 TSDF_OPT_STORE_DEVICE_CHUNKS = 8
 TSDF_OPT_STORE_SPILL_AGE = 9
+TSDF_OPT_LAUNCH_GRAPH = 10
 TSDF_BATCH_OPT_GRAPH = 1
 TSDF_BATCH_OPT_AUTOTUNE = 2
 TSDF_BATCH_OPT_CONFIG = 3

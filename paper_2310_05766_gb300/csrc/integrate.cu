@@ -543,6 +543,30 @@ cudaError_t launch_emit_k(const ScanArgs& a, const MapDev& m, bool pdl, cudaStre
 
 }  // namespace
 
+const void* rays_kernel_fn(bool sort, bool split) {
+    if (sort) return reinterpret_cast<const void*>(rays_kernel<true, false>);
+    return split && TSDF_RAYS_SPLIT ? reinterpret_cast<const void*>(rays_kernel<false, true>)
+                                    : reinterpret_cast<const void*>(rays_kernel<false, false>);
+}
+
+const void* contrib_kernel_fn(int32_t reduce, bool merge, int kpt) {
+    const int k = kpt == 2 || kpt == 4 ? kpt : 1;
+    if (reduce == 0) {
+        if (merge) return k == 4 ? reinterpret_cast<const void*>(contrib_kernel<0, true, 4>)
+                        : k == 2 ? reinterpret_cast<const void*>(contrib_kernel<0, true, 2>)
+                                 : reinterpret_cast<const void*>(contrib_kernel<0, true, 1>);
+        return k == 4 ? reinterpret_cast<const void*>(contrib_kernel<0, false, 4>)
+             : k == 2 ? reinterpret_cast<const void*>(contrib_kernel<0, false, 2>)
+                      : reinterpret_cast<const void*>(contrib_kernel<0, false, 1>);
+    }
+    if (merge) return k == 4 ? reinterpret_cast<const void*>(contrib_kernel<1, true, 4>)
+                    : k == 2 ? reinterpret_cast<const void*>(contrib_kernel<1, true, 2>)
+                             : reinterpret_cast<const void*>(contrib_kernel<1, true, 1>);
+    return k == 4 ? reinterpret_cast<const void*>(contrib_kernel<1, false, 4>)
+         : k == 2 ? reinterpret_cast<const void*>(contrib_kernel<1, false, 2>)
+                  : reinterpret_cast<const void*>(contrib_kernel<1, false, 1>);
+}
+
 cudaError_t launch_rays(const ScanArgs& a, const MapDev& m, bool sort, bool split, bool pdl, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
     const dim3 grid((unsigned)((a.n + kRaysThreads - 1) / kRaysThreads)), block(kRaysThreads);

@@ -179,6 +179,10 @@ int map_reserve_sort(::tsdf_map* map, int64_t n);
 // of at least one voxel each side) from the list's front, the others from
 // its end (the plain contribution kernel takes heavy work first).
 cudaError_t launch_rays(const ScanArgs& a, const MapDev& m, bool sort, bool split, bool pdl, cudaStream_t s);
+// The kernel functions that launch_rays / launch_contrib launch for these
+// arguments (to find their nodes in a captured graph).
+const void* rays_kernel_fn(bool sort, bool split);
+const void* contrib_kernel_fn(int32_t reduce, bool merge, int kpt);
 cudaError_t launch_contrib(const ScanArgs& a, const MapDev& m, int32_t reduce, bool merge, int kpt, bool pdl,
                            cudaStream_t s);
 cudaError_t launch_compact(const MapDev& m, uint32_t bricks, bool pdl, cudaStream_t s);

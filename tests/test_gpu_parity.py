@@ -42,13 +42,15 @@ def test_room_scan_exact(reduce):
 
 
 @pytest.mark.parametrize("reduce", [0, 1])
-@pytest.mark.parametrize("merge,kpt,pdl", [(1, 2, 1), (0, 1, 1), (0, 4, 1), (1, 4, 0), (0, 2, 0), (1, 1, 1)])
-def test_tuning_options_same_result(reduce, merge, kpt, pdl):
+@pytest.mark.parametrize("merge,kpt,pdl,graph", [(1, 2, 1, 1), (0, 1, 1, 1), (0, 4, 1, 1), (1, 4, 0, 1), (0, 2, 0, 1),
+                                                 (1, 1, 1, 1), (0, 4, 1, 0), (1, 2, 0, 0)])
+def test_tuning_options_same_result(reduce, merge, kpt, pdl, graph):
     """Tuning options (warp match-merge, steps per thread, programmatic
-    dependent launch) change speed only: every setting is bit-identical to the
-    oracle."""
+    dependent launch, one graph launch per scan) change speed only: every
+    setting is bit-identical to the oracle."""
     from paper_2310_05766_gb300 import binding as b
-    opts = {b.TSDF_OPT_WARP_MERGE: merge, b.TSDF_OPT_STEPS_PER_THREAD: kpt, b.TSDF_OPT_PDL: pdl}
+    opts = {b.TSDF_OPT_WARP_MERGE: merge, b.TSDF_OPT_STEPS_PER_THREAD: kpt, b.TSDF_OPT_PDL: pdl,
+            b.TSDF_OPT_LAUNCH_GRAPH: graph}
     w = synth.workload_room(reduce=reduce)
     both(w.params, workload_steps(w), options=opts, label=f"room {opts}")
     w2 = synth.workload_outdoor(n_scans=2, reduce=reduce)
@@ -57,12 +59,57 @@ def test_tuning_options_same_result(reduce, merge, kpt, pdl):
     both(dict(p, reduce=reduce), steps, options=opts, label=f"random {opts}")
 
 
+def test_launch_graph_and_plain_launches_exact():
+    """The plain path's captured graph and four launches per scan (the default)
+    both give the oracle's result, also when one map moves between them in
+    the middle of a sequence: an option that rebuilds the graph, profiling
+    (four launches), the graph turned off and on again, empty scans and scans
+    of other sizes (the ray kernel's grid changes), and shifts."""
+    from paper_2310_05766_gb300 import binding as b
+    w = synth.workload_outdoor(n_scans=7)
+    steps = workload_steps(w)
+    sizes = [None, 1000, 0, 33, None, 4097, None]
+    scans = [i for i, st in enumerate(steps) if st[0] == "scan"]
+    for k, i in enumerate(scans):
+        if sizes[k] is not None:
+            steps[i] = ("scan", steps[i][1][:sizes[k]], steps[i][2])
+    actions = {1: [(b.TSDF_OPT_STEPS_PER_THREAD, 2)], 3: ["profile_on"], 4: ["profile_off", (b.TSDF_OPT_LAUNCH_GRAPH, 0)],
+               5: [(b.TSDF_OPT_LAUNCH_GRAPH, 1), (b.TSDF_OPT_STEPS_PER_THREAD, 4)]}
+    m = b.TsdfMap(w.params)
+    stats = []
+    try:
+        b.tsdf_set_option(m.handle, b.TSDF_OPT_LAUNCH_GRAPH, 1)
+        k = 0
+        for st in steps:
+            if st[0] == "shift":
+                m.shift(st[1])
+                continue
+            for act in actions.get(k, []):
+                if act == "profile_on":
+                    b.tsdf_profile_enable(m.handle, 1)
+                elif act == "profile_off":
+                    b.tsdf_profile_enable(m.handle, 0)
+                else:
+                    b.tsdf_set_option(m.handle, act[0], act[1])
+            m.integrate(torch.from_numpy(np.ascontiguousarray(st[1])).cuda(), st[2])
+            stats.append(m.stats())
+            k += 1
+        v, wt = m.read()
+        g = (v, wt, stats, m.origin)
+    finally:
+        m.close()
+    o = run_oracle(w.params, steps)
+    assert_same(g, o, "graph / plain launches")
+    assert stats[2]["hits"] == 0 and stats[0]["hits"] > 1000000
+
+
 def test_invalid_option_rejected():
     from paper_2310_05766_gb300 import binding as b
     w = synth.workload_room()
     m = b.TsdfMap(w.params)
     try:
-        for opt, val in [(b.TSDF_OPT_STEPS_PER_THREAD, 3), (b.TSDF_OPT_WARP_MERGE, 2), (b.TSDF_OPT_PDL, -1), (99, 0)]:
+        for opt, val in [(b.TSDF_OPT_STEPS_PER_THREAD, 3), (b.TSDF_OPT_WARP_MERGE, 2), (b.TSDF_OPT_PDL, -1),
+                         (b.TSDF_OPT_LAUNCH_GRAPH, 2), (99, 0)]:
             with pytest.raises(b.TsdfError):
                 b.tsdf_set_option(m.handle, opt, val)
     finally:
