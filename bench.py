@@ -396,7 +396,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=K, warmup=args.warmup,
         ms_per_step=dev_ms_max / K, higher_is_better=True, scaling="weak", vs_baseline=None,
         dtype="f32 geometry, int64 accumulation, int16 map", data="synthetic",
-        config=dict(workload=wdesc,
+        config=dict(workload=wdesc, seed=w.meta.get("seed"),
                     points_per_scan=int(n_pts), voxel_size=p["voxel_size"], tau=p["tau"], dims=list(p["dims"]),
                     reduce="WSUM", reduction=args.reduction, map_device_bytes=map_bytes, l2=L2Flush.DESCRIPTION,
                     parallelism=f"replicas x{world}"),
@@ -459,7 +459,7 @@ def run_room_bench(steps: int = 200):
         m.close()
     return dict(workload="box room: 16 x 360 beams (5760 points), 256x256x64 window at 0.05 m, tau 0.2 m, "
                          "the same scan integrated every step",
-                steps=steps, us_per_scan=dict(mean=float(us.mean()), p50=float(np.percentile(us, 50)),
+                seed=1, steps=steps, us_per_scan=dict(mean=float(us.mean()), p50=float(np.percentile(us, 50)),
                                               p99=float(np.percentile(us, 99))),
                 scans_per_s=1e6 / float(us.mean()), voxel_updates_per_s=hits / (float(us.mean()) / 1e6),
                 hits_per_scan=hits, note="latency-bound (a few microseconds of work per scan); not judged by roofline")
@@ -508,6 +508,7 @@ def run_drive_bench(n_pos: int = 1000):
     pct = lambda v, q: float(np.percentile(v, q))
     return dict(workload="1 km drive, window 512x512x128 at 0.064 m, a scan (128x1024) and a 1 m shift every metre; "
                          "store device tier limited to the window's brick count, the rest in pinned host memory",
+                seed=w.meta.get("seed"),
                 shifts=len(host_us), shift_host_us=dict(p50=pct(host_us, 50), p99=pct(host_us, 99), mean=float(np.mean(host_us))),
                 shift_device_us=dict(p50=pct(dev_us, 50), p99=pct(dev_us, 99), mean=float(np.mean(dev_us)),
                                      note="from the start event to the end of the shift kernel, including its host time"),
@@ -527,7 +528,7 @@ def run_configs(args):
     a = copy.copy(args)
     a.workload, a.steps, a.warmup, a.no_cpu_baseline = "corridor", 100, 5, True
     c = run_gpu(a, 0, 1, 0)
-    out["corridor"] = dict(workload=c["config"]["workload"], steps=c["steps"], value=c["value"], unit=c["unit"],
+    out["corridor"] = dict(workload=c["config"]["workload"], seed=c["config"].get("seed"), steps=c["steps"], value=c["value"], unit=c["unit"],
                            us_per_scan=c["us_per_scan"], scans_per_s=c["scans_per_s"],
                            hits_per_scan=c["hits_per_scan"], contrib_avg_us=c["kernels"]["contrib"]["avg_us"],
                            l2_reductions_frac_scattered=c["roofline"].get("frac_scattered"),
@@ -535,7 +536,7 @@ def run_configs(args):
     a = copy.copy(args)
     a.steps, a.warmup = 20, 16
     bt = run_batch_bench(a)
-    out["batch"] = dict(workload=bt["config"]["workload"], steps=bt["steps"], ms_per_batch=bt["ms_per_step"],
+    out["batch"] = dict(workload=bt["config"]["workload"], seed=bt["config"].get("seed"), steps=bt["steps"], ms_per_batch=bt["ms_per_step"],
                         value=bt["value"], unit=bt["unit"], scans_per_s=bt["scans_per_s"],
                         plain_ms_per_64_scans=bt["plain_per_scan_launches"]["ms_per_step"],
                         speedup_vs_plain=bt["batch_speedup_vs_plain"], tuned_config=bt["config"]["tuned_config"])
@@ -600,7 +601,7 @@ def run_reference(args, rank: int, world: int):
                 dtype="f32 geometry, int64 accumulation, int16 map", data="synthetic", impl="reference",
                 config=dict(workload="outdoor OS1-128 sequence: 128x1024 beams, 100 scans at 10 Hz, 1 m/s, "
                                      "window 512x512x128 at 0.064 m, tau 0.6 m, shift every 1 m (ping-pong over the sequence)",
-                            points_per_step=131072 // stride, parallelism="host cores"),
+                            seed=2, points_per_step=131072 // stride, parallelism="host cores"),
                 cpu_baseline=dict(kind="oracle", cores=1, sample=sample, value=value, unit=UNIT),
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
 
@@ -665,7 +666,7 @@ def run_batch_bench(args):
                 dtype="f32 geometry, int64 accumulation, int16 map", data="synthetic",
                 config=dict(workload="64 maps, beams {16,32,64,128} x azimuths {512,1024,2048}, grids 256^3 / "
                                      "512x512x128 at 0.064 m, tau 0.6 m, one scan per map per step",
-                            l2=L2Flush.DESCRIPTION, tuned_config=cfg),
+                            seed=3, l2=L2Flush.DESCRIPTION, tuned_config=cfg),
                 scans_per_s=64 / (ms_b / 1e3), plain_per_scan_launches=dict(ms_per_step=ms_p, value=hits / (ms_p / 1e3)),
                 batch_speedup_vs_plain=ms_p / ms_b, hits_per_step=hits)
 
@@ -809,7 +810,8 @@ def run_serving_bench(args):
                                      "%s, scans {16,32,64,128} x {1024,2048}, %g s of arrivals, warm-up discarded, "
                                      "HBM budget 120 GB, 2 streams, batches up to 32, scans %s" %
                                      (load, duration, "pinned (read in place)" if args.serve_pinned else
-                                      "pageable (copied at submission)")),
+                                      "pageable (copied at submission)"),
+                            seeds=dict(sessions=100, arrivals=101)),
                 latency_ms=dict(p50=float(np.percentile(lat, 50)) / 1e3, p99=float(np.percentile(lat, 99)) / 1e3,
                                 mean=float(np.mean(lat)) / 1e3, max=float(np.max(lat)) / 1e3),
                 voxel_updates_per_s=hits / span, mean_batch=st["mean_batch"], batches=st["batches"],
