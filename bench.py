@@ -533,6 +533,17 @@ def run_configs(args):
                            hits_per_scan=c["hits_per_scan"], contrib_avg_us=c["kernels"]["contrib"]["avg_us"],
                            l2_reductions_frac_scattered=c["roofline"].get("frac_scattered"),
                            e2e=c["e2e"]["value"], map_device_bytes=c["config"]["map_device_bytes"])
+    if not args.no_cpu_baseline:
+        # the single-threaded oracle per scan beside the GPU figures (room: its
+        # one scan; corridor: its first scans, about a second of host time)
+        from paper_2310_05766_gb300 import synth
+        for key, wk, budget in (("room", synth.workload_room(), 0.0),
+                                ("corridor", synth.workload_corridor(n_scans=3), 1.0)):
+            rate, n_used, hits, t = oracle_sample(wk, budget)
+            out[key]["cpu_baseline"] = dict(value=rate, unit=UNIT, cores=1, kind="oracle",
+                                            ms_per_scan=1e3 * t / n_used,
+                                            sample=f"first {n_used} scan(s) of the workload, {hits} voxel updates "
+                                                   f"in {t:.2f} s, single-threaded C++ oracle")
     a = copy.copy(args)
     a.steps, a.warmup = 20, 16
     bt = run_batch_bench(a)
