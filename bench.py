@@ -40,10 +40,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "TSDF voxel updates/s (OS1-128-shaped scan)"
-# DRAM bytes (read + write) per launch from the committed ncu captures of these
-# kernels on the outdoor workload, the default one
-# (profiles/contrib_outdoor_128x1024.md, profiles/contrib_apply_outdoor_128x1024.md);
-# other workloads report none. Reset an entry to None whenever its kernel changes.
+# DRAM bytes (read + write) per launch from the committed ncu summaries of these
+# kernels on the outdoor workload, the default one (under profiles/); other
+# workloads report none. Reset an entry to None whenever its kernel changes.
 NCU_DRAM_BYTES = {"contrib": 13.209e6, "apply": 27.350e6, "rays": None}
 UNIT = "voxel_updates/s"
 N_SEQ = 100

@@ -421,6 +421,10 @@ typedef struct tsdf_batch tsdf_batch;   /* opaque; owns pinned and device descri
                                            so that launches on several streams can be resident together */
 #define TSDF_BATCH_OPT_TUNE_SORT  7  /* 1 (default): the autotuner also times the sort configurations, whose first use
                                         allocates each map's sort buffers; 0: only the atomic ones (no allocation) */
+#define TSDF_BATCH_OPT_CTA_BRICK_CACHE 8  /* 1 (default): the warps of a CTA share one cache of the bricks they
+                                              marked (keys tagged with the map), when every map has fewer than
+                                              2^22 bricks and the batch fewer than 1023 maps; 0: one cache per
+                                              warp. Speed only: results are identical. */
 
 /* Create a batch object for up to max_count (1..1024) maps per call, on the
  * current device. Synchronous. Errors: INVALID, OOM, CUDA. */

@@ -50,6 +50,7 @@ TSDF_BATCH_OPT_SPIN_LIMIT = 4
 TSDF_BATCH_OPT_TEST_MISSING_ARRIVALS = 5
 TSDF_BATCH_OPT_GRID_FRACTION = 6
 TSDF_BATCH_OPT_TUNE_SORT = 7
+TSDF_BATCH_OPT_CTA_BRICK_CACHE = 8
 TSDF_STATIC_MAX_VOXELS = 1 << 21
 TSDF_STATIC_MAX_POINTS = 1 << 17
 

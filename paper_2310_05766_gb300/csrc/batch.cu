@@ -57,12 +57,19 @@ constexpr int kBatchMax = 1024;               // maps per batch
 constexpr size_t kApplySmemPerWarp = kBrickVoxels * (4 + 8 + 2);   // grid, accumulator, offsets
 constexpr int kWarpBrickCacheLog2 = 10;                              // per-warp brick cache in phase 2
 static_assert((4u << kWarpBrickCacheLog2) <= kApplySmemPerWarp, "brick cache fits the staging area");
+// Phase 2's brick cache shared by a CTA's warps (in the staging areas of its
+// first warps), used when every map of the batch has fewer than 2^22 bricks
+// and the batch fewer than 1023 maps: map i tags its entries with i << 22.
+constexpr int kCtaBrickCacheLog2 = 11;
+constexpr uint32_t kTagShift = 22;
+static_assert((4u << kCtaBrickCacheLog2) <= 4 * kApplySmemPerWarp, "CTA brick cache fits four warps' staging");
 
 struct BatchHeader {
     int32_t count;
     uint32_t ray_tasks;                      // total CTA ray tasks (256 points each)
     uint32_t word_tasks;                     // total warp compaction tasks (32 flag words each)
     uint32_t extra_arrivals;                 // test hook: barrier arrivals that never come
+    uint32_t cta_cache;                      // 1: phase 2 keeps one brick cache per CTA (map-tagged keys)
     long long spin_limit;                    // polls before a barrier wait gives up
     uint32_t ray_prefix[kBatchMax + 1];      // exclusive prefix of ray tasks per map
     uint32_t word_prefix[kBatchMax + 1];     // exclusive prefix of compaction tasks per map
@@ -167,6 +174,7 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) batch_kernel(const Bat
     constexpr int kBatchWarps = THREADS / 32;
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ uint32_t s_prefix[kBatchMax + 1];
+    __shared__ uint32_t s_live[kBatchMax];   // phase 2: live rays per map, read once per CTA
     __shared__ RaysSmemT<kBatchWarps> rsm;
     const int count = hdr->count;
     const unsigned arrivals = gridDim.x + hdr->extra_arrivals;
@@ -186,8 +194,13 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) batch_kernel(const Bat
     if (!grid_barrier(sync, arrivals, spin)) return;
 
     // ---- phase 2: contributions; per map ceil(live / 32) * ceil((2K+1) / KPT) warp items
+    const bool cta_cache = hdr->cta_cache != 0u;
+    uint32_t* const ctab = reinterpret_cast<uint32_t*>(dyn);
+    if (cta_cache)   // (block_prefix synchronises the CTA before any use)
+        for (int e = (int)threadIdx.x; e < (1 << kCtaBrickCacheLog2); e += THREADS) ctab[e] = kNoVoxel;
     block_prefix(count, [&](int i) {
         const unsigned nl = __ldcg(&items[i].m.ctr->live_count);
+        s_live[i] = nl;
         return (nl + 31u) / 32u * ((unsigned)(2 * items[i].a.K + KPT) / KPT);
     }, s_prefix);
     {
@@ -195,9 +208,14 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) batch_kernel(const Bat
         int cur = -1;
         unsigned hits = 0;
         bool ovf = false;
-        // each warp's brick cache lives in its apply staging area (unused
-        // until phase 4) and is emptied whenever the warp moves to another map
-        const BrickCache bc{reinterpret_cast<uint32_t*>(dyn + w * kApplySmemPerWarp), 32u - kWarpBrickCacheLog2};
+        // the brick cache lives in apply staging memory (unused until phase
+        // 4): one per CTA whose keys carry the map's tag, or else one per
+        // warp, emptied whenever the warp moves to another map. The warps of
+        // a CTA take consecutive items (mostly of one map) and mark the same
+        // bricks, so a shared cache stops more global flag stores.
+        BrickCache bc = cta_cache ? BrickCache{ctab, 32u - kCtaBrickCacheLog2, 0u}
+                                  : BrickCache{reinterpret_cast<uint32_t*>(dyn + w * kApplySmemPerWarp),
+                                               32u - kWarpBrickCacheLog2, 0u};
         for (uint32_t g = gwarp; g < s_prefix[count]; g += nwarps) {   // warp-uniform
             const int i = find_segment(s_prefix, count, g);
             if (i != cur) {
@@ -208,13 +226,17 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) batch_kernel(const Bat
                 ovf = false;
                 last_brick = kNoVoxel;
                 cur = i;
-                for (int e = (int)lane; e < (1 << kWarpBrickCacheLog2); e += 32) bc.tab[e] = kNoVoxel;
-                __syncwarp();
+                if (cta_cache) {
+                    bc.tag = (uint32_t)i << kTagShift;
+                } else {
+                    for (int e = (int)lane; e < (1 << kWarpBrickCacheLog2); e += 32) bc.tab[e] = kNoVoxel;
+                    __syncwarp();
+                }
             }
             const BatchItem& it = items[i];
             const unsigned ngrp = (unsigned)(2 * it.a.K + KPT) / KPT;
             const unsigned local = g - s_prefix[i];
-            const unsigned nl = __ldcg(&it.m.ctr->live_count);
+            const unsigned nl = s_live[i];
             const unsigned ray = (local / ngrp) * 32u + lane;
             float4 A, B;
             load_rays(it.m, nl, ray, A, B);
@@ -388,6 +410,7 @@ struct tsdf_batch {
     // autotuning state
     int trials_per_config = 2;
     bool tune_sort = true;                 // the autotuner also times the sort configurations
+    bool cta_cache = true;                 // phase 2 shares one brick cache per CTA when the maps allow it
     int tuned = -1;                        // chosen config, -1 while tuning
     struct Trial {
         int config;
@@ -585,6 +608,10 @@ int tsdf_batch_set_option(tsdf_batch* b, int32_t option, int64_t value) {
             if (value != 0 && value != 1) return TSDF_ERR_INVALID;
             b->tune_sort = value != 0;
             return TSDF_OK;
+        case TSDF_BATCH_OPT_CTA_BRICK_CACHE:
+            if (value != 0 && value != 1) return TSDF_ERR_INVALID;
+            b->cta_cache = value != 0;
+            return TSDF_OK;
         case TSDF_BATCH_OPT_TEST_MISSING_ARRIVALS:
             if (value < 0 || value > 1024) return TSDF_ERR_INVALID;
             b->extra_arrivals = (int)value;
@@ -645,6 +672,7 @@ int tsdf_batch_integrate(tsdf_batch* b, tsdf_map* const* maps, const float* cons
     BatchHeader* hdr = reinterpret_cast<BatchHeader*>(sl.host);
     BatchItem* items = reinterpret_cast<BatchItem*>(sl.host + sizeof(BatchHeader));
     uint32_t rt = 0, wt = 0;
+    bool small_maps = count < 1023;
     for (int i = 0; i < count; ++i) {
         if (kConfigs[cfg].sort) {   // the sort buffers must exist before the descriptors are taken
             int rc = map_reserve_sort(maps[i], n[i]);
@@ -656,6 +684,7 @@ int tsdf_batch_integrate(tsdf_batch* b, tsdf_map* const* maps, const float* cons
         hdr->word_prefix[i] = wt;
         rt += (uint32_t)((n[i] + kConfigs[cfg].threads - 1) / kConfigs[cfg].threads);
         wt += ((items[i].bricks + 3u) / 4u + 31u) / 32u;
+        small_maps = small_maps && items[i].bricks < (1u << kTagShift);
     }
     hdr->ray_prefix[count] = rt;
     hdr->word_prefix[count] = wt;
@@ -663,6 +692,7 @@ int tsdf_batch_integrate(tsdf_batch* b, tsdf_map* const* maps, const float* cons
     hdr->ray_tasks = rt;
     hdr->word_tasks = wt;
     hdr->extra_arrivals = (uint32_t)b->extra_arrivals;
+    hdr->cta_cache = small_maps && b->cta_cache ? 1u : 0u;
     hdr->spin_limit = b->spin_limit;
 
     cudaError_t e = cudaSuccess;

@@ -13,10 +13,13 @@ constexpr unsigned kNoVoxel = 0xFFFFFFFFu;
 
 // Shared-memory cache of bricks already marked in the scan's brick flags
 // (direct mapped on a multiplicative hash of the brick index). A null table
-// sends every mark to global memory.
+// sends every mark to global memory. An entry holds brick + tag: a table that
+// serves several maps gives each map its own tag, so that keys of different
+// maps never coincide (nor equal kNoVoxel, the empty entry).
 struct BrickCache {
     uint32_t* tab = nullptr;
     unsigned shift = 32;          // 32 - log2(entries)
+    uint32_t tag = 0;
 };
 
 // The per-map contribution kernels keep one cache per CTA.
@@ -387,8 +390,8 @@ __device__ __forceinline__ void lean_sample(const ScanArgs& a, const MapDev& m, 
             last_brick = brick;
             if (bc.tab) {
                 const unsigned h = (brick * 2654435761u) >> bc.shift;
-                if (bc.tab[h] != brick) {
-                    bc.tab[h] = brick;
+                if (bc.tab[h] != brick + bc.tag) {
+                    bc.tab[h] = brick + bc.tag;
                     m.brick_flag[brick] = 1;
                 }
             } else {
@@ -560,8 +563,8 @@ __device__ __forceinline__ void contrib_item(const ScanArgs& a, const MapDev& m,
                 last_brick = brick;
                 if (bc.tab) {
                     const unsigned h = (brick * 2654435761u) >> bc.shift;
-                    if (bc.tab[h] != brick) {
-                        bc.tab[h] = brick;
+                    if (bc.tab[h] != brick + bc.tag) {
+                        bc.tab[h] = brick + bc.tag;
                         m.brick_flag[brick] = 1;
                     }
                 } else {

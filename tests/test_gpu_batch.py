@@ -78,16 +78,36 @@ def test_batch_matches_oracle_and_single():
 
 
 @pytest.mark.parametrize("config", range(12))
-@pytest.mark.parametrize("graph", [0, 1])
-def test_batch_every_config_same_result(config, graph):
+@pytest.mark.parametrize("graph,cta_cache", [(0, 1), (1, 1), (1, 0)])
+def test_batch_every_config_same_result(config, graph, cta_cache):
     from paper_2310_05766_gb300 import binding as b
     ws = _small_batch(5, seed=11)
     mb = _run_batch(b, ws, prefill_steps=1,
-                    options={b.TSDF_BATCH_OPT_CONFIG: config, b.TSDF_BATCH_OPT_GRAPH: graph})
+                    options={b.TSDF_BATCH_OPT_CONFIG: config, b.TSDF_BATCH_OPT_GRAPH: graph,
+                             b.TSDF_BATCH_OPT_CTA_BRICK_CACHE: cta_cache})
     ms = _run_single(b, ws, repeats=2)
     _same(b, mb, ms)
     for m in mb + ms:
         m.close()
+
+
+@pytest.mark.parametrize("cta_cache", [1, 0])
+def test_batch_of_identical_maps(cta_cache):
+    """Eight maps with the same parameters and the same scan in one batch:
+    the warps of a CTA mark equal brick numbers of different maps, which the
+    shared brick cache must keep apart (its keys carry the map). Every map
+    equals the per-map call."""
+    from paper_2310_05766_gb300 import binding as b
+    w = synth.workload_outdoor(n_scans=1)
+    ws = [w] * 8
+    for config in (0, 8, 9):
+        mb = _run_batch(b, ws, options={b.TSDF_BATCH_OPT_CONFIG: config, b.TSDF_BATCH_OPT_CTA_BRICK_CACHE: cta_cache})
+        ms = _run_single(b, ws[:1])
+        for m in mb:
+            assert torch.equal(_grid(b, m), _grid(b, ms[0]))
+            assert m.stats() == ms[0].stats()
+        for m in mb + ms:
+            m.close()
 
 
 def test_batch_autotune_settles_and_is_exact():
