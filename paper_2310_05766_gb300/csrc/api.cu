@@ -777,7 +777,7 @@ static int chain_graph_launch(tsdf_map* map, const ScanArgs& a, cudaStream_t s, 
     }
     void* args[2] = {const_cast<ScanArgs*>(&a), &map->dev};
     cudaKernelNodeParams kr = map->kp_rays;
-    kr.gridDim = dim3((unsigned)((a.n + (int64_t)kr.blockDim.x - 1) / (int64_t)kr.blockDim.x));
+    kr.gridDim = dim3(rays_grid(a.n, false));
     kr.kernelParams = args;
     kr.extra = nullptr;
     cudaKernelNodeParams kc = map->kp_contrib;

@@ -66,7 +66,7 @@ static_assert((4u << kCtaBrickCacheLog2) <= 4 * kApplySmemPerWarp, "CTA brick ca
 
 struct BatchHeader {
     int32_t count;
-    uint32_t ray_tasks;                      // total CTA ray tasks (256 points each)
+    uint32_t ray_tasks;                      // total CTA ray tasks (THREADS points each, kBatchRaysPPT times that without sort)
     uint32_t word_tasks;                     // total warp compaction tasks (32 flag words each)
     uint32_t extra_arrivals;                 // test hook: barrier arrivals that never come
     uint32_t cta_cache;                      // 1: phase 2 keeps one brick cache per CTA (map-tagged keys)
@@ -184,11 +184,16 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) batch_kernel(const Bat
     const unsigned gwarp = blockIdx.x * kBatchWarps + w;
     const unsigned nwarps = gridDim.x * kBatchWarps;
 
-    // ---- phase 1: ray set-up and compaction, one CTA task = THREADS points of a map
+    // ---- phase 1: ray set-up and compaction, one CTA task = THREADS points of a
+    // map (sort configurations) or kBatchRaysPPT THREADS points (that many per thread)
     for (uint32_t t = blockIdx.x; t < hdr->ray_tasks; t += gridDim.x) {
         const int i = find_segment(hdr->ray_prefix, count, t);
-        rays_task<false, SORT, false, kBatchWarps>(items[i].a, items[i].m, (int)((t - hdr->ray_prefix[i]) * THREADS),
-                                                   t, &rsm);
+        if constexpr (SORT)
+            rays_task<false, SORT, false, kBatchWarps>(items[i].a, items[i].m,
+                                                       (int)((t - hdr->ray_prefix[i]) * THREADS), t, &rsm);
+        else
+            rays_task_ppt<false, false, kBatchWarps, kBatchRaysPPT>(
+                items[i].a, items[i].m, (int)((t - hdr->ray_prefix[i]) * THREADS * kBatchRaysPPT), t, &rsm);
         __syncthreads();
     }
     if (!grid_barrier(sync, arrivals, spin)) return;
@@ -682,7 +687,8 @@ int tsdf_batch_integrate(tsdf_batch* b, tsdf_map* const* maps, const float* cons
         if (rc != TSDF_OK) return rc;
         hdr->ray_prefix[i] = rt;
         hdr->word_prefix[i] = wt;
-        rt += (uint32_t)((n[i] + kConfigs[cfg].threads - 1) / kConfigs[cfg].threads);
+        const int64_t task_points = (int64_t)kConfigs[cfg].threads * (kConfigs[cfg].sort ? 1 : kBatchRaysPPT);
+        rt += (uint32_t)((n[i] + task_points - 1) / task_points);
         wt += ((items[i].bricks + 3u) / 4u + 31u) / 32u;
         small_maps = small_maps && items[i].bricks < (1u << kTagShift);
     }

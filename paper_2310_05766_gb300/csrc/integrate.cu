@@ -110,7 +110,11 @@ constexpr int kRaysThreads = TSDF_RAYS_THREADS;
 template <bool SORT, bool SPLIT>
 __global__ void __launch_bounds__(kRaysThreads) rays_kernel(const ScanArgs a, const MapDev m) {
     __shared__ RaysSmemT<kRaysThreads / 32> sm;
-    rays_task<true, SORT, SPLIT, kRaysThreads / 32>(a, m, (int)(blockIdx.x * blockDim.x), blockIdx.x, &sm);
+    if constexpr (SORT)
+        rays_task<true, SORT, SPLIT, kRaysThreads / 32>(a, m, (int)(blockIdx.x * blockDim.x), blockIdx.x, &sm);
+    else
+        rays_task_ppt<true, SPLIT, kRaysThreads / 32, kRaysPPT>(a, m, (int)(blockIdx.x * blockDim.x) * kRaysPPT,
+                                                                blockIdx.x, &sm);
 }
 
 // Contribution work items: (block of 32 consecutive live rays, group of KPT
@@ -567,9 +571,14 @@ const void* contrib_kernel_fn(int32_t reduce, bool merge, int kpt) {
                   : reinterpret_cast<const void*>(contrib_kernel<1, false, 1>);
 }
 
+unsigned rays_grid(int64_t n, bool sort) {
+    const int64_t per_cta = (int64_t)kRaysThreads * (sort ? 1 : kRaysPPT);
+    return (unsigned)((n + per_cta - 1) / per_cta);
+}
+
 cudaError_t launch_rays(const ScanArgs& a, const MapDev& m, bool sort, bool split, bool pdl, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
-    const dim3 grid((unsigned)((a.n + kRaysThreads - 1) / kRaysThreads)), block(kRaysThreads);
+    const dim3 grid(rays_grid(a.n, sort)), block(kRaysThreads);
     if (sort) return launch(rays_kernel<true, false>, grid, block, s, pdl, a, m);
     return split && TSDF_RAYS_SPLIT ? launch(rays_kernel<false, true>, grid, block, s, pdl, a, m)
                                     : launch(rays_kernel<false, false>, grid, block, s, pdl, a, m);

@@ -106,25 +106,12 @@ struct RaysSmemT {
 };
 using RaysSmem = RaysSmemT<8>;
 
-// ---- rays: the CTA's 32 NW threads set up points [base, base + 32 NW) of a
-// scan and append the live ones to the map's ray list. With SORT each live ray also
-// reserves its pair slots (one 64-bit atomic per CTA). With SPLIT the rays
-// whose fill reaches at least one voxel each side at the hit (delta_z r >= vs,
-// the costly ones) go to the front of the list and the others to its end
-// (entry ray_cap - 1 - j for the j-th), so that the contribution kernel can
-// take the costly work first; with both ends counted, they never meet. With
-// PDL the wait for the preceding grid comes before the first access to the
-// map's counters and ray list.
-template <bool PDL, bool SORT, bool SPLIT = false, int NW = 8>
-__device__ __forceinline__ void rays_task(const ScanArgs& a, const MapDev& m, int base, unsigned part,
-                                          RaysSmemT<NW>* sm) {
-    static_assert(!(SORT && SPLIT), "the sort reduction keeps one list");
-    const int i = base + (int)threadIdx.x;
-    const unsigned lane = threadIdx.x & 31u;
-    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-    const bool in = i < a.n;
-    if (in) p = __ldg(a.pts + i);   // the caller's points: no dependency on earlier grids
-    if (PDL) pdl_trigger();
+// One point of a scan (sensor frame; `in`: the point exists): world transform,
+// range test, unit direction, fill direction (Eq. 3 / Eq. 4) and the
+// conservative window culling. ra = (dir, r) with r = -1 for an invalid ray,
+// rb = (fill direction, 1) or zeros without fill.
+__device__ __forceinline__ void ray_setup(const ScanArgs& a, float4 p, bool in, float4& ra, float4& rb, bool& valid,
+                                          bool& live) {
     const float tx = a.t[0], ty = a.t[1], tz = a.t[2];
     const float pwx = fa(fa(fa(fm(a.R[0], p.x), fm(a.R[1], p.y)), fm(a.R[2], p.z)), tx);
     const float pwy = fa(fa(fa(fm(a.R[3], p.x), fm(a.R[4], p.y)), fm(a.R[5], p.z)), ty);
@@ -132,11 +119,11 @@ __device__ __forceinline__ void rays_task(const ScanArgs& a, const MapDev& m, in
     const float vx = fs(pwx, tx), vy = fs(pwy, ty), vz = fs(pwz, tz);
     const float r2 = fa(fa(fm(vx, vx), fm(vy, vy)), fm(vz, vz));
     const float r = __fsqrt_rn(r2);
-    const bool valid = in && (r >= a.rmin) && (r <= a.rmax);
+    valid = in && (r >= a.rmin) && (r <= a.rmax);
 
-    float4 ra = make_float4(0.f, 0.f, 0.f, -1.f);
-    float4 rb = make_float4(0.f, 0.f, 0.f, 0.f);
-    bool live = false;
+    ra = make_float4(0.f, 0.f, 0.f, -1.f);
+    rb = make_float4(0.f, 0.f, 0.f, 0.f);
+    live = false;
     if (valid) {
         const float dx = __fdiv_rn(vx, r), dy = __fdiv_rn(vy, r), dz = __fdiv_rn(vz, r);
         const float ux = a.R[2], uy = a.R[5], uz = a.R[8];   // sensor z axis in the world
@@ -163,10 +150,34 @@ __device__ __forceinline__ void rays_task(const ScanArgs& a, const MapDev& m, in
         live = ex * ex + ey * ey + ez * ez <= reach * reach;
         ra = make_float4(dx, dy, dz, r);
     }
+}
+
+// ---- rays: the CTA's 32 NW threads set up points [base, base + 32 NW) of a
+// scan and append the live ones to the map's ray list. With SORT each live ray also
+// reserves its pair slots (one 64-bit atomic per CTA). With SPLIT the rays
+// whose fill reaches at least one voxel each side at the hit (delta_z r >= vs,
+// the costly ones) go to the front of the list and the others to its end
+// (entry ray_cap - 1 - j for the j-th), so that the contribution kernel can
+// take the costly work first; with both ends counted, they never meet. With
+// PDL the wait for the preceding grid comes before the first access to the
+// map's counters and ray list.
+template <bool PDL, bool SORT, bool SPLIT = false, int NW = 8>
+__device__ __forceinline__ void rays_task(const ScanArgs& a, const MapDev& m, int base, unsigned part,
+                                          RaysSmemT<NW>* sm) {
+    static_assert(!(SORT && SPLIT), "the sort reduction keeps one list");
+    const int i = base + (int)threadIdx.x;
+    const unsigned lane = threadIdx.x & 31u;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool in = i < a.n;
+    if (in) p = __ldg(a.pts + i);   // the caller's points: no dependency on earlier grids
+    if (PDL) pdl_trigger();
+    float4 ra, rb;
+    bool valid, live;
+    ray_setup(a, p, in, ra, rb, valid, live);
     // pair slots of this ray (sort reduction): an inclusive warp scan
     uint32_t nslot = 0, sincl = 0;
     if (SORT) {
-        nslot = live ? ray_slots(a, r, rb.w != 0.f) : 0u;
+        nslot = live ? ray_slots(a, ra.w, rb.w != 0.f) : 0u;
         const uint32_t own = nslot == kNoSlot ? 0u : nslot;
         sincl = own;
         for (int o = 1; o < 32; o <<= 1) {
@@ -227,6 +238,102 @@ __device__ __forceinline__ void rays_task(const ScanArgs& a, const MapDev& m, in
             // slots at or beyond the capacity overflow, sample by sample
             m.ray_slot[off] = nslot == kNoSlot ? kNoSlot
                                                 : (uint32_t)(first < m.pair_cap ? first : (unsigned long long)m.pair_cap);
+        }
+    }
+}
+
+// Points per thread of the plain path's ray set-up (rays_task_ppt): in the
+// per-map ray kernel, whose CTAs are all resident at once, one (4 measured
+// 1.6 us slower per outdoor scan: a quarter of the CTAs, each thread's four
+// points set up one after another); in the batched kernel, whose fixed grid
+// walks the ray tasks of all maps, four (64-map batch 1.34 against 1.40 ms:
+// four point loads in flight per thread).
+#ifndef TSDF_RAYS_PPT
+#define TSDF_RAYS_PPT 1
+#endif
+#ifndef TSDF_BATCH_RAYS_PPT
+#define TSDF_BATCH_RAYS_PPT 4
+#endif
+constexpr int kRaysPPT = TSDF_RAYS_PPT;
+constexpr int kBatchRaysPPT = TSDF_BATCH_RAYS_PPT;
+
+// The plain path's ray set-up with PPT consecutive points per thread: the
+// CTA's threads set up points [base, base + 32 NW PPT), thread t the points
+// base + PPT t .. base + PPT t + PPT - 1, whose loads are all in flight at
+// once, and append the live ones (in point order) to the map's ray list with
+// one list atomic per CTA and list end, as rays_task does for one point per
+// thread. Same rays, same per-ray results; only fewer CTAs and atomics.
+template <bool PDL, bool SPLIT, int NW, int PPT>
+__device__ __forceinline__ void rays_task_ppt(const ScanArgs& a, const MapDev& m, int base, unsigned part,
+                                              RaysSmemT<NW>* sm) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned warp = threadIdx.x >> 5;
+    const int i0 = base + PPT * (int)threadIdx.x;
+    float4 p[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {   // the caller's points: no dependency on earlier grids
+        p[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i0 + k < a.n) p[k] = __ldg(a.pts + i0 + k);
+    }
+    if (PDL) pdl_trigger();
+    float4 ra[PPT], rb[PPT];
+    unsigned hv = 0, lv = 0;   // bit k: point k is a live heavy (front) / light (end) ray
+    unsigned cv = 0;           // valid rays
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        bool valid, live;
+        ray_setup(a, p[k], i0 + k < a.n, ra[k], rb[k], valid, live);
+        const bool heavy = !SPLIT || (live && rb[k].w != 0.f && fm(fm(a.dz, ra[k].w), a.inv_vs) >= 1.f);
+        if (live && heavy) hv |= 1u << k;
+        if (live && !heavy) lv |= 1u << k;
+        cv += valid ? 1u : 0u;
+    }
+    // CTA-level compaction: inclusive warp scans of the per-thread counts
+    const unsigned cl = __popc(hv), cb = __popc(lv);
+    unsigned il = cl, ib = cb;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned yl = __shfl_up_sync(kFull, il, o);
+        const unsigned yb = __shfl_up_sync(kFull, ib, o);
+        if (lane >= (unsigned)o) {
+            il += yl;
+            ib += yb;
+        }
+    }
+    const unsigned wv = __reduce_add_sync(kFull, cv);
+    if (lane == 31) {
+        sm->wl[warp] = il;
+        sm->wb[warp] = ib;
+        sm->wv[warp] = wv;
+    }
+    __syncthreads();
+    if (PDL) pdl_wait();   // the previous scan's finish kernel resets live_count and the counters
+    if (threadIdx.x == 0) {
+        unsigned tl = 0, tv = 0, tb = 0;
+        for (int w = 0; w < NW; ++w) {
+            const unsigned l = sm->wl[w], b = sm->wb[w];
+            sm->wl[w] = tl;
+            tl += l;
+            sm->wb[w] = tb;
+            tb += b;
+            tv += sm->wv[w];
+        }
+        sm->base = tl ? atomicAdd(&m.ctr->live_count, tl) : 0u;
+        sm->bbase = SPLIT && tb ? atomicAdd(&m.ctr->live_back, tb) : 0u;
+        if (tv) atomicAdd(&m.ctr->part[part % kParts].valid, (unsigned long long)tv);
+    }
+    __syncthreads();
+    unsigned off_l = sm->base + sm->wl[warp] + il - cl;     // first front entry of this thread
+    unsigned off_b = sm->bbase + sm->wb[warp] + ib - cb;    // first end entry (counted from the end)
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        if (hv & (1u << k)) {
+            m.ray_a[off_l] = ra[k];
+            m.ray_b[off_l] = rb[k];
+            ++off_l;
+        } else if (lv & (1u << k)) {
+            m.ray_a[m.ray_cap - 1u - off_b] = ra[k];
+            m.ray_b[m.ray_cap - 1u - off_b] = rb[k];
+            ++off_b;
         }
     }
 }

@@ -179,6 +179,8 @@ int map_reserve_sort(::tsdf_map* map, int64_t n);
 // of at least one voxel each side) from the list's front, the others from
 // its end (the plain contribution kernel takes heavy work first).
 cudaError_t launch_rays(const ScanArgs& a, const MapDev& m, bool sort, bool split, bool pdl, cudaStream_t s);
+// CTAs of the ray set-up kernel for a scan of n points.
+unsigned rays_grid(int64_t n, bool sort);
 // The kernel functions that launch_rays / launch_contrib launch for these
 // arguments (to find their nodes in a captured graph).
 const void* rays_kernel_fn(bool sort, bool split);
