@@ -66,7 +66,7 @@ static_assert((4u << kCtaBrickCacheLog2) <= 4 * kApplySmemPerWarp, "CTA brick ca
 
 struct BatchHeader {
     int32_t count;
-    uint32_t ray_tasks;                      // total CTA ray tasks (THREADS points each, kBatchRaysPPT times that without sort)
+    uint32_t ray_tasks;                      // total CTA ray tasks (THREADS times the configuration's points per thread)
     uint32_t word_tasks;                     // total warp compaction tasks (32 flag words each)
     uint32_t extra_arrivals;                 // test hook: barrier arrivals that never come
     uint32_t cta_cache;                      // 1: phase 2 keeps one brick cache per CTA (map-tagged keys)
@@ -167,7 +167,7 @@ __device__ __forceinline__ uint32_t written_slots(const MapDev& m) {
 
 // THREADS: CTA size (a ray task is THREADS points of a map); APAIRS: voxel
 // pairs per lane of a register-apply task (8: a warp per brick, 2: a quarter).
-template <bool MERGE, int KPT, bool SORT, int THREADS, int APAIRS>
+template <bool MERGE, int KPT, bool SORT, int THREADS, int APAIRS, int RPPT = 1>
 __global__ void __launch_bounds__(THREADS, 768 / THREADS) batch_kernel(const BatchItem* __restrict__ items,
                                                                          const BatchHeader* __restrict__ hdr,
                                                                          BatchSync* sync) {
@@ -184,16 +184,17 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) batch_kernel(const Bat
     const unsigned gwarp = blockIdx.x * kBatchWarps + w;
     const unsigned nwarps = gridDim.x * kBatchWarps;
 
-    // ---- phase 1: ray set-up and compaction, one CTA task = THREADS points of a
-    // map (sort configurations) or kBatchRaysPPT THREADS points (that many per thread)
+    // ---- phase 1: ray set-up and compaction, one CTA task = RPPT THREADS points
+    // of a map (RPPT points per thread)
+    static_assert(!(SORT && RPPT > 1), "the sort configurations set up one point per thread");
     for (uint32_t t = blockIdx.x; t < hdr->ray_tasks; t += gridDim.x) {
         const int i = find_segment(hdr->ray_prefix, count, t);
         if constexpr (SORT)
             rays_task<false, SORT, false, kBatchWarps>(items[i].a, items[i].m,
                                                        (int)((t - hdr->ray_prefix[i]) * THREADS), t, &rsm);
         else
-            rays_task_ppt<false, false, kBatchWarps, kBatchRaysPPT>(
-                items[i].a, items[i].m, (int)((t - hdr->ray_prefix[i]) * THREADS * kBatchRaysPPT), t, &rsm);
+            rays_task_ppt<false, false, kBatchWarps, RPPT>(items[i].a, items[i].m,
+                                                           (int)((t - hdr->ray_prefix[i]) * THREADS * RPPT), t, &rsm);
         __syncthreads();
     }
     if (!grid_barrier(sync, arrivals, spin)) return;
@@ -355,16 +356,22 @@ struct Config {
     int threads;
     int ctas_per_sm;
     int apply_pairs;
+    int rays_ppt;   // points per thread in the ray set-up
 };
 constexpr int kP = TSDF_BATCH_APPLY_PAIRS;
 const Config kConfigs[] = {
-    {false, 4, false, 256, 0, kP}, {false, 2, false, 256, 0, kP}, {false, 1, false, 256, 0, kP},
-    {true, 4, false, 256, 0, kP},  {true, 2, false, 256, 0, kP},  {true, 1, false, 256, 0, kP},
-    {false, 4, true, 256, 0, kP},  {false, 2, true, 256, 0, kP},
+    {false, 4, false, 256, 0, kP, 1}, {false, 2, false, 256, 0, kP, 1}, {false, 1, false, 256, 0, kP, 1},
+    {true, 4, false, 256, 0, kP, 1},  {true, 2, false, 256, 0, kP, 1},  {true, 1, false, 256, 0, kP, 1},
+    {false, 4, true, 256, 0, kP, 1},  {false, 2, true, 256, 0, kP, 1},
     // launch shapes of the plain atomic configuration
-    {false, 4, false, 128, 0, kP}, {false, 4, false, 512, 0, kP}, {false, 4, false, 256, 2, kP},
-    {false, 4, false, 256, 0, 2}};
-constexpr int kNumConfigs = 12;
+    {false, 4, false, 128, 0, kP, 1}, {false, 4, false, 512, 0, kP, 1}, {false, 4, false, 256, 2, kP, 1},
+    {false, 4, false, 256, 0, 2, 1},
+    // CTAs of 512 threads, several points per thread in the ray set-up: more
+    // point loads in flight for large batches (64 outdoor-sized scans: 1.34
+    // against 1.40 ms), but its 12 more registers made smaller batches slower
+    // when it was the only form (32 served sessions: 26 k against 30 k scans/s)
+    {false, 4, false, 512, 0, kP, kBatchRaysPPT}};
+constexpr int kNumConfigs = 13;
 
 size_t dyn_smem(const Config& c) { return (size_t)(c.threads / 32) * kApplySmemPerWarp; }
 
@@ -379,6 +386,7 @@ BatchKernel kernel_shape(const Config& c) {
 }
 
 BatchKernel kernel_for(const Config& c) {
+    if (c.rays_ppt > 1) return batch_kernel<false, 4, false, 512, kP, kBatchRaysPPT>;
     if (c.threads == 128) return batch_kernel<false, 4, false, 128, kP>;
     if (c.threads == 512) return batch_kernel<false, 4, false, 512, kP>;
     if (c.apply_pairs == 2) return batch_kernel<false, 4, false, 256, 2>;
@@ -678,6 +686,7 @@ int tsdf_batch_integrate(tsdf_batch* b, tsdf_map* const* maps, const float* cons
     BatchItem* items = reinterpret_cast<BatchItem*>(sl.host + sizeof(BatchHeader));
     uint32_t rt = 0, wt = 0;
     bool small_maps = count < 1023;
+    const int64_t task_points = (int64_t)kConfigs[cfg].threads * kConfigs[cfg].rays_ppt;
     for (int i = 0; i < count; ++i) {
         if (kConfigs[cfg].sort) {   // the sort buffers must exist before the descriptors are taken
             int rc = map_reserve_sort(maps[i], n[i]);
@@ -687,7 +696,6 @@ int tsdf_batch_integrate(tsdf_batch* b, tsdf_map* const* maps, const float* cons
         if (rc != TSDF_OK) return rc;
         hdr->ray_prefix[i] = rt;
         hdr->word_prefix[i] = wt;
-        const int64_t task_points = (int64_t)kConfigs[cfg].threads * (kConfigs[cfg].sort ? 1 : kBatchRaysPPT);
         rt += (uint32_t)((n[i] + task_points - 1) / task_points);
         wt += ((items[i].bricks + 3u) / 4u + 31u) / 32u;
         small_maps = small_maps && items[i].bricks < (1u << kTagShift);

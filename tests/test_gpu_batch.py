@@ -77,7 +77,7 @@ def test_batch_matches_oracle_and_single():
         m.close()
 
 
-@pytest.mark.parametrize("config", range(12))
+@pytest.mark.parametrize("config", range(13))
 @pytest.mark.parametrize("graph,cta_cache", [(0, 1), (1, 1), (1, 0)])
 def test_batch_every_config_same_result(config, graph, cta_cache):
     from paper_2310_05766_gb300 import binding as b
@@ -114,14 +114,14 @@ def test_batch_autotune_settles_and_is_exact():
     from paper_2310_05766_gb300 import binding as b
     ws = _small_batch(4, seed=13)
     batch = b.tsdf_batch_create(8)
-    mb = _run_batch(b, ws, batch=batch, prefill_steps=27)   # 12 configurations timed twice each
+    mb = _run_batch(b, ws, batch=batch, prefill_steps=29)   # 13 configurations timed twice each
     cfg = b.tsdf_batch_get_config(batch)
     b.tsdf_batch_integrate(batch, mb, [torch.from_numpy(w.scans[0]).cuda() for w in ws], [w.poses[0] for w in ws])
     assert b.tsdf_batch_sync(batch) == b.TSDF_OK
     cfg = b.tsdf_batch_get_config(batch)
     assert cfg["tuned"], cfg
     assert cfg["threads_per_cta"] in (128, 256, 512) and cfg["ctas"] >= 1 and cfg["apply_voxel_pairs"] in (2, 8)
-    ms = _run_single(b, ws, repeats=29)
+    ms = _run_single(b, ws, repeats=31)
     _same(b, mb, ms)
     b.tsdf_batch_destroy(batch)
     for m in mb + ms:
@@ -228,7 +228,7 @@ def test_batched_64_maps_every_configuration():
     ws = synth.workload_batch(n_maps=64, seed=3)
     ms = _run_single(b, ws)
     shapes = set()
-    for config in range(12):
+    for config in range(13):
         batch = b.tsdf_batch_create(64)
         mb = _run_batch(b, ws, batch=batch, options={b.TSDF_BATCH_OPT_CONFIG: config})
         c = b.tsdf_batch_get_config(batch)
@@ -254,7 +254,7 @@ def test_batch_rejects_bad_arguments():
         with pytest.raises(b.TsdfError):   # more maps than the object holds
             b.tsdf_batch_integrate(batch, maps + maps[:1], pts + pts[:1], [w.poses[0] for w in ws] + [ws[0].poses[0]])
         with pytest.raises(b.TsdfError):
-            b.tsdf_batch_set_option(batch, b.TSDF_BATCH_OPT_CONFIG, 12)
+            b.tsdf_batch_set_option(batch, b.TSDF_BATCH_OPT_CONFIG, 13)
     finally:
         b.tsdf_batch_destroy(batch)
         for m in maps:
