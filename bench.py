@@ -43,7 +43,7 @@ METRIC = "TSDF voxel updates/s (OS1-128-shaped scan)"
 # DRAM bytes (read + write) per launch from the committed ncu summaries of these
 # kernels on the outdoor workload, the default one (under profiles/); other
 # workloads report none. Reset an entry to None whenever its kernel changes.
-NCU_DRAM_BYTES = {"contrib": 13.209e6, "apply": 27.350e6, "rays": None}
+NCU_DRAM_BYTES = {"contrib": 13.201e6, "apply": 27.350e6, "rays": None}
 UNIT = "voxel_updates/s"
 N_SEQ = 100
 
