@@ -177,6 +177,11 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) batch_kernel(const Bat
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ uint32_t s_prefix[kBatchMax + 1];
     __shared__ uint32_t s_live[kBatchMax];   // phase 2: live rays per map, read once per CTA
+    // phase 2: each warp's copy of its current map's scan arguments and buffers
+    // (the march reads them at every sample; from global memory they compete
+    // for L1 with the rays and the brick flags)
+    __shared__ ScanArgs s_args[kBatchWarps];
+    __shared__ MapDev s_dev[kBatchWarps];
     __shared__ RaysSmemT<kBatchWarps> rsm;
     const int count = hdr->count;
     const unsigned arrivals = gridDim.x + hdr->extra_arrivals;
@@ -239,28 +244,39 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) batch_kernel(const Bat
                     bc.tag = (uint32_t)i << kTagShift;
                 } else {
                     for (int e = (int)lane; e < (1 << kWarpBrickCacheLog2); e += 32) bc.tab[e] = kNoVoxel;
-                    __syncwarp();
                 }
+                __syncwarp();   // the warp is done with the previous map's copies
+                {
+                    const uint32_t* sa = reinterpret_cast<const uint32_t*>(&items[i].a);
+                    uint32_t* da = reinterpret_cast<uint32_t*>(&s_args[w]);
+                    for (int e = (int)lane; e < (int)(sizeof(ScanArgs) / 4); e += 32) da[e] = sa[e];
+                    const uint32_t* sm_ = reinterpret_cast<const uint32_t*>(&items[i].m);
+                    uint32_t* dm = reinterpret_cast<uint32_t*>(&s_dev[w]);
+                    for (int e = (int)lane; e < (int)(sizeof(MapDev) / 4); e += 32) dm[e] = sm_[e];
+                }
+                __syncwarp();
             }
             const BatchItem& it = items[i];
-            const unsigned ngrp = (unsigned)(2 * it.a.K + KPT) / KPT;
+            const ScanArgs& ia = s_args[w];
+            const MapDev& im = s_dev[w];
+            const unsigned ngrp = (unsigned)(2 * ia.K + KPT) / KPT;
             const unsigned local = g - s_prefix[i];
             const unsigned nl = s_live[i];
             const unsigned ray = (local / ngrp) * 32u + lane;
             float4 A, B;
-            load_rays(it.m, nl, ray, A, B);
+            load_rays(im, nl, ray, A, B);
             if (SORT) {
-                const uint32_t sslot = ray < nl ? it.m.ray_slot[ray] : kNoSlot;
+                const uint32_t sslot = ray < nl ? im.ray_slot[ray] : kNoSlot;
                 if (it.reduce == 0)
-                    contrib_item<0, false, KPT, true>(it.a, it.m, local % ngrp, A, B, hits, last_brick, sslot, &ovf,
+                    contrib_item<0, false, KPT, true>(ia, im, local % ngrp, A, B, hits, last_brick, sslot, &ovf,
                                                       nullptr, bc);
-                else contrib_item<1, false, KPT, true>(it.a, it.m, local % ngrp, A, B, hits, last_brick, sslot, &ovf,
+                else contrib_item<1, false, KPT, true>(ia, im, local % ngrp, A, B, hits, last_brick, sslot, &ovf,
                                                        nullptr, bc);
             } else {
                 if (it.reduce == 0)
-                    contrib_item<0, MERGE, KPT>(it.a, it.m, local % ngrp, A, B, hits, last_brick, kNoSlot, nullptr,
+                    contrib_item<0, MERGE, KPT>(ia, im, local % ngrp, A, B, hits, last_brick, kNoSlot, nullptr,
                                                 nullptr, bc);
-                else contrib_item<1, MERGE, KPT>(it.a, it.m, local % ngrp, A, B, hits, last_brick, kNoSlot, nullptr,
+                else contrib_item<1, MERGE, KPT>(ia, im, local % ngrp, A, B, hits, last_brick, kNoSlot, nullptr,
                                                  nullptr, bc);
             }
         }
