@@ -177,9 +177,9 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) batch_kernel(const Bat
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ uint32_t s_prefix[kBatchMax + 1];
     __shared__ uint32_t s_live[kBatchMax];   // phase 2: live rays per map, read once per CTA
-    // phase 2: each warp's copy of its current map's scan arguments and buffers
-    // (the march reads them at every sample; from global memory they compete
-    // for L1 with the rays and the brick flags)
+    // phases 2 and 4: each warp's copy of its current map's scan arguments and
+    // buffers (the march reads them at every sample; from global memory they
+    // compete for L1 with the rays and the brick flags)
     __shared__ ScanArgs s_args[kBatchWarps];
     __shared__ MapDev s_dev[kBatchWarps];
     __shared__ RaysSmemT<kBatchWarps> rsm;
@@ -333,22 +333,28 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) batch_kernel(const Bat
                 }
                 touched = hits = 0;
                 cur = i;
+                __syncwarp();   // (the map's buffers, as in phase 2)
+                const uint32_t* sm_ = reinterpret_cast<const uint32_t*>(&items[i].m);
+                uint32_t* dm = reinterpret_cast<uint32_t*>(&s_dev[w]);
+                for (int e = (int)lane; e < (int)(sizeof(MapDev) / 4); e += 32) dm[e] = sm_[e];
+                __syncwarp();
             }
             const BatchItem& it = items[i];
+            const MapDev& im = s_dev[w];
             const unsigned local = g - s_prefix[i];
             if (SORT) {
-                const bool ovf = __ldcg(&it.m.ctr->overflow) != 0u;
+                const bool ovf = __ldcg(&im.ctr->overflow) != 0u;
                 if (it.reduce == 0)
-                    sort_apply_brick<0>(it.m, it.w_max, it.flags, local, ovf, s_grid, s_acc, s_off, touched, hits);
-                else sort_apply_brick<1>(it.m, it.w_max, it.flags, local, ovf, s_grid, s_acc, s_off, touched, hits);
+                    sort_apply_brick<0>(im, it.w_max, it.flags, local, ovf, s_grid, s_acc, s_off, touched, hits);
+                else sort_apply_brick<1>(im, it.w_max, it.flags, local, ovf, s_grid, s_acc, s_off, touched, hits);
             } else {
 #if TSDF_BATCH_APPLY_REG
                 if (it.reduce == 0)
-                    apply_part_reg<0, APAIRS>(it.m, it.w_max, it.flags, local, touched, hits);
-                else apply_part_reg<1, APAIRS>(it.m, it.w_max, it.flags, local, touched, hits);
+                    apply_part_reg<0, APAIRS>(im, it.w_max, it.flags, local, touched, hits);
+                else apply_part_reg<1, APAIRS>(im, it.w_max, it.flags, local, touched, hits);
 #else
-                if (it.reduce == 0) apply_brick<0>(it.m, it.w_max, it.flags, local, s_grid, s_acc, s_off, touched, hits);
-                else apply_brick<1>(it.m, it.w_max, it.flags, local, s_grid, s_acc, s_off, touched, hits);
+                if (it.reduce == 0) apply_brick<0>(im, it.w_max, it.flags, local, s_grid, s_acc, s_off, touched, hits);
+                else apply_brick<1>(im, it.w_max, it.flags, local, s_grid, s_acc, s_off, touched, hits);
 #endif
             }
         }
