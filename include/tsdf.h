@@ -415,7 +415,7 @@ typedef struct tsdf_batch tsdf_batch;   /* opaque; owns pinned and device descri
                                         threads, as many per SM as fit, whole-brick apply tasks); 8..11: atomic
                                         reduction, no merge, 4 steps per item, with CTAs of 128 threads, of 512
                                         threads, of 256 threads but 2 per SM, or quarter-brick apply tasks; 12:
-                                        as 9 with four points per thread in the ray set-up */
+                                        as 8 with four points per thread in the ray set-up */
 #define TSDF_BATCH_OPT_SPIN_LIMIT 4  /* polls before a grid-barrier wait gives up (default 2^24, about a second) */
 #define TSDF_BATCH_OPT_TEST_MISSING_ARRIVALS 5  /* test hook: the barrier waits for this many CTAs that do not exist (default 0) */
 #define TSDF_BATCH_OPT_GRID_FRACTION 6  /* percent (1..100, default 100) of the device's co-resident CTAs the launch uses,

@@ -391,11 +391,12 @@ const Config kConfigs[] = {
     // launch shapes of the plain atomic configuration
     {false, 4, false, 128, 0, kP, 1}, {false, 4, false, 512, 0, kP, 1}, {false, 4, false, 256, 2, kP, 1},
     {false, 4, false, 256, 0, 2, 1},
-    // CTAs of 512 threads, several points per thread in the ray set-up: more
-    // point loads in flight for large batches (64 outdoor-sized scans: 1.34
-    // against 1.40 ms), but its 12 more registers made smaller batches slower
-    // when it was the only form (32 served sessions: 26 k against 30 k scans/s)
-    {false, 4, false, 512, 0, kP, kBatchRaysPPT}};
+    // CTAs of 128 threads, several points per thread in the ray set-up: more
+    // point loads in flight for large batches (64 outdoor-sized scans: 1.17-
+    // 1.19 against 1.21 ms), a configuration of its own because the form
+    // costs registers in the whole kernel (when every configuration had it,
+    // 32 served sessions ran at 26 k instead of 30 k scans/s)
+    {false, 4, false, 128, 0, kP, kBatchRaysPPT}};
 constexpr int kNumConfigs = 13;
 
 // Dynamic shared memory of a configuration: the apply staging area (per warp)
@@ -420,7 +421,7 @@ BatchKernel kernel_shape(const Config& c) {
 }
 
 BatchKernel kernel_for(const Config& c) {
-    if (c.rays_ppt > 1) return batch_kernel<false, 4, false, 512, kP, kBatchRaysPPT>;
+    if (c.rays_ppt > 1) return batch_kernel<false, 4, false, 128, kP, kBatchRaysPPT>;
     if (c.threads == 128) return batch_kernel<false, 4, false, 128, kP>;
     if (c.threads == 512) return batch_kernel<false, 4, false, 512, kP>;
     if (c.apply_pairs == 2) return batch_kernel<false, 4, false, 256, 2>;

@@ -247,8 +247,8 @@ __device__ __forceinline__ void rays_task(const ScanArgs& a, const MapDev& m, in
 // 1.6 us slower per outdoor scan: a quarter of the CTAs, each thread's four
 // points set up one after another); in the batched kernel, whose fixed grid
 // walks the ray tasks of all maps, four in one of its configurations (64-map
-// batch 1.34 against 1.40 ms: four point loads in flight per thread), one in
-// the others.
+// batch 1.17-1.19 against 1.21 ms: four point loads in flight per thread), one
+// in the others.
 #ifndef TSDF_RAYS_PPT
 #define TSDF_RAYS_PPT 1
 #endif
