@@ -1630,6 +1630,8 @@ int map_device(const ::tsdf_map* map) { return map->device; }
 
 const long long* map_last_counters(const ::tsdf_map* map) { return &map->dev.ctr->last_valid; }
 
+const volatile long long* map_host_counters(const ::tsdf_map* map) { return map->host_last; }
+
 int map_reserve_points(::tsdf_map* map, int64_t n) {
     if (!map || n < 0 || n > TSDF_MAX_POINTS) return TSDF_ERR_INVALID;
     DeviceScope ds(map->device);

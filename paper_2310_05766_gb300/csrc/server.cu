@@ -11,7 +11,9 @@
 // submission order. Each batch goes to a free stream slot: host-to-device
 // copies of the points, the shifts, one batched integration launch
 // (tsdf_batch_integrate, a persistent cooperative kernel over all maps of the
-// batch), and device-to-host copies of each map's counters, then an event.
+// batch, whose last phase also writes each map's counters into mapped host
+// memory), then an event; a map without that mapped copy gets a
+// device-to-host copy of its counters.
 // While one slot's batch runs, requests that arrive are formed into the next
 // batch on the other slot, so copies and kernels of consecutive batches
 // overlap on the device. Because each map's integration is bit-identical in
@@ -65,9 +67,10 @@ struct Slot {
     cudaStream_t stream = nullptr;
     tsdf_batch* batch = nullptr;
     float4* dev_pts = nullptr;          // max_batch x max_points
-    long long* counters = nullptr;      // pinned, max_batch x 3
+    long long* counters = nullptr;      // pinned, max_batch x 3 (maps without mapped counters)
     cudaEvent_t done = nullptr;
     std::vector<Request*> reqs;
+    std::vector<const volatile long long*> src;   // per request: where its counters are read
     bool busy = false;
     bool launching = false;             // being filled by the worker outside the lock
 };
@@ -152,9 +155,17 @@ int launch_batch(tsdf_server* s, int k, std::vector<Request*>& reqs, const std::
     if (e != cudaSuccess) return TSDF_ERR_CUDA;
     int rc = tsdf_batch_integrate(sl.batch, maps.data(), pts.data(), ns.data(), poses.data(), count, sl.stream);
     if (rc != TSDF_OK) return rc;
-    for (int i = 0; i < count && e == cudaSuccess; ++i)
-        e = cudaMemcpyAsync(sl.counters + 3 * i, map_last_counters(maps[i]), 3 * sizeof(long long),
-                            cudaMemcpyDeviceToHost, sl.stream);
+    // counters: the mapped host copy the batch writes (no copy to issue), else
+    // a device-to-host copy (one call per map costs microseconds of host time)
+    sl.src.resize(count);
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        sl.src[i] = map_host_counters(maps[i]);
+        if (!sl.src[i]) {
+            e = cudaMemcpyAsync(sl.counters + 3 * i, map_last_counters(maps[i]), 3 * sizeof(long long),
+                                cudaMemcpyDeviceToHost, sl.stream);
+            sl.src[i] = sl.counters + 3 * i;
+        }
+    }
     if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
     if (e != cudaSuccess) return TSDF_ERR_CUDA;
     return TSDF_OK;
@@ -171,9 +182,9 @@ void worker_loop(tsdf_server* s) {
             const double t = now_us();
             for (size_t i = 0; i < sl.reqs.size(); ++i) {
                 Request* r = sl.reqs[i];
-                r->res.stats.valid_rays = sl.counters[3 * i + 0];
-                r->res.stats.hits = sl.counters[3 * i + 1];
-                r->res.stats.touched = sl.counters[3 * i + 2];
+                r->res.stats.valid_rays = sl.src[i][0];
+                r->res.stats.hits = sl.src[i][1];
+                r->res.stats.touched = sl.src[i][2];
                 r->res.t_done_us = t;
                 r->res.batch_size = (int32_t)sl.reqs.size();
                 r->res.status = TSDF_OK;

@@ -167,6 +167,9 @@ int map_device(const ::tsdf_map* map);
 // Device address of the map's published counters (last_valid, last_hits,
 // last_touched: three contiguous int64).
 const long long* map_last_counters(const ::tsdf_map* map);
+// Host address of the mapped pinned copy of those counters, which the last CTA
+// of every integration (per-map or batched) writes; null when the map has none.
+const volatile long long* map_host_counters(const ::tsdf_map* map);
 // Grow the map's per-ray buffers to hold n points (synchronous allocation).
 int map_reserve_points(::tsdf_map* map, int64_t n);
 
