@@ -12,7 +12,8 @@
 // copies of the points, the shifts, one batched integration launch
 // (tsdf_batch_integrate, a persistent cooperative kernel over all maps of the
 // batch, whose last phase also writes each map's counters into mapped host
-// memory), then an event; a map without that mapped copy gets a
+// memory; a batch of one or two requests runs as plain per-map integrations,
+// which publish their counters the same way), then an event; a map without that mapped copy gets a
 // device-to-host copy of its counters.
 // While one slot's batch runs, requests that arrive are formed into the next
 // batch on the other slot, so copies and kernels of consecutive batches
@@ -115,6 +116,15 @@ struct tsdf_server {
 
 namespace {
 
+// Batches of at most this many requests run as plain per-map integrations
+// (four short kernels each) instead of one cooperative batched launch, whose
+// fixed cost (five phases, grid barriers) dominates when it carries only a
+// scan or two: the latency of a lone request is what a lightly loaded server
+// sees.
+#ifndef TSDF_SERVER_PLAIN_BATCH
+#define TSDF_SERVER_PLAIN_BATCH 2
+#endif
+
 void release_request(tsdf_server* s, Request* r) {
     if (r->slab >= 0) s->free_slabs.push_back(r->slab);
     delete r;
@@ -153,7 +163,13 @@ int launch_batch(tsdf_server* s, int k, std::vector<Request*>& reqs, const std::
         r->res.t_start_us = t0;
     }
     if (e != cudaSuccess) return TSDF_ERR_CUDA;
-    int rc = tsdf_batch_integrate(sl.batch, maps.data(), pts.data(), ns.data(), poses.data(), count, sl.stream);
+    int rc = TSDF_OK;
+    if (count <= TSDF_SERVER_PLAIN_BATCH) {
+        for (int i = 0; i < count && rc == TSDF_OK; ++i)
+            rc = tsdf_integrate(maps[i], pts[i], ns[i], &poses[12 * (size_t)i], sl.stream);
+    } else {
+        rc = tsdf_batch_integrate(sl.batch, maps.data(), pts.data(), ns.data(), poses.data(), count, sl.stream);
+    }
     if (rc != TSDF_OK) return rc;
     // counters: the mapped host copy the batch writes (no copy to issue), else
     // a device-to-host copy (one call per map costs microseconds of host time)

@@ -211,8 +211,13 @@ def test_serving_config_shapes_equal_oracle():
         sids = [b.tsdf_server_open_session(srv, w.params) for w in ws]
         order = [(i, k) for k in range(2) for i in np.random.default_rng(5).permutation(len(ws))]
         tickets = {i: [] for i in range(len(ws))}
-        for i, k in order:
-            tickets[i].append(b.tsdf_server_submit(srv, sids[i], ws[i].scans[k], ws[i].poses[k]))
+        # all 64 scans in one call, so that batches of many sessions form
+        # (requests submitted one at a time are served as they come)
+        got = b.tsdf_server_submit_many(srv, [sids[i] for i, k in order], [ws[i].scans[k] for i, k in order],
+                                        [ws[i].poses[k] for i, k in order])
+        assert len(got) == len(order)
+        for (i, k), t in zip(order, got):
+            tickets[i].append(t)
         for i, w in enumerate(ws):
             res = [b.tsdf_server_wait(srv, t) for t in tickets[i]]
             assert all(r["status"] == 0 for r in res)
