@@ -30,6 +30,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <sys/prctl.h>
+
 #include "tsdf_internal.cuh"
 #include "../../include/tsdf.h"
 
@@ -187,7 +189,15 @@ int launch_batch(tsdf_server* s, int k, std::vector<Request*>& reqs, const std::
     return TSDF_OK;
 }
 
+// Poll interval of the worker while batches are in flight. The thread's
+// timer slack is set to 1 us so that the short waits are not stretched to the
+// default 50 us, which would add that much to every request's latency.
+#ifndef TSDF_SERVER_POLL_US
+#define TSDF_SERVER_POLL_US 5
+#endif
+
 void worker_loop(tsdf_server* s) {
+    prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);   // nanoseconds; failure only costs latency
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
     while (!s->stop) {
@@ -260,7 +270,7 @@ void worker_loop(tsdf_server* s) {
         bool any_busy = false;
         for (Slot& sl : s->slots) any_busy = any_busy || sl.busy;
         if (!progress) {
-            if (any_busy) s->cv_work.wait_for(lk, std::chrono::microseconds(20));
+            if (any_busy) s->cv_work.wait_for(lk, std::chrono::microseconds(TSDF_SERVER_POLL_US));
             else s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
         }
     }

@@ -211,9 +211,11 @@ def test_serving_config_shapes_equal_oracle():
         sids = [b.tsdf_server_open_session(srv, w.params) for w in ws]
         order = [(i, k) for k in range(2) for i in np.random.default_rng(5).permutation(len(ws))]
         tickets = {i: [] for i in range(len(ws))}
-        # all 64 scans in one call, so that batches of many sessions form
-        # (requests submitted one at a time are served as they come)
-        got = b.tsdf_server_submit_many(srv, [sids[i] for i, k in order], [ws[i].scans[k] for i, k in order],
+        # all 64 scans in one call from pinned memory (read in place, so the
+        # call queues them at once), so that batches of many sessions form;
+        # requests that arrive one at a time are served as they come
+        pinned = {(i, k): torch.from_numpy(ws[i].scans[k]).pin_memory() for i, k in order}
+        got = b.tsdf_server_submit_many(srv, [sids[i] for i, k in order], [pinned[(i, k)] for i, k in order],
                                         [ws[i].poses[k] for i, k in order])
         assert len(got) == len(order)
         for (i, k), t in zip(order, got):
