@@ -19,6 +19,7 @@
 // batch on the other slot, so copies and kernels of consecutive batches
 // overlap on the device. Because each map's integration is bit-identical in
 // any batch composition, a session's result is the same alone and in the mix.
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -103,6 +104,7 @@ struct tsdf_server {
     std::condition_variable cv_work, cv_done;
     std::thread worker;
     bool stop = false;
+    std::atomic<uint64_t> submitted{0};   // requests queued so far (an idle worker spins on it briefly)
     int worker_error = TSDF_OK;
     std::map<int32_t, Session> sessions;
     int32_t next_session = 1;
@@ -195,6 +197,12 @@ int launch_batch(tsdf_server* s, int k, std::vector<Request*>& reqs, const std::
 #ifndef TSDF_SERVER_POLL_US
 #define TSDF_SERVER_POLL_US 5
 #endif
+// An idle worker watches for the next submission this long (yielding the
+// core between checks) before it sleeps on the condition variable, whose
+// wake-up would add its latency to the request.
+#ifndef TSDF_SERVER_IDLE_SPIN_US
+#define TSDF_SERVER_IDLE_SPIN_US 500
+#endif
 
 void worker_loop(tsdf_server* s) {
     prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);   // nanoseconds; failure only costs latency
@@ -270,8 +278,18 @@ void worker_loop(tsdf_server* s) {
         bool any_busy = false;
         for (Slot& sl : s->slots) any_busy = any_busy || sl.busy;
         if (!progress) {
-            if (any_busy) s->cv_work.wait_for(lk, std::chrono::microseconds(TSDF_SERVER_POLL_US));
-            else s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+            if (any_busy) {
+                s->cv_work.wait_for(lk, std::chrono::microseconds(TSDF_SERVER_POLL_US));
+            } else {
+                const uint64_t seen = s->submitted.load(std::memory_order_acquire);
+                lk.unlock();
+                const double t0 = now_us();
+                while (s->submitted.load(std::memory_order_acquire) == seen && now_us() - t0 < TSDF_SERVER_IDLE_SPIN_US)
+                    std::this_thread::yield();
+                lk.lock();
+                if (!s->stop && s->submitted.load(std::memory_order_acquire) == seen)
+                    s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+            }
         }
     }
 }
@@ -465,6 +483,7 @@ int tsdf_server_submit(tsdf_server* s, int32_t session, const float* points_host
     it->second.outstanding++;
     s->requests[r->ticket] = r;
     *ticket = r->ticket;
+    s->submitted.fetch_add(1, std::memory_order_release);
     lk.unlock();
     s->cv_work.notify_one();
     return TSDF_OK;
