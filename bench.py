@@ -230,10 +230,11 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         if val is not None:
             b.tsdf_set_option(h, opt, val)
     cur = tuple(p["origin"])
+    origins = [tuple(int(v) for v in o) for o in w.origins]   # (outside the timed steps)
 
     def step(i, host=False):
         nonlocal cur
-        o = tuple(w.origins[i])
+        o = origins[i]
         if o != cur:
             b.tsdf_shift(h, o, stream)
             cur = o
