@@ -295,6 +295,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     step_ms, t_wall, _ = timed_pass(False)          # headline: no per-kernel events
     if clocks:
         clocks.mark_end()
+    # the sampler stops with the timed region: its nvidia-smi queries share the
+    # driver with the host calls that the end-to-end steps below time
+    clk = clocks.stop() if clocks else None
     prof_step_ms, _, prof = timed_pass(True)        # same steps again, per-kernel events on
     dev_ms = float(sum(step_ms))
     hits_timed = int(sum(hits[i] for i in timed))
@@ -321,7 +324,6 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     # ---- reduce over ranks: total units / slowest rank
     (hits_all, e2e_hits_all), (dev_ms_max, t_e2e_max) = aggregate_ranks(
         [float(hits_timed), float(e2e_hits)], [dev_ms, t_e2e], dev if world > 1 else None)
-    clk = clocks.stop() if clocks else None
     if rank != 0:
         return None
 
