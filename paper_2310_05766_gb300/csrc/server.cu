@@ -13,8 +13,8 @@
 // (tsdf_batch_integrate, a persistent cooperative kernel over all maps of the
 // batch, whose last phase also writes each map's counters into mapped host
 // memory; a batch of one or two requests runs as plain per-map integrations,
-// which publish their counters the same way), then an event; a map without that mapped copy gets a
-// device-to-host copy of its counters.
+// which publish their counters the same way), then an event; a map without
+// that mapped copy gets a device-to-host copy of its counters.
 // While one slot's batch runs, requests that arrive are formed into the next
 // batch on the other slot, so copies and kernels of consecutive batches
 // overlap on the device. Because each map's integration is bit-identical in
