@@ -467,13 +467,18 @@ def run_room_bench(steps: int = 200):
                 hits_per_scan=hits, note="latency-bound (a few microseconds of work per scan); not judged by roofline")
 
 
-def run_drive_bench(n_pos: int = 1000):
+def run_drive_bench(n_pos: int = 1000, file_host_chunks=None):
     """A 1 km drive of the outdoor window (512 x 512 x 128 at 0.064 m), a scan and
     a shift every metre: the global store's device tier fills to its limit (the
     window's brick count) and the oldest chunks move to pinned host memory.
     Reports the shift's host time and device time (events on the stream) and
     the map's device memory. Scans: the first 20 of the outdoor sequence, each
-    placed at the next metre (a synthetic drive, not a ray-cast of a 1 km scene)."""
+    placed at the next metre (a synthetic drive, not a ray-cast of a 1 km scene).
+    With `file_host_chunks` the store has a file tier (a scratch file in the
+    temporary directory) behind a host tier of that many chunks, and the drive
+    goes n_pos / 2 metres out and the same way back, so that chunks are both
+    written to and read back from the file."""
+    import tempfile
     import torch
     from paper_2310_05766_gb300 import binding as b, synth
     w = synth.workload_outdoor(n_scans=20)
@@ -482,12 +487,16 @@ def run_drive_bench(n_pos: int = 1000):
     stream = torch.cuda.current_stream()
     m = b.TsdfMap(w.params)
     host_us, dev_us, dev_bytes = [], [], []
+    tmpdir = tempfile.TemporaryDirectory() if file_host_chunks is not None else None
     try:
+        if tmpdir is not None:
+            b.tsdf_map_set_store_file(m.handle, os.path.join(tmpdir.name, "store.bin"), file_host_chunks)
         cur = tuple(w.params["origin"])
         for k in range(n_pos):
             j = k % len(pts)
             pose = np.array(w.poses[j], np.float32).reshape(3, 4).copy()
-            pose[:, 3] = (float(k), 0.0, 0.0)
+            x = float(k) if tmpdir is None or k < n_pos // 2 else float(n_pos - 1 - k)
+            pose[:, 3] = (x, 0.0, 0.0)
             o = synth.window_origin(pose[:, 3].astype(np.float64), dims, vs)
             if o != cur:
                 e0 = torch.cuda.Event(enable_timing=True)
@@ -507,9 +516,17 @@ def run_drive_bench(n_pos: int = 1000):
         st = b.tsdf_get_store_stats(m.handle)
     finally:
         m.close()
+        if tmpdir is not None:
+            tmpdir.cleanup()
     pct = lambda v, q: float(np.percentile(v, q))
-    return dict(workload="1 km drive, window 512x512x128 at 0.064 m, a scan (128x1024) and a 1 m shift every metre; "
-                         "store device tier limited to the window's brick count, the rest in pinned host memory",
+    if tmpdir is None:
+        wl = ("1 km drive, window 512x512x128 at 0.064 m, a scan (128x1024) and a 1 m shift every metre; "
+              "store device tier limited to the window's brick count, the rest in pinned host memory")
+    else:
+        wl = (f"{n_pos // 2} m out and back, window 512x512x128 at 0.064 m, a scan (128x1024) and a 1 m shift every "
+              f"metre; store device tier limited to the window's brick count, host tier to {file_host_chunks} chunks "
+              f"at each shift, the rest in a scratch file (temporary directory) written by the map's writer thread")
+    return dict(workload=wl,
                 seed=w.meta.get("seed"),
                 shifts=len(host_us), shift_host_us=dict(p50=pct(host_us, 50), p99=pct(host_us, 99), mean=float(np.mean(host_us))),
                 shift_device_us=dict(p50=pct(dev_us, 50), p99=pct(dev_us, 99), mean=float(np.mean(dev_us)),
@@ -522,7 +539,8 @@ def run_configs(args):
     """The configured workloads besides the headline one, each short, as
     sub-records of the default line: box room (us per scan), the 64-map batch
     against 64 plain calls, the high-resolution corridor, a 1 km drive through
-    the two-tier global store (shift latency) and a 32-session serving run at
+    the global store's device and host tiers and a drive out and back through
+    its file tier (shift latency), and a 32-session serving run at
     Poisson 500 scans/s (p50 / p99 latency)."""
     import copy
     out = {}
@@ -554,6 +572,7 @@ def run_configs(args):
                         plain_ms_per_64_scans=bt["plain_per_scan_launches"]["ms_per_step"],
                         speedup_vs_plain=bt["batch_speedup_vs_plain"], tuned_config=bt["config"]["tuned_config"])
     out["drive"] = run_drive_bench(1000)
+    out["drive_file_tier"] = run_drive_bench(500, file_host_chunks=16384)
     a = copy.copy(args)
     a.serve_seconds, a.serve_rate, a.serve_pinned = 6.0, 500.0, 1
     sv = run_serving_bench(a)

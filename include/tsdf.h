@@ -150,7 +150,7 @@ int tsdf_integrate_host(tsdf_map* map, const float* points_host, int64_t n, cons
  * leave it, freeing their slot), or set to (0, 0) if not stored. (Introduction
  * of the paper: the local map is shifted, map parts leaving it are written out
  * and previously mapped parts are read back.)
- * The store has two tiers of 2 KiB slots: device memory, up to
+ * The store has two tiers of 2 KiB slots (a third, a file, on request): device memory, up to
  * TSDF_OPT_STORE_DEVICE_CHUNKS slots, and pinned host memory mapped into the
  * device, which the shift kernel reads and writes in place. When the device
  * tier is full, its chunks stored longest ago move to the host tier first
@@ -158,7 +158,12 @@ int tsdf_integrate_host(tsdf_map* map, const float* points_host, int64_t n, cons
  * Asynchronous on `stream`, except that it waits for the previous shift's
  * kernel (whose per-chunk "held data" flags it needs), and that growing a tier
  * allocates synchronously (8 MiB segments; see tsdf_map_reserve_store to
- * allocate the device tier up front). Errors: INVALID, OOM, CUDA. */
+ * allocate the device tier up front). With a file tier
+ * (tsdf_map_set_store_file) the host-tier chunks beyond its limit are queued
+ * for the file first, and entering file-tier chunks are read back into host
+ * slots before the kernel is enqueued. Errors: INVALID, OOM, CUDA, IO (a file
+ * write failed earlier, or an entering chunk could not be read: the shift is
+ * done all the same and that chunk enters as (0, 0)). */
 int tsdf_shift(tsdf_map* map, const int64_t new_origin[3], void* stream);
 
 /* Allocate the device tier of the map's global store now: `device_chunks`
@@ -176,8 +181,27 @@ typedef struct tsdf_store_stats {
     int64_t host_capacity;      /* host-tier slots allocated */
     int64_t spilled;            /* chunks moved from device to host memory so far */
     int64_t dropped;            /* leaving chunks found empty (all voxels zero) and not stored, so far */
+    int64_t file_chunks;        /* chunks held in the file tier */
+    int64_t to_file;            /* chunks moved from host memory to the file so far */
+    int64_t from_file;          /* file-tier chunks read back when they re-entered the window, so far */
 } tsdf_store_stats;
 int tsdf_get_store_stats(tsdf_map* map, tsdf_store_stats* out);
+
+/* Give the map's global store a third tier in a file, for maps larger than
+ * host memory (the paper keeps the global map on disk: map parts that leave
+ * the local window are written out and earlier parts read back; Introduction,
+ * and the Evaluation's closing remarks on an SSD). From the next shift on, at
+ * the start of every shift the host tier keeps at most `host_chunks` chunks
+ * (host_chunks >= 0; it may hold more until the next shift); the chunks that
+ * entered it longest ago move to the file. Writes are asynchronous: a writer
+ * thread of the map writes them while the caller goes on (up to 4096 chunks,
+ * 8 MiB, wait to be written; a shift that queues more waits for room). A chunk
+ * that re-enters the window is read back from the file (or from its queued
+ * copy) by the shift. `path` is created or truncated; it holds 2 KiB records
+ * and no header (tsdf_map_save writes the map file), and it is removed by
+ * tsdf_map_destroy. Once per map. Errors: INVALID (null map or path,
+ * host_chunks < 0, a file already set), IO (the file cannot be created). */
+int tsdf_map_set_store_file(tsdf_map* map, const char* path, int64_t host_chunks);
 
 /* Copy the global voxel box [lo, hi) (must lie inside the current window) to
  * the host in [z][y][x] order: value_host and weight_host each receive

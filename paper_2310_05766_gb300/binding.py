@@ -138,6 +138,7 @@ def lib():
     L.tsdf_map_device_bytes.argtypes = [vp, P(i64)]
     L.tsdf_map_reserve_store.argtypes = [vp, i64]
     L.tsdf_get_store_stats.argtypes = [vp, vp]
+    L.tsdf_map_set_store_file.argtypes = [vp, ctypes.c_char_p, i64]
     L.tsdf_get_reduction.argtypes = [vp, P(ctypes.c_int32)]
     L.tsdf_extract_mesh.argtypes = [vp, ctypes.c_int32, vp, i64, P(i64), vp]
     L.tsdf_register_system.argtypes = [vp, vp, i64, f32p, ctypes.c_int32, P(ctypes.c_double), vp]
@@ -590,7 +591,8 @@ def tsdf_map_device_bytes(handle: int) -> int:
 class tsdf_store_stats(ctypes.Structure):
     _fields_ = [("device_chunks", ctypes.c_int64), ("device_capacity", ctypes.c_int64),
                 ("host_chunks", ctypes.c_int64), ("host_capacity", ctypes.c_int64),
-                ("spilled", ctypes.c_int64), ("dropped", ctypes.c_int64)]
+                ("spilled", ctypes.c_int64), ("dropped", ctypes.c_int64),
+                ("file_chunks", ctypes.c_int64), ("to_file", ctypes.c_int64), ("from_file", ctypes.c_int64)]
 
 
 def tsdf_map_reserve_store(handle: int, device_chunks: int) -> None:
@@ -601,6 +603,10 @@ def tsdf_get_store_stats(handle: int) -> dict:
     st = tsdf_store_stats()
     _check(lib().tsdf_get_store_stats(handle, ctypes.byref(st)), "tsdf_get_store_stats")
     return {k: int(getattr(st, k)) for k, _ in tsdf_store_stats._fields_}
+
+
+def tsdf_map_set_store_file(handle: int, path: str, host_chunks: int) -> None:
+    _check(lib().tsdf_map_set_store_file(handle, os.fsencode(path), int(host_chunks)), "tsdf_map_set_store_file")
 
 
 def tsdf_map_save(handle: int, path: str, stream=None) -> None:

@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/tsdf.h: argument validation,
-// device memory ownership, the two-tier global chunk store (device memory,
-// then pinned host memory) and the launch sequence of each call. No float arithmetic of the method runs here
+// device memory ownership, the tiered global chunk store (device memory,
+// then pinned host memory, then optionally a file) and the launch sequence of
+// each call. No float arithmetic of the method runs here
 // beyond the per-map constants 1/voxel, QMAX/tau and K, derived once in
 // binary64 and rounded to binary32.
 #include <algorithm>
@@ -8,10 +9,12 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <unordered_map>
 #include <vector>
 
+#include "chunk_file.h"
 #include "chunk_store.h"
 #include "tsdf_internal.cuh"
 #include "../../include/tsdf.h"
@@ -94,6 +97,13 @@ struct tsdf_map {
     uint64_t shift_serial = 0;           // shifts done so far
     uint64_t chunks_spilled = 0;         // chunks moved from the device tier to the host tier
     uint64_t chunks_dropped = 0;         // leaving chunks found empty (not stored)
+    // optional third tier (tsdf_map_set_store_file): at the start of a shift
+    // the host tier keeps at most store_host_cap chunks, the older ones go to
+    // the file, and entering file-tier chunks are read into host slots
+    std::unique_ptr<ChunkFile> store_file;
+    size_t store_host_cap = 0;
+    uint64_t chunks_to_file = 0;         // chunks moved from the host tier to the file
+    uint64_t chunks_from_file = 0;       // file-tier chunks read back on re-entry
     // per shift item: the candidate the kernel claimed for the leaving brick,
     // or -1 (pinned host memory written by the kernel in place)
     int* claim_host = nullptr;
@@ -313,6 +323,12 @@ unsigned long long store_addr(const tsdf_map* m, uint32_t loc) {
     return (unsigned long long)(m->store_seg[t][slot / kSegChunks] + (size_t)(slot % kSegChunks) * kChunkBytes);
 }
 
+// Host address of a host-tier location.
+char* store_host_ptr(const tsdf_map* m, uint32_t loc) {
+    const uint32_t slot = ChunkStore::slot_of(loc);
+    return m->store_seg_host[slot / kSegChunks] + (size_t)(slot % kSegChunks) * kChunkBytes;
+}
+
 // Adds `segs` segments to a tier: device memory, or pinned host memory mapped
 // into the device's address space. Returns false when the allocation fails.
 bool store_grow(tsdf_map* m, int tier, size_t segs) {
@@ -356,6 +372,26 @@ int store_resolve(tsdf_map* m) {
     TSDF_CU(cudaEventSynchronize(m->flags_event));
     const size_t n = m->leave_keys.size();
     m->chunks_dropped += n - m->store.commit(m->claim_host);
+    return TSDF_OK;
+}
+
+// File tier, at the start of a shift (after store_resolve): the host tier's
+// chunks beyond its limit move to the file, oldest first. Host slots are
+// written by the device (shift kernel, tier copies), so the last shift's work
+// is waited for before any is read here.
+int store_trim_host(tsdf_map* m) {
+    if (!m->store_file || m->store.used(1) <= m->store_host_cap) return TSDF_OK;
+    TSDF_CU(cudaEventSynchronize(m->flags_event));
+    while (m->store.used(1) > m->store_host_cap) {
+        if (m->store.free_count(2) == 0) {
+            if (m->store.capacity(2) + kSegChunks > ((size_t)1 << 30)) return TSDF_ERR_OOM;
+            m->store.add_slots(2, (uint32_t)m->store.capacity(2), (uint32_t)kSegChunks);   // the file grows
+        }
+        uint32_t from = 0, to = 0;
+        if (!m->store.spill_oldest_host(&from, &to)) break;
+        if (!m->store_file->put(ChunkStore::slot_of(to), store_host_ptr(m, from))) return TSDF_ERR_IO;
+        ++m->chunks_to_file;
+    }
     return TSDF_OK;
 }
 
@@ -1004,6 +1040,7 @@ int tsdf_shift(tsdf_map* map, const int64_t new_origin[3], void* stream) {
             map->items_event_pending = false;
         }
         int rc = store_resolve(map);   // the previous shift's empty chunks are dropped
+        if (rc == TSDF_OK) rc = store_trim_host(map);
         if (rc == TSDF_OK) rc = ensure_shift_buffers(map, cnt);
         if (rc == TSDF_OK) rc = store_make_room(map, cnt, s);
         if (rc != TSDF_OK) return rc;
@@ -1031,13 +1068,42 @@ int tsdf_shift(tsdf_map* map, const int64_t new_origin[3], void* stream) {
                 }
             }
         }
+        if (map->store_file) {
+            // entering file-tier chunks are read into host slots that are not
+            // this shift's candidates: make room for both (nothing is taken
+            // yet), and let the last shift's kernel finish reading its slots
+            size_t from_file = 0;
+            for (size_t i = 0; i < cnt; ++i) {
+                const long long b = items[i].brick;
+                const long long sx = b % C[0], sy = (b / C[0]) % C[1], sz = b / (C[0] * C[1]);
+                const long long loc = map->store.find(ChunkKey{newc[0][sx], newc[1][sy], newc[2][sz]});
+                from_file += (loc >= 0 && ChunkStore::is_file((uint32_t)loc)) ? 1 : 0;
+            }
+            const size_t dev_free = map->store.free_count(0);
+            const size_t host_need = (cnt > dev_free ? cnt - dev_free : 0) + from_file;
+            while (map->store.free_count(1) < host_need)
+                if (!store_grow(map, 1, (host_need - map->store.free_count(1) + kSegChunks - 1) / kSegChunks))
+                    return TSDF_ERR_OOM;
+            if (from_file > 0) TSDF_CU(cudaEventSynchronize(map->flags_event));
+        }
         if (!map->store.candidates(map->leave_keys, stamp, &map->cand_locs)) return TSDF_ERR_OOM;
+        int io = TSDF_OK;
         for (size_t i = 0; i < cnt; ++i) {
             ShiftItem& it = items[i];
             it.out_ptr = store_addr(map, map->cand_locs[i]);   // candidate i, claimed in order by the kernel
             const long long b = it.brick;
             const long long sx = b % C[0], sy = (b / C[0]) % C[1], sz = b / (C[0] * C[1]);
-            const long long loc = map->store.take(ChunkKey{newc[0][sx], newc[1][sy], newc[2][sz]});
+            long long loc = map->store.take(ChunkKey{newc[0][sx], newc[1][sy], newc[2][sz]});
+            if (loc >= 0 && ChunkStore::is_file((uint32_t)loc)) {
+                const long long h = map->store.take_slot(1);   // free: reserved above
+                if (h < 0 || !map->store_file->get(ChunkStore::slot_of((uint32_t)loc), store_host_ptr(map, (uint32_t)h))) {
+                    io = TSDF_ERR_IO;
+                    loc = -1;   // the chunk is lost: it enters as empty
+                } else {
+                    ++map->chunks_from_file;
+                    loc = h;
+                }
+            }
             it.in_ptr = loc >= 0 ? store_addr(map, (uint32_t)loc) : 0ull;
         }
         map->store.end_shift();
@@ -1050,6 +1116,8 @@ int tsdf_shift(tsdf_map* map, const int64_t new_origin[3], void* stream) {
                              map->claim_dev, s));
         prof_push(map, kShift, e0, prof_mark(map, s));
         TSDF_CU(cudaEventRecord(map->flags_event, s));   // the claims have reached claim_host
+        for (int a = 0; a < 3; ++a) map->origin[a] = new_origin[a];
+        return io;
     }
     for (int a = 0; a < 3; ++a) map->origin[a] = new_origin[a];
     return TSDF_OK;
@@ -1236,6 +1304,18 @@ int tsdf_get_store_stats(tsdf_map* map, tsdf_store_stats* out) {
     out->host_capacity = (int64_t)map->store.capacity(1);
     out->spilled = (int64_t)map->chunks_spilled;
     out->dropped = (int64_t)map->chunks_dropped;
+    out->file_chunks = (int64_t)map->store.used(2);
+    out->to_file = (int64_t)map->chunks_to_file;
+    out->from_file = (int64_t)map->chunks_from_file;
+    return TSDF_OK;
+}
+
+int tsdf_map_set_store_file(tsdf_map* map, const char* path, int64_t host_chunks) {
+    if (!map || !path || host_chunks < 0 || map->store_file) return TSDF_ERR_INVALID;
+    std::unique_ptr<ChunkFile> f(new ChunkFile());
+    if (!f->open(path, kSegChunks)) return TSDF_ERR_IO;
+    map->store_file = std::move(f);
+    map->store_host_cap = (size_t)host_chunks;
     return TSDF_OK;
 }
 
@@ -1337,9 +1417,10 @@ int tsdf_map_save(tsdf_map* map, const char* path, void* stream) {
     int rc = store_resolve(map);
     if (rc != TSDF_OK) return rc;
     std::vector<std::vector<std::pair<uint32_t, ChunkKey>>> by_seg(map->store_seg[0].size());
-    std::vector<std::pair<uint32_t, ChunkKey>> on_host;
+    std::vector<std::pair<uint32_t, ChunkKey>> on_host, on_file;
     map->store.for_each([&](const ChunkKey& k, uint32_t loc) {
         if (ChunkStore::is_host(loc)) on_host.push_back({ChunkStore::slot_of(loc), k});
+        else if (ChunkStore::is_file(loc)) on_file.push_back({ChunkStore::slot_of(loc), k});
         else by_seg[loc / kSegChunks].push_back({loc % kSegChunks, k});
     });
     auto put = [&](const uint32_t* w, const ChunkKey& k) -> bool {
@@ -1364,6 +1445,10 @@ int tsdf_map_save(tsdf_map* map, const char* path, void* stream) {
         const uint32_t* w = reinterpret_cast<const uint32_t*>(map->store_seg_host[e.first / kSegChunks] +
                                                               (size_t)(e.first % kSegChunks) * kChunkBytes);
         if (!put(w, e.second)) return TSDF_ERR_IO;
+    }
+    for (const auto& e : on_file) {
+        if (!map->store_file->get(e.first, stage.p)) return TSDF_ERR_IO;
+        if (!put(sw, e.second)) return TSDF_ERR_IO;
     }
     h.chunk_count = count;
     if (std::fseek(fc.f, 0, SEEK_SET) != 0 || std::fwrite(&h, sizeof(h), 1, fc.f) != 1) return TSDF_ERR_IO;

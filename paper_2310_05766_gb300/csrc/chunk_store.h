@@ -1,11 +1,13 @@
 // Host bookkeeping of the global chunk store (used by api.cu; plain C++ with
 // no CUDA dependency, so that it is also unit-tested on the host).
 //
-// The global map outside the window is kept as 8^3 chunks of 2 KiB in two
-// tiers of slots: tier 0 in device memory, tier 1 in pinned host memory that
-// the device reads and writes in place. This class only decides which slot
-// holds which chunk; the owner allocates the memory behind the slots (it adds
-// slots with add_slots), copies chunks between tiers and runs the shift.
+// The global map outside the window is kept as 8^3 chunks of 2 KiB in up to
+// three tiers of slots: tier 0 in device memory, tier 1 in pinned host memory
+// that the device reads and writes in place, and, optionally, tier 2 in a
+// file (records the host writes and reads; the device never addresses them).
+// This class only decides which slot holds which chunk; the owner allocates
+// the memory behind the slots (it adds slots with add_slots), copies chunks
+// between tiers and runs the shift.
 //
 // A shift hands its kernel one candidate slot per leaving chunk (candidates:
 // device-tier slots first), and the kernel claims candidates in order for the
@@ -16,7 +18,10 @@
 // after the candidates of the same shift are out of the free lists, so that no
 // slot is read and written by one kernel. Device-tier chunks are queued in the
 // order they were stored, so that the oldest can be moved to the host tier
-// first (oldest_device, spill_oldest).
+// first (oldest_device, spill_oldest); host-tier chunks are queued in the
+// order they entered that tier, so that the oldest move to the file first
+// (spill_oldest_host). A chunk in the file tier is read back into a host slot
+// (take_slot) before the shift kernel reads it.
 #pragma once
 
 #include <cstddef>
@@ -31,10 +36,14 @@ namespace tsdf {
 class ChunkStore {
 public:
     static constexpr uint32_t kHostBit = 0x80000000u;   // location = tier bit | slot
+    static constexpr uint32_t kFileBit = 0x40000000u;   // (slots stay below 2^30)
     static bool is_host(uint32_t loc) { return (loc & kHostBit) != 0; }
-    static uint32_t slot_of(uint32_t loc) { return loc & ~kHostBit; }
+    static bool is_file(uint32_t loc) { return (loc & kFileBit) != 0; }
+    static int tier_of(uint32_t loc) { return is_host(loc) ? 1 : (is_file(loc) ? 2 : 0); }
+    static uint32_t slot_of(uint32_t loc) { return loc & ~(kHostBit | kFileBit); }
+    static uint32_t loc_of(int tier, uint32_t slot) { return slot | (tier == 1 ? kHostBit : tier == 2 ? kFileBit : 0u); }
 
-    // New free slots [first, first + n) of a tier (0 device, 1 host).
+    // New free slots [first, first + n) of a tier (0 device, 1 host, 2 file).
     void add_slots(int tier, uint32_t first, uint32_t n) {
         for (uint32_t i = 0; i < n; ++i) free_[tier].push_back(first + n - 1 - i);   // lowest slot popped first
         cap_[tier] += n;
@@ -83,6 +92,7 @@ public:
             const uint32_t loc = cand_[(size_t)c];
             index_.insert(keys_[i], loc);
             if (!is_host(loc)) fifo_.push_back(Entry{keys_[i], loc, stamp_});
+            else fifo_host_.push_back(Entry{keys_[i], loc, stamp_});
             cand_[(size_t)c] = kClaimed;
             ++stored;
         }
@@ -90,7 +100,8 @@ public:
             if (loc != kClaimed) release(loc);
         cand_.clear();
         keys_.clear();
-        if (fifo_.size() > 64 && fifo_.size() > 2 * index_.size()) compact_fifo();
+        if (fifo_.size() > 64 && fifo_.size() > 2 * index_.size()) compact_fifo(&fifo_);
+        if (fifo_host_.size() > 64 && fifo_host_.size() > 2 * index_.size()) compact_fifo(&fifo_host_);
         return stored;
     }
 
@@ -103,6 +114,17 @@ public:
             taken_.push_back((uint32_t)loc);
         }
         return loc;
+    }
+
+    // A free slot of `tier` that is freed again by end_shift() (a host slot
+    // into which an entering file-tier chunk is read), or -1 when the tier
+    // has no free slot.
+    long long take_slot(int tier) {
+        if (free_[tier].empty()) return -1;
+        const uint32_t loc = loc_of(tier, free_[tier].back());
+        free_[tier].pop_back();
+        taken_.push_back(loc);
+        return (long long)loc;
     }
 
     // After a shift's candidates are out: the entering chunks' slots become free.
@@ -140,10 +162,32 @@ public:
         const uint32_t h = free_[1].back() | kHostBit;
         free_[1].pop_back();
         index_.insert(k, h);
+        fifo_host_.push_back(Entry{k, h, stamp});
         release(loc);
         *from = loc;
         *to = h;
         return true;
+    }
+
+    // The same from the host tier to the file tier: the oldest host-tier
+    // chunk (by when it entered that tier) moves to a free file slot; false
+    // when the host tier holds none or no file slot is free. The host slot is
+    // free at once (the caller writes the chunk out first).
+    bool spill_oldest_host(uint32_t* from, uint32_t* to) {
+        if (free_[2].empty()) return false;
+        while (!fifo_host_.empty()) {
+            const Entry e = fifo_host_.front();
+            fifo_host_.pop_front();
+            if (index_.find(e.key) != (long long)e.loc) continue;   // re-entered or moved
+            const uint32_t f = free_[2].back() | kFileBit;
+            free_[2].pop_back();
+            index_.insert(e.key, f);
+            release(e.loc);
+            *from = e.loc;
+            *to = f;
+            return true;
+        }
+        return false;
     }
 
     // Every stored chunk (after commit(): a shift's candidates are not listed).
@@ -151,7 +195,7 @@ public:
     void for_each(F&& f) const { index_.for_each(f); }
 
     // A chunk written directly (loading a saved map): a free slot, device tier
-    // first, recorded as stored; -1 when both tiers are full.
+    // first, recorded as stored; -1 when both memory tiers are full.
     long long insert_stored(const ChunkKey& k, uint64_t stamp) {
         uint32_t loc;
         if (!free_[0].empty()) {
@@ -161,6 +205,7 @@ public:
         } else if (!free_[1].empty()) {
             loc = free_[1].back() | kHostBit;
             free_[1].pop_back();
+            fifo_host_.push_back(Entry{k, loc, stamp});
         } else {
             return -1;
         }
@@ -175,24 +220,22 @@ private:
         uint32_t loc;
         uint64_t stamp;
     };
-    void release(uint32_t loc) {
-        if (is_host(loc)) free_[1].push_back(slot_of(loc));
-        else free_[0].push_back(loc);
-    }
-    void compact_fifo() {
+    void release(uint32_t loc) { free_[tier_of(loc)].push_back(slot_of(loc)); }
+    void compact_fifo(std::deque<Entry>* q) {
         std::deque<Entry> keep;
-        for (const Entry& e : fifo_)
+        for (const Entry& e : *q)
             if (index_.find(e.key) == (long long)e.loc) keep.push_back(e);
-        fifo_.swap(keep);
+        q->swap(keep);
     }
     ChunkIndex index_;
-    std::vector<uint32_t> free_[2];
-    size_t cap_[2] = {0, 0};
+    std::vector<uint32_t> free_[3];
+    size_t cap_[3] = {0, 0, 0};
     std::vector<uint32_t> cand_;     // the last shift's candidate slots (kClaimed once recorded)
     std::vector<ChunkKey> keys_;     // the last shift's leaving chunks, in item order
     uint64_t stamp_ = 0;
     std::vector<uint32_t> taken_;
     std::deque<Entry> fifo_;         // device-tier chunks in the order they were stored (stale entries skipped)
+    std::deque<Entry> fifo_host_;    // host-tier chunks in the order they entered that tier (likewise)
 };
 
 }  // namespace tsdf

@@ -87,6 +87,7 @@ def test_host_side_validation_without_gpu():
     pose = (ctypes.c_float * 12)()
     assert b.lib().tsdf_integrate(None, None, 0, pose, None) == b.TSDF_ERR_INVALID
     assert b.lib().tsdf_shift(None, None, None) == b.TSDF_ERR_INVALID
+    assert b.lib().tsdf_map_set_store_file(None, b"store.bin", 0) == b.TSDF_ERR_INVALID
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

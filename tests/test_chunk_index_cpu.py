@@ -33,3 +33,22 @@ def test_chunk_store_slots_across_tiers(tmp_path):
                    check=True)
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
+
+
+def test_chunk_store_file_tier(tmp_path):
+    """The store's file tier (csrc/chunk_file.h with csrc/chunk_store.h) over
+    3000 random shifts with a real scratch file and the asynchronous writer:
+    reads right after writes return the latest content, every re-entering
+    chunk reads back the content it left with (from the file or the write
+    queue), the host tier stays within its limit, and the file is removed
+    when the writer is destroyed."""
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    exe = str(tmp_path / "chunk_file_check")
+    subprocess.run([cxx, "-std=c++17", "-O2", "-pthread", "-I", CSRC, os.path.join(HERE, "chunk_file_check.cpp"),
+                    "-o", exe], check=True)
+    scratch = str(tmp_path / "scratch.bin")
+    r = subprocess.run([exe, scratch], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
+    assert not os.path.exists(scratch)

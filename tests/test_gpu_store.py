@@ -5,6 +5,8 @@ stored; the store's device tier is bounded and spills its oldest chunks to
 pinned host memory, which the shift kernel reads and writes in place. Every
 window is compared with the oracle, whose store keeps exactly the non-empty
 chunks (std::map, no tiers)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -164,6 +166,66 @@ def test_saved_map_includes_host_tier_chunks(tmp_path):
         om.close()
         if m2 is not None:
             m2.close()
+
+
+def test_store_file_tier_reads_back_exactly(tmp_path):
+    """The walk of the host-tier test with a third tier in a file: the device
+    tier limited to one segment (4096 chunks), the host tier kept to 256
+    chunks at the start of every shift, older chunks written to a scratch file
+    by the map's writer thread. The map saved at the far end holds exactly the
+    oracle's global map (file-tier chunks included); on the way back the
+    window equals the oracle's at every position (chunks read back from the
+    file, or from the write queue); the scratch file goes with the map."""
+    from paper_2310_05766_gb300 import binding as b
+    p = synth.params_dict((64, 64, 64), 0.1, 0.3, 64, 0.05, 0.3, 3.0, 0, (0, 0, 0))
+    pts = torch.from_numpy(_ball_scan(seed=33)).cuda()
+    pts_np = pts.cpu().numpy()
+    scratch = str(tmp_path / "store.bin")
+    m = b.TsdfMap(p)
+    om = oracle.OracleMap(p)
+    try:
+        b.tsdf_set_option(m.handle, b.TSDF_OPT_STORE_DEVICE_CHUNKS, 4096)
+        b.tsdf_map_set_store_file(m.handle, scratch, 256)
+        with pytest.raises(b.TsdfError):
+            b.tsdf_map_set_store_file(m.handle, scratch, 256)   # once per map
+        assert os.path.exists(scratch)
+        xs = list(range(0, 27)) + list(range(25, -1, -1))
+        checked = 0
+        for k, xi in enumerate(xs):
+            o = (64 * xi, 0, 0)
+            if k:
+                m.shift(o)
+                om.shift(o)
+            pose = synth.pose12(synth.rot_zyx(0.1 * k, 0.0, 0.0), np.array([(o[0] + 32) * 0.1, 3.2, 3.2]))
+            m.integrate(pts, pose)
+            om.integrate(pts_np, pose)
+            if k == 26:
+                st = b.tsdf_get_store_stats(m.handle)
+                assert st["to_file"] > 0 and st["file_chunks"] > 0
+                path = str(tmp_path / "map.tsdf")
+                m.save(path)
+                _, chunks = b.read_map_file(path)
+                ref = om.global_chunks()
+                assert chunks.keys() == ref.keys()
+                for key, (v, w) in ref.items():
+                    words = v.astype(np.uint16).astype(np.uint32) | (w.astype(np.uint16).astype(np.uint32) << 16)
+                    assert np.array_equal(chunks[key], words), key
+            if k > 26:
+                vg, wg = m.read()
+                vo, wo = om.read()
+                assert np.array_equal(vg, vo) and np.array_equal(wg, wo), f"back at x = {64 * xi}"
+                checked += 1
+        st = b.tsdf_get_store_stats(m.handle)
+        assert checked == 26 and st["from_file"] > 0
+        assert st["device_capacity"] == 4096
+        o = om.origin
+        lo = [o[a] // 8 for a in range(3)]
+        outside = [q for q in om.global_chunks() if any(not (lo[a] <= q[a] < lo[a] + 8) for a in range(3))]
+        assert st["device_chunks"] + st["host_chunks"] + st["file_chunks"] == len(outside)
+    finally:
+        m.close()
+        om.close()
+    assert not os.path.exists(scratch)
 
 
 def test_serving_charges_the_store_reservation():
