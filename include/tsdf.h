@@ -162,8 +162,9 @@ int tsdf_integrate_host(tsdf_map* map, const float* points_host, int64_t n, cons
  * (tsdf_map_set_store_file) the host-tier chunks beyond its limit are queued
  * for the file first, and entering file-tier chunks are read back into host
  * slots before the kernel is enqueued. Errors: INVALID, OOM, CUDA, IO (a file
- * write failed earlier, or an entering chunk could not be read: the shift is
- * done all the same and that chunk enters as (0, 0)). */
+ * write failed earlier, or an entering file-tier chunk could not be read or
+ * given a host slot: the shift is done all the same and that chunk enters as
+ * (0, 0); the error is then IO, OOM or CUDA). */
 int tsdf_shift(tsdf_map* map, const int64_t new_origin[3], void* stream);
 
 /* Allocate the device tier of the map's global store now: `device_chunks`

@@ -1068,26 +1068,9 @@ int tsdf_shift(tsdf_map* map, const int64_t new_origin[3], void* stream) {
                 }
             }
         }
-        if (map->store_file) {
-            // entering file-tier chunks are read into host slots that are not
-            // this shift's candidates: make room for both (nothing is taken
-            // yet), and let the last shift's kernel finish reading its slots
-            size_t from_file = 0;
-            for (size_t i = 0; i < cnt; ++i) {
-                const long long b = items[i].brick;
-                const long long sx = b % C[0], sy = (b / C[0]) % C[1], sz = b / (C[0] * C[1]);
-                const long long loc = map->store.find(ChunkKey{newc[0][sx], newc[1][sy], newc[2][sz]});
-                from_file += (loc >= 0 && ChunkStore::is_file((uint32_t)loc)) ? 1 : 0;
-            }
-            const size_t dev_free = map->store.free_count(0);
-            const size_t host_need = (cnt > dev_free ? cnt - dev_free : 0) + from_file;
-            while (map->store.free_count(1) < host_need)
-                if (!store_grow(map, 1, (host_need - map->store.free_count(1) + kSegChunks - 1) / kSegChunks))
-                    return TSDF_ERR_OOM;
-            if (from_file > 0) TSDF_CU(cudaEventSynchronize(map->flags_event));
-        }
         if (!map->store.candidates(map->leave_keys, stamp, &map->cand_locs)) return TSDF_ERR_OOM;
         int io = TSDF_OK;
+        bool waited = false;
         for (size_t i = 0; i < cnt; ++i) {
             ShiftItem& it = items[i];
             it.out_ptr = store_addr(map, map->cand_locs[i]);   // candidate i, claimed in order by the kernel
@@ -1095,10 +1078,20 @@ int tsdf_shift(tsdf_map* map, const int64_t new_origin[3], void* stream) {
             const long long sx = b % C[0], sy = (b / C[0]) % C[1], sz = b / (C[0] * C[1]);
             long long loc = map->store.take(ChunkKey{newc[0][sx], newc[1][sy], newc[2][sz]});
             if (loc >= 0 && ChunkStore::is_file((uint32_t)loc)) {
-                const long long h = map->store.take_slot(1);   // free: reserved above
+                // read into a free host slot (not one of this shift's
+                // candidates, which are out of the free list), after the last
+                // shift's kernel has finished reading the slots it freed
+                if (!waited) {
+                    const cudaError_t e = cudaEventSynchronize(map->flags_event);
+                    if (e != cudaSuccess) io = cuda_fail(e);
+                    waited = true;
+                }
+                long long h = map->store.take_slot(1);
+                if (h < 0 && store_grow(map, 1, 1)) h = map->store.take_slot(1);
+                if (io == TSDF_OK && h < 0) io = TSDF_ERR_OOM;
                 if (h < 0 || !map->store_file->get(ChunkStore::slot_of((uint32_t)loc), store_host_ptr(map, (uint32_t)h))) {
-                    io = TSDF_ERR_IO;
-                    loc = -1;   // the chunk is lost: it enters as empty
+                    if (io == TSDF_OK) io = TSDF_ERR_IO;
+                    loc = -1;   // the chunk is lost: it enters as (0, 0)
                 } else {
                     ++map->chunks_from_file;
                     loc = h;
