@@ -198,10 +198,11 @@ int tsdf_get_store_stats(tsdf_map* map, tsdf_store_stats* out);
  * thread of the map writes them while the caller goes on (up to 4096 chunks,
  * 8 MiB, wait to be written; a shift that queues more waits for room). A chunk
  * that re-enters the window is read back from the file (or from its queued
- * copy) by the shift. `path` is created or truncated; it holds 2 KiB records
- * and no header (tsdf_map_save writes the map file), and it is removed by
- * tsdf_map_destroy. Once per map. Errors: INVALID (null map or path,
- * host_chunks < 0, a file already set), IO (the file cannot be created). */
+ * copy) by the shift. `path` must not exist: the call creates it; it holds
+ * 2 KiB records and no header (tsdf_map_save writes the map file), and it is
+ * removed by tsdf_map_destroy. Once per map. Errors: INVALID (null map or
+ * path, host_chunks < 0, a file already set), IO (the path exists or the file
+ * cannot be created). */
 int tsdf_map_set_store_file(tsdf_map* map, const char* path, int64_t host_chunks);
 
 /* Copy the global voxel box [lo, hi) (must lie inside the current window) to

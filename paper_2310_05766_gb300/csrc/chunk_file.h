@@ -13,13 +13,15 @@
 // whose write has not finished copies the pending chunk instead of reading
 // the file. put() and get() are called from one thread (the map's); the
 // writer thread only writes. A failed write or read makes every later call
-// fail (failed()). The file is created (or truncated) by open() and removed
-// when the object is destroyed.
+// fail (failed()). The file is created by open(), which refuses a path that
+// already exists (so that no other file is overwritten or later removed), and
+// removed when the object is destroyed.
 #pragma once
 
 #include <condition_variable>
 #include <cstddef>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -43,13 +45,16 @@ public:
     ChunkFile& operator=(const ChunkFile&) = delete;
     ~ChunkFile() { close(); }
 
-    // Creates (or truncates) the file and starts the writer; at most
-    // `max_pending` chunks wait to be written (put() blocks beyond that).
+    // Creates the file (false if it exists or cannot be created) and starts
+    // the writer; at most `max_pending` chunks wait to be written (put()
+    // blocks beyond that).
     bool open(const char* path, size_t max_pending) {
         if (fd_ >= 0 || max_pending == 0) return false;
-        fd_ = ::open(path, O_RDWR | O_CREAT | O_TRUNC | O_CLOEXEC, 0600);
+        fd_ = ::open(path, O_RDWR | O_CREAT | O_EXCL | O_CLOEXEC, 0600);
         if (fd_ < 0) return false;
-        path_ = path;
+        char* full = ::realpath(path, nullptr);   // removed by this name even if the working directory changes
+        path_ = full ? full : path;
+        std::free(full);
         buf_.resize(max_pending * kBytes);
         free_bufs_.clear();
         for (size_t i = max_pending; i-- > 0;) free_bufs_.push_back((uint32_t)i);

@@ -52,6 +52,18 @@ int main(int argc, char** argv) {
         std::printf("open failed\n");
         return 1;
     }
+    {
+        // a path that exists is refused and left in place
+        ChunkFile other;
+        if (other.open(argv[1], 8) || other.is_open()) {
+            std::printf("an existing path was opened\n");
+            return 1;
+        }
+    }
+    if (::access(argv[1], F_OK) != 0) {
+        std::printf("the refused open removed the file\n");
+        return 1;
+    }
     // reads right after writes (mostly served from the queue) and rewrites of
     // one slot: each read returns the slot's latest content
     {
