@@ -711,6 +711,14 @@ class TsdfMap:
     def save(self, path: str, stream=None):
         tsdf_map_save(self.handle, path, stream)
 
+    def set_store_file(self, path: str, host_chunks: int):
+        """A file tier for the global store behind `host_chunks` host-memory chunks
+        (`path` must not exist; it is removed when the map is closed)."""
+        tsdf_map_set_store_file(self.handle, path, host_chunks)
+
+    def store_stats(self) -> dict:
+        return tsdf_get_store_stats(self.handle)
+
     @classmethod
     def load(cls, path: str, stream=None) -> "TsdfMap":
         """A new map from a file written by save()."""

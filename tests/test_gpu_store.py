@@ -185,7 +185,7 @@ def test_store_file_tier_reads_back_exactly(tmp_path):
     om = oracle.OracleMap(p)
     try:
         b.tsdf_set_option(m.handle, b.TSDF_OPT_STORE_DEVICE_CHUNKS, 4096)
-        b.tsdf_map_set_store_file(m.handle, scratch, 256)
+        m.set_store_file(scratch, 256)
         with pytest.raises(b.TsdfError):
             b.tsdf_map_set_store_file(m.handle, scratch, 256)   # once per map
         assert os.path.exists(scratch)
@@ -215,7 +215,7 @@ def test_store_file_tier_reads_back_exactly(tmp_path):
                 vo, wo = om.read()
                 assert np.array_equal(vg, vo) and np.array_equal(wg, wo), f"back at x = {64 * xi}"
                 checked += 1
-        st = b.tsdf_get_store_stats(m.handle)
+        st = m.store_stats()
         assert checked == 26 and st["from_file"] > 0
         assert st["device_capacity"] == 4096
         o = om.origin
