@@ -13,14 +13,19 @@
 // Checked: every re-entering chunk reads back its last content, the host tier
 // holds at most kHostCap chunks after each trim, every stored chunk is stored
 // once, and at the end every file-tier chunk reads back from the file after
-// the writer has drained. Prints "ok". Usage: chunk_file_check <scratch path>.
+// the writer has drained. Last, a write that fails (the process's file size
+// limit lowered to 8 KiB) must make flush, put and get report the failure.
+// Prints "ok". Usage: chunk_file_check <scratch path> <second scratch path>.
 #include <algorithm>
+#include <csignal>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <random>
 #include <set>
 #include <vector>
+
+#include <sys/resource.h>
 
 #include "chunk_file.h"
 #include "chunk_store.h"
@@ -42,7 +47,7 @@ void pattern(long long x, long long v, char* out) {
 }  // namespace
 
 int main(int argc, char** argv) {
-    if (argc < 2) return 2;
+    if (argc < 3) return 2;
     std::mt19937_64 rng(4242);
     const long long W = 24;                       // window: chunks [o, o + W) along x
     const uint32_t kDev = 32, kHostCap = 20, kHostSeg = 16, kFileSeg = 64;
@@ -216,7 +221,23 @@ int main(int argc, char** argv) {
         std::printf("final: ok=%d checked=%zu to_file=%zu from_file=%zu\n", (int)ok, checked, to_file, from_file);
         return 1;
     }
-    std::printf("ok %zu to file, %zu read back, %zu in the file at the end, %llu from the queue\n", to_file,
-                from_file, checked, (unsigned long long)file.pending_hits());
+    file.close();
+    // a failing write (beyond the file size limit: EFBIG instead of SIGXFSZ)
+    std::signal(SIGXFSZ, SIG_IGN);
+    struct rlimit lim = {8192, 8192};
+    if (::setrlimit(RLIMIT_FSIZE, &lim) != 0) { std::printf("setrlimit failed\n"); return 1; }
+    {
+        ChunkFile bad;
+        if (!bad.open(argv[2], 8)) { std::printf("open of the second path failed\n"); return 1; }
+        pattern(1, 1, want);
+        if (!bad.put(0, want) || !bad.flush()) { std::printf("a write within the limit failed\n"); return 1; }
+        if (!bad.get(0, buf) || std::memcmp(buf, want, kB) != 0) { std::printf("read back within the limit\n"); return 1; }
+        bad.put(9, want);   // offset 18 KiB: over the limit
+        if (bad.flush() || !bad.failed()) { std::printf("a failed write was not reported\n"); return 1; }
+        if (bad.put(1, want) || bad.get(0, buf)) { std::printf("calls after a failed write succeeded\n"); return 1; }
+    }
+    if (::access(argv[2], F_OK) == 0) { std::printf("the second file was not removed\n"); return 1; }
+    std::printf("ok %zu to file, %zu read back, %zu in the file at the end, %llu from the queue; failed write "
+                "reported\n", to_file, from_file, checked, (unsigned long long)file.pending_hits());
     return 0;
 }

@@ -40,15 +40,16 @@ def test_chunk_store_file_tier(tmp_path):
     3000 random shifts with a real scratch file and the asynchronous writer:
     reads right after writes return the latest content, every re-entering
     chunk reads back the content it left with (from the file or the write
-    queue), the host tier stays within its limit, and the file is removed
-    when the writer is destroyed."""
+    queue), the host tier stays within its limit, the file is removed when the
+    writer is destroyed, and a failed write (past a lowered file size limit)
+    is reported by every later call."""
     cxx = shutil.which("g++") or shutil.which("c++")
     if cxx is None:
         pytest.skip("no host C++ compiler")
     exe = str(tmp_path / "chunk_file_check")
     subprocess.run([cxx, "-std=c++17", "-O2", "-pthread", "-I", CSRC, os.path.join(HERE, "chunk_file_check.cpp"),
                     "-o", exe], check=True)
-    scratch = str(tmp_path / "scratch.bin")
-    r = subprocess.run([exe, scratch], capture_output=True, text=True, timeout=120)
+    scratch, scratch2 = str(tmp_path / "scratch.bin"), str(tmp_path / "scratch2.bin")
+    r = subprocess.run([exe, scratch, scratch2], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
-    assert not os.path.exists(scratch)
+    assert not os.path.exists(scratch) and not os.path.exists(scratch2)
